@@ -1,0 +1,292 @@
+// CPU oracle for the process-mining summaries of a columnar event log.
+//
+// TEST INFRASTRUCTURE. This file is a plain, slow, single-threaded statement of
+// what the engine computes, written from the paper's definitions. It is linked
+// or executed only by the tests, by the smoke check and by the benchmark's CPU
+// baseline leg; the engine never calls it and shares no code with it.
+//
+// Paper: Berti, Phan Nghia, van der Aalst, "PM4Py-GPU: a High-Performance
+// General-Purpose Library for Process Mining" (arXiv 2204.04898).
+//
+// Readings of the paper used here (where it is silent or ambiguous):
+//  * Ordering (Section 3, the first formatting step): events are ordered by case
+//    identifier, then timestamp, then the event's absolute row index. Case ids
+//    compare as signed int32, timestamps as signed int64, rows ascending.
+//  * A case is a maximal run of equal case ids in that order; cases appear in
+//    ascending case id order.
+//  * Directly-follows pairs (Section 3, the directly-follows level and the
+//    second formatting step, which adds each event's previous activity and
+//    timestamp): consecutive events (i, j) of one case. The duration is
+//    ts_j - ts_i as an unsigned 64-bit value (exact, since ts_j >= ts_i).
+//  * Performance DFG aggregate (Section 3, dfg.py, aggregate unnamed): per edge
+//    the count, the exact sum of durations (128-bit), the minimum, the maximum,
+//    and mean = (double)sum / (double)count, formed once from the exact sum.
+//  * Start/end activities (Section 3, start_end_activities.py): the activity of
+//    each case's first and last event; activity frequency (Section 3, event-level
+//    aggregation example): occurrences per activity.
+//  * Variants (Section 3, variant level and variants.py): a case's variant is its
+//    exact activity sequence. Variants are ordered by count descending, then by
+//    the smallest case id having the variant; the variant id is the rank.
+//  * Filters (Section 3, timestamp.py and attributes.py): the case attribute is
+//    its value at the case's first event; a case is kept iff the attribute set is
+//    empty or holds that value. Time windows are closed [t_lo, t_hi]: EVENTS keeps
+//    the events inside the window, CASES_CONTAINED keeps whole cases whose first
+//    and last timestamps are inside, CASES_INTERSECTING keeps whole cases whose
+//    span overlaps the window. The result keeps the original rows.
+//
+// Status codes: 0 ok, -1 invalid argument, -2 activity code outside [0, A).
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+namespace {
+
+typedef unsigned __int128 u128;
+
+struct EdgeAgg {
+  uint64_t count = 0;
+  u128 sum = 0;
+  uint64_t min = ~0ULL;
+  uint64_t max = 0;
+};
+
+struct VariantAgg {
+  uint64_t count = 0;
+  int32_t min_case = 0;
+};
+
+struct Result {
+  int64_t n_events = 0;
+  int32_t n_activities = 0;
+  std::vector<int64_t> sorted_rows;  // rows in (case, ts, row) order
+  std::vector<int32_t> case_ids;     // ascending
+  std::vector<int64_t> case_off;     // n_cases + 1 offsets into sorted_rows
+  std::vector<std::pair<std::pair<int32_t, int32_t>, EdgeAgg>> edges;  // ascending (src, dst)
+  std::vector<uint64_t> start, end, freq;
+  std::vector<uint64_t> var_count;
+  std::vector<int32_t> var_min_case;
+  std::vector<std::vector<int32_t>> var_seq;
+  std::vector<int32_t> case_variant;  // per case, aligned with case_ids
+};
+
+int validate(const int32_t *case_id, const int32_t *act, const int64_t *ts, int64_t n, int32_t A) {
+  if (n < 0 || A <= 0) return -1;
+  if (n > 0 && (!case_id || !act || !ts)) return -1;
+  for (int64_t r = 0; r < n; ++r)
+    if (act[r] < 0 || act[r] >= A) return -2;
+  return 0;
+}
+
+// Section 3, formatting step 1: order by (case id, timestamp, absolute row).
+std::vector<int64_t> sort_rows(const int32_t *case_id, const int64_t *ts, int64_t n) {
+  std::vector<int64_t> rows(n);
+  for (int64_t r = 0; r < n; ++r) rows[r] = r;
+  std::sort(rows.begin(), rows.end(), [&](int64_t a, int64_t b) {
+    return std::make_tuple(case_id[a], ts[a], a) < std::make_tuple(case_id[b], ts[b], b);
+  });
+  return rows;
+}
+
+void summarize(const int32_t *case_id, const int32_t *act, const int64_t *ts, int64_t n, int32_t A,
+               Result &R) {
+  R.n_events = n;
+  R.n_activities = A;
+  R.sorted_rows = sort_rows(case_id, ts, n);
+  const std::vector<int64_t> &s = R.sorted_rows;
+
+  // Cases: maximal runs of equal case ids in sorted order.
+  for (int64_t i = 0; i < n; ++i) {
+    if (i == 0 || case_id[s[i]] != case_id[s[i - 1]]) {
+      R.case_ids.push_back(case_id[s[i]]);
+      R.case_off.push_back(i);
+    }
+  }
+  R.case_off.push_back(n);
+  const int64_t C = (int64_t)R.case_ids.size();
+
+  // Directly-follows pairs and their durations (Section 3, directly-follows level).
+  std::map<std::pair<int32_t, int32_t>, EdgeAgg> dfg;
+  R.start.assign(A, 0);
+  R.end.assign(A, 0);
+  R.freq.assign(A, 0);
+  for (int64_t c = 0; c < C; ++c) {
+    const int64_t b = R.case_off[c], e = R.case_off[c + 1];
+    R.start[act[s[b]]] += 1;
+    R.end[act[s[e - 1]]] += 1;
+    for (int64_t i = b; i < e; ++i) R.freq[act[s[i]]] += 1;
+    for (int64_t i = b; i + 1 < e; ++i) {
+      const int64_t x = s[i], y = s[i + 1];
+      const uint64_t delta = (uint64_t)ts[y] - (uint64_t)ts[x];
+      EdgeAgg &g = dfg[std::make_pair(act[x], act[y])];
+      g.count += 1;
+      g.sum += (u128)delta;
+      g.min = std::min(g.min, delta);
+      g.max = std::max(g.max, delta);
+    }
+  }
+  R.edges.assign(dfg.begin(), dfg.end());
+
+  // Variants: exact activity sequences (Section 3, variant level).
+  std::map<std::vector<int32_t>, VariantAgg> var;
+  std::vector<std::vector<int32_t>> case_seq(C);
+  for (int64_t c = 0; c < C; ++c) {
+    std::vector<int32_t> seq;
+    for (int64_t i = R.case_off[c]; i < R.case_off[c + 1]; ++i) seq.push_back(act[s[i]]);
+    auto it = var.find(seq);
+    if (it == var.end()) {
+      VariantAgg v;
+      v.count = 1;
+      v.min_case = R.case_ids[c];
+      var.emplace(seq, v);
+    } else {
+      it->second.count += 1;
+      it->second.min_case = std::min(it->second.min_case, R.case_ids[c]);
+    }
+    case_seq[c] = std::move(seq);
+  }
+  std::vector<std::pair<std::vector<int32_t>, VariantAgg>> vv(var.begin(), var.end());
+  std::sort(vv.begin(), vv.end(), [](const auto &a, const auto &b) {
+    if (a.second.count != b.second.count) return a.second.count > b.second.count;
+    return a.second.min_case < b.second.min_case;
+  });
+  std::map<std::vector<int32_t>, int32_t> rank;
+  for (size_t k = 0; k < vv.size(); ++k) {
+    R.var_count.push_back(vv[k].second.count);
+    R.var_min_case.push_back(vv[k].second.min_case);
+    R.var_seq.push_back(vv[k].first);
+    rank[vv[k].first] = (int32_t)k;
+  }
+  R.case_variant.resize(C);
+  for (int64_t c = 0; c < C; ++c) R.case_variant[c] = rank[case_seq[c]];
+}
+
+}  // namespace
+
+extern "C" {
+
+// Computes every summary of the log (Section 3). Returns a status code; on
+// success *out holds a result handle to be released with oracle_free.
+int oracle_summarize(const int32_t *case_id, const int32_t *act, const int64_t *ts, int64_t n,
+                     int32_t n_activities, void **out) {
+  if (!out) return -1;
+  *out = nullptr;
+  int st = validate(case_id, act, ts, n, n_activities);
+  if (st != 0) return st;
+  Result *R = new Result();
+  summarize(case_id, act, ts, n, n_activities, *R);
+  *out = R;
+  return 0;
+}
+
+void oracle_free(void *h) { delete static_cast<Result *>(h); }
+
+int64_t oracle_n_events(void *h) { return static_cast<Result *>(h)->n_events; }
+int64_t oracle_n_cases(void *h) { return (int64_t) static_cast<Result *>(h)->case_ids.size(); }
+int64_t oracle_n_edges(void *h) { return (int64_t) static_cast<Result *>(h)->edges.size(); }
+int64_t oracle_n_variants(void *h) { return (int64_t) static_cast<Result *>(h)->var_count.size(); }
+
+// Rows in (case, timestamp, row) order: the formatted log of Section 3.
+void oracle_sorted_rows(void *h, int64_t *rows) {
+  const Result *R = static_cast<Result *>(h);
+  std::copy(R->sorted_rows.begin(), R->sorted_rows.end(), rows);
+}
+
+// Frequency and performance DFG, edges ascending by (src, dst).
+void oracle_edges(void *h, int32_t *src, int32_t *dst, uint64_t *count, uint64_t *sum_lo,
+                  uint64_t *sum_hi, uint64_t *mn, uint64_t *mx, double *mean) {
+  const Result *R = static_cast<Result *>(h);
+  for (size_t k = 0; k < R->edges.size(); ++k) {
+    const auto &e = R->edges[k];
+    src[k] = e.first.first;
+    dst[k] = e.first.second;
+    count[k] = e.second.count;
+    sum_lo[k] = (uint64_t)e.second.sum;
+    sum_hi[k] = (uint64_t)(e.second.sum >> 64);
+    mn[k] = e.second.min;
+    mx[k] = e.second.max;
+    mean[k] = (double)e.second.sum / (double)e.second.count;
+  }
+}
+
+// Start, end and frequency counts per activity code (arrays of n_activities).
+void oracle_endpoints(void *h, uint64_t *start, uint64_t *end, uint64_t *freq) {
+  const Result *R = static_cast<Result *>(h);
+  std::copy(R->start.begin(), R->start.end(), start);
+  std::copy(R->end.begin(), R->end.end(), end);
+  std::copy(R->freq.begin(), R->freq.end(), freq);
+}
+
+// Number of activity codes over all variant sequences (CSR payload length).
+int64_t oracle_n_variant_acts(void *h) {
+  const Result *R = static_cast<Result *>(h);
+  int64_t t = 0;
+  for (const auto &s : R->var_seq) t += (int64_t)s.size();
+  return t;
+}
+
+// Variants in rank order: count, smallest case id, CSR offsets and activities.
+void oracle_variants(void *h, uint64_t *count, int32_t *min_case, int64_t *off, int32_t *acts) {
+  const Result *R = static_cast<Result *>(h);
+  int64_t o = 0;
+  for (size_t k = 0; k < R->var_seq.size(); ++k) {
+    count[k] = R->var_count[k];
+    min_case[k] = R->var_min_case[k];
+    off[k] = o;
+    for (int32_t a : R->var_seq[k]) acts[o++] = a;
+  }
+  off[R->var_seq.size()] = o;
+}
+
+// Per case (ascending case id): id, number of events, variant id.
+void oracle_cases(void *h, int32_t *case_ids, int64_t *case_len, int32_t *case_variant) {
+  const Result *R = static_cast<Result *>(h);
+  for (size_t c = 0; c < R->case_ids.size(); ++c) {
+    case_ids[c] = R->case_ids[c];
+    case_len[c] = R->case_off[c + 1] - R->case_off[c];
+    case_variant[c] = R->case_variant[c];
+  }
+}
+
+// Drill-down filter (Section 3, timestamp.py and attributes.py). Writes the kept
+// rows, ascending, to rows_out (capacity n) and returns their number, or a
+// negative status. mode: 0 none, 1 events, 2 cases contained, 3 cases
+// intersecting. attr may be NULL only when n_attr == 0.
+int64_t oracle_filter(const int32_t *case_id, const int32_t *act, const int64_t *ts,
+                      const int32_t *attr, int64_t n, int32_t n_activities, const int32_t *attr_set,
+                      int32_t n_attr, int64_t t_lo, int64_t t_hi, int32_t mode, int64_t *rows_out) {
+  int st = validate(case_id, act, ts, n, n_activities);
+  if (st != 0) return st;
+  if (mode < 0 || mode > 3 || n_attr < 0 || (n_attr > 0 && (!attr || !attr_set))) return -1;
+  std::vector<int64_t> s = sort_rows(case_id, ts, n);
+  std::vector<char> keep(n, 0);
+  int64_t b = 0;
+  while (b < n) {
+    int64_t e = b + 1;
+    while (e < n && case_id[s[e]] == case_id[s[b]]) ++e;
+    bool case_ok = true;
+    if (n_attr > 0) {
+      const int32_t v = attr[s[b]];
+      case_ok = std::find(attr_set, attr_set + n_attr, v) != attr_set + n_attr;
+    }
+    const int64_t first = ts[s[b]], last = ts[s[e - 1]];
+    if (case_ok && mode == 2) case_ok = first >= t_lo && last <= t_hi;
+    if (case_ok && mode == 3) case_ok = first <= t_hi && last >= t_lo;
+    for (int64_t i = b; i < e; ++i) {
+      bool k = case_ok;
+      if (k && mode == 1) k = ts[s[i]] >= t_lo && ts[s[i]] <= t_hi;
+      keep[s[i]] = k ? 1 : 0;
+    }
+    b = e;
+  }
+  int64_t m = 0;
+  for (int64_t r = 0; r < n; ++r)
+    if (keep[r]) rows_out[m++] = r;
+  return m;
+}
+
+}  // extern "C"
