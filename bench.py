@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Throughput of the single-log pass: load and format a columnar event log,
+then frequency DFG, performance DFG, start/end activities and the variant
+table, on one B300 per process.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload very_large_log]
+    python bench.py --impl reference ...    # the CPU oracle on host cores
+
+One step = pm4g_load_log (device-resident columns) + pm4g_dfg + pm4g_perf_dfg +
+pm4g_start_end + pm4g_variants(top_k) + pm4g_log_free. Prints one JSON line.
+Under torchrun every rank processes its own copy of the workload (replicas;
+weak scaling); value = events of all ranks / max rank time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pm4g_synth as synth  # noqa: E402
+
+METRIC = "events/s for DFG+perf-DFG+variants (single-log pass)"
+UNIT = "events/s"
+FALLBACK_HBM_GBS = 6400.0
+# Algorithmic bytes (the byte model of the method, not of this implementation):
+# read case+activity+timestamp once (16 B/event), write activity+timestamp once
+# in case-grouped order (12 B/event), read them back (12 B/event), write the
+# case-to-variant id (4 B/case). Split by the kernel that does each part.
+ALG_BYTES = {
+    "bucket_scatter": (28.0, 0.0),  # (per event, per case)
+    "segment": (12.0, 0.0),
+    "variants": (0.0, 4.0),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    p.add_argument("--workload", default="very_large_log", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--cases", type=int, default=0, help="override the number of cases (0 = workload default)")
+    p.add_argument("--top-k", type=int, default=1000)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-cases", type=int, default=1_000_000)
+    return p.parse_args()
+
+
+def workload_spec(args):
+    spec = synth.WORKLOADS[args.workload]()
+    if args.cases:
+        spec = spec.scaled(args.cases, spec.name)
+    return spec
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples over the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="pm4g_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args):
+    """The CPU oracle on the machine's host cores, on a bounded sample per step."""
+    import oracle
+    rank, world, _ = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    spec = workload_spec(args)
+    sample_cases = max(1000, min(spec.n_cases, args.cpu_sample_cases // 4))
+    L = synth.generate(spec.scaled(sample_cases))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        oracle.summarize(L.case_id, L.activity, L.ts_ns, L.n_activities)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = L.n_events * len(times) / total
+    sample = f"{spec.name} law with {sample_cases} cases ({L.n_events} events) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": spec.name, "n_cases": sample_cases, "n_events": L.n_events,
+                       "n_activities": spec.n_activities},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2204_04898_b300 import pm4g
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    spec = workload_spec(args)
+    t_gen = time.perf_counter()
+    L = synth.generate(spec, pinned=True)
+    t_gen = time.perf_counter() - t_gen
+    N = L.n_events
+    A = L.n_activities
+    dev = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns)]
+    stream = torch.cuda.Stream()
+    ctx = pm4g.pm4g_ctx_create(local, stream=stream.cuda_stream)
+    info = {}
+
+    def step(cols, k=args.top_k):
+        log = pm4g.pm4g_load_log(ctx, *cols, n_activities=A)
+        try:
+            d = pm4g.pm4g_dfg(log)
+            p = pm4g.pm4g_perf_dfg(log)
+            s, e, f = pm4g.pm4g_start_end(log, A)
+            v = pm4g.pm4g_variants(log, top_k=k)
+            info["C"] = pm4g.pm4g_log_info(log)[1]
+            info["E"] = int(d["src"].shape[0])
+            info["V"] = int(v.n_variants)
+            info["d2h"] = (d["src"].nbytes + d["dst"].nbytes + d["count"].nbytes + 5 * 8 * p.n_edges
+                           + 8 * 3 * A + v.count.nbytes + v.min_case.nbytes + 4 * v.off.nbytes // 2
+                           + v.acts.nbytes)
+        finally:
+            pm4g.pm4g_log_free(log)
+
+    for _ in range(args.warmup):
+        step(dev)
+    # timed region: device-resident inputs (3 columns, larger than L2)
+    torch.cuda.synchronize()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(dev)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = max_over_ranks(ms)
+    value = N * world * 1e3 / ms_max
+
+    # per-kernel device times (CUDA events on the context stream), same steps
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 1)
+    pm4g.pm4g_ctx_timing_reset(ctx)
+    for _ in range(args.steps):
+        step(dev)
+    kt = {}
+    for name in pm4g.pm4g_kernel_names():
+        n_l, t_ms = pm4g.pm4g_ctx_timing(ctx, name)
+        if n_l:
+            kt[name] = (n_l, t_ms)
+    launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
+    total_kt = sum(v[1] for v in kt.values()) or 1.0
+    dom = max(kt, key=lambda k: kt[k][1])
+    peak, peak_kind = peaks()
+    C = info["C"]
+    per_ev, per_case = ALG_BYTES.get(dom, (0.0, 0.0))
+    alg = per_ev * N + per_case * C
+    launch_ms = kt[dom][1] / kt[dom][0]
+    # bytes per launch: the kernel runs once per step for the modelled kernels
+    per_launch = alg * args.steps / kt[dom][0]
+    achieved = per_launch / (launch_ms * 1e-3) / 1e9
+    b_alg = 40.0 * N + 4.0 * C
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [L.case_id, L.activity, L.ts_ns]
+        step(host)
+        torch.cuda.synchronize()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            step(host)
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t)
+        e2e = {"value": N * world * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+               "d2h_bytes_per_step": int(info["d2h"])}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        sample_cases = max(1000, min(spec.n_cases, args.cpu_sample_cases))
+        S = synth.generate(spec.scaled(sample_cases))
+        t = time.perf_counter()
+        oracle.summarize(S.case_id, S.activity, S.ts_ns, S.n_activities)
+        dt = time.perf_counter() - t
+        cpu = {"value": S.n_events / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{spec.name} law with {sample_cases} cases ({S.n_events} events), one run, "
+                         f"{dt:.1f} s on 1 of {os.cpu_count()} host cores"}
+
+    pm4g.pm4g_ctx_destroy(ctx)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": spec.name, "n_events": N, "n_cases": C, "n_activities": A, "n_edges": info["E"],
+                   "n_variants": info["V"], "top_k": args.top_k,
+                   "l2": "inputs (16 B/event, %.1f GB) larger than L2; no flush" % (16 * N / 1e9),
+                   "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": per_launch, "launch_ms": launch_ms,
+                     "path_alg_bytes": b_alg, "path_frac": b_alg / (ms_max * 1e-3) / 1e9 / peak},
+        "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kt.items(), key=lambda x: -x[1][1])},
+        "kernel_share": {k: round(v[1] / total_kt, 4) for k, v in kt.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

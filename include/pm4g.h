@@ -1,0 +1,210 @@
+/*
+ * pm4g.h - C ABI of a B300-native engine for the process-mining summaries of a
+ * columnar event log.
+ *
+ * Paper: A. Berti, M. Phan Nghia, W.M.P. van der Aalst, "PM4Py-GPU: a
+ * High-Performance General-Purpose Library for Process Mining", arXiv
+ * 2204.04898. The calls follow the paper's usage (Section 3, Listing 1): a log
+ * is ingested and formatted once (ordering by case, timestamp and absolute
+ * index), then queried for the frequency/performance directly-follows graph,
+ * start/end activities and variants, and drilled down with timestamp and
+ * attribute filters.
+ *
+ * Conventions
+ *  - Every function returns an int status: PM4G_OK (0) or a negative code.
+ *    No C++ exception crosses this boundary. pm4g_last_error() returns a
+ *    message for the calling thread's most recent failure.
+ *  - A context (pm4g_ctx) binds one CUDA device and one stream; all work of
+ *    the context and of its logs runs in order on that stream. A context is
+ *    used by one thread at a time.
+ *  - Input columns are owned by the caller. Host inputs are copied. Device
+ *    inputs are read only until pm4g_load_log returns.
+ *  - Log handles and result arrays are owned by the library. Result arrays are
+ *    host memory (malloc) released by the matching *_free call.
+ *  - Limits: 0 <= n_events <= 2^31 - 1; 1 <= n_activities <= 2048.
+ *
+ * Outputs are exact: counts and duration sums/min/max are integers (durations
+ * are unsigned 64-bit nanosecond differences, sums 128-bit); the mean duration
+ * is (double)sum / (double)count, formed once from the exact sum.
+ */
+#ifndef PM4G_H
+#define PM4G_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes */
+#define PM4G_OK 0
+#define PM4G_EINVAL (-1)   /* null pointer, negative size, bad mode or option */
+#define PM4G_ERANGE (-2)   /* an activity code outside [0, n_activities) */
+#define PM4G_ENOMEM (-3)   /* the allocator returned NULL */
+#define PM4G_ECUDA (-4)    /* a CUDA runtime call failed */
+#define PM4G_ETIMEOUT (-5) /* a bounded device wait gave up */
+
+/* pm4g_load_log flags: where the input columns live */
+#define PM4G_HOST_PTRS 0x1u
+#define PM4G_DEVICE_PTRS 0x2u
+
+/* pm4g_variants flags */
+#define PM4G_VARIANTS_CASES 0x1u /* also return case_ids[] and case_variant[] */
+
+/* Time-window modes of pm4g_filter (Section 3, timestamp.py) */
+#define PM4G_TW_NONE 0
+#define PM4G_TW_EVENTS 1
+#define PM4G_TW_CASES_CONTAINED 2
+#define PM4G_TW_CASES_INTERSECTING 3
+
+/* Context options (pm4g_ctx_set_option) */
+#define PM4G_OPT_TIMING 1            /* 1 = time every kernel launch with CUDA events */
+#define PM4G_OPT_TEST_HASH_BITS 2    /* test only: keep this many bits (1..63) of the
+                                        variant key, forcing the collision path; 0 = off */
+#define PM4G_OPT_TEST_BUCKET_CAP 3   /* test only: events a bucket may hold in shared
+                                        memory (>= 32); smaller values force the
+                                        global-memory path; 0 = default */
+
+typedef struct pm4g_ctx pm4g_ctx;
+typedef struct pm4g_log pm4g_log;
+
+/* Device-memory hook. alloc returns device memory of `bytes` bytes usable on
+ * `stream` (a cudaStream_t), or NULL on failure; free releases it in stream
+ * order. `user` is passed through. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *user);
+  void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+  void *user;
+} pm4g_allocator;
+
+/* Creates a context on CUDA device `device`. cuda_stream is a cudaStream_t to
+ * run on (borrowed, not destroyed), or NULL for a stream the context owns.
+ * alloc may be NULL: stream-ordered cudaMallocAsync is used. *out is set only
+ * on success. */
+int pm4g_ctx_create(pm4g_ctx **out, int device, void *cuda_stream, const pm4g_allocator *alloc);
+
+/* Destroys a context. Its logs must have been freed. NULL is accepted. */
+int pm4g_ctx_destroy(pm4g_ctx *ctx);
+
+/* Sets one PM4G_OPT_* option. */
+int pm4g_ctx_set_option(pm4g_ctx *ctx, int option, int64_t value);
+
+/* Kernel timing (when PM4G_OPT_TIMING is on): for kernel `name` (see
+ * pm4g_kernel_names), the number of launches and their total device time in
+ * milliseconds since the last reset, measured with CUDA events on the context
+ * stream. Synchronizes the stream. Unknown names give 0 launches. The name
+ * "launches" gives the number of kernels the context launched since the last
+ * reset (counted whether or not timing is on). */
+int pm4g_ctx_timing(pm4g_ctx *ctx, const char *name, int64_t *launches, double *total_ms);
+int pm4g_ctx_timing_reset(pm4g_ctx *ctx);
+
+/* Comma-separated names of the engine's kernels (static string). */
+const char *pm4g_kernel_names(void);
+
+/* Ingests and formats a log (Section 3: the log is ordered by case identifier,
+ * timestamp and absolute row index; each event's predecessor in its case and
+ * a per-case table are derived). Columns have n_events entries:
+ *   case_id   int32  case identifier (any int32 values)
+ *   activity  int32  activity code in [0, n_activities)
+ *   ts_ns     int64  timestamp (any int64 values; nanoseconds by convention)
+ *   case_attr int32  optional case attribute (NULL: none); a case's value is
+ *                    its value at the case's first event
+ * flags is PM4G_HOST_PTRS or PM4G_DEVICE_PTRS. The frequency/performance DFG
+ * and endpoints are computed during this call; variants on first request.
+ * Errors: EINVAL, ERANGE (nothing is kept), ENOMEM, ECUDA. */
+int pm4g_load_log(pm4g_ctx *ctx, const int32_t *case_id, const int32_t *activity,
+                  const int64_t *ts_ns, const int32_t *case_attr, int64_t n_events,
+                  int32_t n_activities, uint32_t flags, pm4g_log **out);
+
+/* Number of events and of cases (distinct case ids) of a log. */
+int pm4g_log_info(const pm4g_log *log, int64_t *n_events, int64_t *n_cases);
+
+/* Releases a log and its device memory. NULL is accepted. */
+int pm4g_log_free(pm4g_log *log);
+
+/* The formatted log (Section 3, format.py): every event in (case id,
+ * timestamp, row) order. Each output is a host array of n_events entries, or
+ * NULL to skip it. row is the event's 0-based row in the originally loaded
+ * columns (a filtered log keeps those rows). */
+int pm4g_log_export(pm4g_log *log, int32_t *case_id, int32_t *activity, int64_t *ts_ns,
+                    int64_t *row);
+
+/* Frequency DFG (Section 3, dfg.py): edges (src, dst) with count > 0,
+ * ascending by (src, dst). An edge counts consecutive events of one case. */
+typedef struct {
+  int64_t n_edges;
+  int32_t *src;
+  int32_t *dst;
+  uint64_t *count;
+} pm4g_dfg_t;
+int pm4g_dfg(pm4g_log *log, pm4g_dfg_t *out);
+int pm4g_dfg_free(pm4g_dfg_t *res);
+
+/* Performance DFG (Section 3, dfg.py): the frequency DFG plus, per edge, the
+ * exact sum (sum_lo + 2^64 * sum_hi), minimum and maximum of the durations
+ * ts(next) - ts(prev) as unsigned 64-bit values, and mean = (double)sum /
+ * (double)count. */
+typedef struct {
+  int64_t n_edges;
+  int32_t *src;
+  int32_t *dst;
+  uint64_t *count;
+  uint64_t *sum_lo;
+  uint64_t *sum_hi;
+  uint64_t *min;
+  uint64_t *max;
+  double *mean;
+} pm4g_perf_dfg_t;
+int pm4g_perf_dfg(pm4g_log *log, pm4g_perf_dfg_t *out);
+int pm4g_perf_dfg_free(pm4g_perf_dfg_t *res);
+
+/* Start and end activity counts (Section 3, start_end_activities.py) and
+ * activity frequency (Section 3, event-level aggregation). Caller-provided
+ * host arrays of n_activities entries; freq may be NULL. */
+int pm4g_start_end(pm4g_log *log, uint64_t *start, uint64_t *end, uint64_t *freq);
+
+/* Variants (Section 3, variants.py): a case's variant is its exact activity
+ * sequence. Variants are ranked by count descending, then by smallest case id;
+ * the rank is the variant id. top_k < 0 returns all, otherwise the first
+ * min(top_k, n_variants). With PM4G_VARIANTS_CASES, case_ids (ascending) and
+ * case_variant (variant id of each case) are returned for all n_cases cases. */
+typedef struct {
+  int64_t n_variants; /* total V */
+  int64_t n_out;      /* variants returned */
+  uint64_t *count;    /* [n_out] */
+  int32_t *min_case;  /* [n_out] smallest case id with the variant */
+  int64_t *off;       /* [n_out + 1] CSR offsets into acts */
+  int32_t *acts;      /* [off[n_out]] activity sequences */
+  int64_t n_cases;    /* entries of case_ids / case_variant (0 without the flag) */
+  int32_t *case_ids;
+  int32_t *case_variant;
+} pm4g_variants_t;
+int pm4g_variants(pm4g_log *log, int64_t top_k, uint32_t flags, pm4g_variants_t *out);
+int pm4g_variants_free(pm4g_variants_t *res);
+
+/* Drill-down filter (Section 3, timestamp.py and attributes.py; Section 1,
+ * drill-down). A case is kept iff n_attr == 0 or its attribute value (at its
+ * first event) is in attr_set[0..n_attr). Then the closed window [t_lo, t_hi]
+ * applies: EVENTS keeps the events inside it; CASES_CONTAINED keeps cases whose
+ * first and last timestamps are inside; CASES_INTERSECTING keeps cases whose
+ * span overlaps it; NONE ignores it. The result is a new log (still ordered,
+ * original rows kept) owned by the caller, to be freed with pm4g_log_free.
+ * attr_set is a host array. A log loaded without case_attr accepts only
+ * n_attr == 0. */
+typedef struct {
+  const int32_t *attr_set;
+  int32_t n_attr;
+  int64_t t_lo;
+  int64_t t_hi;
+  int32_t mode;
+} pm4g_filter_spec;
+int pm4g_filter(pm4g_log *log, const pm4g_filter_spec *spec, pm4g_log **out);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *pm4g_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM4G_H */

@@ -1,0 +1,1296 @@
+// C ABI of the engine (include/pm4g.h): contexts, log handles, the formatting
+// and segment passes, and the queries of Section 3 (DFG, performance DFG,
+// start/end activities, variants, drill-down filters, formatted-log export).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "engine.h"
+#include "kernels.h"
+#include "variants.h"
+
+using namespace pm4g;
+
+// ---------------------------------------------------------------------------
+// errors, memory, timing
+// ---------------------------------------------------------------------------
+namespace pm4g {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int check_launch(Ctx *c, const char *what) {
+  c->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("launch of %s failed: %s", what, cudaGetErrorString(e));
+    return PM4G_ECUDA;
+  }
+  return PM4G_OK;
+}
+
+void *dalloc(Ctx *c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (c->has_alloc) return c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dfree(Ctx *c, void *p, size_t bytes) {
+  if (!p) return;
+  if (c->has_alloc) {
+    c->alloc.free(p, bytes, (void *)c->stream, c->alloc.user);
+    return;
+  }
+  cudaFreeAsync(p, c->stream);
+}
+
+static cudaEvent_t get_event(Ctx *c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+KTime::KTime(Ctx *ctx, const char *nm) : c(ctx), name(nm) {
+  if (c->timing) {
+    a = get_event(c);
+    cudaEventRecord(a, c->stream);
+  }
+}
+
+KTime::~KTime() {
+  if (c->timing && a) {
+    b = get_event(c);
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({name, a, b});
+  }
+}
+
+}  // namespace pm4g
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct pm4g_ctx : public pm4g::Ctx {};
+
+struct pm4g_log {
+  Ctx *ctx = nullptr;
+  int64_t n = 0;
+  int32_t A = 1;
+  int64_t C = 0;
+  int32_t min_case = 0;
+  uint64_t R = 0;  // case slots
+  int clb = 0;
+  int act_bits = 0;
+  uint32_t nb = 0;
+  bool has_attr = false;
+  DBuf<uint4> rec;
+  DBuf<uint32_t> bucket_off;
+  DBuf<int32_t> act_s;
+  DBuf<uint32_t> len;
+  DBuf<uint64_t> hash;
+  DBuf<int32_t> cattr;
+  DBuf<int32_t> uniq;  // sorted distinct case ids when renumbered
+  DBuf<unsigned long long> dfg;  // 5 * A * A: cnt, lo, hi, min, max
+  DBuf<unsigned long long> ends; // 2 * A: start, end
+  // caches
+  bool edges_ready = false;
+  std::vector<int32_t> e_src, e_dst;
+  std::vector<uint64_t> e_cnt, e_lo, e_hi, e_min, e_max, h_start, h_end, h_freq;
+  bool span_ready = false;
+  DBuf<int64_t> span;  // first_ts[R], last_ts[R]
+  bool var_ready = false;
+  uint32_t V = 0;
+  DBuf<uint32_t> off, rep_slots, order, vcount, rep_of;
+  DBuf<int32_t> cvar;
+};
+
+template <class T>
+static int alloc_buf(Ctx *c, DBuf<T> &b, size_t n) {
+  b.n = n;
+  b.p = (T *)dalloc(c, (n ? n : 1) * sizeof(T));
+  if (!b.p) {
+    set_error("device allocation of %zu bytes failed", (n ? n : 1) * sizeof(T));
+    return PM4G_ENOMEM;
+  }
+  return PM4G_OK;
+}
+
+template <class T>
+static void free_buf(Ctx *c, DBuf<T> &b) {
+  if (b.p) dfree(c, b.p, (b.n ? b.n : 1) * sizeof(T));
+  b.p = nullptr;
+  b.n = 0;
+}
+
+static void release_log(pm4g_log *L) {
+  if (!L) return;
+  Ctx *c = L->ctx;
+  free_buf(c, L->rec);
+  free_buf(c, L->bucket_off);
+  free_buf(c, L->act_s);
+  free_buf(c, L->len);
+  free_buf(c, L->hash);
+  free_buf(c, L->cattr);
+  free_buf(c, L->uniq);
+  free_buf(c, L->dfg);
+  free_buf(c, L->ends);
+  free_buf(c, L->span);
+  free_buf(c, L->off);
+  free_buf(c, L->rep_slots);
+  free_buf(c, L->order);
+  free_buf(c, L->vcount);
+  free_buf(c, L->rep_of);
+  free_buf(c, L->cvar);
+  c->live_logs--;
+  delete L;
+}
+
+static int d2h(Ctx *c, void *dst, const void *src, size_t bytes) {
+  if (!bytes) return PM4G_OK;
+  PM4G_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+  PM4G_CK(cudaStreamSynchronize(c->stream));
+  return PM4G_OK;
+}
+
+// ---------------------------------------------------------------------------
+// segment pass configuration
+// ---------------------------------------------------------------------------
+struct SegConfig {
+  int cap, a_s, tbl_mode, tbl_slots;
+  size_t smem;
+};
+
+static SegConfig seg_config(Ctx *c, int clb, int32_t A) {
+  SegConfig s;
+  const int ncl = 1 << clb;
+  s.a_s = A <= 2048 ? A : 0;
+  const int64_t cells = (int64_t)A * A;
+  if (cells <= 4096) {
+    s.tbl_mode = 0;
+    s.tbl_slots = (int)cells;
+  } else {
+    s.tbl_mode = 1;
+    s.tbl_slots = 4096;
+  }
+  const size_t fixed = seg_smem_layout(0, ncl, s.a_s, s.tbl_slots, s.tbl_mode).total + 64;
+  int64_t cap = ((int64_t)c->smem_optin - (int64_t)fixed) / 18;
+  cap = std::min<int64_t>(cap, 65535);
+  cap = cap / 32 * 32;
+  if (c->test_bucket_cap > 0) cap = std::min<int64_t>(cap, c->test_bucket_cap);
+  s.cap = (int)std::max<int64_t>(cap, 0);
+  s.smem = seg_smem_layout(s.cap, ncl, s.a_s, s.tbl_slots, s.tbl_mode).total;
+  return s;
+}
+
+static SegArgs seg_args(pm4g_log *L, const SegConfig &sc, uint32_t *work, uint32_t *ovf, uint32_t *n_ovf,
+                        unsigned long long *n_cases) {
+  SegArgs a{};
+  a.rec = L->rec.p;
+  a.bucket_off = L->bucket_off.p;
+  a.nb = L->nb;
+  a.clb = L->clb;
+  a.act_bits = L->act_bits;
+  a.n_act = (uint32_t)L->A;
+  a.n_slots = L->R;
+  a.cap = sc.cap;
+  a.ep_smem = sc.a_s > 0;
+  a.tbl_mode = sc.tbl_mode;
+  a.tbl_slots = sc.tbl_slots;
+  a.work = work;
+  a.act_s = L->act_s.p;
+  a.len = L->len.p;
+  a.hash = L->hash.p;
+  a.seed = 0;
+  const size_t cells = (size_t)L->A * L->A;
+  a.g.cnt = L->dfg.p;
+  a.g.lo = L->dfg.p + cells;
+  a.g.hi = L->dfg.p + 2 * cells;
+  a.g.mn = L->dfg.p + 3 * cells;
+  a.g.mx = L->dfg.p + 4 * cells;
+  a.g_start = L->ends.p;
+  a.g_end = L->ends.p + L->A;
+  a.ovf = ovf;
+  a.n_ovf = n_ovf;
+  a.n_cases = n_cases;
+  a.min_case = L->min_case;
+  a.uniq = L->uniq.p;
+  return a;
+}
+
+// Global-memory path for one bucket (too many events, or a case too long to
+// sort on chip): radix sort by (case slot, timestamp, row), then the same
+// per-position computation with global atomics.
+static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) {
+  Ctx *c = L->ctx;
+  uint32_t lohi[2];
+  PM4G_TRY(d2h(c, lohi, L->bucket_off.p + b, sizeof(lohi)));
+  const uint32_t lo = lohi[0], n = lohi[1] - lohi[0];
+  const int ncl = 1 << L->clb;
+  Scratch S(c);
+  uint32_t *keys = S.get<uint32_t>(n), *vals = S.get<uint32_t>(n);
+  uint32_t *keys2 = S.get<uint32_t>(n), *vals2 = S.get<uint32_t>(n);
+  uint64_t *k64 = S.get<uint64_t>(n), *k64b = S.get<uint64_t>(n);
+  uint4 *srec = S.get<uint4>(n);
+  uint32_t *ccnt = S.get<uint32_t>(ncl), *cstart = S.get<uint32_t>(ncl + 1);
+  if (!keys || !vals || !keys2 || !vals2 || !k64 || !k64b || !srec || !ccnt || !cstart) {
+    set_error("bucket fallback: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  const uint4 *rec = L->rec.p + lo;
+  const unsigned g = grid_for(n, 256, 8192);
+  {
+    KTime t(c, "fallback");
+    k_fb_keys_row<<<g, 256, 0, c->stream>>>(rec, n, keys, vals);
+    PM4G_TRY(check_launch(c, "k_fb_keys_row"));
+  }
+  PM4G_TRY(radix_sort_u32(c, keys, vals, keys2, vals2, n, 0, 32));
+  {
+    KTime t(c, "fallback");
+    k_fb_keys_ts<<<g, 256, 0, c->stream>>>(rec, vals, n, k64);
+    PM4G_TRY(check_launch(c, "k_fb_keys_ts"));
+  }
+  PM4G_TRY(radix_sort_u64(c, k64, vals, k64b, vals2, n, 0, 64));
+  if (L->clb > 0) {
+    {
+      KTime t(c, "fallback");
+      k_fb_keys_case<<<g, 256, 0, c->stream>>>(rec, vals, n, L->act_bits, keys);
+      PM4G_TRY(check_launch(c, "k_fb_keys_case"));
+    }
+    PM4G_TRY(radix_sort_u32(c, keys, vals, keys2, vals2, n, 0, L->clb));
+  }
+  PM4G_CK(cudaMemsetAsync(ccnt, 0, ncl * sizeof(uint32_t), c->stream));
+  {
+    KTime t(c, "fallback");
+    k_fb_gather<<<g, 256, 0, c->stream>>>(rec, vals, n, srec);
+    PM4G_TRY(check_launch(c, "k_fb_gather"));
+    k_fb_hist<<<g, 256, 0, c->stream>>>(srec, n, L->act_bits, ccnt);
+    PM4G_TRY(check_launch(c, "k_fb_hist"));
+  }
+  PM4G_TRY(scan_u32(c, ccnt, cstart, ncl));
+  if (!exp) {
+    const uint64_t s0 = (uint64_t)b << L->clb;
+    const uint64_t s1 = std::min<uint64_t>(L->R, s0 + (uint64_t)ncl);
+    PM4G_CK(cudaMemsetAsync(L->hash.p + s0, 0, (s1 - s0) * sizeof(uint64_t), c->stream));
+  }
+  KTime t(c, "fallback");
+  c->launches++;
+  PM4G_CK(launch_fb_compute(exp, a, srec, n, b, cstart, g, c->stream));
+  k_fb_cases<<<(ncl + 255) / 256, 256, 0, c->stream>>>(a, srec, b, ccnt, cstart, ncl, exp ? 0 : 1);
+  return check_launch(c, "k_fb_cases");
+}
+
+// Runs the segment pass over a bucketed log: fills act_s, len, hash, the DFG
+// table, the endpoint counts and (at load) the per-case attribute; sets C.
+static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr) {
+  Ctx *c = L->ctx;
+  const size_t cells = (size_t)L->A * L->A;
+  PM4G_TRY(alloc_buf(c, L->act_s, L->n));
+  PM4G_TRY(alloc_buf(c, L->len, L->R));
+  PM4G_TRY(alloc_buf(c, L->hash, L->R));
+  PM4G_TRY(alloc_buf(c, L->dfg, 5 * cells));
+  PM4G_TRY(alloc_buf(c, L->ends, 2 * (size_t)L->A));
+  PM4G_CK(cudaMemsetAsync(L->dfg.p, 0, 3 * cells * sizeof(unsigned long long), c->stream));
+  PM4G_CK(cudaMemsetAsync(L->dfg.p + 3 * cells, 0xFF, cells * sizeof(unsigned long long), c->stream));
+  PM4G_CK(cudaMemsetAsync(L->dfg.p + 4 * cells, 0, cells * sizeof(unsigned long long), c->stream));
+  PM4G_CK(cudaMemsetAsync(L->ends.p, 0, 2 * L->A * sizeof(unsigned long long), c->stream));
+  if (write_cattr) {
+    PM4G_TRY(alloc_buf(c, L->cattr, L->R));
+    PM4G_CK(cudaMemsetAsync(L->cattr.p, 0, L->R * sizeof(int32_t), c->stream));
+  }
+  PM4G_CK(cudaMemsetAsync(L->len.p, 0, L->R * sizeof(uint32_t), c->stream));
+  if (L->n == 0 || L->nb == 0) {
+    L->C = 0;
+    return PM4G_OK;
+  }
+  Scratch S(c);
+  uint32_t *ctr = S.get<uint32_t>(4);  // work, n_ovf
+  unsigned long long *n_cases = S.get<unsigned long long>(1);
+  uint32_t *ovf = S.get<uint32_t>(L->nb);
+  if (!ctr || !n_cases || !ovf) {
+    set_error("segment pass: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  PM4G_CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), c->stream));
+  PM4G_CK(cudaMemsetAsync(n_cases, 0, sizeof(unsigned long long), c->stream));
+  const SegConfig sc = seg_config(c, L->clb, L->A);
+  SegArgs a = seg_args(L, sc, ctr, ovf, ctr + 1, n_cases);
+  a.attr_in = attr_in;
+  a.cattr = write_cattr ? L->cattr.p : nullptr;
+  if (sc.cap >= 32) {
+    const unsigned grid = std::min<unsigned>(L->nb, (unsigned)c->num_sms);
+    KTime t(c, "segment");
+    c->launches++;
+    PM4G_CK(launch_segment(false, a, grid, sc.smem, c->stream));
+  } else {
+    // nothing fits on chip: every bucket takes the global-memory path
+    std::vector<uint32_t> all(L->nb);
+    for (uint32_t b = 0; b < L->nb; ++b) all[b] = b;
+    PM4G_CK(cudaMemcpyAsync(ovf, all.data(), L->nb * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+    const uint32_t nbv = L->nb;
+    PM4G_CK(cudaMemcpyAsync(ctr + 1, &nbv, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+  }
+  uint32_t n_ovf = 0;
+  PM4G_TRY(d2h(c, &n_ovf, ctr + 1, sizeof(uint32_t)));
+  if (n_ovf) {
+    std::vector<uint32_t> list(n_ovf);
+    PM4G_TRY(d2h(c, list.data(), ovf, n_ovf * sizeof(uint32_t)));
+    std::sort(list.begin(), list.end());
+    for (uint32_t b : list) PM4G_TRY(fallback_bucket(L, a, b, false));
+  }
+  unsigned long long nc = 0;
+  PM4G_TRY(d2h(c, &nc, n_cases, sizeof(nc)));
+  L->C = (int64_t)nc;
+  return PM4G_OK;
+}
+
+// Chooses the bucket width (2^clb case slots) so that a bucket's expected
+// events stay well inside the on-chip capacity.
+static int choose_clb(Ctx *c, int64_t n, uint64_t R, int32_t A, int act_bits) {
+  const double avg = (double)n / (double)std::max<uint64_t>(R, 1);
+  int best = 0;
+  for (int clb = 10; clb >= 0; --clb) {
+    if (clb + act_bits > 32) continue;
+    const SegConfig sc = seg_config(c, clb, A);
+    if (avg * (double)(1 << clb) <= 0.72 * (double)sc.cap) {
+      best = clb;
+      break;
+    }
+  }
+  // keep at least two buckets per SM when the log allows it
+  while (best > 3 && ((R + (1ull << best) - 1) >> best) < 2ull * (uint64_t)c->num_sms) --best;
+  return best;
+}
+
+// The API functions below take C linkage from their declarations in pm4g.h.
+
+const char *pm4g_last_error(void) { return pm4g::g_err; }
+
+const char *pm4g_kernel_names(void) { return "stats,bucket_hist,bucket_scatter,segment,fallback,scan,radix_sort,filter,variants,dfg"; }
+
+int pm4g_ctx_create(pm4g_ctx **out, int device, void *cuda_stream, const pm4g_allocator *alloc) {
+  if (!out) {
+    set_error("pm4g_ctx_create: out is NULL");
+    return PM4G_EINVAL;
+  }
+  *out = nullptr;
+  int ndev = 0;
+  PM4G_CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) {
+    set_error("pm4g_ctx_create: device %d out of range (%d devices)", device, ndev);
+    return PM4G_EINVAL;
+  }
+  if (alloc && (!alloc->alloc || !alloc->free)) {
+    set_error("pm4g_ctx_create: allocator needs both alloc and free");
+    return PM4G_EINVAL;
+  }
+  PM4G_CK(cudaSetDevice(device));
+  pm4g_ctx *c = new (std::nothrow) pm4g_ctx();
+  if (!c) return PM4G_ENOMEM;
+  c->device = device;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      set_error("pm4g_ctx_create: stream creation failed");
+      return PM4G_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  if (alloc) {
+    c->alloc = *alloc;
+    c->has_alloc = true;
+  } else {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;  // keep freed blocks cached in this process
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  *out = c;
+  return PM4G_OK;
+}
+
+int pm4g_ctx_destroy(pm4g_ctx *c) {
+  if (!c) return PM4G_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto &p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->free_events) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return PM4G_OK;
+}
+
+int pm4g_ctx_set_option(pm4g_ctx *c, int option, int64_t value) {
+  if (!c) {
+    set_error("pm4g_ctx_set_option: ctx is NULL");
+    return PM4G_EINVAL;
+  }
+  switch (option) {
+    case PM4G_OPT_TIMING:
+      c->timing = value != 0;
+      return PM4G_OK;
+    case PM4G_OPT_TEST_HASH_BITS:
+      if (value < 0 || value > 63) break;
+      c->test_hash_bits = (int)value;
+      return PM4G_OK;
+    case PM4G_OPT_TEST_BUCKET_CAP:
+      if (value != 0 && (value < 32 || value > 65535)) break;
+      c->test_bucket_cap = (int)value;
+      return PM4G_OK;
+    default:
+      break;
+  }
+  set_error("pm4g_ctx_set_option: bad option %d or value %lld", option, (long long)value);
+  return PM4G_EINVAL;
+}
+
+int pm4g_ctx_timing(pm4g_ctx *c, const char *name, int64_t *launches, double *total_ms) {
+  if (!c || !name || !launches || !total_ms) {
+    set_error("pm4g_ctx_timing: NULL argument");
+    return PM4G_EINVAL;
+  }
+  cudaSetDevice(c->device);
+  PM4G_CK(cudaStreamSynchronize(c->stream));
+  for (auto &p : c->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    auto &t = c->totals[p.name];
+    t.first += 1;
+    t.second += ms;
+    c->free_events.push_back(p.a);
+    c->free_events.push_back(p.b);
+  }
+  c->pending.clear();
+  if (strcmp(name, "launches") == 0) {
+    *launches = c->launches;
+    *total_ms = 0.0;
+    return PM4G_OK;
+  }
+  auto it = c->totals.find(name);
+  *launches = it == c->totals.end() ? 0 : it->second.first;
+  *total_ms = it == c->totals.end() ? 0.0 : it->second.second;
+  return PM4G_OK;
+}
+
+int pm4g_ctx_timing_reset(pm4g_ctx *c) {
+  if (!c) return PM4G_EINVAL;
+  int64_t l;
+  double ms;
+  pm4g_ctx_timing(c, "", &l, &ms);
+  c->totals.clear();
+  c->launches = 0;
+  return PM4G_OK;
+}
+
+int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, const int64_t *ts_ns,
+                  const int32_t *case_attr, int64_t n, int32_t A, uint32_t flags, pm4g_log **out) {
+  if (!c || !out) {
+    set_error("pm4g_load_log: ctx or out is NULL");
+    return PM4G_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 0 || n > INT32_MAX) {
+    set_error("pm4g_load_log: n_events %lld outside [0, 2^31-1]", (long long)n);
+    return PM4G_EINVAL;
+  }
+  if (A < 1 || A > 2048) {
+    set_error("pm4g_load_log: n_activities %d outside [1, 2048]", A);
+    return PM4G_EINVAL;
+  }
+  if (flags != PM4G_HOST_PTRS && flags != PM4G_DEVICE_PTRS) {
+    set_error("pm4g_load_log: flags must be PM4G_HOST_PTRS or PM4G_DEVICE_PTRS");
+    return PM4G_EINVAL;
+  }
+  if (n > 0 && (!case_id || !activity || !ts_ns)) {
+    set_error("pm4g_load_log: NULL column");
+    return PM4G_EINVAL;
+  }
+  PM4G_CK(cudaSetDevice(c->device));
+  pm4g_log *L = new (std::nothrow) pm4g_log();
+  if (!L) return PM4G_ENOMEM;
+  L->ctx = c;
+  c->live_logs++;
+  L->n = n;
+  L->A = A;
+  L->has_attr = case_attr != nullptr;
+  L->act_bits = bits_for((uint64_t)(A - 1));
+  int st = PM4G_OK;
+  {
+    Scratch S(c);
+    const int32_t *dcase = case_id, *dact = activity, *dattr = case_attr;
+    const int64_t *dts = ts_ns;
+    auto fail = [&](int s) {
+      st = s;
+      return s;
+    };
+    do {
+      if (flags == PM4G_HOST_PTRS && n > 0) {
+        int32_t *hc = S.get<int32_t>(n), *ha = S.get<int32_t>(n);
+        int64_t *ht = S.get<int64_t>(n);
+        int32_t *hat = case_attr ? S.get<int32_t>(n) : nullptr;
+        if (!hc || !ha || !ht || (case_attr && !hat)) {
+          set_error("pm4g_load_log: out of device memory for input columns");
+          fail(PM4G_ENOMEM);
+          break;
+        }
+        KTime t(c, "h2d");
+        if (cudaMemcpyAsync(hc, case_id, n * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(ha, activity, n * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(ht, ts_ns, n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            (hat && cudaMemcpyAsync(hat, case_attr, n * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)) {
+          set_error("pm4g_load_log: host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+          fail(PM4G_ECUDA);
+          break;
+        }
+        dcase = hc;
+        dact = ha;
+        dts = ht;
+        dattr = hat;
+      }
+      if (n == 0) {
+        L->R = 0;
+        L->nb = 0;
+        if (fail(alloc_buf(c, L->bucket_off, 1))) break;
+        if (cudaMemsetAsync(L->bucket_off.p, 0, 4, c->stream) != cudaSuccess) {
+          fail(PM4G_ECUDA);
+          break;
+        }
+        if (fail(run_segment(L, nullptr, L->has_attr))) break;
+        break;
+      }
+      // stats: case id range (column reduction)
+      const unsigned gs = (unsigned)c->num_sms * 4;
+      int2 *part = S.get<int2>(gs);
+      if (!part) {
+        fail(PM4G_ENOMEM);
+        break;
+      }
+      {
+        KTime t(c, "stats");
+        k_stats<<<gs, 256, 0, c->stream>>>(dcase, n, part);
+        if (fail(check_launch(c, "k_stats"))) break;
+      }
+      std::vector<int2> hp(gs);
+      if (fail(d2h(c, hp.data(), part, gs * sizeof(int2)))) break;
+      int mn = INT32_MAX, mx = INT32_MIN;
+      for (auto &p : hp) {
+        mn = std::min(mn, p.x);
+        mx = std::max(mx, p.y);
+      }
+      uint64_t R = (uint64_t)((int64_t)mx - (int64_t)mn + 1);
+      const int32_t *keycol = dcase;
+      L->min_case = mn;
+      if (R > std::max<uint64_t>(2 * (uint64_t)n, 1u << 20)) {
+        // sparse case ids: dense renumbering by rank of the distinct ids
+        uint32_t *keys = S.get<uint32_t>(n), *vals = S.get<uint32_t>(n);
+        uint32_t *k2 = S.get<uint32_t>(n), *v2 = S.get<uint32_t>(n);
+        uint32_t *head = S.get<uint32_t>(n), *hpos = S.get<uint32_t>(n + 1);
+        int32_t *dense = S.get<int32_t>(n);
+        int32_t *uq = S.get<int32_t>(n);
+        if (!keys || !vals || !k2 || !v2 || !head || !hpos || !dense || !uq) {
+          set_error("pm4g_load_log: out of device memory for case renumbering");
+          fail(PM4G_ENOMEM);
+          break;
+        }
+        const unsigned g = grid_for(n, 256, 8192);
+        k_case_keys<<<g, 256, 0, c->stream>>>(dcase, n, keys, vals);
+        if (fail(check_launch(c, "k_case_keys"))) break;
+        if (fail(radix_sort_u32(c, keys, vals, k2, v2, n, 0, 32))) break;
+        k_case_heads<<<g, 256, 0, c->stream>>>(keys, n, head);
+        if (fail(check_launch(c, "k_case_heads"))) break;
+        if (fail(scan_u32(c, head, hpos, n))) break;
+        uint32_t Cu = 0;
+        if (fail(d2h(c, &Cu, hpos + n, 4))) break;
+        if (fail(alloc_buf(c, L->uniq, Cu))) break;
+        k_case_dense<<<g, 256, 0, c->stream>>>(keys, vals, head, hpos, n, dense, L->uniq.p);
+        if (fail(check_launch(c, "k_case_dense"))) break;
+        (void)uq;
+        keycol = dense;
+        L->min_case = 0;
+        R = Cu;
+      }
+      L->R = R;
+      L->clb = choose_clb(c, n, R, A, L->act_bits);
+      const int ncl = 1 << L->clb;
+      const uint64_t nb64 = (R + ncl - 1) >> L->clb;
+      if (nb64 > 0xFFFFFFF0ull) {
+        set_error("pm4g_load_log: too many buckets");
+        fail(PM4G_EINVAL);
+        break;
+      }
+      L->nb = (uint32_t)nb64;
+      // bucket histogram, offsets and scatter
+      int64_t chunk = (n + c->num_sms - 1) / c->num_sms;
+      chunk = (chunk + 3) / 4 * 4;
+      const int p_ctas = (int)((n + chunk - 1) / chunk);
+      uint32_t *mat = S.get<uint32_t>((size_t)p_ctas * L->nb);
+      uint32_t *total = S.get<uint32_t>(L->nb);
+      uint32_t *err = S.get<uint32_t>(1);
+      if (!mat || !total || !err) {
+        set_error("pm4g_load_log: out of device memory for the bucket matrix");
+        fail(PM4G_ENOMEM);
+        break;
+      }
+      if (fail(alloc_buf(c, L->bucket_off, (size_t)L->nb + 1))) break;
+      if (fail(alloc_buf(c, L->rec, n))) break;
+      if (cudaMemsetAsync(err, 0, 4, c->stream) != cudaSuccess) {
+        fail(PM4G_ECUDA);
+        break;
+      }
+      FormatArgs fa{};
+      fa.case_id = keycol;
+      fa.activity = dact;
+      fa.ts = dts;
+      fa.n = n;
+      fa.chunk = chunk;
+      fa.min_case = L->min_case;
+      fa.clb = L->clb;
+      fa.act_bits = L->act_bits;
+      fa.n_act = A;
+      fa.nb = L->nb;
+      fa.mat = mat;
+      fa.bucket_off = L->bucket_off.p;
+      fa.rec = L->rec.p;
+      fa.err_flags = err;
+      const uint32_t nbs_max = (uint32_t)std::min<int64_t>(((int64_t)c->smem_optin - 1024) / 4, 1 << 20);
+      cudaFuncSetAttribute(k_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, nbs_max * 4);
+      cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, nbs_max * 4);
+      for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
+        const uint32_t nbs = std::min(nbs_max, L->nb - b0);
+        KTime t(c, "bucket_hist");
+        k_bucket_hist<<<p_ctas, 1024, nbs * 4, c->stream>>>(fa, b0, nbs);
+        fail(check_launch(c, "k_bucket_hist"));
+      }
+      if (st) break;
+      {
+        KTime t(c, "scan");
+        k_bucket_colprefix<<<(L->nb + 255) / 256, 256, 0, c->stream>>>(mat, L->nb, p_ctas, total);
+        if (fail(check_launch(c, "k_bucket_colprefix"))) break;
+      }
+      if (fail(scan_u32(c, total, L->bucket_off.p, L->nb))) break;
+      for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
+        const uint32_t nbs = std::min(nbs_max, L->nb - b0);
+        KTime t(c, "bucket_scatter");
+        k_bucket_scatter<<<p_ctas, 1024, nbs * 4, c->stream>>>(fa, b0, nbs);
+        fail(check_launch(c, "k_bucket_scatter"));
+      }
+      if (st) break;
+      if (fail(run_segment(L, dattr, L->has_attr))) break;
+      uint32_t errv = 0;
+      if (fail(d2h(c, &errv, err, 4))) break;
+      if (errv & 1u) {
+        set_error("pm4g_load_log: activity code outside [0, %d)", A);
+        fail(PM4G_ERANGE);
+        break;
+      }
+    } while (0);
+  }
+  if (st != PM4G_OK) {
+    release_log(L);
+    return st;
+  }
+  *out = L;
+  return PM4G_OK;
+}
+
+int pm4g_log_info(const pm4g_log *L, int64_t *n_events, int64_t *n_cases) {
+  if (!L) {
+    set_error("pm4g_log_info: log is NULL");
+    return PM4G_EINVAL;
+  }
+  if (n_events) *n_events = L->n;
+  if (n_cases) *n_cases = L->C;
+  return PM4G_OK;
+}
+
+int pm4g_log_free(pm4g_log *L) {
+  if (!L) return PM4G_OK;
+  cudaSetDevice(L->ctx->device);
+  release_log(L);
+  return PM4G_OK;
+}
+
+int pm4g_log_export(pm4g_log *L, int32_t *case_out, int32_t *act_out, int64_t *ts_out, int64_t *row_out) {
+  if (!L) {
+    set_error("pm4g_log_export: log is NULL");
+    return PM4G_EINVAL;
+  }
+  Ctx *c = L->ctx;
+  PM4G_CK(cudaSetDevice(c->device));
+  if (L->n == 0) return PM4G_OK;
+  Scratch S(c);
+  int32_t *ec = S.get<int32_t>(L->n), *ea = S.get<int32_t>(L->n);
+  int64_t *et = S.get<int64_t>(L->n), *er = S.get<int64_t>(L->n);
+  uint32_t *ctr = S.get<uint32_t>(4);
+  uint32_t *ovf = S.get<uint32_t>(L->nb);
+  unsigned long long *dummy = S.get<unsigned long long>(1);
+  if (!ec || !ea || !et || !er || !ctr || !ovf || !dummy) {
+    set_error("pm4g_log_export: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  PM4G_CK(cudaMemsetAsync(ctr, 0, 16, c->stream));
+  const SegConfig sc = seg_config(c, L->clb, L->A);
+  SegArgs a = seg_args(L, sc, ctr, ovf, ctr + 1, dummy);
+  a.act_s = ea;
+  a.ex_case = ec;
+  a.ex_ts = et;
+  a.ex_row = er;
+  uint32_t n_ovf = 0;
+  if (sc.cap >= 32) {
+    KTime t(c, "export");
+    c->launches++;
+    PM4G_CK(launch_segment(true, a, std::min<unsigned>(L->nb, (unsigned)c->num_sms), sc.smem, c->stream));
+    PM4G_TRY(d2h(c, &n_ovf, ctr + 1, 4));
+  } else {
+    n_ovf = L->nb;
+  }
+  std::vector<uint32_t> list(n_ovf);
+  if (sc.cap >= 32) {
+    PM4G_TRY(d2h(c, list.data(), ovf, n_ovf * 4));
+  } else {
+    for (uint32_t b = 0; b < n_ovf; ++b) list[b] = b;
+  }
+  for (uint32_t b : list) PM4G_TRY(fallback_bucket(L, a, b, true));
+  if (case_out) PM4G_CK(cudaMemcpyAsync(case_out, ec, L->n * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (act_out) PM4G_CK(cudaMemcpyAsync(act_out, ea, L->n * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (ts_out) PM4G_CK(cudaMemcpyAsync(ts_out, et, L->n * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (row_out) PM4G_CK(cudaMemcpyAsync(row_out, er, L->n * 8, cudaMemcpyDeviceToHost, c->stream));
+  PM4G_CK(cudaStreamSynchronize(c->stream));
+  return PM4G_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DFG / endpoints
+// ---------------------------------------------------------------------------
+static int ensure_edges(pm4g_log *L) {
+  if (L->edges_ready) return PM4G_OK;
+  Ctx *c = L->ctx;
+  const int64_t cells = (int64_t)L->A * L->A;
+  const uint32_t A = (uint32_t)L->A;
+  Scratch S(c);
+  uint32_t *flags = S.get<uint32_t>(cells), *pos = S.get<uint32_t>(cells + 1);
+  unsigned long long *freq = S.get<unsigned long long>(A);
+  if (!flags || !pos || !freq) {
+    set_error("dfg: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  const unsigned long long *g = L->dfg.p;
+  {
+    KTime t(c, "dfg");
+    k_dfg_flags<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(g, cells, flags);
+    PM4G_TRY(check_launch(c, "k_dfg_flags"));
+  }
+  PM4G_TRY(scan_u32(c, flags, pos, cells));
+  uint32_t E = 0;
+  PM4G_TRY(d2h(c, &E, pos + cells, 4));
+  int32_t *src = S.get<int32_t>(E), *dst = S.get<int32_t>(E);
+  unsigned long long *o[5];
+  for (auto &p : o) p = S.get<unsigned long long>(E);
+  if (!src || !dst || !o[0] || !o[1] || !o[2] || !o[3] || !o[4]) return PM4G_ENOMEM;
+  DfgTable t{L->dfg.p, L->dfg.p + cells, L->dfg.p + 2 * cells, L->dfg.p + 3 * cells, L->dfg.p + 4 * cells};
+  {
+    KTime tk(c, "dfg");
+    k_dfg_compact<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(t, cells, A, flags, pos, src, dst, o[0], o[1],
+                                                                     o[2], o[3], o[4]);
+    PM4G_TRY(check_launch(c, "k_dfg_compact"));
+    k_freq<<<A, 256, 0, c->stream>>>(t.cnt, L->ends.p + A, A, freq);
+    PM4G_TRY(check_launch(c, "k_freq"));
+  }
+  L->e_src.resize(E);
+  L->e_dst.resize(E);
+  L->e_cnt.resize(E);
+  L->e_lo.resize(E);
+  L->e_hi.resize(E);
+  L->e_min.resize(E);
+  L->e_max.resize(E);
+  L->h_start.resize(A);
+  L->h_end.resize(A);
+  L->h_freq.resize(A);
+  cudaStream_t s = c->stream;
+  PM4G_CK(cudaMemcpyAsync(L->e_src.data(), src, E * 4, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->e_dst.data(), dst, E * 4, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->e_cnt.data(), o[0], E * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->e_lo.data(), o[1], E * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->e_hi.data(), o[2], E * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->e_min.data(), o[3], E * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->e_max.data(), o[4], E * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->h_start.data(), L->ends.p, A * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->h_end.data(), L->ends.p + A, A * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(L->h_freq.data(), freq, A * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaStreamSynchronize(s));
+  L->edges_ready = true;
+  return PM4G_OK;
+}
+
+template <class T>
+static T *host_copy(const std::vector<T> &v) {
+  T *p = (T *)malloc(std::max<size_t>(v.size(), 1) * sizeof(T));
+  if (p && !v.empty()) memcpy(p, v.data(), v.size() * sizeof(T));
+  return p;
+}
+
+int pm4g_dfg(pm4g_log *L, pm4g_dfg_t *out) {
+  if (!L || !out) {
+    set_error("pm4g_dfg: NULL argument");
+    return PM4G_EINVAL;
+  }
+  memset(out, 0, sizeof(*out));
+  PM4G_CK(cudaSetDevice(L->ctx->device));
+  PM4G_TRY(ensure_edges(L));
+  out->n_edges = (int64_t)L->e_src.size();
+  out->src = host_copy(L->e_src);
+  out->dst = host_copy(L->e_dst);
+  out->count = host_copy(L->e_cnt);
+  if (!out->src || !out->dst || !out->count) {
+    pm4g_dfg_free(out);
+    return PM4G_ENOMEM;
+  }
+  return PM4G_OK;
+}
+
+int pm4g_dfg_free(pm4g_dfg_t *r) {
+  if (!r) return PM4G_OK;
+  free(r->src);
+  free(r->dst);
+  free(r->count);
+  memset(r, 0, sizeof(*r));
+  return PM4G_OK;
+}
+
+int pm4g_perf_dfg(pm4g_log *L, pm4g_perf_dfg_t *out) {
+  if (!L || !out) {
+    set_error("pm4g_perf_dfg: NULL argument");
+    return PM4G_EINVAL;
+  }
+  memset(out, 0, sizeof(*out));
+  PM4G_CK(cudaSetDevice(L->ctx->device));
+  PM4G_TRY(ensure_edges(L));
+  const size_t E = L->e_src.size();
+  out->n_edges = (int64_t)E;
+  out->src = host_copy(L->e_src);
+  out->dst = host_copy(L->e_dst);
+  out->count = host_copy(L->e_cnt);
+  out->sum_lo = host_copy(L->e_lo);
+  out->sum_hi = host_copy(L->e_hi);
+  out->min = host_copy(L->e_min);
+  out->max = host_copy(L->e_max);
+  out->mean = (double *)malloc(std::max<size_t>(E, 1) * sizeof(double));
+  if (!out->src || !out->dst || !out->count || !out->sum_lo || !out->sum_hi || !out->min || !out->max || !out->mean) {
+    pm4g_perf_dfg_free(out);
+    return PM4G_ENOMEM;
+  }
+  for (size_t k = 0; k < E; ++k) {
+    const u128 s = ((u128)L->e_hi[k] << 64) | (u128)L->e_lo[k];
+    out->mean[k] = (double)s / (double)L->e_cnt[k];
+  }
+  return PM4G_OK;
+}
+
+int pm4g_perf_dfg_free(pm4g_perf_dfg_t *r) {
+  if (!r) return PM4G_OK;
+  free(r->src);
+  free(r->dst);
+  free(r->count);
+  free(r->sum_lo);
+  free(r->sum_hi);
+  free(r->min);
+  free(r->max);
+  free(r->mean);
+  memset(r, 0, sizeof(*r));
+  return PM4G_OK;
+}
+
+int pm4g_start_end(pm4g_log *L, uint64_t *start, uint64_t *end, uint64_t *freq) {
+  if (!L || !start || !end) {
+    set_error("pm4g_start_end: NULL argument");
+    return PM4G_EINVAL;
+  }
+  PM4G_CK(cudaSetDevice(L->ctx->device));
+  PM4G_TRY(ensure_edges(L));
+  memcpy(start, L->h_start.data(), L->A * 8);
+  memcpy(end, L->h_end.data(), L->A * 8);
+  if (freq) memcpy(freq, L->h_freq.data(), L->A * 8);
+  return PM4G_OK;
+}
+
+// ---------------------------------------------------------------------------
+// variants
+// ---------------------------------------------------------------------------
+static uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+static int ensure_variants(pm4g_log *L) {
+  if (L->var_ready) return PM4G_OK;
+  Ctx *c = L->ctx;
+  const uint64_t R = L->R;
+  PM4G_TRY(alloc_buf(c, L->off, R + 1));
+  PM4G_TRY(alloc_buf(c, L->vcount, R));
+  PM4G_TRY(alloc_buf(c, L->rep_of, R));
+  PM4G_TRY(alloc_buf(c, L->cvar, R));
+  PM4G_TRY(scan_u32(c, L->len.p, L->off.p, (int64_t)R));
+  if (L->C == 0) {
+    L->V = 0;
+    PM4G_TRY(alloc_buf(c, L->rep_slots, 0));
+    PM4G_TRY(alloc_buf(c, L->order, 0));
+    L->var_ready = true;
+    return PM4G_OK;
+  }
+  Scratch S(c);
+  const uint64_t T = next_pow2(std::max<uint64_t>(2 * (uint64_t)L->C, 1024));
+  unsigned long long *tkey = S.get<unsigned long long>(T);
+  uint32_t *tcnt = S.get<uint32_t>(T), *tmin = S.get<uint32_t>(T);
+  uint32_t *grp = S.get<uint32_t>(R);
+  uint8_t *isbad = S.get<uint8_t>(R);
+  uint32_t *listA = S.get<uint32_t>(L->C), *listB = S.get<uint32_t>(L->C);
+  uint32_t *n_bad = S.get<uint32_t>(1);
+  if (!tkey || !tcnt || !tmin || !grp || !isbad || !listA || !listB || !n_bad) {
+    set_error("variants: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  VarArgs a{};
+  a.n_slots = R;
+  a.len = L->len.p;
+  a.hash = L->hash.p;
+  a.off = L->off.p;
+  a.act_s = L->act_s.p;
+  a.bits = c->test_hash_bits;
+  a.tkey = tkey;
+  a.tcnt = tcnt;
+  a.tmin = tmin;
+  a.grp = grp;
+  a.rep_of = L->rep_of.p;
+  a.vcount = L->vcount.p;
+  a.isbad = isbad;
+  const uint32_t *list = nullptr;
+  uint32_t n_list = 0;
+  uint32_t *out_list = listA;
+  for (uint32_t round = 0;; ++round) {
+    const uint64_t items = list ? n_list : R;
+    const uint64_t Tr = next_pow2(std::max<uint64_t>(2 * (list ? n_list : (uint64_t)L->C), 1024));
+    a.tmask = (uint32_t)(Tr - 1);
+    PM4G_CK(cudaMemsetAsync(tkey, 0, Tr * 8, c->stream));
+    PM4G_CK(cudaMemsetAsync(tcnt, 0, Tr * 4, c->stream));
+    PM4G_CK(cudaMemsetAsync(tmin, 0xFF, Tr * 4, c->stream));
+    PM4G_CK(cudaMemsetAsync(n_bad, 0, 4, c->stream));
+    const unsigned g = grid_for((int64_t)items, 256, 65535);
+    KTime t(c, "variants");
+    k_var_insert<<<g, 256, 0, c->stream>>>(a, list, n_list, round);
+    PM4G_TRY(check_launch(c, "k_var_insert"));
+    k_var_verify<<<g, 256, 0, c->stream>>>(a, list, n_list, out_list, n_bad);
+    PM4G_TRY(check_launch(c, "k_var_verify"));
+    k_var_final<<<g, 256, 0, c->stream>>>(a, list, n_list);
+    PM4G_TRY(check_launch(c, "k_var_final"));
+    uint32_t nb = 0;
+    PM4G_TRY(d2h(c, &nb, n_bad, 4));
+    if (nb == 0) break;
+    if (round > 1000000) {
+      set_error("variants: collision rounds did not converge");
+      return PM4G_ETIMEOUT;
+    }
+    list = out_list;
+    n_list = nb;
+    out_list = (out_list == listA) ? listB : listA;
+  }
+  // rank representatives by (count desc, smallest case asc)
+  uint32_t *flags = S.get<uint32_t>(R), *pos = S.get<uint32_t>(R + 1);
+  if (!flags || !pos) return PM4G_ENOMEM;
+  const unsigned gR = grid_for((int64_t)R, 256, 65535);
+  k_rep_flags<<<gR, 256, 0, c->stream>>>(a, flags);
+  PM4G_TRY(check_launch(c, "k_rep_flags"));
+  PM4G_TRY(scan_u32(c, flags, pos, (int64_t)R));
+  uint32_t V = 0;
+  PM4G_TRY(d2h(c, &V, pos + R, 4));
+  L->V = V;
+  PM4G_TRY(alloc_buf(c, L->rep_slots, V));
+  PM4G_TRY(alloc_buf(c, L->order, V));
+  uint32_t *keys = S.get<uint32_t>(V), *k2 = S.get<uint32_t>(V), *v2 = S.get<uint32_t>(V);
+  uint32_t *rank_of = S.get<uint32_t>(V);
+  if (!keys || !k2 || !v2 || !rank_of) return PM4G_ENOMEM;
+  const int cbits = bits_for((uint64_t)L->C);
+  const uint32_t cmask = cbits >= 32 ? 0xFFFFFFFFu : ((1u << cbits) - 1);
+  {
+    KTime t(c, "variants");
+    k_rep_compact<<<gR, 256, 0, c->stream>>>(a, flags, pos, cmask, L->rep_slots.p, keys, L->order.p);
+    PM4G_TRY(check_launch(c, "k_rep_compact"));
+  }
+  PM4G_TRY(radix_sort_u32(c, keys, L->order.p, k2, v2, V, 0, cbits));
+  {
+    KTime t(c, "variants");
+    k_rank_scatter<<<grid_for(V, 256, 65535), 256, 0, c->stream>>>(L->order.p, V, rank_of);
+    PM4G_TRY(check_launch(c, "k_rank_scatter"));
+    k_case_variant<<<gR, 256, 0, c->stream>>>(a, pos, rank_of, L->cvar.p);
+    PM4G_TRY(check_launch(c, "k_case_variant"));
+  }
+  PM4G_CK(cudaStreamSynchronize(c->stream));
+  L->var_ready = true;
+  return PM4G_OK;
+}
+
+int pm4g_variants(pm4g_log *L, int64_t top_k, uint32_t flags, pm4g_variants_t *out) {
+  if (!L || !out) {
+    set_error("pm4g_variants: NULL argument");
+    return PM4G_EINVAL;
+  }
+  memset(out, 0, sizeof(*out));
+  if (flags & ~PM4G_VARIANTS_CASES) {
+    set_error("pm4g_variants: unknown flags");
+    return PM4G_EINVAL;
+  }
+  Ctx *c = L->ctx;
+  PM4G_CK(cudaSetDevice(c->device));
+  PM4G_TRY(ensure_variants(L));
+  const uint32_t V = L->V;
+  const uint32_t k = top_k < 0 ? V : (uint32_t)std::min<int64_t>(top_k, V);
+  out->n_variants = V;
+  out->n_out = k;
+  Scratch S(c);
+  unsigned long long *oc = S.get<unsigned long long>(k);
+  int32_t *om = S.get<int32_t>(k);
+  uint32_t *ol = S.get<uint32_t>(k), *oo = S.get<uint32_t>(k + 1);
+  if (!oc || !om || !ol || !oo) return PM4G_ENOMEM;
+  VarArgs a{};
+  a.n_slots = L->R;
+  a.len = L->len.p;
+  a.off = L->off.p;
+  a.act_s = L->act_s.p;
+  a.vcount = L->vcount.p;
+  a.rep_of = L->rep_of.p;
+  uint32_t total = 0;
+  if (k > 0) {
+    KTime t(c, "variants");
+    k_var_out_head<<<grid_for(k, 256, 65535), 256, 0, c->stream>>>(a, L->order.p, L->rep_slots.p, k, L->min_case,
+                                                                    L->uniq.p, oc, om, ol);
+    PM4G_TRY(check_launch(c, "k_var_out_head"));
+  }
+  PM4G_TRY(scan_u32(c, ol, oo, k));
+  PM4G_TRY(d2h(c, &total, oo + k, 4));
+  int32_t *oa = S.get<int32_t>(total);
+  if (!oa) return PM4G_ENOMEM;
+  if (k > 0) {
+    KTime t(c, "variants");
+    k_var_out_acts<<<grid_for(k, 256, 65535), 256, 0, c->stream>>>(a, L->order.p, L->rep_slots.p, k, oo, oa);
+    PM4G_TRY(check_launch(c, "k_var_out_acts"));
+  }
+  out->count = (uint64_t *)malloc(std::max<size_t>(k, 1) * 8);
+  out->min_case = (int32_t *)malloc(std::max<size_t>(k, 1) * 4);
+  out->off = (int64_t *)malloc(((size_t)k + 1) * 8);
+  out->acts = (int32_t *)malloc(std::max<size_t>(total, 1) * 4);
+  std::vector<uint32_t> hoff((size_t)k + 1);
+  if (!out->count || !out->min_case || !out->off || !out->acts) {
+    pm4g_variants_free(out);
+    return PM4G_ENOMEM;
+  }
+  cudaStream_t s = c->stream;
+  PM4G_CK(cudaMemcpyAsync(out->count, oc, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(out->min_case, om, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(hoff.data(), oo, ((size_t)k + 1) * 4, cudaMemcpyDeviceToHost, s));
+  PM4G_CK(cudaMemcpyAsync(out->acts, oa, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
+  if (flags & PM4G_VARIANTS_CASES) {
+    const uint64_t R = L->R;
+    uint32_t *pf = S.get<uint32_t>(R), *pp = S.get<uint32_t>(R + 1);
+    int32_t *cid = S.get<int32_t>(L->C), *cv = S.get<int32_t>(L->C);
+    if (!pf || !pp || !cid || !cv) return PM4G_ENOMEM;
+    const unsigned gR = grid_for((int64_t)R, 256, 65535);
+    k_present_flags<<<gR, 256, 0, s>>>(L->len.p, R, pf);
+    PM4G_TRY(check_launch(c, "k_present_flags"));
+    PM4G_TRY(scan_u32(c, pf, pp, (int64_t)R));
+    k_cases_out<<<gR, 256, 0, s>>>(L->len.p, R, pp, L->cvar.p, L->min_case, L->uniq.p, cid, cv);
+    PM4G_TRY(check_launch(c, "k_cases_out"));
+    out->n_cases = L->C;
+    out->case_ids = (int32_t *)malloc(std::max<size_t>(L->C, 1) * 4);
+    out->case_variant = (int32_t *)malloc(std::max<size_t>(L->C, 1) * 4);
+    if (!out->case_ids || !out->case_variant) {
+      pm4g_variants_free(out);
+      return PM4G_ENOMEM;
+    }
+    PM4G_CK(cudaMemcpyAsync(out->case_ids, cid, L->C * 4, cudaMemcpyDeviceToHost, s));
+    PM4G_CK(cudaMemcpyAsync(out->case_variant, cv, L->C * 4, cudaMemcpyDeviceToHost, s));
+  }
+  PM4G_CK(cudaStreamSynchronize(s));
+  for (size_t i = 0; i <= k; ++i) out->off[i] = hoff[i];
+  return PM4G_OK;
+}
+
+int pm4g_variants_free(pm4g_variants_t *r) {
+  if (!r) return PM4G_OK;
+  free(r->count);
+  free(r->min_case);
+  free(r->off);
+  free(r->acts);
+  free(r->case_ids);
+  free(r->case_variant);
+  memset(r, 0, sizeof(*r));
+  return PM4G_OK;
+}
+
+// ---------------------------------------------------------------------------
+// filter
+// ---------------------------------------------------------------------------
+int pm4g_filter(pm4g_log *L, const pm4g_filter_spec *spec, pm4g_log **out) {
+  if (!L || !spec || !out) {
+    set_error("pm4g_filter: NULL argument");
+    return PM4G_EINVAL;
+  }
+  *out = nullptr;
+  if (spec->mode < PM4G_TW_NONE || spec->mode > PM4G_TW_CASES_INTERSECTING || spec->n_attr < 0 ||
+      (spec->n_attr > 0 && !spec->attr_set)) {
+    set_error("pm4g_filter: bad mode or attribute set");
+    return PM4G_EINVAL;
+  }
+  if (spec->n_attr > 0 && !L->has_attr) {
+    set_error("pm4g_filter: the log was loaded without a case attribute");
+    return PM4G_EINVAL;
+  }
+  Ctx *c = L->ctx;
+  PM4G_CK(cudaSetDevice(c->device));
+  pm4g_log *F = new (std::nothrow) pm4g_log();
+  if (!F) return PM4G_ENOMEM;
+  F->ctx = c;
+  c->live_logs++;
+  F->A = L->A;
+  F->min_case = L->min_case;
+  F->R = L->R;
+  F->clb = L->clb;
+  F->act_bits = L->act_bits;
+  F->nb = L->nb;
+  F->has_attr = L->has_attr;
+  int st = PM4G_OK;
+  do {
+    Scratch S(c);
+    const uint64_t R = L->R;
+    if ((st = alloc_buf(c, F->bucket_off, (size_t)L->nb + 1))) break;
+    if (L->has_attr) {
+      if ((st = alloc_buf(c, F->cattr, R))) break;
+      if (R && cudaMemcpyAsync(F->cattr.p, L->cattr.p, R * 4, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+        st = PM4G_ECUDA;
+        break;
+      }
+    }
+    if (L->uniq.p) {
+      if ((st = alloc_buf(c, F->uniq, L->uniq.n))) break;
+      if (cudaMemcpyAsync(F->uniq.p, L->uniq.p, L->uniq.n * 4, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+        st = PM4G_ECUDA;
+        break;
+      }
+    }
+    if (L->n == 0 || L->nb == 0) {
+      F->n = 0;
+      if (cudaMemsetAsync(F->bucket_off.p, 0, 4 * ((size_t)L->nb + 1), c->stream) != cudaSuccess) {
+        st = PM4G_ECUDA;
+        break;
+      }
+      st = run_segment(F, nullptr, false);
+      break;
+    }
+    const int ncl = 1 << L->clb;
+    if (!L->span_ready) {
+      if ((st = alloc_buf(c, L->span, 2 * R))) break;
+      FilterArgs fa{};
+      fa.rec = L->rec.p;
+      fa.bucket_off = L->bucket_off.p;
+      fa.nb = L->nb;
+      fa.clb = L->clb;
+      fa.act_bits = L->act_bits;
+      fa.n_slots = R;
+      fa.first_ts = L->span.p;
+      fa.last_ts = L->span.p + R;
+      KTime t(c, "filter");
+      k_case_span<<<std::min<unsigned>(L->nb, 4u * c->num_sms), 256, (size_t)ncl * 16, c->stream>>>(fa);
+      if ((st = check_launch(c, "k_case_span"))) break;
+      L->span_ready = true;
+    }
+    std::vector<int32_t> aset(spec->attr_set, spec->attr_set + spec->n_attr);
+    std::sort(aset.begin(), aset.end());
+    aset.erase(std::unique(aset.begin(), aset.end()), aset.end());
+    int32_t *dset = S.get<int32_t>(aset.size());
+    uint8_t *ok = S.get<uint8_t>(R);
+    uint32_t *kept = S.get<uint32_t>(L->nb);
+    if (!dset || !ok || !kept) {
+      st = PM4G_ENOMEM;
+      break;
+    }
+    if (!aset.empty() &&
+        cudaMemcpyAsync(dset, aset.data(), aset.size() * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+      st = PM4G_ECUDA;
+      break;
+    }
+    FilterArgs fa{};
+    fa.rec = L->rec.p;
+    fa.bucket_off = L->bucket_off.p;
+    fa.nb = L->nb;
+    fa.clb = L->clb;
+    fa.act_bits = L->act_bits;
+    fa.n_slots = R;
+    fa.first_ts = L->span.p;
+    fa.last_ts = L->span.p + R;
+    fa.cattr = L->cattr.p;
+    fa.attr_set = dset;
+    fa.n_attr = (int32_t)aset.size();
+    fa.t_lo = spec->t_lo;
+    fa.t_hi = spec->t_hi;
+    fa.mode = spec->mode;
+    fa.case_ok = ok;
+    fa.kept = kept;
+    fa.new_off = F->bucket_off.p;
+    const unsigned gb = std::min<unsigned>(L->nb, 8u * c->num_sms);
+    {
+      KTime t(c, "filter");
+      k_case_ok<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(fa);
+      if ((st = check_launch(c, "k_case_ok"))) break;
+      k_filter_count<<<gb, 256, 0, c->stream>>>(fa);
+      if ((st = check_launch(c, "k_filter_count"))) break;
+    }
+    if ((st = scan_u32(c, kept, F->bucket_off.p, L->nb))) break;
+    uint32_t nsub = 0;
+    if ((st = d2h(c, &nsub, F->bucket_off.p + L->nb, 4))) break;
+    F->n = nsub;
+    if ((st = alloc_buf(c, F->rec, nsub))) break;
+    fa.out = F->rec.p;
+    {
+      KTime t(c, "filter");
+      k_filter_write<<<gb, 256, 0, c->stream>>>(fa);
+      if ((st = check_launch(c, "k_filter_write"))) break;
+    }
+    st = run_segment(F, nullptr, false);
+  } while (0);
+  if (st != PM4G_OK) {
+    if (st == PM4G_ENOMEM) set_error("pm4g_filter: out of device memory");
+    release_log(F);
+    return st;
+  }
+  *out = F;
+  return PM4G_OK;
+}
+
+

@@ -1,0 +1,177 @@
+// Device helpers shared by the engine's kernels: the bucketed event record,
+// hashing for variant keys, warp-level reductions and the warp bitonic sort
+// used to order each case's events by (timestamp, row).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pm4g {
+
+typedef unsigned __int128 u128;
+
+constexpr int kWarp = 32;
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// Bucketed event record (16 bytes, one 128-bit store/load):
+//   x = (case_lo << act_bits) | activity   case_lo: case slot within its bucket
+//   y = row                                 0-based row in the loaded columns
+//   z, w = timestamp low / high 32 bits     signed int64
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 make_rec(uint32_t case_lo, uint32_t act, int act_bits, uint32_t row,
+                                          int64_t ts) {
+  uint64_t t = (uint64_t)ts;
+  return make_uint4((case_lo << act_bits) | act, row, (uint32_t)t, (uint32_t)(t >> 32));
+}
+__device__ __forceinline__ uint32_t rec_case_lo(uint4 r, int act_bits) { return r.x >> act_bits; }
+__device__ __forceinline__ uint32_t rec_act(uint4 r, uint32_t act_mask) { return r.x & act_mask; }
+__device__ __forceinline__ int64_t rec_ts(uint4 r) {
+  return (int64_t)(((uint64_t)r.w << 32) | (uint64_t)r.z);
+}
+// Order-preserving map of a signed timestamp to an unsigned key.
+__device__ __forceinline__ uint64_t ts_key(int64_t ts) { return (uint64_t)ts ^ 0x8000000000000000ULL; }
+
+// ---------------------------------------------------------------------------
+// Hashing. fmix64 is the 64-bit finalizer of MurmurHash3 (Austin Appleby,
+// public domain). A case's variant hash is the wrap-around sum over its events
+// of fmix64 applied to (activity, position in case, seed): order-sensitive
+// through the position, and computable by any thread for any event. It only
+// accelerates grouping; equality of sequences is always verified.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdULL;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ULL;
+  k ^= k >> 33;
+  return k;
+}
+__host__ __device__ __forceinline__ uint64_t event_hash(uint32_t act, uint32_t pos, uint64_t seed) {
+  return fmix64((((uint64_t)act << 32) | pos) + seed * 0x9E3779B97F4A7C15ULL + 0x632BE59BD9B4E019ULL);
+}
+// Grouping key of a case from its sequence hash and length; never 0 (0 marks
+// an empty table slot). bits < 64 truncates it (tests force collisions).
+__host__ __device__ __forceinline__ uint64_t variant_key(uint64_t h, uint32_t len, int bits) {
+  uint64_t k = fmix64(h ^ fmix64((uint64_t)len * 0xD6E8FEB86659FD93ULL + 1));
+  if (bits > 0 && bits < 64) k &= ((1ULL << bits) - 1);
+  return k == 0 ? 1 : k;
+}
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Exact sum of 64-bit values over the lanes of `peers` (all lanes of `peers`
+// must call with the same mask). Split into 22-bit limbs so that each
+// redux.sync sum stays below 2^32.
+__device__ __forceinline__ u128 peer_sum_u64(uint32_t peers, uint64_t v) {
+  uint32_t p0 = (uint32_t)(v & 0x3FFFFF), p1 = (uint32_t)((v >> 22) & 0x3FFFFF), p2 = (uint32_t)(v >> 44);
+  uint32_t s0 = __reduce_add_sync(peers, p0);
+  uint32_t s1 = __reduce_add_sync(peers, p1);
+  uint32_t s2 = __reduce_add_sync(peers, p2);
+  return (u128)s0 + ((u128)s1 << 22) + ((u128)s2 << 44);
+}
+
+// ---------------------------------------------------------------------------
+// Warp bitonic sort of up to 32*E (key, row, payload) triples held in
+// registers, blocked layout: lane l holds elements l*E .. l*E+E-1. Sorted
+// ascending by (key, row). Pads must use key = ~0, row = ~0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool kr_less(uint64_t ka, uint32_t ra, uint64_t kb, uint32_t rb) {
+  return ka < kb || (ka == kb && ra < rb);
+}
+
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(uint64_t (&key)[E], uint32_t (&row)[E], uint32_t (&pay)[E]) {
+  constexpr int N = 32 * E;
+  const int lane = (int)lane_id();
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < E) {
+        // partner inside this lane
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int ei = e ^ j;
+          if (ei > e) {
+            const int i = lane * E + e;
+            const bool asc = (i & k) == 0;
+            const bool sw = asc ? kr_less(key[ei], row[ei], key[e], row[e]) : kr_less(key[e], row[e], key[ei], row[ei]);
+            if (sw) {
+              uint64_t tk = key[e]; key[e] = key[ei]; key[ei] = tk;
+              uint32_t tr = row[e]; row[e] = row[ei]; row[ei] = tr;
+              uint32_t tp = pay[e]; pay[e] = pay[ei]; pay[ei] = tp;
+            }
+          }
+        }
+      } else {
+        const int lm = j / E;  // partner lane distance
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lane * E + e;
+          const uint64_t ok = __shfl_xor_sync(kFull, key[e], lm);
+          const uint32_t orow = __shfl_xor_sync(kFull, row[e], lm);
+          const uint32_t opay = __shfl_xor_sync(kFull, pay[e], lm);
+          const bool lower = (lane & lm) == 0;     // this element has the lower index
+          const bool asc = (i & k) == 0;
+          const bool other_less = kr_less(ok, orow, key[e], row[e]);
+          // lower index keeps the min when ascending, the max when descending
+          const bool take = (lower == asc) ? other_less : !other_less;
+          if (take) {
+            key[e] = ok;
+            row[e] = orow;
+            pay[e] = opay;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Block-wide exclusive scan of one value per thread (NT threads); returns the
+// thread's exclusive prefix and writes the block total. s_warp holds 32 words.
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp, uint32_t &total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < NT / 32 ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < NT / 32) s_warp[lane] = t;
+  }
+  __syncthreads();
+  total = s_warp[NT / 32 - 1];
+  const uint32_t before = w > 0 ? s_warp[w - 1] : 0;
+  const uint32_t r = before + x - v;
+  __syncthreads();
+  return r;
+}
+
+}  // namespace pm4g

@@ -1,0 +1,195 @@
+// Formatting kernels (Section 3, first formatting step: ordering by case
+// identifier, timestamp and absolute index).
+//
+// The engine orders the log in two levels. Here, one scatter moves every event
+// into the bucket of its case: a bucket holds 2^clb consecutive case slots
+// (slot = case id - smallest case id) and is small enough for shared memory.
+// The per-bucket ordering by (case, timestamp, row) then happens on chip in the
+// segment pass. Offsets come from per-CTA bucket histograms (a CTA x bucket
+// count matrix, prefixed per bucket over CTAs and scanned over buckets), so
+// the scatter needs no global atomics: each CTA owns a private cursor per bucket
+// in shared memory.
+#include "device_common.cuh"
+#include "engine.h"
+#include "kernels.h"
+
+namespace pm4g {
+
+// ---------------------------------------------------------------------------
+// Stats: per-block min/max of the case column (column reduction, Section 2.1).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_stats(const int32_t *__restrict__ case_id, int64_t n,
+                                               int2 *__restrict__ partial) {
+  int mn = INT_MAX, mx = INT_MIN;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (((uintptr_t)case_id & 15) == 0) {
+    const int4 *v = reinterpret_cast<const int4 *>(case_id);
+    const int64_t nv = n >> 2;
+    for (int64_t i = tid; i < nv; i += stride) {
+      int4 q = __ldcs(v + i);
+      mn = min(mn, min(min(q.x, q.y), min(q.z, q.w)));
+      mx = max(mx, max(max(q.x, q.y), max(q.z, q.w)));
+    }
+    for (int64_t i = (nv << 2) + tid; i < n; i += stride) {
+      mn = min(mn, case_id[i]);
+      mx = max(mx, case_id[i]);
+    }
+  } else {
+    for (int64_t i = tid; i < n; i += stride) {
+      mn = min(mn, case_id[i]);
+      mx = max(mx, case_id[i]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+    mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  }
+  __shared__ int2 s[8];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = make_int2(mn, mx);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mn = min(mn, s[w].x);
+      mx = max(mx, s[w].y);
+    }
+    partial[blockIdx.x] = make_int2(mn, mx);
+  }
+}
+
+// Loads four consecutive int32 starting at i (i % 4 == 0) as one vector when the
+// column is 16-byte aligned, else element by element; q.* beyond n are unset.
+__device__ __forceinline__ int4 load4_i32(const int32_t *__restrict__ p, int64_t i, int64_t n, bool aligned) {
+  if (aligned && i + 3 < n) return __ldcs(reinterpret_cast<const int4 *>(p + i));
+  int4 q = make_int4(0, 0, 0, 0);
+  if (i < n) q.x = p[i];
+  if (i + 1 < n) q.y = p[i + 1];
+  if (i + 2 < n) q.z = p[i + 2];
+  if (i + 3 < n) q.w = p[i + 3];
+  return q;
+}
+
+// ---------------------------------------------------------------------------
+// Bucket histogram of one CTA's row chunk, for buckets [b_lo, b_lo + nbs).
+// mat is CTA-major: mat[p * nb + b].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_bucket_hist(FormatArgs a, uint32_t b_lo, uint32_t nbs) {
+  extern __shared__ uint32_t s_h[];
+  for (uint32_t b = threadIdx.x; b < nbs; b += blockDim.x) s_h[b] = 0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * a.chunk;
+  const int64_t r1 = min(a.n, r0 + a.chunk);
+  const bool al = ((uintptr_t)a.case_id & 15) == 0;
+  for (int64_t i = r0 + (int64_t)threadIdx.x * 4; i < r1; i += (int64_t)blockDim.x * 4) {
+    const int4 q = load4_i32(a.case_id, i, r1, al);
+    const int32_t cc[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (i + k < r1) {
+        const uint32_t slot = (uint32_t)cc[k] - (uint32_t)a.min_case;
+        const uint32_t b = (slot >> a.clb) - b_lo;
+        if (b < nbs) atomicAdd(&s_h[b], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t *row = a.mat + (int64_t)blockIdx.x * a.nb + b_lo;
+  for (uint32_t b = threadIdx.x; b < nbs; b += blockDim.x) row[b] = s_h[b];
+}
+
+// Per bucket: exclusive prefix of the counts over CTAs (in place) and the
+// bucket total.
+__global__ void k_bucket_colprefix(uint32_t *__restrict__ mat, uint32_t nb, int p_ctas,
+                                   uint32_t *__restrict__ total) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  uint32_t acc = 0;
+  for (int p = 0; p < p_ctas; ++p) {
+    uint32_t *q = mat + (int64_t)p * nb + b;
+    const uint32_t v = *q;
+    *q = acc;
+    acc += v;
+  }
+  total[b] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Scatter: every event of buckets [b_lo, b_lo + nbs) goes to its bucket as one
+// 16-byte record. Activity codes outside [0, A) raise the error flag and are
+// stored as 0 so that every later index stays in bounds.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_bucket_scatter(FormatArgs a, uint32_t b_lo, uint32_t nbs) {
+  extern __shared__ uint32_t s_cur[];
+  {
+    const uint32_t *row = a.mat + (int64_t)blockIdx.x * a.nb + b_lo;
+    for (uint32_t b = threadIdx.x; b < nbs; b += blockDim.x) s_cur[b] = a.bucket_off[b_lo + b] + row[b];
+  }
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * a.chunk;
+  const int64_t r1 = min(a.n, r0 + a.chunk);
+  const bool al = ((uintptr_t)a.case_id & 15) == 0 && ((uintptr_t)a.activity & 15) == 0 &&
+                  ((uintptr_t)a.ts & 15) == 0;
+  const uint32_t ncl_mask = (1u << a.clb) - 1;
+  bool bad = false;
+  for (int64_t i = r0 + (int64_t)threadIdx.x * 4; i < r1; i += (int64_t)blockDim.x * 4) {
+    const int4 qc = load4_i32(a.case_id, i, r1, al);
+    const int4 qa = load4_i32(a.activity, i, r1, al);
+    int64_t tt[4];
+    if (al && i + 3 < r1) {
+      const longlong2 t0 = __ldcs(reinterpret_cast<const longlong2 *>(a.ts + i));
+      const longlong2 t1 = __ldcs(reinterpret_cast<const longlong2 *>(a.ts + i + 2));
+      tt[0] = t0.x; tt[1] = t0.y; tt[2] = t1.x; tt[3] = t1.y;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tt[k] = i + k < r1 ? a.ts[i + k] : 0;
+    }
+    const int32_t cc[4] = {qc.x, qc.y, qc.z, qc.w};
+    const int32_t aa[4] = {qa.x, qa.y, qa.z, qa.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (i + k < r1) {
+        const uint32_t slot = (uint32_t)cc[k] - (uint32_t)a.min_case;
+        const uint32_t b = (slot >> a.clb) - b_lo;
+        if (b < nbs) {
+          uint32_t act = (uint32_t)aa[k];
+          if (act >= (uint32_t)a.n_act) {
+            bad = true;
+            act = 0;
+          }
+          const uint32_t pos = atomicAdd(&s_cur[b], 1u);
+          a.rec[pos] = make_rec(slot & ncl_mask, act, a.act_bits, (uint32_t)(i + k), tt[k]);
+        }
+      }
+    }
+  }
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(a.err_flags, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Sparse case ids: dense renumbering by rank among the distinct ids.
+// ---------------------------------------------------------------------------
+__global__ void k_case_keys(const int32_t *__restrict__ case_id, int64_t n, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    keys[i] = (uint32_t)case_id[i] ^ 0x80000000u;
+    vals[i] = (uint32_t)i;
+  }
+}
+
+__global__ void k_case_heads(const uint32_t *__restrict__ keys, int64_t n, uint32_t *__restrict__ head) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_case_dense(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ rows,
+                             const uint32_t *__restrict__ head, const uint32_t *__restrict__ head_excl, int64_t n,
+                             int32_t *__restrict__ dense, int32_t *__restrict__ uniq) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = head_excl[i] + head[i] - 1;
+    dense[rows[i]] = (int32_t)r;
+    if (head[i]) uniq[r] = (int32_t)(keys[i] ^ 0x80000000u);
+  }
+}
+
+}  // namespace pm4g

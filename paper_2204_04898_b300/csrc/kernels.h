@@ -1,0 +1,164 @@
+// Kernel argument blocks and launch declarations shared between the .cu files.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pm4g {
+
+struct FormatArgs {
+  const int32_t *case_id;
+  const int32_t *activity;
+  const int64_t *ts;
+  int64_t n;
+  int64_t chunk;     // rows per CTA (multiple of 4)
+  int32_t min_case;  // slot = case id - min_case
+  int clb;           // log2(case slots per bucket)
+  int act_bits;
+  int32_t n_act;
+  uint32_t nb;       // number of buckets
+  uint32_t *mat;     // CTA-major bucket counts [ctas * nb]
+  const uint32_t *bucket_off;
+  uint4 *rec;
+  uint32_t *err_flags;
+};
+
+__global__ void k_stats(const int32_t *case_id, int64_t n, int2 *partial);
+__global__ void k_bucket_hist(FormatArgs a, uint32_t b_lo, uint32_t nbs);
+__global__ void k_bucket_colprefix(uint32_t *mat, uint32_t nb, int p_ctas, uint32_t *total);
+__global__ void k_bucket_scatter(FormatArgs a, uint32_t b_lo, uint32_t nbs);
+__global__ void k_case_keys(const int32_t *case_id, int64_t n, uint32_t *keys, uint32_t *vals);
+__global__ void k_case_heads(const uint32_t *keys, int64_t n, uint32_t *head);
+__global__ void k_case_dense(const uint32_t *keys, const uint32_t *rows, const uint32_t *head,
+                             const uint32_t *head_excl, int64_t n, int32_t *dense, int32_t *uniq);
+
+// Global DFG table: dense over A*A cells.
+struct DfgTable {
+  unsigned long long *cnt, *lo, *hi, *mn, *mx;
+};
+
+struct SegArgs {
+  const uint4 *rec;
+  const uint32_t *bucket_off;
+  uint32_t nb;
+  int clb;
+  int act_bits;
+  uint32_t n_act;
+  uint64_t n_slots;
+  int cap;        // events a bucket may hold in shared memory
+  int ep_smem;    // 1: start/end counts privatised in shared memory
+  int tbl_mode;   // 0: dense shared table over A*A cells, 1: hashed shared table
+  int tbl_slots;  // shared table slots (power of two in hashed mode)
+  uint32_t *work; // bucket work counter
+  int32_t *act_s;
+  uint32_t *len;
+  uint64_t *hash;
+  uint64_t seed;
+  const int32_t *attr_in;
+  int32_t *cattr;
+  DfgTable g;
+  unsigned long long *g_start, *g_end;
+  uint32_t *ovf;
+  uint32_t *n_ovf;
+  unsigned long long *n_cases;
+  // export mode (formatted log in sorted order)
+  int32_t *ex_case;
+  int64_t *ex_ts;
+  int64_t *ex_row;
+  int32_t min_case;
+  const int32_t *uniq;
+};
+
+struct SegSmem {
+  size_t rec, tlo, chash, idx, ccnt, cstart, ccur, st, en, tkey, tcnt, thi, misc, total;
+};
+
+__host__ __device__ inline size_t seg_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, int tbl_slots, int tbl_mode) {
+  SegSmem L;
+  size_t o = 0;
+  L.rec = o;
+  o += (size_t)cap * 16;
+  L.tlo = o;
+  o += (size_t)tbl_slots * 8;
+  L.chash = o;
+  o += (size_t)ncl * 8;
+  L.idx = o;
+  o += seg_align((size_t)cap * 2, 16);
+  L.ccnt = o;
+  o += (size_t)(ncl + 1) * 4;
+  L.cstart = o;
+  o += (size_t)(ncl + 1) * 4;
+  L.ccur = o;
+  o += (size_t)ncl * 4;
+  L.st = o;
+  o += (size_t)a_s * 4;
+  L.en = o;
+  o += (size_t)a_s * 4;
+  L.tkey = o;
+  o += (size_t)(tbl_mode ? tbl_slots : 0) * 4;
+  L.tcnt = o;
+  o += (size_t)tbl_slots * 4;
+  L.thi = o;
+  o += (size_t)tbl_slots * 4;
+  L.misc = seg_align(o, 16);
+  o = L.misc + 256;
+  L.total = seg_align(o, 16);
+  return L;
+}
+
+constexpr int kSegThreads = 512;
+constexpr int kMaxCaseSmem = 512;  // longest case sorted on chip
+
+// Host launchers (the kernels are templates on the export mode).
+cudaError_t launch_segment(bool exp, const SegArgs &a, unsigned grid, size_t smem, cudaStream_t s);
+cudaError_t launch_fb_compute(bool exp, const SegArgs &a, const uint4 *srec, uint32_t n, uint32_t bucket,
+                              const uint32_t *cstart, unsigned grid, cudaStream_t s);
+
+// Global-memory path for one bucket whose records were sorted by
+// (case slot, timestamp, row) into srec.
+__global__ void k_fb_hist(const uint4 *srec, uint32_t n, int act_bits, uint32_t *ccnt);
+__global__ void k_fb_cases(SegArgs a, const uint4 *srec, uint32_t bucket, const uint32_t *ccnt,
+                           const uint32_t *cstart, int ncl, int write_cases);
+__global__ void k_fb_keys_row(const uint4 *rec, uint32_t n, uint32_t *keys, uint32_t *vals);
+__global__ void k_fb_keys_ts(const uint4 *rec, const uint32_t *perm, uint32_t n, uint64_t *keys);
+__global__ void k_fb_keys_case(const uint4 *rec, const uint32_t *perm, uint32_t n, int act_bits, uint32_t *keys);
+__global__ void k_fb_gather(const uint4 *rec, const uint32_t *perm, uint32_t n, uint4 *out);
+__global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v);
+
+// Filter kernels (one CTA per bucket, records streamed from global memory).
+struct FilterArgs {
+  const uint4 *rec;
+  const uint32_t *bucket_off;
+  uint32_t nb;
+  int clb;
+  int act_bits;
+  uint64_t n_slots;
+  int64_t *first_ts;  // per slot
+  int64_t *last_ts;   // per slot
+  const int32_t *cattr;
+  const int32_t *attr_set;  // sorted, device
+  int32_t n_attr;
+  int64_t t_lo, t_hi;
+  int32_t mode;
+  uint8_t *case_ok;  // per slot
+  uint32_t *kept;    // per bucket
+  const uint32_t *new_off;
+  uint4 *out;
+};
+__global__ void k_case_span(FilterArgs a);
+__global__ void k_case_ok(FilterArgs a);
+__global__ void k_filter_count(FilterArgs a);
+__global__ void k_filter_write(FilterArgs a);
+
+// Summaries (summaries.cu)
+__global__ void k_dfg_flags(const unsigned long long *cnt, int64_t cells, uint32_t *flags);
+__global__ void k_dfg_compact(DfgTable g, int64_t cells, uint32_t n_act, const uint32_t *flags,
+                              const uint32_t *pos, int32_t *src, int32_t *dst, unsigned long long *cnt,
+                              unsigned long long *lo, unsigned long long *hi, unsigned long long *mn,
+                              unsigned long long *mx);
+__global__ void k_freq(const unsigned long long *cnt, const unsigned long long *end, uint32_t n_act,
+                       unsigned long long *freq);
+
+}  // namespace pm4g

@@ -1,0 +1,213 @@
+// Summary kernels: DFG edge compaction, activity frequency, and the variant
+// table (Section 3, variants.py: a double aggregation, events into cases and
+// cases into variants).
+//
+// Variants: cases are grouped by a key made of their sequence hash and length
+// in an open-addressing table; each group's representative is its smallest
+// case slot. Every other member compares its full activity sequence with the
+// representative's. A member that differs leaves the group and is grouped
+// again in the next round with a freshly seeded hash, until no member differs,
+// so the grouping is exact whatever the hash does. Groups are then ranked by
+// (count descending, smallest case id ascending) with a stable radix sort of
+// the representatives listed in ascending case order.
+#include "device_common.cuh"
+#include "engine.h"
+#include "kernels.h"
+#include "variants.h"
+
+namespace pm4g {
+
+__global__ void k_dfg_flags(const unsigned long long *__restrict__ cnt, int64_t cells, uint32_t *__restrict__ flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x)
+    flags[i] = cnt[i] ? 1u : 0u;
+}
+
+__global__ void k_dfg_compact(DfgTable g, int64_t cells, uint32_t n_act, const uint32_t *__restrict__ flags,
+                              const uint32_t *__restrict__ pos, int32_t *src, int32_t *dst, unsigned long long *cnt,
+                              unsigned long long *lo, unsigned long long *hi, unsigned long long *mn,
+                              unsigned long long *mx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!flags[i]) continue;
+    const uint32_t p = pos[i];
+    src[p] = (int32_t)(i / n_act);
+    dst[p] = (int32_t)(i % n_act);
+    cnt[p] = g.cnt[i];
+    lo[p] = g.lo[i];
+    hi[p] = g.hi[i];
+    mn[p] = g.mn[i];
+    mx[p] = g.mx[i];
+  }
+}
+
+// Activity frequency: every event is either followed by another event of its
+// case (one out-edge) or is its case's last event, so freq(a) = sum over b of
+// count(a, b) + end(a).
+__global__ void k_freq(const unsigned long long *__restrict__ cnt, const unsigned long long *__restrict__ end,
+                       uint32_t n_act, unsigned long long *__restrict__ freq) {
+  const uint32_t a = blockIdx.x;
+  unsigned long long s = 0;
+  for (uint32_t b = threadIdx.x; b < n_act; b += blockDim.x) s += cnt[(uint64_t)a * n_act + b];
+  __shared__ unsigned long long s_p[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  if ((threadIdx.x & 31) == 0) s_p[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_p[w];
+    freq[a] = t + end[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Variants
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool var_item(const VarArgs &a, const uint32_t *list, uint32_t n_list, uint64_t i,
+                                         uint32_t &s) {
+  if (list) {
+    if (i >= n_list) return false;
+    s = list[i];
+    return true;
+  }
+  if (i >= a.n_slots) return false;
+  s = (uint32_t)i;
+  return a.len[s] != 0;
+}
+
+__global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t round) {
+  const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t s;
+    if (!var_item(a, list, n_list, i, s)) continue;
+    const uint32_t L = a.len[s];
+    uint64_t h;
+    if (round == 0) {
+      h = a.hash[s];
+    } else {
+      h = 0;
+      const int32_t *q = a.act_s + a.off[s];
+      for (uint32_t k = 0; k < L; ++k) h += event_hash((uint32_t)q[k], k, round);
+    }
+    const unsigned long long key = variant_key(h, L, a.bits);
+    uint32_t g = (uint32_t)fmix64(key ^ round) & a.tmask;
+    for (uint32_t it = 0; it <= a.tmask; ++it) {
+      const unsigned long long k = *(volatile unsigned long long *)&a.tkey[g];
+      if (k == key) break;
+      if (k == 0) {
+        const unsigned long long old = atomicCAS(&a.tkey[g], 0ull, key);
+        if (old == 0 || old == key) break;
+      }
+      g = (g + 1) & a.tmask;
+    }
+    a.grp[s] = g;
+    atomicAdd(&a.tcnt[g], 1u);
+    atomicMin(&a.tmin[g], s);
+  }
+}
+
+__global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out,
+                             uint32_t *n_bad) {
+  const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t s;
+    if (!var_item(a, list, n_list, i, s)) continue;
+    const uint32_t g = a.grp[s];
+    const uint32_t rep = a.tmin[g];
+    bool same = true;
+    if (rep != s) {
+      const uint32_t L = a.len[s];
+      same = a.len[rep] == L;
+      if (same) {
+        const int32_t *x = a.act_s + a.off[s];
+        const int32_t *y = a.act_s + a.off[rep];
+        for (uint32_t k = 0; k < L; ++k)
+          if (x[k] != y[k]) {
+            same = false;
+            break;
+          }
+      }
+    }
+    a.isbad[s] = same ? 0 : 1;
+    if (!same) {
+      atomicSub(&a.tcnt[g], 1u);
+      bad_out[atomicAdd(n_bad, 1u)] = s;
+    }
+  }
+}
+
+__global__ void k_var_final(VarArgs a, const uint32_t *list, uint32_t n_list) {
+  const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t s;
+    if (!var_item(a, list, n_list, i, s)) continue;
+    if (a.isbad[s]) continue;
+    const uint32_t g = a.grp[s];
+    const uint32_t rep = a.tmin[g];
+    a.rep_of[s] = rep;
+    if (rep == s) a.vcount[s] = a.tcnt[g];
+  }
+}
+
+__global__ void k_rep_flags(VarArgs a, uint32_t *flags) {
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_slots; s += (uint64_t)gridDim.x * blockDim.x)
+    flags[s] = (a.len[s] != 0 && a.rep_of[s] == (uint32_t)s) ? 1u : 0u;
+}
+
+__global__ void k_rep_compact(VarArgs a, const uint32_t *flags, const uint32_t *pos, uint32_t cmask,
+                              uint32_t *rep_slots, uint32_t *keys, uint32_t *vals) {
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_slots; s += (uint64_t)gridDim.x * blockDim.x) {
+    if (!flags[s]) continue;
+    const uint32_t v = pos[s];
+    rep_slots[v] = (uint32_t)s;
+    keys[v] = (~a.vcount[s]) & cmask;
+    vals[v] = v;
+  }
+}
+
+__global__ void k_rank_scatter(const uint32_t *order, uint32_t V, uint32_t *rank_of) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < V; k += gridDim.x * blockDim.x) rank_of[order[k]] = k;
+}
+
+__global__ void k_case_variant(VarArgs a, const uint32_t *rep_pos, const uint32_t *rank_of, int32_t *cvar) {
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_slots; s += (uint64_t)gridDim.x * blockDim.x)
+    if (a.len[s]) cvar[s] = (int32_t)rank_of[rep_pos[a.rep_of[s]]];
+}
+
+__global__ void k_present_flags(const uint32_t *len, uint64_t n_slots, uint32_t *flags) {
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_slots; s += (uint64_t)gridDim.x * blockDim.x)
+    flags[s] = len[s] ? 1u : 0u;
+}
+
+__global__ void k_cases_out(const uint32_t *len, uint64_t n_slots, const uint32_t *pos, const int32_t *cvar,
+                            int32_t min_case, const int32_t *uniq, int32_t *case_ids, int32_t *case_variant) {
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_slots; s += (uint64_t)gridDim.x * blockDim.x) {
+    if (!len[s]) continue;
+    const uint32_t p = pos[s];
+    case_ids[p] = uniq ? uniq[s] : (int32_t)((uint32_t)min_case + (uint32_t)s);
+    case_variant[p] = cvar[s];
+  }
+}
+
+__global__ void k_var_out_head(VarArgs a, const uint32_t *order, const uint32_t *rep_slots, uint32_t k_out,
+                               int32_t min_case, const int32_t *uniq, unsigned long long *o_count, int32_t *o_min,
+                               uint32_t *o_len) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k_out; i += gridDim.x * blockDim.x) {
+    const uint32_t rep = rep_slots[order[i]];
+    o_count[i] = a.vcount[rep];
+    o_min[i] = uniq ? uniq[rep] : (int32_t)((uint32_t)min_case + rep);
+    o_len[i] = a.len[rep];
+  }
+}
+
+__global__ void k_var_out_acts(VarArgs a, const uint32_t *order, const uint32_t *rep_slots, uint32_t k_out,
+                               const uint32_t *o_off, int32_t *o_acts) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k_out; i += gridDim.x * blockDim.x) {
+    const uint32_t rep = rep_slots[order[i]];
+    const int32_t *q = a.act_s + a.off[rep];
+    const uint32_t L = a.len[rep];
+    int32_t *o = o_acts + o_off[i];
+    for (uint32_t j = 0; j < L; ++j) o[j] = q[j];
+  }
+}
+
+}  // namespace pm4g

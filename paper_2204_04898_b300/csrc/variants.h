@@ -1,0 +1,43 @@
+// Variant-table kernel arguments and declarations.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pm4g {
+
+struct VarArgs {
+  uint64_t n_slots;
+  const uint32_t *len;     // per case slot, 0 = no case
+  const uint64_t *hash;    // per case slot, sequence hash (seed 0)
+  const uint32_t *off;     // per case slot, first position in the ordered log
+  const int32_t *act_s;    // activity of every event in (case, ts, row) order
+  int bits;                // key truncation (tests only), 0 = full key
+  unsigned long long *tkey;
+  uint32_t *tcnt;
+  uint32_t *tmin;
+  uint32_t tmask;
+  uint32_t *grp;
+  uint32_t *rep_of;
+  uint32_t *vcount;
+  uint8_t *isbad;
+};
+
+__global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t round);
+__global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out, uint32_t *n_bad);
+__global__ void k_var_final(VarArgs a, const uint32_t *list, uint32_t n_list);
+__global__ void k_rep_flags(VarArgs a, uint32_t *flags);
+__global__ void k_rep_compact(VarArgs a, const uint32_t *flags, const uint32_t *pos, uint32_t cmask,
+                              uint32_t *rep_slots, uint32_t *keys, uint32_t *vals);
+__global__ void k_rank_scatter(const uint32_t *order, uint32_t V, uint32_t *rank_of);
+__global__ void k_case_variant(VarArgs a, const uint32_t *rep_pos, const uint32_t *rank_of, int32_t *cvar);
+__global__ void k_present_flags(const uint32_t *len, uint64_t n_slots, uint32_t *flags);
+__global__ void k_cases_out(const uint32_t *len, uint64_t n_slots, const uint32_t *pos, const int32_t *cvar,
+                            int32_t min_case, const int32_t *uniq, int32_t *case_ids, int32_t *case_variant);
+__global__ void k_var_out_head(VarArgs a, const uint32_t *order, const uint32_t *rep_slots, uint32_t k_out,
+                               int32_t min_case, const int32_t *uniq, unsigned long long *o_count, int32_t *o_min,
+                               uint32_t *o_len);
+__global__ void k_var_out_acts(VarArgs a, const uint32_t *order, const uint32_t *rep_slots, uint32_t k_out,
+                               const uint32_t *o_off, int32_t *o_acts);
+
+}  // namespace pm4g

@@ -1,0 +1,284 @@
+"""Python binding of the C ABI in include/pm4g.h (argument marshalling only).
+
+Every function here has the name of the C call it wraps and does nothing but
+turn tensors/arrays into pointers and sizes, call the library, and turn the
+library's host result arrays into numpy arrays. All computation runs in the
+CUDA kernels of libpm4g.so. There is no fallback: if the library is missing,
+importing this module fails.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ERANGE, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
+HOST_PTRS, DEVICE_PTRS = 0x1, 0x2
+VARIANTS_CASES = 0x1
+TW_NONE, TW_EVENTS, TW_CASES_CONTAINED, TW_CASES_INTERSECTING = 0, 1, 2, 3
+OPT_TIMING, OPT_TEST_HASH_BITS, OPT_TEST_BUCKET_CAP = 1, 2, 3
+
+_P = ctypes.c_void_p
+_i32, _i64, _u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+
+
+class _Alloc(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(_P, ctypes.c_size_t, _P, _P)),
+                ("free", ctypes.CFUNCTYPE(None, _P, ctypes.c_size_t, _P, _P)),
+                ("user", _P)]
+
+
+class _Dfg(ctypes.Structure):
+    _fields_ = [("n_edges", _i64), ("src", _P), ("dst", _P), ("count", _P)]
+
+
+class _PerfDfg(ctypes.Structure):
+    _fields_ = [("n_edges", _i64), ("src", _P), ("dst", _P), ("count", _P), ("sum_lo", _P),
+                ("sum_hi", _P), ("min", _P), ("max", _P), ("mean", _P)]
+
+
+class _Variants(ctypes.Structure):
+    _fields_ = [("n_variants", _i64), ("n_out", _i64), ("count", _P), ("min_case", _P), ("off", _P),
+                ("acts", _P), ("n_cases", _i64), ("case_ids", _P), ("case_variant", _P)]
+
+
+class _FilterSpec(ctypes.Structure):
+    _fields_ = [("attr_set", _P), ("n_attr", _i32), ("t_lo", _i64), ("t_hi", _i64), ("mode", _i32)]
+
+
+LIBRARY = _build.LIB
+if not os.path.exists(LIBRARY):
+    raise ImportError(f"{LIBRARY} is missing: build it with `python -m paper_2204_04898_b300.build`")
+lib = ctypes.CDLL(LIBRARY)
+
+lib.pm4g_ctx_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(_Alloc)]
+lib.pm4g_ctx_destroy.argtypes = [_P]
+lib.pm4g_ctx_set_option.argtypes = [_P, ctypes.c_int, _i64]
+lib.pm4g_ctx_timing.argtypes = [_P, ctypes.c_char_p, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]
+lib.pm4g_ctx_timing_reset.argtypes = [_P]
+lib.pm4g_kernel_names.restype = ctypes.c_char_p
+lib.pm4g_kernel_names.argtypes = []
+lib.pm4g_load_log.argtypes = [_P, _P, _P, _P, _P, _i64, _i32, _u32, ctypes.POINTER(_P)]
+lib.pm4g_log_info.argtypes = [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+lib.pm4g_log_free.argtypes = [_P]
+lib.pm4g_log_export.argtypes = [_P, _P, _P, _P, _P]
+lib.pm4g_dfg.argtypes = [_P, ctypes.POINTER(_Dfg)]
+lib.pm4g_dfg_free.argtypes = [ctypes.POINTER(_Dfg)]
+lib.pm4g_perf_dfg.argtypes = [_P, ctypes.POINTER(_PerfDfg)]
+lib.pm4g_perf_dfg_free.argtypes = [ctypes.POINTER(_PerfDfg)]
+lib.pm4g_start_end.argtypes = [_P, _P, _P, _P]
+lib.pm4g_variants.argtypes = [_P, _i64, _u32, ctypes.POINTER(_Variants)]
+lib.pm4g_variants_free.argtypes = [ctypes.POINTER(_Variants)]
+lib.pm4g_filter.argtypes = [_P, ctypes.POINTER(_FilterSpec), ctypes.POINTER(_P)]
+lib.pm4g_last_error.restype = ctypes.c_char_p
+lib.pm4g_last_error.argtypes = []
+
+
+class Pm4gError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib.pm4g_last_error().decode(errors="replace")
+        super().__init__(f"{what}: status {status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, what: str) -> None:
+    if st != OK:
+        raise Pm4gError(st, what)
+
+
+def _np(ptr, n, dtype):
+    if n == 0:
+        return np.empty(0, dtype=dtype)
+    buf = (ctypes.c_char * (n * np.dtype(dtype).itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype=dtype).copy()
+
+
+def pm4g_last_error() -> str:
+    return lib.pm4g_last_error().decode(errors="replace")
+
+
+def pm4g_kernel_names() -> list[str]:
+    return lib.pm4g_kernel_names().decode().split(",")
+
+
+def pm4g_ctx_create(device: int = 0, stream: int | None = None, allocator=None) -> int:
+    """Create a context on `device`. `stream` is a raw cudaStream_t (e.g.
+    torch.cuda.current_stream().cuda_stream) or None for a private stream.
+    `allocator` is an optional (alloc(bytes, stream) -> ptr, free(ptr, bytes,
+    stream)) pair of Python callables."""
+    h = _P()
+    a = None
+    if allocator is not None:
+        fa, ff = allocator
+        a = _Alloc(_Alloc._fields_[0][1](lambda n, s, u: fa(int(n), s) or None),
+                   _Alloc._fields_[1][1](lambda p, n, s, u: ff(p, int(n), s)), None)
+    _check(lib.pm4g_ctx_create(ctypes.byref(h), device, stream, ctypes.byref(a) if a else None),
+           "pm4g_ctx_create")
+    if a is not None:
+        _keepalive[h.value] = a
+    return h.value
+
+
+_keepalive: dict = {}
+
+
+def pm4g_ctx_destroy(ctx: int) -> None:
+    _check(lib.pm4g_ctx_destroy(ctx), "pm4g_ctx_destroy")
+    _keepalive.pop(ctx, None)
+
+
+def pm4g_ctx_set_option(ctx: int, option: int, value: int) -> None:
+    _check(lib.pm4g_ctx_set_option(ctx, option, value), "pm4g_ctx_set_option")
+
+
+def pm4g_ctx_timing(ctx: int, name: str) -> tuple[int, float]:
+    n, ms = _i64(), ctypes.c_double()
+    _check(lib.pm4g_ctx_timing(ctx, name.encode(), ctypes.byref(n), ctypes.byref(ms)), "pm4g_ctx_timing")
+    return n.value, ms.value
+
+
+def pm4g_ctx_timing_reset(ctx: int) -> None:
+    _check(lib.pm4g_ctx_timing_reset(ctx), "pm4g_ctx_timing_reset")
+
+
+def _column(x, dtype, name):
+    """(pointer, n, is_device) of a 1-D contiguous column (torch tensor or numpy)."""
+    if x is None:
+        return None, None, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+            if x.dtype != want or x.dim() != 1 or not x.is_contiguous():
+                raise TypeError(f"{name}: need a contiguous 1-D {want} tensor")
+            return x.data_ptr(), x.numel(), x.is_cuda
+    except ImportError:
+        pass
+    a = np.asarray(x)
+    if a.dtype != np.dtype(dtype) or a.ndim != 1 or not a.flags.c_contiguous:
+        raise TypeError(f"{name}: need a contiguous 1-D {np.dtype(dtype)} array")
+    return a.ctypes.data, a.shape[0], False
+
+
+def pm4g_load_log(ctx: int, case_id, activity, ts_ns, case_attr=None, n_activities: int = 0) -> int:
+    """Ingest and format a log. Columns are all torch CUDA tensors (device
+    pointers) or all host arrays/tensors (copied by the library)."""
+    pc, n, dc = _column(case_id, np.int32, "case_id")
+    pa, na, da = _column(activity, np.int32, "activity")
+    pt, nt, dt = _column(ts_ns, np.int64, "ts_ns")
+    px, nx, dx = _column(case_attr, np.int32, "case_attr")
+    if not (n == na == nt) or (px is not None and nx != n):
+        raise ValueError("columns differ in length")
+    devs = {dc, da, dt} | ({dx} if px is not None else set())
+    if len(devs) != 1:
+        raise ValueError("columns must all live on the device or all on the host")
+    flags = DEVICE_PTRS if dc else HOST_PTRS
+    h = _P()
+    _check(lib.pm4g_load_log(ctx, pc, pa, pt, px, n, n_activities, flags, ctypes.byref(h)), "pm4g_load_log")
+    return h.value
+
+
+def pm4g_log_info(log: int) -> tuple[int, int]:
+    ne, nc = _i64(), _i64()
+    _check(lib.pm4g_log_info(log, ctypes.byref(ne), ctypes.byref(nc)), "pm4g_log_info")
+    return ne.value, nc.value
+
+
+def pm4g_log_free(log: int) -> None:
+    _check(lib.pm4g_log_free(log), "pm4g_log_free")
+
+
+def pm4g_log_export(log: int) -> dict:
+    """The formatted log: every event in (case, timestamp, row) order."""
+    n, _ = pm4g_log_info(log)
+    out = {"case_id": np.empty(n, np.int32), "activity": np.empty(n, np.int32),
+           "ts_ns": np.empty(n, np.int64), "row": np.empty(n, np.int64)}
+    _check(lib.pm4g_log_export(log, *(out[k].ctypes.data for k in ("case_id", "activity", "ts_ns", "row"))),
+           "pm4g_log_export")
+    return out
+
+
+@dataclass
+class PerfDfg:
+    src: np.ndarray
+    dst: np.ndarray
+    count: np.ndarray
+    sum_lo: np.ndarray
+    sum_hi: np.ndarray
+    min: np.ndarray
+    max: np.ndarray
+    mean: np.ndarray
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.src.shape[0])
+
+
+def pm4g_dfg(log: int) -> dict:
+    r = _Dfg()
+    _check(lib.pm4g_dfg(log, ctypes.byref(r)), "pm4g_dfg")
+    try:
+        E = r.n_edges
+        return {"src": _np(r.src, E, np.int32), "dst": _np(r.dst, E, np.int32),
+                "count": _np(r.count, E, np.uint64)}
+    finally:
+        lib.pm4g_dfg_free(ctypes.byref(r))
+
+
+def pm4g_perf_dfg(log: int) -> PerfDfg:
+    r = _PerfDfg()
+    _check(lib.pm4g_perf_dfg(log, ctypes.byref(r)), "pm4g_perf_dfg")
+    try:
+        E = r.n_edges
+        u = np.uint64
+        return PerfDfg(_np(r.src, E, np.int32), _np(r.dst, E, np.int32), _np(r.count, E, u),
+                       _np(r.sum_lo, E, u), _np(r.sum_hi, E, u), _np(r.min, E, u), _np(r.max, E, u),
+                       _np(r.mean, E, np.float64))
+    finally:
+        lib.pm4g_perf_dfg_free(ctypes.byref(r))
+
+
+def pm4g_start_end(log: int, n_activities: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    s, e, f = (np.empty(n_activities, np.uint64) for _ in range(3))
+    _check(lib.pm4g_start_end(log, s.ctypes.data, e.ctypes.data, f.ctypes.data), "pm4g_start_end")
+    return s, e, f
+
+
+@dataclass
+class Variants:
+    n_variants: int
+    count: np.ndarray      # uint64[n_out]
+    min_case: np.ndarray   # int32[n_out]
+    off: np.ndarray        # int64[n_out+1]
+    acts: np.ndarray       # int32
+    case_ids: np.ndarray | None
+    case_variant: np.ndarray | None
+
+
+def pm4g_variants(log: int, top_k: int = -1, cases: bool = False) -> Variants:
+    r = _Variants()
+    _check(lib.pm4g_variants(log, top_k, VARIANTS_CASES if cases else 0, ctypes.byref(r)), "pm4g_variants")
+    try:
+        k = r.n_out
+        off = _np(r.off, k + 1, np.int64)
+        acts = _np(r.acts, int(off[-1]) if k else 0, np.int32)
+        cids = _np(r.case_ids, r.n_cases, np.int32) if cases else None
+        cvar = _np(r.case_variant, r.n_cases, np.int32) if cases else None
+        return Variants(r.n_variants, _np(r.count, k, np.uint64), _np(r.min_case, k, np.int32), off, acts,
+                        cids, cvar)
+    finally:
+        lib.pm4g_variants_free(ctypes.byref(r))
+
+
+def pm4g_filter(log: int, attr_set=None, t_lo: int = -(2**63), t_hi: int = 2**63 - 1,
+                mode: int = TW_NONE) -> int:
+    aset = np.ascontiguousarray(np.asarray(attr_set if attr_set is not None else [], dtype=np.int32))
+    spec = _FilterSpec(aset.ctypes.data if aset.size else None, int(aset.size), int(t_lo), int(t_hi), int(mode))
+    h = _P()
+    _check(lib.pm4g_filter(log, ctypes.byref(spec), ctypes.byref(h)), "pm4g_filter")
+    return h.value

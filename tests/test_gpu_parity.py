@@ -1,0 +1,238 @@
+"""CUDA path against the CPU oracle, bit-exact (tolerance 0): counts, 128-bit
+duration sums, min/max, FP64 means formed from the exact sums, start/end and
+frequency counts, variant ids, counts, sequences and order, the case-to-variant
+map and the formatted (case, timestamp, row) order. All calls go through the C
+ABI (libpm4g.so)."""
+
+import numpy as np
+import pytest
+
+import oracle
+import pm4g_synth as synth
+from tests import oracle_pins as pins
+from tests.gpu_util import check_log, gpu_run, assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm4g():
+    from paper_2204_04898_b300 import pm4g as m
+    return m
+
+
+@pytest.fixture()
+def ctx(pm4g):
+    c = pm4g.pm4g_ctx_create(0)
+    yield c
+    pm4g.pm4g_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("name", ["fine_process_example.json", "signed_ties_example.json"])
+def test_golden(pm4g, ctx, name):
+    g = pins.load_golden(name)
+    lg = g["log"]
+    check_log(pm4g, ctx, np.array(lg["case"], np.int32), np.array(lg["activity"], np.int32),
+              np.array(lg["ts"], np.int64), g["n_activities"])
+
+
+def test_random_tiny_logs(pm4g, ctx):
+    rng = np.random.default_rng(1)
+    for t in range(120):
+        n = int(rng.integers(1, 40))
+        A = int(rng.integers(1, 6))
+        case = rng.choice([-2**31, -7, 0, 5, 9, 2**31 - 1], size=n).astype(np.int32)
+        act = rng.integers(0, A, n).astype(np.int32)
+        if t % 3 == 0:
+            ts = rng.choice(np.array([-2**63, -1, 0, 1, 2**62, 2**63 - 1], np.int64), size=n)
+        else:
+            ts = rng.integers(0, 5, n).astype(np.int64)
+        check_log(pm4g, ctx, case, act, ts, A)
+
+
+def test_empty_log(pm4g, ctx):
+    e = np.empty(0, np.int32)
+    check_log(pm4g, ctx, e, e, np.empty(0, np.int64), 3, device=False)
+
+
+@pytest.mark.parametrize("spec", [synth.single_log(), synth.large_log(40_000), synth.very_large_log(40_000),
+                                  synth.drilldown_log(20_000)], ids=lambda s: s.name)
+def test_workloads(pm4g, ctx, spec):
+    L = synth.generate(spec)
+    check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities, case_attr=L.case_attr)
+
+
+def test_host_pointers(pm4g, ctx):
+    L = synth.generate(synth.large_log(5_000))
+    check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities, device=False)
+
+
+def test_sparse_case_ids(pm4g, ctx):
+    """Case ids spread over the whole int32 range take the renumbering path."""
+    L = synth.generate(synth.single_log(3000))
+    rng = np.random.default_rng(5)
+    ids = np.unique(rng.integers(-2**31, 2**31 - 1, 6000))[:3000]
+    rng.shuffle(ids)
+    case = ids[L.case_id].astype(np.int32)
+    check_log(pm4g, ctx, case, L.activity, L.ts_ns, L.n_activities)
+
+
+def test_special_cases(pm4g, ctx):
+    rng = np.random.default_rng(2)
+    case = rng.integers(0, 300, 5000).astype(np.int32)
+    ts = rng.integers(0, 50, 5000).astype(np.int64)
+    check_log(pm4g, ctx, case, np.zeros(5000, np.int32), ts, 1)           # A = 1
+    case = rng.permutation(4000).astype(np.int32)
+    check_log(pm4g, ctx, case, rng.integers(0, 9, 4000).astype(np.int32), ts[:4000], 9)  # all L = 1
+
+
+def test_long_cases_take_global_path(pm4g, ctx):
+    """Cases longer than the on-chip sort limit (512 events) and buckets larger
+    than shared memory go through the global-memory path."""
+    rng = np.random.default_rng(3)
+    lens = np.array([1, 600, 3, 2000, 513, 7, 40000], np.int64)
+    case = np.repeat(np.arange(lens.size, dtype=np.int32) * 3, lens)
+    n = case.size
+    p = rng.permutation(n)
+    case = case[p]
+    act = rng.integers(0, 7, n).astype(np.int32)
+    ts = rng.integers(0, 10**6, n).astype(np.int64)
+    check_log(pm4g, ctx, case, act, ts, 7)
+
+
+def test_forced_small_buckets(pm4g, ctx):
+    """A tiny on-chip capacity sends most buckets down the global path."""
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TEST_BUCKET_CAP, 64)
+    L = synth.generate(synth.large_log(3000))
+    check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities)
+
+
+@pytest.mark.parametrize("bits", [1, 4, 8])
+def test_forced_hash_collisions(pm4g, ctx, bits):
+    """Truncated variant keys collide constantly; the full-sequence check must
+    still give the exact variant table."""
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TEST_HASH_BITS, bits)
+    L = synth.generate(synth.single_log(3000))
+    check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities)
+
+
+def test_top_k(pm4g, ctx):
+    L = synth.generate(synth.large_log(4000))
+    for k in (0, 1, 10, 10**9):
+        check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities, export=False, top_k=k)
+
+
+def test_errors(pm4g, ctx):
+    c = np.array([1, 1], np.int32)
+    t = np.array([0, 1], np.int64)
+    with pytest.raises(pm4g.Pm4gError) as e:
+        pm4g.pm4g_load_log(ctx, c, np.array([0, 3], np.int32), t, n_activities=3)
+    assert e.value.status == pm4g.ERANGE
+    with pytest.raises(pm4g.Pm4gError) as e:
+        pm4g.pm4g_load_log(ctx, c, np.array([-1, 0], np.int32), t, n_activities=3)
+    assert e.value.status == pm4g.ERANGE
+    with pytest.raises(pm4g.Pm4gError) as e:
+        pm4g.pm4g_load_log(ctx, c, np.array([0, 0], np.int32), t, n_activities=0)
+    assert e.value.status == pm4g.EINVAL
+    with pytest.raises(pm4g.Pm4gError) as e:
+        pm4g.pm4g_ctx_set_option(ctx, 99, 1)
+    assert e.value.status == pm4g.EINVAL
+    # the context still works after errors
+    check_log(pm4g, ctx, c, np.array([0, 1], np.int32), t, 3)
+
+
+def test_allocator_hook_failure_is_enomem(pm4g):
+    import torch
+    calls = {"n": 0}
+    live = {}
+
+    def alloc(nbytes, stream):
+        calls["n"] += 1
+        if calls["n"] >= 6:
+            return 0
+        t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def free(ptr, nbytes, stream):
+        live.pop(ptr, None)
+
+    ctx = pm4g.pm4g_ctx_create(0, allocator=(alloc, free))
+    try:
+        L = synth.generate(synth.single_log(2000))
+        with pytest.raises(pm4g.Pm4gError) as e:
+            pm4g.pm4g_load_log(ctx, *[torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns)],
+                               n_activities=L.n_activities)
+        assert e.value.status == pm4g.ENOMEM
+        torch.cuda.synchronize()
+        assert not live, "a failed load leaked device buffers"
+    finally:
+        pm4g.pm4g_ctx_destroy(ctx)
+
+
+# ---------------- drill-down filters ----------------
+def _filter_parity(pm4g, ctx, L, aset, t_lo, t_hi, mode):
+    rows = oracle.filter_rows(L.case_id, L.activity, L.ts_ns, L.case_attr, L.n_activities, aset, t_lo, t_hi, mode)
+    sub = L.take(rows)
+    R = oracle.summarize(sub.case_id, sub.activity, sub.ts_ns, L.n_activities)
+    return rows, sub, R
+
+
+def test_filters(pm4g, ctx):
+    L = synth.generate(synth.drilldown_log(6000))
+    import torch
+    cols = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns, L.case_attr)]
+    log = pm4g.pm4g_load_log(ctx, *cols[:3], case_attr=cols[3], n_activities=L.n_activities)
+    try:
+        t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+        rng = np.random.default_rng(4)
+        specs = [([], t0, t1, 0), ([], t0, t1, 1), ([], t0, t1, 2), ([], t0, t1, 3)]
+        for _ in range(6):
+            aset = np.unique(rng.integers(0, 4096, int(rng.integers(1, 2000))))
+            lo = t0 + int(rng.uniform(0, 0.5) * (t1 - t0))
+            hi = lo + int(rng.uniform(0.1, 0.5) * (t1 - t0))
+            for mode in range(4):
+                specs.append((aset, lo, hi, mode))
+        for aset, lo, hi, mode in specs:
+            rows, sub, R = _filter_parity(pm4g, ctx, L, aset, lo, hi, mode)
+            f = pm4g.pm4g_filter(log, aset, lo, hi, mode)
+            try:
+                got = {"info": pm4g.pm4g_log_info(f), "dfg": pm4g.pm4g_dfg(f), "perf": pm4g.pm4g_perf_dfg(f),
+                       "var": pm4g.pm4g_variants(f, cases=True)}
+                got["start"], got["end"], got["freq"] = pm4g.pm4g_start_end(f, L.n_activities)
+                e = pm4g.pm4g_log_export(f)
+                # exported rows are original rows; relabel the oracle's sub-log order
+                got["export"] = dict(e, row=np.searchsorted(rows, e["row"]))
+                assert np.array_equal(rows[got["export"]["row"]], e["row"])
+                assert_same(got, R, sub.case_id, sub.activity, sub.ts_ns)
+            finally:
+                pm4g.pm4g_log_free(f)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_filter_chain_and_reuse(pm4g, ctx):
+    """A filtered log is a log: it can be queried repeatedly and filtered again."""
+    L = synth.generate(synth.drilldown_log(3000))
+    import torch
+    cols = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns, L.case_attr)]
+    log = pm4g.pm4g_load_log(ctx, *cols[:3], case_attr=cols[3], n_activities=L.n_activities)
+    t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+    mid = (t0 + t1) // 2
+    f1 = pm4g.pm4g_filter(log, [], t0, mid, pm4g.TW_CASES_INTERSECTING)
+    f2 = pm4g.pm4g_filter(f1, [], mid - (mid - t0) // 2, t1, pm4g.TW_EVENTS)
+    try:
+        r1 = oracle.filter_rows(L.case_id, L.activity, L.ts_ns, None, L.n_activities, [], t0, mid, 3)
+        s1 = L.take(r1)
+        r2 = oracle.filter_rows(s1.case_id, s1.activity, s1.ts_ns, None, L.n_activities, [],
+                                mid - (mid - t0) // 2, t1, 1)
+        s2 = s1.take(r2)
+        R = oracle.summarize(s2.case_id, s2.activity, s2.ts_ns, L.n_activities)
+        for _ in range(2):
+            got = {"info": pm4g.pm4g_log_info(f2), "dfg": pm4g.pm4g_dfg(f2), "perf": pm4g.pm4g_perf_dfg(f2),
+                   "var": pm4g.pm4g_variants(f2, cases=True)}
+            got["start"], got["end"], got["freq"] = pm4g.pm4g_start_end(f2, L.n_activities)
+            assert_same(got, R, export=False)
+    finally:
+        for h in (f2, f1, log):
+            pm4g.pm4g_log_free(h)
