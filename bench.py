@@ -253,6 +253,7 @@ def main():
         if n_l:
             kt[name] = (n_l, t_ms)
     launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
+    sorted_windows = pm4g.pm4g_ctx_timing(ctx, "sorted_windows")[0] // max(1, args.steps)
     pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
     total_kt = sum(v[1] for v in kt.values()) or 1.0
     dom = max(kt, key=lambda k: kt[k][1])
@@ -311,6 +312,7 @@ def main():
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kt.items(), key=lambda x: -x[1][1])},
         "kernel_share": {k: round(v[1] / total_kt, 4) for k, v in kt.items()},
         "gpu_launches": int(launches),
+        "sorted_windows_per_step": int(sorted_windows),
         "clocks": clk.summary(),
         "e2e": e2e,
         "cpu_baseline": cpu,

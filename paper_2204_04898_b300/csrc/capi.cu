@@ -325,16 +325,17 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr) {
   }
   Scratch S(c);
   uint32_t *ctr = S.get<uint32_t>(4);  // work, n_ovf
-  unsigned long long *n_cases = S.get<unsigned long long>(1);
+  unsigned long long *n_cases = S.get<unsigned long long>(2);  // cases, sorted windows
   uint32_t *ovf = S.get<uint32_t>(L->nb);
   if (!ctr || !n_cases || !ovf) {
     set_error("segment pass: out of device memory");
     return PM4G_ENOMEM;
   }
   PM4G_CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), c->stream));
-  PM4G_CK(cudaMemsetAsync(n_cases, 0, sizeof(unsigned long long), c->stream));
+  PM4G_CK(cudaMemsetAsync(n_cases, 0, 2 * sizeof(unsigned long long), c->stream));
   const SegConfig sc = seg_config(c, L->clb, L->A);
   SegArgs a = seg_args(L, sc, ctr, ovf, ctr + 1, n_cases);
+  a.n_sorted = n_cases + 1;
   a.attr_in = attr_in;
   a.cattr = write_cattr ? L->cattr.p : nullptr;
   if (sc.cap >= 32) {
@@ -358,9 +359,11 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr) {
     std::sort(list.begin(), list.end());
     for (uint32_t b : list) PM4G_TRY(fallback_bucket(L, a, b, false));
   }
-  unsigned long long nc = 0;
-  PM4G_TRY(d2h(c, &nc, n_cases, sizeof(nc)));
-  L->C = (int64_t)nc;
+  unsigned long long nc[2] = {0, 0};
+  PM4G_TRY(d2h(c, nc, n_cases, sizeof(nc)));
+  L->C = (int64_t)nc[0];
+  auto &sw = c->totals["sorted_windows"];
+  sw.first += (int64_t)nc[1];
   return PM4G_OK;
 }
 
@@ -369,7 +372,7 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr) {
 static int choose_clb(Ctx *c, int64_t n, uint64_t R, int32_t A, int act_bits) {
   const double avg = (double)n / (double)std::max<uint64_t>(R, 1);
   int best = 0;
-  for (int clb = 10; clb >= 0; --clb) {
+  for (int clb = 8; clb >= 0; --clb) {  // per-warp case counts hold at most 256 slots
     if (clb + act_bits > 32) continue;
     const SegConfig sc = seg_config(c, clb, A);
     if (avg * (double)(1 << clb) <= 0.72 * (double)sc.cap) {

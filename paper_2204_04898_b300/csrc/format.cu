@@ -118,8 +118,20 @@ __global__ void k_bucket_colprefix(uint32_t *__restrict__ mat, uint32_t nb, int 
 // Scatter: every event of buckets [b_lo, b_lo + nbs) goes to its bucket as one
 // 16-byte record. Activity codes outside [0, A) raise the error flag and are
 // stored as 0 so that every later index stays in bounds.
+//
+// The scatter preserves row order inside each bucket: CTAs own consecutive
+// row chunks (their cursors start at the CTA-major prefix of the count
+// matrix), a CTA walks its chunk in sub-steps of blockDim rows with a barrier
+// between sub-steps, and lanes of a warp that hit the same bucket are ranked
+// by lane (match + popc). Order is an optimisation only: every record keeps
+// its row, so the segment pass sorts any case that arrives out of order.
+// The next tile's columns are prefetched into registers while the current
+// tile is scattered.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_bucket_scatter(FormatArgs a, uint32_t b_lo, uint32_t nbs) {
+constexpr int kScatterThreads = 1024;
+constexpr int kScatterSub = 4;  // sub-steps per tile
+
+__global__ void __launch_bounds__(kScatterThreads) k_bucket_scatter(FormatArgs a, uint32_t b_lo, uint32_t nbs) {
   extern __shared__ uint32_t s_cur[];
   {
     const uint32_t *row = a.mat + (int64_t)blockIdx.x * a.nb + b_lo;
@@ -128,42 +140,58 @@ __global__ void __launch_bounds__(1024) k_bucket_scatter(FormatArgs a, uint32_t 
   __syncthreads();
   const int64_t r0 = (int64_t)blockIdx.x * a.chunk;
   const int64_t r1 = min(a.n, r0 + a.chunk);
-  const bool al = ((uintptr_t)a.case_id & 15) == 0 && ((uintptr_t)a.activity & 15) == 0 &&
-                  ((uintptr_t)a.ts & 15) == 0;
   const uint32_t ncl_mask = (1u << a.clb) - 1;
+  const int lane = threadIdx.x & 31;
+  constexpr int64_t kTile = (int64_t)kScatterThreads * kScatterSub;
+  int32_t nc[kScatterSub], na[kScatterSub];
+  int64_t nt[kScatterSub];
+#pragma unroll
+  for (int k = 0; k < kScatterSub; ++k) {
+    const int64_t i = r0 + k * kScatterThreads + threadIdx.x;
+    nc[k] = i < r1 ? __ldcs(a.case_id + i) : 0;
+    na[k] = i < r1 ? __ldcs(a.activity + i) : 0;
+    nt[k] = i < r1 ? __ldcs(a.ts + i) : 0;
+  }
   bool bad = false;
-  for (int64_t i = r0 + (int64_t)threadIdx.x * 4; i < r1; i += (int64_t)blockDim.x * 4) {
-    const int4 qc = load4_i32(a.case_id, i, r1, al);
-    const int4 qa = load4_i32(a.activity, i, r1, al);
-    int64_t tt[4];
-    if (al && i + 3 < r1) {
-      const longlong2 t0 = __ldcs(reinterpret_cast<const longlong2 *>(a.ts + i));
-      const longlong2 t1 = __ldcs(reinterpret_cast<const longlong2 *>(a.ts + i + 2));
-      tt[0] = t0.x; tt[1] = t0.y; tt[2] = t1.x; tt[3] = t1.y;
-    } else {
+  for (int64_t base = r0; base < r1; base += kTile) {
+    int32_t cc[kScatterSub], aa[kScatterSub];
+    int64_t tt[kScatterSub];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) tt[k] = i + k < r1 ? a.ts[i + k] : 0;
+    for (int k = 0; k < kScatterSub; ++k) {
+      cc[k] = nc[k];
+      aa[k] = na[k];
+      tt[k] = nt[k];
     }
-    const int32_t cc[4] = {qc.x, qc.y, qc.z, qc.w};
-    const int32_t aa[4] = {qa.x, qa.y, qa.z, qa.w};
+    if (base + kTile < r1) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (i + k < r1) {
-        const uint32_t slot = (uint32_t)cc[k] - (uint32_t)a.min_case;
-        const uint32_t b = (slot >> a.clb) - b_lo;
-        if (b < nbs) {
-          uint32_t act = (uint32_t)aa[k];
-          if (act >= (uint32_t)a.n_act) {
-            bad = true;
-            act = 0;
-          }
-          const uint32_t pos = atomicAdd(&s_cur[b], 1u);
-          a.rec[pos] = make_rec(slot & ncl_mask, act, a.act_bits, (uint32_t)(i + k), tt[k]);
-        }
+      for (int k = 0; k < kScatterSub; ++k) {
+        const int64_t i = base + kTile + k * kScatterThreads + threadIdx.x;
+        nc[k] = i < r1 ? __ldcs(a.case_id + i) : 0;
+        na[k] = i < r1 ? __ldcs(a.activity + i) : 0;
+        nt[k] = i < r1 ? __ldcs(a.ts + i) : 0;
       }
     }
+#pragma unroll
+    for (int k = 0; k < kScatterSub; ++k) {
+      const int64_t i = base + k * kScatterThreads + threadIdx.x;
+      const uint32_t slot = (uint32_t)cc[k] - (uint32_t)a.min_case;
+      const uint32_t b = (slot >> a.clb) - b_lo;
+      const bool in = i < r1 && b < nbs;
+      uint32_t act = (uint32_t)aa[k];
+      if (in && act >= (uint32_t)a.n_act) {
+        bad = true;
+        act = 0;
+      }
+      const uint32_t peers = __match_any_sync(kFull, in ? b : 0xFFFFFFFFu);
+      const int leader = __ffs(peers) - 1;
+      uint32_t pos = 0;
+      if (in && lane == leader) pos = atomicAdd(&s_cur[b], (uint32_t)__popc(peers));
+      pos = __shfl_sync(kFull, pos, leader) + (uint32_t)__popc(peers & lanemask_lt());
+      if (in) __stcs(a.rec + pos, make_rec(slot & ncl_mask, act, a.act_bits, (uint32_t)i, tt[k]));
+      __syncthreads();
+    }
   }
-  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(a.err_flags, 1u);
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err_flags, 1u);
 }
 
 // ---------------------------------------------------------------------------

@@ -61,6 +61,7 @@ struct SegArgs {
   uint32_t *ovf;
   uint32_t *n_ovf;
   unsigned long long *n_cases;
+  unsigned long long *n_sorted;  // optional: windows/cases that needed sorting
   // export mode (formatted log in sorted order)
   int32_t *ex_case;
   int64_t *ex_ts;
@@ -70,11 +71,18 @@ struct SegArgs {
 };
 
 struct SegSmem {
-  size_t rec, tlo, chash, idx, ccnt, cstart, ccur, st, en, tkey, tcnt, thi, misc, total;
+  size_t rec, tlo, chash, idx, hw, rng, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;
 };
+
+constexpr int kSegThreads = 512;
+constexpr int kSegWarps = kSegThreads / 32;
 
 __host__ __device__ inline size_t seg_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Shared-memory layout of the segment kernel: cap records of 16 bytes, the
+// ordered index (2 bytes per record), per-warp case counts, per-case arrays,
+// endpoint counts and the edge table (key, count, 64-bit sum, high words of the
+// pushed min and max).
 __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, int tbl_slots, int tbl_mode) {
   SegSmem L;
   size_t o = 0;
@@ -86,12 +94,14 @@ __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, in
   o += (size_t)ncl * 8;
   L.idx = o;
   o += seg_align((size_t)cap * 2, 16);
+  L.hw = o;
+  o += seg_align((size_t)kSegWarps * ncl * 2, 16);
+  L.rng = o;
+  o += (size_t)(2 * ncl + 4) * 4;
   L.ccnt = o;
   o += (size_t)(ncl + 1) * 4;
   L.cstart = o;
   o += (size_t)(ncl + 1) * 4;
-  L.ccur = o;
-  o += (size_t)ncl * 4;
   L.st = o;
   o += (size_t)a_s * 4;
   L.en = o;
@@ -100,7 +110,9 @@ __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, in
   o += (size_t)(tbl_mode ? tbl_slots : 0) * 4;
   L.tcnt = o;
   o += (size_t)tbl_slots * 4;
-  L.thi = o;
+  L.tminh = o;
+  o += (size_t)tbl_slots * 4;
+  L.tmaxh = o;
   o += (size_t)tbl_slots * 4;
   L.misc = seg_align(o, 16);
   o = L.misc + 256;
@@ -108,7 +120,6 @@ __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, in
   return L;
 }
 
-constexpr int kSegThreads = 512;
 constexpr int kMaxCaseSmem = 512;  // longest case sorted on chip
 
 // Host launchers (the kernels are templates on the export mode).

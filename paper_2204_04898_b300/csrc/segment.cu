@@ -5,26 +5,32 @@
 // consecutive events of a case).
 //
 // One persistent CTA per SM takes buckets from a work counter. For a bucket it
-//  1. loads the bucket's 16-byte records into shared memory;
-//  2. counting-sorts them by case slot into an index array;
-//  3. orders each case by (timestamp, row) with a warp bitonic sort (skipped
-//     when the case is already in order, e.g. for time-ordered input);
-//  4. walks the ordered positions warp by warp: writes the activity sequence,
-//     counts start/end activities, forms the directly-follows pair
-//     (a_i, a_{i+1}) with duration ts_{i+1} - ts_i, aggregates pairs of a warp
-//     with equal edges (match + redux) into a shared-memory edge table, and
-//     adds each event's term of the case's sequence hash.
-// The shared edge table is dense over A*A cells when that fits, otherwise an
-// open-addressing table keyed by src*A+dst; misses fall back to global
-// atomics. Duration sums are exact: a 64-bit add whose carry-out is added to a
-// high word. Minimum and maximum go straight to global memory, guarded by a
-// plain read (a stale value is never wrong for a monotone min/max, it only
-// costs an extra atomic).
+//  1. loads the bucket's 16-byte records into shared memory (a bucket larger
+//     than the on-chip capacity is processed in case-slot ranges that fit,
+//     streaming the bucket once per range);
+//  2. counting-sorts them by case slot, stably: per-warp counts over
+//     contiguous record ranges, then placement in record order, so each case
+//     keeps the order the scatter wrote, which is row order for most cases;
+//  3. flags every case whose events are not in (timestamp, row) order and
+//     sorts only those, one warp per case (warp bitonic sort);
+//  4. walks the ordered positions 32 at a time per warp: writes the activity
+//     sequence, counts start/end activities, forms the directly-follows pair
+//     (a_i, a_{i+1}) with duration ts_{i+1} - ts_i and aggregates it, and sums
+//     each case's sequence-hash terms with a segmented warp scan.
+// Pair aggregation uses full-warp operations only: twice, the lanes holding
+// the same edge as the first pending lane are reduced together (count, exact
+// sum, min, max) and one lane updates the table; the remaining lanes update it
+// one by one (the hardware serialises equal addresses). The table lives in
+// shared memory (dense over A*A cells when that fits, otherwise open
+// addressing on src*A+dst; misses go to global atomics) and is flushed once
+// per CTA. Sums are exact: 32-bit low and middle words with every carry out of
+// bit 63 added to the global high word. Minimum and maximum are pushed to
+// global memory with fire-and-forget atomics only when they can improve: the
+// table keeps the high 32 bits of the extremes this CTA already pushed, and a
+// value whose high word is beyond them cannot win.
 //
-// Buckets that do not fit (too many events, or a case longer than
-// kMaxCaseSmem) are listed and handled by the global-memory path below, which
-// sorts the bucket with the device radix sort and runs the same per-position
-// code on global memory.
+// Buckets holding a case longer than kMaxCaseSmem go to the global-memory path
+// at the end of this file (device radix sort, then the same per-position code).
 #include "device_common.cuh"
 #include "engine.h"
 #include "kernels.h"
@@ -35,28 +41,33 @@ namespace {
 
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 
-__device__ __forceinline__ void global_edge_group(const DfgTable &g, uint32_t key, uint32_t cnt, uint64_t lo,
-                                                  uint64_t hi) {
-  atomicAdd(&g.cnt[key], (unsigned long long)cnt);
+__device__ __forceinline__ void global_sum(const DfgTable &g, uint32_t key, uint64_t lo, uint64_t hi) {
   const unsigned long long old = atomicAdd(&g.lo[key], (unsigned long long)lo);
   const unsigned long long h2 = hi + (old + lo < old ? 1ull : 0ull);
   if (h2) atomicAdd(&g.hi[key], h2);
 }
 
-__device__ __forceinline__ void global_minmax(const DfgTable &g, uint32_t key, uint64_t d) {
-  unsigned long long *pm = g.mn + key;
-  if (d < *(volatile unsigned long long *)pm) atomicMin(pm, (unsigned long long)d);
-  unsigned long long *px = g.mx + key;
-  if (d > *(volatile unsigned long long *)px) atomicMax(px, (unsigned long long)d);
+__device__ __forceinline__ void global_edge_group(const DfgTable &g, uint32_t key, uint32_t cnt, uint64_t lo,
+                                                  uint64_t hi) {
+  atomicAdd(&g.cnt[key], (unsigned long long)cnt);
+  global_sum(g, key, lo, hi);
+}
+
+// 64-bit wrap-around add into two 32-bit shared words (low, high).
+__device__ __forceinline__ void smem_add64(uint32_t *lo, uint32_t *hi, uint64_t v) {
+  const uint32_t l = (uint32_t)v;
+  const uint32_t old = atomicAdd(lo, l);
+  const uint32_t h = (uint32_t)(v >> 32) + (old + l < old ? 1u : 0u);
+  if (h) atomicAdd(hi, h);
 }
 
 struct SmemSink {
-  uint32_t *tkey, *tcnt, *thi;
-  unsigned long long *tlo;
+  uint32_t *tkey, *tcnt, *tminh, *tmaxh;
+  uint32_t *tl, *tm;  // low and middle 32-bit words of the slot's sum
   uint32_t mask;
   int mode;
   uint32_t *st, *en;
-  unsigned long long *chash;
+  uint32_t *hl, *hh;  // per-case sequence hash, low and high words
   const SegArgs *a;
 
   __device__ __forceinline__ int find(uint32_t key) {
@@ -73,17 +84,38 @@ struct SmemSink {
     }
     return -1;
   }
-  __device__ __forceinline__ void edge_group(uint32_t key, uint32_t cnt, u128 sum) {
-    const unsigned long long lo = (unsigned long long)sum;
-    const uint32_t hi = (uint32_t)(sum >> 64);
+  // The shared sum of a slot is two 32-bit words (low, middle) updated with
+  // native 32-bit atomics; every carry out of bit 63 goes to the global high
+  // word at once.
+  __device__ __forceinline__ void edge_group(uint32_t key, uint32_t cnt, u128 sum, uint64_t mn, uint64_t mx) {
+    const uint64_t lo64 = (uint64_t)sum;
+    uint64_t top = (uint64_t)(sum >> 64);
     const int s = find(key);
     if (s >= 0) {
       atomicAdd(&tcnt[s], cnt);
-      const unsigned long long old = atomicAdd(&tlo[s], lo);
-      const uint32_t h2 = hi + (old + lo < old ? 1u : 0u);
-      if (h2) atomicAdd(&thi[s], h2);
+      const uint32_t l = (uint32_t)lo64;
+      const uint32_t old_l = atomicAdd(&tl[s], l);
+      const uint64_t madd = (lo64 >> 32) + (old_l + l < old_l ? 1u : 0u);
+      if (madd >> 32) {
+        top += 1;
+      } else if (madd) {
+        const uint32_t old_m = atomicAdd(&tm[s], (uint32_t)madd);
+        if (old_m + (uint32_t)madd < old_m) top += 1;
+      }
+      if (top) atomicAdd(&a->g.hi[key], (unsigned long long)top);
+      const uint32_t mnh = (uint32_t)(mn >> 32), mxh = (uint32_t)(mx >> 32);
+      if (mnh <= *(volatile uint32_t *)&tminh[s]) {
+        atomicMin(&tminh[s], mnh);
+        atomicMin(&a->g.mn[key], (unsigned long long)mn);
+      }
+      if (mxh >= *(volatile uint32_t *)&tmaxh[s]) {
+        atomicMax(&tmaxh[s], mxh);
+        atomicMax(&a->g.mx[key], (unsigned long long)mx);
+      }
     } else {
-      global_edge_group(a->g, key, cnt, lo, hi);
+      global_edge_group(a->g, key, cnt, lo64, top);
+      atomicMin(&a->g.mn[key], (unsigned long long)mn);
+      atomicMax(&a->g.mx[key], (unsigned long long)mx);
     }
   }
   __device__ __forceinline__ void start(uint32_t act) {
@@ -94,14 +126,16 @@ struct SmemSink {
     if (en) atomicAdd(&en[act], 1u);
     else atomicAdd(&a->g_end[act], 1ull);
   }
-  __device__ __forceinline__ void hash_add(uint32_t c, uint64_t v) { atomicAdd(&chash[c], (unsigned long long)v); }
+  __device__ __forceinline__ void hash_add(uint32_t c, uint64_t v) { smem_add64(&hl[c], &hh[c], v); }
 };
 
 struct GlobalSink {
   const SegArgs *a;
   uint64_t slot_base;
-  __device__ __forceinline__ void edge_group(uint32_t key, uint32_t cnt, u128 sum) {
+  __device__ __forceinline__ void edge_group(uint32_t key, uint32_t cnt, u128 sum, uint64_t mn, uint64_t mx) {
     global_edge_group(a->g, key, cnt, (uint64_t)sum, (uint64_t)(sum >> 64));
+    atomicMin(&a->g.mn[key], (unsigned long long)mn);
+    atomicMax(&a->g.mx[key], (unsigned long long)mx);
   }
   __device__ __forceinline__ void start(uint32_t act) { atomicAdd(&a->g_start[act], 1ull); }
   __device__ __forceinline__ void end(uint32_t act) { atomicAdd(&a->g_end[act], 1ull); }
@@ -110,23 +144,57 @@ struct GlobalSink {
   }
 };
 
+// Aggregates the warp's directly-follows pairs with full-warp operations.
+// Twice: the pending lanes whose edge equals the first pending lane's edge are
+// reduced together (count, exact 128-bit sum, min, max; non-members add
+// neutral values) and that first lane updates the sink once. Every lane still
+// pending then updates the sink on its own.
+template <class Sink>
+__device__ __forceinline__ void aggregate_edges(Sink &sink, bool has_edge, uint32_t key, uint64_t d) {
+  const int lane = (int)lane_id();
+  uint32_t rem = __ballot_sync(kFull, has_edge);
+  const uint32_t hi = (uint32_t)(d >> 32), lo = (uint32_t)d;
+#pragma unroll
+  for (int round = 0; round < 2; ++round) {
+    if (rem == 0) return;
+    const int src = __ffs(rem) - 1;
+    const uint32_t cand = __shfl_sync(kFull, key, src);
+    const bool mem = ((rem >> lane) & 1u) && key == cand;
+    const uint32_t grp = __ballot_sync(kFull, mem);
+    const uint32_t s0 = __reduce_add_sync(kFull, mem ? (uint32_t)(d & 0x3FFFFF) : 0u);
+    const uint32_t s1 = __reduce_add_sync(kFull, mem ? (uint32_t)((d >> 22) & 0x3FFFFF) : 0u);
+    const uint32_t s2 = __reduce_add_sync(kFull, mem ? (uint32_t)(d >> 44) : 0u);
+    const uint32_t mnh = __reduce_min_sync(kFull, mem ? hi : 0xFFFFFFFFu);
+    const uint32_t mnl = __reduce_min_sync(kFull, (mem && hi == mnh) ? lo : 0xFFFFFFFFu);
+    const uint32_t mxh = __reduce_max_sync(kFull, mem ? hi : 0u);
+    const uint32_t mxl = __reduce_max_sync(kFull, (mem && hi == mxh) ? lo : 0u);
+    if (lane == src) {
+      const u128 sum = (u128)s0 + ((u128)s1 << 22) + ((u128)s2 << 44);
+      sink.edge_group(cand, (uint32_t)__popc(grp), sum, ((uint64_t)mnh << 32) | mnl, ((uint64_t)mxh << 32) | mxl);
+    }
+    rem &= ~grp;
+  }
+  if ((rem >> lane) & 1u) sink.edge_group(key, 1u, (u128)d, d, d);
+}
+
 // One warp handles 32 consecutive ordered positions p = base + lane of a
 // bucket. fetch(p) returns the record at ordered position p; cstart[c] is the
-// first ordered position of case slot c (cstart[ncl] = n).
+// first ordered position of case slot c (cstart[ncl] = n). Outputs go to
+// ordered position out_base + p.
 template <bool kExport, class Sink, class Fetch>
 __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, const Fetch &fetch,
                                                   const uint32_t *cstart, int p, int n, int64_t out_base,
                                                   uint64_t slot_base, uint32_t act_mask) {
   const int lane = (int)lane_id();
   const bool valid = p < n;
-  uint32_t c = 0xFFFFFFFFu, act = 0, row = 0, cs = 0, ce = 0;
+  uint32_t c = 0xFFFFFFFFu, act = 0, cs = 0, ce = 0;
   int64_t ts = 0;
+  uint4 r = make_uint4(0, 0, 0, 0);
   if (valid) {
-    const uint4 r = fetch(p);
+    r = fetch(p);
     c = r.x >> a.act_bits;
     act = r.x & act_mask;
     ts = rec_ts(r);
-    row = r.y;
     cs = cstart[c];
     ce = cstart[c + 1];
   }
@@ -136,7 +204,7 @@ __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, 
       a.act_s[out_base + p] = (int32_t)act;
       a.ex_case[out_base + p] = a.uniq ? a.uniq[slot] : (int32_t)((uint32_t)a.min_case + (uint32_t)slot);
       a.ex_ts[out_base + p] = ts;
-      a.ex_row[out_base + p] = (int64_t)row;
+      a.ex_row[out_base + p] = (int64_t)r.y;
     }
     return;
   }
@@ -145,22 +213,20 @@ __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, 
   if (valid) a.act_s[out_base + p] = (int32_t)act;
   if (first) sink.start(act);
   if (last) sink.end(act);
+  // the next event of the case: the next lane's, or one fetch for lane 31
+  uint32_t nx = __shfl_down_sync(kFull, r.x, 1);
+  uint32_t nz = __shfl_down_sync(kFull, r.z, 1);
+  uint32_t nw = __shfl_down_sync(kFull, r.w, 1);
   const bool has_edge = valid && !last;
-  uint32_t key = 0;
-  uint64_t delta = 0;
-  if (has_edge) {
+  if (lane == 31 && has_edge) {
     const uint4 r2 = fetch(p + 1);
-    key = act * a.n_act + (r2.x & act_mask);
-    delta = (uint64_t)rec_ts(r2) - (uint64_t)ts;
+    nx = r2.x;
+    nz = r2.z;
+    nw = r2.w;
   }
-  const uint32_t emask = __ballot_sync(kFull, has_edge);
-  if (has_edge) {
-    const uint32_t peers = __match_any_sync(emask, key);
-    const u128 sum = peer_sum_u64(peers, delta);
-    if (lane == __ffs(peers) - 1) sink.edge_group(key, (uint32_t)__popc(peers), sum);
-    global_minmax(a.g, key, delta);
-  }
-  // variant hash: segmented inclusive sum over lanes holding the same case
+  const int64_t nts = (int64_t)(((uint64_t)nw << 32) | nz);
+  aggregate_edges(sink, has_edge, act * a.n_act + (nx & act_mask), (uint64_t)nts - (uint64_t)ts);
+  // sequence hash: segmented inclusive sum over lanes holding the same case
   uint64_t v = valid ? event_hash(act, (uint32_t)p - cs, a.seed) : 0ull;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -202,6 +268,126 @@ __device__ __forceinline__ void sort_case(const uint4 *rec_s, uint16_t *idx_s, u
   __syncwarp();
 }
 
+struct SegShared {
+  uint4 *rec;
+  uint16_t *idx;
+  uint32_t *ccnt, *cstart;
+  uint32_t *hl, *hh;
+};
+
+// Processes the n_r records now in S.rec, all of bucket b with case slots in
+// [c_a, c_b); their ordered positions start at out_base in the bucketed log.
+// Returns false (having written nothing) if a case is too long to sort on chip.
+template <bool kExport>
+__device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared &S, uint16_t *hw, uint32_t *misc,
+                              uint32_t b, uint32_t n_r, uint32_t c_a, uint32_t c_b, int64_t out_base,
+                              uint32_t act_mask, uint32_t &n_sorted) {
+  const int ncl = 1 << a.clb;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = tid; j < kSegWarps * ncl; j += kSegThreads) hw[j] = 0;
+  for (int c = tid; c < ncl; c += kSegThreads) {
+    S.hl[c] = 0;
+    S.hh[c] = 0;
+  }
+  __syncthreads();
+  // stable counting sort by case slot
+  const uint32_t per = ((n_r + kSegWarps - 1) / kSegWarps + 31) & ~31u;
+  const uint32_t w_lo = min(n_r, (uint32_t)warp * per), w_hi = min(n_r, w_lo + per);
+  uint16_t *myh = hw + warp * ncl;
+  for (uint32_t j = w_lo; j < w_hi; j += 32) {
+    const uint32_t i = j + lane;
+    const bool v = i < w_hi;
+    const uint32_t c = v ? (S.rec[i].x >> a.act_bits) : 0xFFFFu;
+    const uint32_t peers = __match_any_sync(kFull, c);
+    if (v && lane == __ffs(peers) - 1) myh[c] = (uint16_t)(myh[c] + __popc(peers));
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    uint32_t tot = 0;
+    if (tid < ncl)
+      for (int w = 0; w < kSegWarps; ++w) tot += hw[w * ncl + tid];
+    uint32_t all;
+    const uint32_t pre = block_exclusive_scan<kSegThreads>(tot, misc + 8, all);
+    if (tid < ncl) {
+      S.ccnt[tid] = tot;
+      S.cstart[tid] = pre;
+      uint32_t run = pre;
+      for (int w = 0; w < kSegWarps; ++w) {
+        const uint32_t t = hw[w * ncl + tid];
+        hw[w * ncl + tid] = (uint16_t)run;
+        run += t;
+      }
+    }
+    if (tid == 0) S.cstart[ncl] = n_r;
+    if (__syncthreads_or(tot > (uint32_t)kMaxCaseSmem)) return false;
+  }
+  for (uint32_t j = w_lo; j < w_hi; j += 32) {
+    const uint32_t i = j + lane;
+    const bool v = i < w_hi;
+    const uint32_t c = v ? (S.rec[i].x >> a.act_bits) : 0xFFFFu;
+    const uint32_t peers = __match_any_sync(kFull, c);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (v && lane == leader) {
+      base = myh[c];
+      myh[c] = (uint16_t)(base + __popc(peers));
+    }
+    base = __shfl_sync(kFull, base, leader);
+    if (v) S.idx[base + __popc(peers & lanemask_lt())] = (uint16_t)i;
+    __syncwarp();
+  }
+  __syncthreads();
+  // flag the cases whose events are out of (timestamp, row) order; hw is free
+  uint16_t *unsorted = hw;
+  for (int c = tid; c < ncl; c += kSegThreads) unsorted[c] = 0;
+  __syncthreads();
+  for (uint32_t p = tid + 1; p < n_r; p += kSegThreads) {
+    const uint4 x = S.rec[S.idx[p - 1]], y = S.rec[S.idx[p]];
+    const uint32_t cx = x.x >> a.act_bits, cy = y.x >> a.act_bits;
+    if (cx == cy && !kr_less(ts_key(rec_ts(x)), x.y, ts_key(rec_ts(y)), y.y)) unsorted[cy] = 1;
+  }
+  __syncthreads();
+  for (uint32_t c = c_a + warp; c < c_b; c += kSegWarps) {
+    if (!unsorted[c]) continue;
+    const uint32_t s0 = S.cstart[c], L = S.ccnt[c];
+    if (L <= 32) sort_case<1>(S.rec, S.idx, s0, L);
+    else if (L <= 64) sort_case<2>(S.rec, S.idx, s0, L);
+    else if (L <= 128) sort_case<4>(S.rec, S.idx, s0, L);
+    else if (L <= 256) sort_case<8>(S.rec, S.idx, s0, L);
+    else sort_case<16>(S.rec, S.idx, s0, L);
+    ++n_sorted;
+  }
+  __syncthreads();
+  // every ordered position, 32 per warp at a time
+  const uint64_t slot_base = (uint64_t)b << a.clb;
+  {
+    auto fetch = [&](int p) { return S.rec[S.idx[p]]; };
+    for (uint32_t base = (uint32_t)warp * 32; base < n_r; base += kSegThreads)
+      process_warp_tile<kExport>(a, sink, fetch, S.cstart, (int)(base + lane), (int)n_r, out_base, slot_base,
+                                 act_mask);
+  }
+  __syncthreads();
+  // per-case outputs
+  if (!kExport) {
+    uint32_t present = 0;
+    for (uint32_t c = c_a + tid; c < c_b; c += kSegThreads) {
+      const uint64_t slot = slot_base + c;
+      if (slot < a.n_slots) {
+        const uint32_t Lc = S.ccnt[c];
+        a.len[slot] = Lc;
+        a.hash[slot] = Lc ? (((uint64_t)S.hh[c] << 32) | S.hl[c]) : 0ull;
+        if (a.cattr) a.cattr[slot] = (Lc && a.attr_in) ? a.attr_in[S.rec[S.idx[S.cstart[c]]].y] : 0;
+        present += Lc ? 1u : 0u;
+      }
+    }
+    present = __reduce_add_sync(kFull, present);
+    if (lane == 0 && present) atomicAdd(a.n_cases, (unsigned long long)present);
+  }
+  __syncthreads();
+  return true;
+}
+
 }  // namespace
 
 template <bool kExport>
@@ -210,28 +396,34 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   const int ncl = 1 << a.clb;
   const int a_s = a.ep_smem ? (int)a.n_act : 0;
   const SegSmem L = seg_smem_layout(a.cap, ncl, a_s, a.tbl_slots, a.tbl_mode);
-  uint4 *rec_s = reinterpret_cast<uint4 *>(smem + L.rec);
-  unsigned long long *tlo = reinterpret_cast<unsigned long long *>(smem + L.tlo);
-  unsigned long long *chash = reinterpret_cast<unsigned long long *>(smem + L.chash);
-  uint16_t *idx_s = reinterpret_cast<uint16_t *>(smem + L.idx);
-  uint32_t *ccnt = reinterpret_cast<uint32_t *>(smem + L.ccnt);
-  uint32_t *cstart = reinterpret_cast<uint32_t *>(smem + L.cstart);
-  uint32_t *ccur = reinterpret_cast<uint32_t *>(smem + L.ccur);
+  SegShared S;
+  S.rec = reinterpret_cast<uint4 *>(smem + L.rec);
+  S.idx = reinterpret_cast<uint16_t *>(smem + L.idx);
+  S.ccnt = reinterpret_cast<uint32_t *>(smem + L.ccnt);
+  S.cstart = reinterpret_cast<uint32_t *>(smem + L.cstart);
+  S.hl = reinterpret_cast<uint32_t *>(smem + L.chash);
+  S.hh = S.hl + ncl;
+  uint32_t *tl = reinterpret_cast<uint32_t *>(smem + L.tlo);
+  uint32_t *tm = tl + a.tbl_slots;
+  uint16_t *hw = reinterpret_cast<uint16_t *>(smem + L.hw);
+  uint32_t *rng = reinterpret_cast<uint32_t *>(smem + L.rng);
   uint32_t *st = reinterpret_cast<uint32_t *>(smem + L.st);
   uint32_t *en = reinterpret_cast<uint32_t *>(smem + L.en);
   uint32_t *tkey = reinterpret_cast<uint32_t *>(smem + L.tkey);
   uint32_t *tcnt = reinterpret_cast<uint32_t *>(smem + L.tcnt);
-  uint32_t *thi = reinterpret_cast<uint32_t *>(smem + L.thi);
+  uint32_t *tminh = reinterpret_cast<uint32_t *>(smem + L.tminh);
+  uint32_t *tmaxh = reinterpret_cast<uint32_t *>(smem + L.tmaxh);
   uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kWarps = kSegThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t act_mask = (1u << a.act_bits) - 1;
 
   if (!kExport) {
     for (int i = tid; i < a.tbl_slots; i += kSegThreads) {
       tcnt[i] = 0;
-      thi[i] = 0;
-      tlo[i] = 0;
+      tl[i] = 0;
+      tm[i] = 0;
+      tminh[i] = 0xFFFFFFFFu;
+      tmaxh[i] = 0;
       if (a.tbl_mode) tkey[i] = kEmptyKey;
     }
     for (int i = tid; i < a_s; i += kSegThreads) {
@@ -239,8 +431,9 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
       en[i] = 0;
     }
   }
-  SmemSink sink{tkey, tcnt, thi, tlo, (uint32_t)(a.tbl_slots - 1), a.tbl_mode, a_s ? st : nullptr,
-                a_s ? en : nullptr, chash, &a};
+  SmemSink sink{tkey, tcnt, tminh, tmaxh, tl, tm, (uint32_t)(a.tbl_slots - 1), a.tbl_mode,
+                a_s ? st : nullptr, a_s ? en : nullptr, S.hl, S.hh, &a};
+  uint32_t n_sorted = 0;
   __syncthreads();
 
   for (;;) {
@@ -250,87 +443,80 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
     if (b >= a.nb) break;
     const uint32_t lo = a.bucket_off[b];
     const uint32_t n = a.bucket_off[b + 1] - lo;
-    if (n > (uint32_t)a.cap) {
-      if (tid == 0) a.ovf[atomicAdd(a.n_ovf, 1u)] = b;
-      __syncthreads();
-      continue;
-    }
     const uint4 *src = a.rec + lo;
-    for (uint32_t i = tid; i < n; i += kSegThreads) rec_s[i] = __ldcs(src + i);
-    for (int c = tid; c < ncl; c += kSegThreads) {
-      ccnt[c] = 0;
-      chash[c] = 0;
-    }
-    __syncthreads();
-    for (uint32_t i = tid; i < n; i += kSegThreads) atomicAdd(&ccnt[rec_s[i].x >> a.act_bits], 1u);
-    __syncthreads();
-    {
-      const int c0 = 2 * tid;
-      const uint32_t v0 = c0 < ncl ? ccnt[c0] : 0u, v1 = c0 + 1 < ncl ? ccnt[c0 + 1] : 0u;
-      uint32_t tot;
-      const uint32_t pre = block_exclusive_scan<kSegThreads>(v0 + v1, misc + 8, tot);
-      if (c0 < ncl) cstart[c0] = ccur[c0] = pre;
-      if (c0 + 1 < ncl) cstart[c0 + 1] = ccur[c0 + 1] = pre + v0;
-      if (tid == 0) cstart[ncl] = n;
-      const int too_long = __syncthreads_or(max(v0, v1) > (uint32_t)kMaxCaseSmem);
-      if (too_long) {
-        if (tid == 0) a.ovf[atomicAdd(a.n_ovf, 1u)] = b;
-        __syncthreads();
-        continue;
+    bool ok = true;
+    if (n <= (uint32_t)a.cap) {
+      for (uint32_t i0 = tid; i0 < n; i0 += 4 * kSegThreads) {
+        uint4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i0 + k * kSegThreads < n) v[k] = __ldcs(src + i0 + k * kSegThreads);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i0 + k * kSegThreads < n) S.rec[i0 + k * kSegThreads] = v[k];
       }
-    }
-    for (uint32_t i = tid; i < n; i += kSegThreads) {
-      const uint32_t p = atomicAdd(&ccur[rec_s[i].x >> a.act_bits], 1u);
-      idx_s[p] = (uint16_t)i;
-    }
-    __syncthreads();
-    // order each case by (timestamp, row)
-    for (int c = warp; c < ncl; c += kWarps) {
-      const uint32_t Lc = ccnt[c];
-      if (Lc < 2) continue;
-      const uint32_t s0 = cstart[c];
-      bool ok = true;
-      for (uint32_t j = lane; j + 1 < Lc; j += 32) {
-        const uint4 x = rec_s[idx_s[s0 + j]], y = rec_s[idx_s[s0 + j + 1]];
-        if (!kr_less(ts_key(rec_ts(x)), x.y, ts_key(rec_ts(y)), y.y)) ok = false;
-      }
-      if (__all_sync(kFull, ok)) continue;
-      if (Lc <= 32) sort_case<1>(rec_s, idx_s, s0, Lc);
-      else if (Lc <= 64) sort_case<2>(rec_s, idx_s, s0, Lc);
-      else if (Lc <= 128) sort_case<4>(rec_s, idx_s, s0, Lc);
-      else if (Lc <= 256) sort_case<8>(rec_s, idx_s, s0, Lc);
-      else sort_case<16>(rec_s, idx_s, s0, Lc);
-    }
-    __syncthreads();
-    {
-      const uint64_t slot_base = (uint64_t)b << a.clb;
-      auto fetch = [&](int p) { return rec_s[idx_s[p]]; };
-      for (int base = warp * 32; base < (int)n; base += kSegThreads)
-        process_warp_tile<kExport>(a, sink, fetch, cstart, base + lane, (int)n, (int64_t)lo, slot_base, act_mask);
-    }
-    __syncthreads();
-    if (!kExport) {
-      const uint64_t slot0 = (uint64_t)b << a.clb;
-      uint32_t present = 0;
-      for (int c = tid; c < ncl; c += kSegThreads) {
-        const uint64_t slot = slot0 + (uint64_t)c;
-        if (slot < a.n_slots) {
-          const uint32_t Lc = ccnt[c];
-          a.len[slot] = Lc;
-          a.hash[slot] = chash[c];
-          if (a.cattr) a.cattr[slot] = (Lc && a.attr_in) ? a.attr_in[rec_s[idx_s[cstart[c]]].y] : 0;
-          present += Lc ? 1u : 0u;
+      ok = process_range<kExport>(a, sink, S, hw, misc, b, n, 0, (uint32_t)ncl, (int64_t)lo, act_mask, n_sorted);
+    } else {
+      // too large for one pass: split the case slots into ranges that fit
+      for (int c = tid; c < ncl; c += kSegThreads) S.ccnt[c] = 0;
+      __syncthreads();
+      for (uint32_t i = tid; i < n; i += kSegThreads) atomicAdd(&S.ccnt[__ldcg(src + i).x >> a.act_bits], 1u);
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t nr = 0, acc = 0, pos = 0;
+        bool fits = true;
+        rng[0] = 0;
+        rng[ncl + 2] = 0;
+        for (int c = 0; c < ncl; ++c) {
+          const uint32_t v = S.ccnt[c];
+          if (v > (uint32_t)a.cap || v > (uint32_t)kMaxCaseSmem) fits = false;
+          if (acc + v > (uint32_t)a.cap) {
+            rng[++nr] = (uint32_t)c;  // range nr-1 is [rng[nr-1], c)
+            rng[ncl + 2 + nr] = pos;  // its first ordered position
+            acc = 0;
+          }
+          acc += v;
+          pos += v;
         }
+        rng[++nr] = (uint32_t)ncl;
+        misc[2] = fits ? nr : 0u;
       }
-      present = __reduce_add_sync(kFull, present);
-      if (lane == 0 && present) atomicAdd(a.n_cases, (unsigned long long)present);
+      __syncthreads();
+      const uint32_t nr = misc[2];
+      ok = nr > 0;
+      for (uint32_t r = 0; r < nr && ok; ++r) {
+        const uint32_t c_a = rng[r], c_b = rng[r + 1];
+        const uint32_t pos_a = rng[ncl + 2 + r];
+        uint32_t cnt = 0;
+        for (uint32_t t0 = 0; t0 < n; t0 += kSegThreads) {
+          const uint32_t i = t0 + tid;
+          uint4 rv = make_uint4(0, 0, 0, 0);
+          bool keep = false;
+          if (i < n) {
+            rv = __ldcg(src + i);
+            const uint32_t c = rv.x >> a.act_bits;
+            keep = c >= c_a && c < c_b;
+          }
+          uint32_t tot;
+          const uint32_t pre = block_exclusive_scan<kSegThreads>(keep ? 1u : 0u, misc + 8, tot);
+          if (keep) S.rec[cnt + pre] = rv;
+          cnt += tot;
+        }
+        __syncthreads();
+        ok = process_range<kExport>(a, sink, S, hw, misc, b, cnt, c_a, c_b, (int64_t)lo + pos_a, act_mask,
+                                    n_sorted);
+      }
+    }
+    if (!ok) {
+      if (tid == 0) a.ovf[atomicAdd(a.n_ovf, 1u)] = b;
     }
     __syncthreads();
   }
+  if (a.n_sorted && lane == 0 && n_sorted) atomicAdd(a.n_sorted, (unsigned long long)n_sorted);
   if (!kExport) {
     for (int s = tid; s < a.tbl_slots; s += kSegThreads) {
       const uint32_t cnt = tcnt[s];
-      if (cnt) global_edge_group(a.g, a.tbl_mode ? tkey[s] : (uint32_t)s, cnt, tlo[s], thi[s]);
+      if (cnt) global_edge_group(a.g, a.tbl_mode ? tkey[s] : (uint32_t)s, cnt, tl[s] | ((uint64_t)tm[s] << 32), 0);
     }
     for (int i = tid; i < a_s; i += kSegThreads) {
       if (st[i]) atomicAdd(&a.g_start[i], (unsigned long long)st[i]);
