@@ -274,7 +274,7 @@ static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) 
   if (L->clb > 0) {
     {
       KTime t(c, "fallback");
-      k_fb_keys_case<<<g, 256, 0, c->stream>>>(rec, vals, n, L->act_bits, keys);
+      k_fb_keys_case<<<g, 256, 0, c->stream>>>(rec, vals, n, L->act_bits, (uint32_t)ncl - 1, keys);
       PM4G_TRY(check_launch(c, "k_fb_keys_case"));
     }
     PM4G_TRY(radix_sort_u32(c, keys, vals, keys2, vals2, n, 0, L->clb));
@@ -284,7 +284,7 @@ static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) 
     KTime t(c, "fallback");
     k_fb_gather<<<g, 256, 0, c->stream>>>(rec, vals, n, srec);
     PM4G_TRY(check_launch(c, "k_fb_gather"));
-    k_fb_hist<<<g, 256, 0, c->stream>>>(srec, n, L->act_bits, ccnt);
+    k_fb_hist<<<g, 256, 0, c->stream>>>(srec, n, L->act_bits, (uint32_t)ncl - 1, ccnt);
     PM4G_TRY(check_launch(c, "k_fb_hist"));
   }
   PM4G_TRY(scan_u32(c, ccnt, cstart, ncl));
@@ -389,7 +389,9 @@ static int choose_clb(Ctx *c, int64_t n, uint64_t R, int32_t A, int act_bits) {
 
 const char *pm4g_last_error(void) { return pm4g::g_err; }
 
-const char *pm4g_kernel_names(void) { return "stats,bucket_hist,bucket_scatter,segment,fallback,scan,radix_sort,filter,variants,dfg"; }
+const char *pm4g_kernel_names(void) {
+  return "stats,bucket_hist,bucket_scatter,partition,segment,fallback,scan,radix_sort,filter,variants,dfg";
+}
 
 int pm4g_ctx_create(pm4g_ctx **out, int device, void *cuda_stream, const pm4g_allocator *alloc) {
   if (!out) {
@@ -650,8 +652,9 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         break;
       }
       L->nb = (uint32_t)nb64;
-      // bucket histogram, offsets and scatter
-      int64_t chunk = (n + c->num_sms - 1) / c->num_sms;
+      // bucket histogram, offsets and partition. Row chunks: two per SM.
+      const int64_t n_chunks = 2 * (int64_t)c->num_sms;
+      int64_t chunk = (n + n_chunks - 1) / n_chunks;
       chunk = (chunk + 3) / 4 * 4;
       const int p_ctas = (int)((n + chunk - 1) / chunk);
       uint32_t *mat = S.get<uint32_t>((size_t)p_ctas * L->nb);
@@ -693,17 +696,111 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         fail(check_launch(c, "k_bucket_hist"));
       }
       if (st) break;
+      // Partition levels: one level when the buckets fit the bins of a pass,
+      // two when coarse buckets of 2^fbits final buckets do; the record-by-
+      // record scatter otherwise.
+      int fbits = 0;
+      while (fbits < 8 && ((L->nb + (1u << fbits) - 1) >> fbits) > kPartMaxBins) ++fbits;
+      const uint32_t nc = (L->nb + (1u << fbits) - 1) >> fbits;
+      const bool two_level = fbits > 0 && nc <= kPartMaxBins && L->clb + fbits <= 16;
+      uint32_t *mat1 = mat;
+      if (two_level) {
+        mat1 = S.get<uint32_t>((size_t)p_ctas * nc);
+        if (!mat1) {
+          fail(PM4G_ENOMEM);
+          break;
+        }
+        KTime t(c, "scan");
+        const int64_t k = (int64_t)p_ctas * nc;
+        k_coarse_counts<<<(unsigned)((k + 255) / 256), 256, 0, c->stream>>>(mat, L->nb, p_ctas, fbits, nc, mat1);
+        if (fail(check_launch(c, "k_coarse_counts"))) break;
+      }
       {
         KTime t(c, "scan");
         k_bucket_colprefix<<<(L->nb + 255) / 256, 256, 0, c->stream>>>(mat, L->nb, p_ctas, total);
         if (fail(check_launch(c, "k_bucket_colprefix"))) break;
       }
       if (fail(scan_u32(c, total, L->bucket_off.p, L->nb))) break;
-      for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
-        const uint32_t nbs = std::min(nbs_max, L->nb - b0);
-        KTime t(c, "bucket_scatter");
-        k_bucket_scatter<<<p_ctas, 1024, nbs * 4, c->stream>>>(fa, b0, nbs);
-        fail(check_launch(c, "k_bucket_scatter"));
+      if (fbits == 0 || two_level) {
+        PartArgs pa{};
+        pa.case_id = keycol;
+        pa.activity = dact;
+        pa.ts = dts;
+        pa.n = n;
+        pa.chunk = chunk;
+        pa.min_case = L->min_case;
+        pa.n_act = A;
+        pa.act_bits = L->act_bits;
+        pa.clb = L->clb;
+        pa.fbits = fbits;
+        pa.bucket_off = L->bucket_off.p;
+        pa.nb = L->nb;
+        pa.err_flags = err;
+        uint4 *tmp = nullptr;
+        if (two_level) {
+          {
+            KTime t(c, "scan");
+            const int64_t k = (int64_t)p_ctas * nc;
+            k_bucket_colprefix<<<(nc + 255) / 256, 256, 0, c->stream>>>(mat1, nc, p_ctas, total);
+            if (fail(check_launch(c, "k_bucket_colprefix"))) break;
+            k_add_base<<<(unsigned)((k + 255) / 256), 256, 0, c->stream>>>(mat1, p_ctas, nc, L->bucket_off.p, fbits);
+            if (fail(check_launch(c, "k_add_base"))) break;
+          }
+          tmp = S.get<uint4>(n);
+          if (!tmp) {
+            set_error("pm4g_load_log: out of device memory for the partition buffer");
+            fail(PM4G_ENOMEM);
+            break;
+          }
+          pa.nbins = nc;
+          pa.cur1 = mat1;
+          pa.rec_out = tmp;
+          {
+            KTime t(c, "partition");
+            c->launches++;
+            if (launch_partition(1, pa, (unsigned)p_ctas, c->stream) != cudaSuccess) {
+              set_error("launch of k_partition<1> failed: %s", cudaGetErrorString(cudaGetLastError()));
+              fail(PM4G_ECUDA);
+              break;
+            }
+          }
+          pa.nbins = 1u << fbits;
+          pa.rec_in = tmp;
+          pa.rec_out = L->rec.p;
+          {
+            KTime t(c, "partition");
+            c->launches++;
+            if (launch_partition(2, pa, nc, c->stream) != cudaSuccess) {
+              set_error("launch of k_partition<2> failed: %s", cudaGetErrorString(cudaGetLastError()));
+              fail(PM4G_ECUDA);
+              break;
+            }
+          }
+        } else {
+          {
+            KTime t(c, "scan");
+            const int64_t k = (int64_t)p_ctas * L->nb;
+            k_add_base<<<(unsigned)((k + 255) / 256), 256, 0, c->stream>>>(mat, p_ctas, L->nb, L->bucket_off.p, 0);
+            if (fail(check_launch(c, "k_add_base"))) break;
+          }
+          pa.nbins = L->nb;
+          pa.cur1 = mat;
+          pa.rec_out = L->rec.p;
+          KTime t(c, "partition");
+          c->launches++;
+          if (launch_partition(1, pa, (unsigned)p_ctas, c->stream) != cudaSuccess) {
+            set_error("launch of k_partition<1> failed: %s", cudaGetErrorString(cudaGetLastError()));
+            fail(PM4G_ECUDA);
+            break;
+          }
+        }
+      } else {
+        for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
+          const uint32_t nbs = std::min(nbs_max, L->nb - b0);
+          KTime t(c, "bucket_scatter");
+          k_bucket_scatter<<<p_ctas, 1024, nbs * 4, c->stream>>>(fa, b0, nbs);
+          fail(check_launch(c, "k_bucket_scatter"));
+        }
       }
       if (st) break;
       if (fail(run_segment(L, dattr, L->has_attr))) break;

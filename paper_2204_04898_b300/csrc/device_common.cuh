@@ -12,10 +12,13 @@ typedef unsigned __int128 u128;
 
 constexpr int kWarp = 32;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kSlotLoMask = 0xFFFFu;  // case-slot bits kept in a record
 
 // ---------------------------------------------------------------------------
 // Bucketed event record (16 bytes, one 128-bit store/load):
-//   x = (case_lo << act_bits) | activity   case_lo: case slot within its bucket
+//   x = (slot_lo << act_bits) | activity   slot_lo: low 16 bits of the case slot;
+//                                           its low clb bits are the slot within
+//                                           the bucket
 //   y = row                                 0-based row in the loaded columns
 //   z, w = timestamp low / high 32 bits     signed int64
 // ---------------------------------------------------------------------------
@@ -23,6 +26,18 @@ __device__ __forceinline__ uint4 make_rec(uint32_t case_lo, uint32_t act, int ac
                                           int64_t ts) {
   uint64_t t = (uint64_t)ts;
   return make_uint4((case_lo << act_bits) | act, row, (uint32_t)t, (uint32_t)(t >> 32));
+}
+// 16-byte store that asks L2 to keep the line (a bucket front's sector is
+// completed by a later store of the same CTA).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void st_evict_last(uint4 *p, uint4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
 }
 __device__ __forceinline__ uint32_t rec_case_lo(uint4 r, int act_bits) { return r.x >> act_bits; }
 __device__ __forceinline__ uint32_t rec_act(uint4 r, uint32_t act_mask) { return r.x & act_mask; }
@@ -74,6 +89,20 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// Ranks lanes by runs of equal keys on consecutive lanes (inactive lanes pass
+// key = ~0): returns the lane of this lane's run head and the run length (valid
+// on the head). A key repeated on non-adjacent lanes forms separate runs.
+__device__ __forceinline__ uint32_t run_head(uint32_t key, uint32_t &run_len) {
+  const uint32_t lane = lane_id();
+  const uint32_t prev = __shfl_up_sync(kFull, key, 1);
+  const uint32_t heads = __ballot_sync(kFull, lane == 0 || prev != key);
+  const uint32_t head = 31 - __clz(heads & (0xFFFFFFFFu >> (31 - lane)));
+  const uint32_t above = heads & ~(0xFFFFFFFFu >> (31 - lane));  // heads after this lane
+  const uint32_t next = above ? (uint32_t)(__ffs(above) - 1) : 32u;
+  run_len = next - lane;
+  return head;
 }
 
 // Exact sum of 64-bit values over the lanes of `peers` (all lanes of `peers`

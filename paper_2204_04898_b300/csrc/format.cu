@@ -119,12 +119,16 @@ __global__ void k_bucket_colprefix(uint32_t *__restrict__ mat, uint32_t nb, int 
 // 16-byte record. Activity codes outside [0, A) raise the error flag and are
 // stored as 0 so that every later index stays in bounds.
 //
-// The scatter preserves row order inside each bucket: CTAs own consecutive
-// row chunks (their cursors start at the CTA-major prefix of the count
-// matrix), a CTA walks its chunk in sub-steps of blockDim rows with a barrier
-// between sub-steps, and lanes of a warp that hit the same bucket are ranked
-// by lane (match + popc). Order is an optimisation only: every record keeps
-// its row, so the segment pass sorts any case that arrives out of order.
+// The scatter keeps row order inside each bucket for almost every case: CTAs
+// own consecutive row chunks (their cursors start at the CTA-major prefix of
+// the count matrix), a CTA walks its chunk in tiles with a barrier between
+// tiles, sub-step k of a tile covers rows k*blockDim .. with consecutive rows
+// on consecutive lanes, and a run of consecutive lanes hitting the same bucket
+// reserves its slots with one atomic, in lane order. Only events of one case
+// that fall in one tile on different warps, or on non-adjacent lanes of one
+// warp, can swap. Order is an optimisation only: every
+// record keeps its row, so the segment pass sorts any case that arrives out
+// of order.
 // The next tile's columns are prefetched into registers while the current
 // tile is scattered.
 // ---------------------------------------------------------------------------
@@ -140,7 +144,6 @@ __global__ void __launch_bounds__(kScatterThreads) k_bucket_scatter(FormatArgs a
   __syncthreads();
   const int64_t r0 = (int64_t)blockIdx.x * a.chunk;
   const int64_t r1 = min(a.n, r0 + a.chunk);
-  const uint32_t ncl_mask = (1u << a.clb) - 1;
   const int lane = threadIdx.x & 31;
   constexpr int64_t kTile = (int64_t)kScatterThreads * kScatterSub;
   int32_t nc[kScatterSub], na[kScatterSub];
@@ -153,6 +156,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_bucket_scatter(FormatArgs a
     nt[k] = i < r1 ? __ldcs(a.ts + i) : 0;
   }
   bool bad = false;
+  const uint64_t pol = l2_evict_last_policy();
   for (int64_t base = r0; base < r1; base += kTile) {
     int32_t cc[kScatterSub], aa[kScatterSub];
     int64_t tt[kScatterSub];
@@ -182,14 +186,16 @@ __global__ void __launch_bounds__(kScatterThreads) k_bucket_scatter(FormatArgs a
         bad = true;
         act = 0;
       }
-      const uint32_t peers = __match_any_sync(kFull, in ? b : 0xFFFFFFFFu);
-      const int leader = __ffs(peers) - 1;
+      uint32_t run;
+      const uint32_t head = run_head(in ? b : 0xFFFFFFFFu, run);
       uint32_t pos = 0;
-      if (in && lane == leader) pos = atomicAdd(&s_cur[b], (uint32_t)__popc(peers));
-      pos = __shfl_sync(kFull, pos, leader) + (uint32_t)__popc(peers & lanemask_lt());
-      if (in) __stcs(a.rec + pos, make_rec(slot & ncl_mask, act, a.act_bits, (uint32_t)i, tt[k]));
-      __syncthreads();
+      if (in && (uint32_t)lane == head) pos = atomicAdd(&s_cur[b], run);
+      pos = __shfl_sync(kFull, pos, (int)head) + ((uint32_t)lane - head);
+      // a half-written sector must stay in L2 until the next record of the
+      // same bucket front fills it
+      if (in) st_evict_last(a.rec + pos, make_rec(slot & kSlotLoMask, act, a.act_bits, (uint32_t)i, tt[k]), pol);
     }
+    __syncthreads();
   }
   if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err_flags, 1u);
 }
@@ -221,3 +227,169 @@ __global__ void k_case_dense(const uint32_t *__restrict__ keys, const uint32_t *
 }
 
 }  // namespace pm4g
+
+namespace pm4g {
+
+// ---------------------------------------------------------------------------
+// Bucket partition with coalesced writes (replaces the record-by-record
+// scatter whenever the bucket count allows it). Scattered 16-byte stores run
+// about 8x slower than streaming ones on this GPU, so a tile of kPartTile
+// events is first ordered by digit in shared memory and then written out as
+// one contiguous run per digit.
+//
+// Level 1 reads the input columns; its digit is the coarse bucket
+// slot >> (clb + fbits), and CTA p owns row chunk p (cursors from the CTA-major
+// prefix of the coarse count matrix). With fbits = 0 the coarse bucket is the
+// final bucket and level 1 is the only pass. Level 2 reads level 1's output;
+// CTA C owns coarse bucket C and its digit is the final bucket inside it,
+// (slot_lo >> clb) & (2^fbits - 1); its cursors are the final bucket offsets.
+// Both levels keep row order within every digit: items of a tile are ranked by
+// warp (warps own consecutive items), then by round, then by lane (match).
+// ---------------------------------------------------------------------------
+template <int kLevel>
+__global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const uint32_t nbins = a.nbins;
+  uint4 *stg = reinterpret_cast<uint4 *>(sm);
+  uint16_t *dig = reinterpret_cast<uint16_t *>(sm + (size_t)kPartTile * 16);
+  uint16_t *wh = reinterpret_cast<uint16_t *>(sm + (size_t)kPartTile * 18);
+  uint32_t *cur = reinterpret_cast<uint32_t *>(sm + (size_t)kPartTile * 18 + part_wh_bytes(nbins));
+  uint32_t *tst = cur + nbins;   // tile start of every digit, nbins + 1
+  uint32_t *sw = tst + nbins + 1;  // block-scan scratch, 32 words
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  int64_t i0, i1;
+  if (kLevel == 1) {
+    i0 = (int64_t)blockIdx.x * a.chunk;
+    i1 = min(a.n, i0 + a.chunk);
+    for (uint32_t d = tid; d < nbins; d += kPartThreads) cur[d] = a.cur1[(int64_t)blockIdx.x * nbins + d];
+  } else {
+    const uint32_t b0 = blockIdx.x << a.fbits;
+    const uint32_t b1 = min(a.nb, b0 + (1u << a.fbits));
+    i0 = a.bucket_off[b0];
+    i1 = a.bucket_off[b1];
+    for (uint32_t d = tid; d < nbins; d += kPartThreads) cur[d] = b0 + d < a.nb ? a.bucket_off[b0 + d] : 0u;
+  }
+  __syncthreads();
+  const uint32_t fmask = (1u << a.fbits) - 1;
+  bool bad = false;
+  for (int64_t base = i0; base < i1; base += kPartTile) {
+    uint4 rec[kPartItems];
+    uint32_t dg[kPartItems];
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+      const int64_t i = base + warp * (32 * kPartItems) + r * 32 + lane;
+      dg[r] = 0xFFFFFFFFu;
+      rec[r] = make_uint4(0, 0, 0, 0);
+      if (i < i1) {
+        if (kLevel == 1) {
+          const uint32_t slot = (uint32_t)__ldcs(a.case_id + i) - (uint32_t)a.min_case;
+          uint32_t act = (uint32_t)__ldcs(a.activity + i);
+          if (act >= (uint32_t)a.n_act) {
+            bad = true;
+            act = 0;
+          }
+          rec[r] = make_rec(slot & kSlotLoMask, act, a.act_bits, (uint32_t)i, __ldcs(a.ts + i));
+          dg[r] = slot >> (a.clb + a.fbits);
+        } else {
+          rec[r] = __ldcs(a.rec_in + i);
+          dg[r] = ((rec[r].x >> a.act_bits) >> a.clb) & fmask;
+        }
+      }
+    }
+    for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) wh[j] = 0;
+    __syncthreads();
+    uint32_t rk[kPartItems];
+    uint16_t *myh = wh + warp * nbins;
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+      const uint32_t peers = __match_any_sync(kFull, dg[r]);
+      const int leader = __ffs(peers) - 1;
+      uint32_t b = 0;
+      if (lane == leader && dg[r] != 0xFFFFFFFFu) {
+        b = myh[dg[r]];
+        myh[dg[r]] = (uint16_t)(b + __popc(peers));
+      }
+      b = __shfl_sync(kFull, b, leader);
+      rk[r] = b + __popc(peers & lanemask_lt());
+      __syncwarp();
+    }
+    __syncthreads();
+    {
+      uint32_t tot = 0;
+      if ((uint32_t)tid < nbins)
+        for (int w = 0; w < kPartWarps; ++w) tot += wh[w * nbins + tid];
+      uint32_t all;
+      const uint32_t pre = block_exclusive_scan<kPartThreads>(tot, sw, all);
+      if ((uint32_t)tid < nbins) {
+        tst[tid] = pre;
+        uint32_t run = pre;
+        for (int w = 0; w < kPartWarps; ++w) {
+          const uint32_t t = wh[w * nbins + tid];
+          wh[w * nbins + tid] = (uint16_t)run;
+          run += t;
+        }
+      }
+      if (tid == 0) tst[nbins] = all;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+      if (dg[r] != 0xFFFFFFFFu) {
+        const uint32_t pos = myh[dg[r]] + rk[r];
+        stg[pos] = rec[r];
+        dig[pos] = (uint16_t)dg[r];
+      }
+    }
+    __syncthreads();
+    const uint32_t cnt = tst[nbins];
+    for (uint32_t j = tid; j < cnt; j += kPartThreads) {
+      const uint32_t d = dig[j];
+      a.rec_out[cur[d] + (j - tst[d])] = stg[j];
+    }
+    __syncthreads();
+    if ((uint32_t)tid < nbins) cur[tid] += tst[tid + 1] - tst[tid];
+    __syncthreads();
+  }
+  if (kLevel == 1 && __any_sync(kFull, bad) && lane == 0) atomicOr(a.err_flags, 1u);
+}
+
+cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s) {
+  const size_t smem = part_smem_bytes(a.nbins);
+  cudaError_t e;
+  if (level == 1) {
+    e = cudaFuncSetAttribute(k_partition<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_partition<1><<<grid, kPartThreads, smem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(k_partition<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_partition<2><<<grid, kPartThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Coarse count matrix: mat1[p][C] = sum of mat[p][b] over the final buckets b
+// of coarse bucket C.
+__global__ void k_coarse_counts(const uint32_t *__restrict__ mat, uint32_t nb, int p_ctas, int fbits, uint32_t nc,
+                                uint32_t *__restrict__ mat1) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)p_ctas * nc) return;
+  const int64_t p = k / nc;
+  const uint32_t C = (uint32_t)(k % nc);
+  const uint32_t b0 = C << fbits, b1 = min(nb, b0 + (1u << fbits));
+  uint32_t s = 0;
+  for (uint32_t b = b0; b < b1; ++b) s += mat[p * nb + b];
+  mat1[p * nc + C] = s;
+}
+
+// Adds the coarse bucket's first position to every CTA's prefix.
+__global__ void k_add_base(uint32_t *__restrict__ mat1, int p_ctas, uint32_t nc, const uint32_t *__restrict__ bucket_off,
+                           int fbits) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)p_ctas * nc) return;
+  mat1[k] += bucket_off[(uint32_t)(k % nc) << fbits];
+}
+
+}  // namespace pm4g
+

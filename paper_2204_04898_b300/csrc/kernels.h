@@ -23,6 +23,42 @@ struct FormatArgs {
   uint32_t *err_flags;
 };
 
+// Bucket partition (format.cu)
+constexpr int kPartThreads = 512;
+constexpr int kPartWarps = kPartThreads / 32;
+constexpr int kPartItems = 8;
+constexpr int kPartTile = kPartThreads * kPartItems;
+constexpr uint32_t kPartMaxBins = 512;
+
+struct PartArgs {
+  const int32_t *case_id;
+  const int32_t *activity;
+  const int64_t *ts;
+  int64_t n;
+  int64_t chunk;
+  int32_t min_case;
+  int32_t n_act;
+  int act_bits;
+  int clb;
+  int fbits;
+  uint32_t nbins;
+  const uint4 *rec_in;
+  const uint32_t *bucket_off;
+  uint32_t nb;
+  const uint32_t *cur1;
+  uint4 *rec_out;
+  uint32_t *err_flags;
+};
+
+__host__ __device__ inline size_t part_wh_bytes(uint32_t nbins) { return ((size_t)kPartWarps * nbins * 2 + 15) / 16 * 16; }
+__host__ __device__ inline size_t part_smem_bytes_hd(uint32_t nbins) {
+  return (size_t)kPartTile * 18 + (((size_t)kPartWarps * nbins * 2 + 15) / 16 * 16) + (size_t)(2 * nbins + 1 + 32) * 4;
+}
+inline size_t part_smem_bytes(uint32_t nbins) { return part_smem_bytes_hd(nbins); }
+cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s);
+__global__ void k_coarse_counts(const uint32_t *mat, uint32_t nb, int p_ctas, int fbits, uint32_t nc, uint32_t *mat1);
+__global__ void k_add_base(uint32_t *mat1, int p_ctas, uint32_t nc, const uint32_t *bucket_off, int fbits);
+
 __global__ void k_stats(const int32_t *case_id, int64_t n, int2 *partial);
 __global__ void k_bucket_hist(FormatArgs a, uint32_t b_lo, uint32_t nbs);
 __global__ void k_bucket_colprefix(uint32_t *mat, uint32_t nb, int p_ctas, uint32_t *total);
@@ -95,7 +131,7 @@ __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, in
   L.idx = o;
   o += seg_align((size_t)cap * 2, 16);
   L.hw = o;
-  o += seg_align((size_t)kSegWarps * ncl * 2, 16);
+  o += seg_align((size_t)kSegWarps * ((ncl + 1) & ~1) * 2, 16);
   L.rng = o;
   o += (size_t)(2 * ncl + 4) * 4;
   L.ccnt = o;
@@ -129,12 +165,13 @@ cudaError_t launch_fb_compute(bool exp, const SegArgs &a, const uint4 *srec, uin
 
 // Global-memory path for one bucket whose records were sorted by
 // (case slot, timestamp, row) into srec.
-__global__ void k_fb_hist(const uint4 *srec, uint32_t n, int act_bits, uint32_t *ccnt);
+__global__ void k_fb_hist(const uint4 *srec, uint32_t n, int act_bits, uint32_t cmask, uint32_t *ccnt);
 __global__ void k_fb_cases(SegArgs a, const uint4 *srec, uint32_t bucket, const uint32_t *ccnt,
                            const uint32_t *cstart, int ncl, int write_cases);
 __global__ void k_fb_keys_row(const uint4 *rec, uint32_t n, uint32_t *keys, uint32_t *vals);
 __global__ void k_fb_keys_ts(const uint4 *rec, const uint32_t *perm, uint32_t n, uint64_t *keys);
-__global__ void k_fb_keys_case(const uint4 *rec, const uint32_t *perm, uint32_t n, int act_bits, uint32_t *keys);
+__global__ void k_fb_keys_case(const uint4 *rec, const uint32_t *perm, uint32_t n, int act_bits, uint32_t cmask,
+                               uint32_t *keys);
 __global__ void k_fb_gather(const uint4 *rec, const uint32_t *perm, uint32_t n, uint4 *out);
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v);
 

@@ -65,6 +65,7 @@ struct SmemSink {
   uint32_t *tkey, *tcnt, *tminh, *tmaxh;
   uint32_t *tl, *tm;  // low and middle 32-bit words of the slot's sum
   uint32_t mask;
+  uint32_t shift;  // 32 - log2(slots), for the multiplicative slot hash
   int mode;
   uint32_t *st, *en;
   uint32_t *hl, *hh;  // per-case sequence hash, low and high words
@@ -72,7 +73,7 @@ struct SmemSink {
 
   __device__ __forceinline__ int find(uint32_t key) {
     if (mode == 0) return (int)key;
-    uint32_t h = fmix32(key) & mask;
+    uint32_t h = (key * 0x9E3779B1u) >> shift;
     for (int it = 0; it < 64; ++it) {
       const uint32_t k = *(volatile uint32_t *)&tkey[h];
       if (k == key) return (int)h;
@@ -145,22 +146,29 @@ struct GlobalSink {
 };
 
 // Aggregates the warp's directly-follows pairs with full-warp operations.
-// Twice: the pending lanes whose edge equals the first pending lane's edge are
-// reduced together (count, exact 128-bit sum, min, max; non-members add
-// neutral values) and that first lane updates the sink once. Every lane still
-// pending then updates the sink on its own.
+// Up to twice, the pending lanes whose edge equals the first pending lane's
+// edge are reduced together (count, exact 128-bit sum, min, max; non-members
+// add neutral values) when there are at least two of them. Then a single pass
+// updates the sink: each group through its first lane, every other pending
+// lane on its own.
 template <class Sink>
 __device__ __forceinline__ void aggregate_edges(Sink &sink, bool has_edge, uint32_t key, uint64_t d) {
   const int lane = (int)lane_id();
   uint32_t rem = __ballot_sync(kFull, has_edge);
+  if (rem == 0) return;
   const uint32_t hi = (uint32_t)(d >> 32), lo = (uint32_t)d;
+  uint32_t u_cnt = 1;
+  u128 u_sum = (u128)d;
+  uint64_t u_mn = d, u_mx = d;
+  bool leader = false;
 #pragma unroll
   for (int round = 0; round < 2; ++round) {
-    if (rem == 0) return;
+    if (rem == 0) break;
     const int src = __ffs(rem) - 1;
     const uint32_t cand = __shfl_sync(kFull, key, src);
     const bool mem = ((rem >> lane) & 1u) && key == cand;
     const uint32_t grp = __ballot_sync(kFull, mem);
+    if (__popc(grp) < 2) break;
     const uint32_t s0 = __reduce_add_sync(kFull, mem ? (uint32_t)(d & 0x3FFFFF) : 0u);
     const uint32_t s1 = __reduce_add_sync(kFull, mem ? (uint32_t)((d >> 22) & 0x3FFFFF) : 0u);
     const uint32_t s2 = __reduce_add_sync(kFull, mem ? (uint32_t)(d >> 44) : 0u);
@@ -169,12 +177,15 @@ __device__ __forceinline__ void aggregate_edges(Sink &sink, bool has_edge, uint3
     const uint32_t mxh = __reduce_max_sync(kFull, mem ? hi : 0u);
     const uint32_t mxl = __reduce_max_sync(kFull, (mem && hi == mxh) ? lo : 0u);
     if (lane == src) {
-      const u128 sum = (u128)s0 + ((u128)s1 << 22) + ((u128)s2 << 44);
-      sink.edge_group(cand, (uint32_t)__popc(grp), sum, ((uint64_t)mnh << 32) | mnl, ((uint64_t)mxh << 32) | mxl);
+      u_cnt = (uint32_t)__popc(grp);
+      u_sum = (u128)s0 + ((u128)s1 << 22) + ((u128)s2 << 44);
+      u_mn = ((uint64_t)mnh << 32) | mnl;
+      u_mx = ((uint64_t)mxh << 32) | mxl;
+      leader = true;
     }
     rem &= ~grp;
   }
-  if ((rem >> lane) & 1u) sink.edge_group(key, 1u, (u128)d, d, d);
+  if (leader || ((rem >> lane) & 1u)) sink.edge_group(key, u_cnt, u_sum, u_mn, u_mx);
 }
 
 // One warp handles 32 consecutive ordered positions p = base + lane of a
@@ -192,7 +203,7 @@ __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, 
   uint4 r = make_uint4(0, 0, 0, 0);
   if (valid) {
     r = fetch(p);
-    c = r.x >> a.act_bits;
+    c = (r.x >> a.act_bits) & ((1u << a.clb) - 1);
     act = r.x & act_mask;
     ts = rec_ts(r);
     cs = cstart[c];
@@ -226,16 +237,8 @@ __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, 
   }
   const int64_t nts = (int64_t)(((uint64_t)nw << 32) | nz);
   aggregate_edges(sink, has_edge, act * a.n_act + (nx & act_mask), (uint64_t)nts - (uint64_t)ts);
-  // sequence hash: segmented inclusive sum over lanes holding the same case
-  uint64_t v = valid ? event_hash(act, (uint32_t)p - cs, a.seed) : 0ull;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint64_t y = __shfl_up_sync(kFull, v, o);
-    const uint32_t cy = __shfl_up_sync(kFull, c, o);
-    if (lane >= o && cy == c) v += y;
-  }
-  const uint32_t cn = __shfl_down_sync(kFull, c, 1);
-  if (valid && (lane == 31 || cn != c)) sink.hash_add(c, v);
+  // sequence hash: each event adds its term to its case's sum
+  if (valid) sink.hash_add(c, event_hash(act, (uint32_t)p - cs, a.seed));
 }
 
 template <int E>
@@ -283,8 +286,10 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
                               uint32_t b, uint32_t n_r, uint32_t c_a, uint32_t c_b, int64_t out_base,
                               uint32_t act_mask, uint32_t &n_sorted) {
   const int ncl = 1 << a.clb;
+  const int hws = (ncl + 1) & ~1;  // per-warp row of 16-bit counts, 4-byte aligned
+  const uint32_t cmask = (uint32_t)ncl - 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int j = tid; j < kSegWarps * ncl; j += kSegThreads) hw[j] = 0;
+  for (int j = tid; j < kSegWarps * hws; j += kSegThreads) hw[j] = 0;
   for (int c = tid; c < ncl; c += kSegThreads) {
     S.hl[c] = 0;
     S.hh[c] = 0;
@@ -293,20 +298,22 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   // stable counting sort by case slot
   const uint32_t per = ((n_r + kSegWarps - 1) / kSegWarps + 31) & ~31u;
   const uint32_t w_lo = min(n_r, (uint32_t)warp * per), w_hi = min(n_r, w_lo + per);
-  uint16_t *myh = hw + warp * ncl;
+  uint16_t *myh = hw + warp * hws;
+  // myh holds 16-bit counts, two per 32-bit word (no count reaches 2^16)
+  uint32_t *myw = reinterpret_cast<uint32_t *>(myh);
   for (uint32_t j = w_lo; j < w_hi; j += 32) {
     const uint32_t i = j + lane;
     const bool v = i < w_hi;
-    const uint32_t c = v ? (S.rec[i].x >> a.act_bits) : 0xFFFFu;
-    const uint32_t peers = __match_any_sync(kFull, c);
-    if (v && lane == __ffs(peers) - 1) myh[c] = (uint16_t)(myh[c] + __popc(peers));
-    __syncwarp();
+    const uint32_t c = v ? ((S.rec[i].x >> a.act_bits) & cmask) : 0xFFFFFFFFu;
+    uint32_t run;
+    const uint32_t head = run_head(c, run);
+    if (v && (uint32_t)lane == head) atomicAdd(&myw[c >> 1], run << (16 * (c & 1)));
   }
   __syncthreads();
   {
     uint32_t tot = 0;
     if (tid < ncl)
-      for (int w = 0; w < kSegWarps; ++w) tot += hw[w * ncl + tid];
+      for (int w = 0; w < kSegWarps; ++w) tot += hw[w * hws + tid];
     uint32_t all;
     const uint32_t pre = block_exclusive_scan<kSegThreads>(tot, misc + 8, all);
     if (tid < ncl) {
@@ -314,8 +321,8 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
       S.cstart[tid] = pre;
       uint32_t run = pre;
       for (int w = 0; w < kSegWarps; ++w) {
-        const uint32_t t = hw[w * ncl + tid];
-        hw[w * ncl + tid] = (uint16_t)run;
+        const uint32_t t = hw[w * hws + tid];
+        hw[w * hws + tid] = (uint16_t)run;
         run += t;
       }
     }
@@ -325,17 +332,13 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   for (uint32_t j = w_lo; j < w_hi; j += 32) {
     const uint32_t i = j + lane;
     const bool v = i < w_hi;
-    const uint32_t c = v ? (S.rec[i].x >> a.act_bits) : 0xFFFFu;
-    const uint32_t peers = __match_any_sync(kFull, c);
-    const int leader = __ffs(peers) - 1;
+    const uint32_t c = v ? ((S.rec[i].x >> a.act_bits) & cmask) : 0xFFFFFFFFu;
+    uint32_t run;
+    const uint32_t head = run_head(c, run);
     uint32_t base = 0;
-    if (v && lane == leader) {
-      base = myh[c];
-      myh[c] = (uint16_t)(base + __popc(peers));
-    }
-    base = __shfl_sync(kFull, base, leader);
-    if (v) S.idx[base + __popc(peers & lanemask_lt())] = (uint16_t)i;
-    __syncwarp();
+    if (v && (uint32_t)lane == head) base = (atomicAdd(&myw[c >> 1], run << (16 * (c & 1))) >> (16 * (c & 1))) & 0xFFFFu;
+    base = __shfl_sync(kFull, base, (int)head);
+    if (v) S.idx[base + ((uint32_t)lane - head)] = (uint16_t)i;
   }
   __syncthreads();
   // flag the cases whose events are out of (timestamp, row) order; hw is free
@@ -344,7 +347,7 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   __syncthreads();
   for (uint32_t p = tid + 1; p < n_r; p += kSegThreads) {
     const uint4 x = S.rec[S.idx[p - 1]], y = S.rec[S.idx[p]];
-    const uint32_t cx = x.x >> a.act_bits, cy = y.x >> a.act_bits;
+    const uint32_t cx = (x.x >> a.act_bits) & cmask, cy = (y.x >> a.act_bits) & cmask;
     if (cx == cy && !kr_less(ts_key(rec_ts(x)), x.y, ts_key(rec_ts(y)), y.y)) unsorted[cy] = 1;
   }
   __syncthreads();
@@ -416,6 +419,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t act_mask = (1u << a.act_bits) - 1;
+  const uint32_t cmask = (uint32_t)ncl - 1;
 
   if (!kExport) {
     for (int i = tid; i < a.tbl_slots; i += kSegThreads) {
@@ -431,7 +435,8 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
       en[i] = 0;
     }
   }
-  SmemSink sink{tkey, tcnt, tminh, tmaxh, tl, tm, (uint32_t)(a.tbl_slots - 1), a.tbl_mode,
+  SmemSink sink{tkey, tcnt, tminh, tmaxh, tl, tm, (uint32_t)(a.tbl_slots - 1),
+                (uint32_t)__clz((uint32_t)a.tbl_slots) + 1u, a.tbl_mode,
                 a_s ? st : nullptr, a_s ? en : nullptr, S.hl, S.hh, &a};
   uint32_t n_sorted = 0;
   __syncthreads();
@@ -460,7 +465,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
       // too large for one pass: split the case slots into ranges that fit
       for (int c = tid; c < ncl; c += kSegThreads) S.ccnt[c] = 0;
       __syncthreads();
-      for (uint32_t i = tid; i < n; i += kSegThreads) atomicAdd(&S.ccnt[__ldcg(src + i).x >> a.act_bits], 1u);
+      for (uint32_t i = tid; i < n; i += kSegThreads) atomicAdd(&S.ccnt[(__ldcg(src + i).x >> a.act_bits) & cmask], 1u);
       __syncthreads();
       if (tid == 0) {
         uint32_t nr = 0, acc = 0, pos = 0;
@@ -494,7 +499,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
           bool keep = false;
           if (i < n) {
             rv = __ldcg(src + i);
-            const uint32_t c = rv.x >> a.act_bits;
+            const uint32_t c = (rv.x >> a.act_bits) & cmask;
             keep = c >= c_a && c < c_b;
           }
           uint32_t tot;
@@ -554,18 +559,18 @@ __global__ void k_fb_keys_ts(const uint4 *__restrict__ rec, const uint32_t *__re
     keys[i] = ts_key(rec_ts(rec[perm[i]]));
 }
 __global__ void k_fb_keys_case(const uint4 *__restrict__ rec, const uint32_t *__restrict__ perm, uint32_t n,
-                               int act_bits, uint32_t *keys) {
+                               int act_bits, uint32_t cmask, uint32_t *keys) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    keys[i] = rec[perm[i]].x >> act_bits;
+    keys[i] = (rec[perm[i]].x >> act_bits) & cmask;
 }
 __global__ void k_fb_gather(const uint4 *__restrict__ rec, const uint32_t *__restrict__ perm, uint32_t n,
                             uint4 *out) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     out[i] = rec[perm[i]];
 }
-__global__ void k_fb_hist(const uint4 *__restrict__ srec, uint32_t n, int act_bits, uint32_t *ccnt) {
+__global__ void k_fb_hist(const uint4 *__restrict__ srec, uint32_t n, int act_bits, uint32_t cmask, uint32_t *ccnt) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    atomicAdd(&ccnt[srec[i].x >> act_bits], 1u);
+    atomicAdd(&ccnt[(srec[i].x >> act_bits) & cmask], 1u);
 }
 
 template <bool kExport>
@@ -627,7 +632,7 @@ __global__ void __launch_bounds__(256) k_case_span(FilterArgs a) {
     const uint32_t lo = a.bucket_off[b], hi = a.bucket_off[b + 1];
     for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       const uint4 r = a.rec[i];
-      const uint32_t c = r.x >> a.act_bits;
+      const uint32_t c = (r.x >> a.act_bits) & ((1u << a.clb) - 1);
       const unsigned long long k = ts_key(rec_ts(r));
       atomicMin(&mn[c], k);
       atomicMax(&mx[c], k);
@@ -667,7 +672,7 @@ __global__ void k_case_ok(FilterArgs a) {
 }
 
 __device__ __forceinline__ bool filter_keep(const FilterArgs &a, uint32_t b, uint4 r) {
-  const uint64_t slot = ((uint64_t)b << a.clb) + (r.x >> a.act_bits);
+  const uint64_t slot = ((uint64_t)b << a.clb) + ((r.x >> a.act_bits) & ((1u << a.clb) - 1));
   if (!a.case_ok[slot]) return false;
   if (a.mode == PM4G_TW_EVENTS) {
     const int64_t t = rec_ts(r);

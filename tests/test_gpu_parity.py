@@ -62,6 +62,13 @@ def test_workloads(pm4g, ctx, spec):
     check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities, case_attr=L.case_attr)
 
 
+@pytest.mark.parametrize("spec", [synth.large_log(300_000), synth.very_large_log(300_000)], ids=lambda s: s.name)
+def test_two_level_partition(pm4g, ctx, spec):
+    """Logs with more than 512 buckets are partitioned in two levels."""
+    L = synth.generate(spec)
+    check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities, export=False)
+
+
 def test_host_pointers(pm4g, ctx):
     L = synth.generate(synth.large_log(5_000))
     check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities, device=False)
