@@ -201,6 +201,31 @@ typedef struct {
 } pm4g_filter_spec;
 int pm4g_filter(pm4g_log *log, const pm4g_filter_spec *spec, pm4g_log **out);
 
+/* Allocation-free frequency/performance DFG and start/end counts of a small
+ * log. The paper has no counterpart: this serves callers that cannot allocate
+ * device memory when they need the summary (code running under CUDA graph
+ * capture, serving processes with a fixed memory budget, hosts whose device
+ * memory belongs to another framework's pool).
+ *   case_id, activity, ts_ns: device columns of n_events entries
+ *     (0 <= n_events <= 262144; max case id - min case id < 262144; no case
+ *     longer than 512 events; activity in [0, n_activities), n_activities <=
+ *     2048). Larger inputs are rejected with PM4G_EINVAL.
+ *   count, sum_lo, sum_hi, min, max: device arrays of n_activities^2 cells,
+ *     cell src * n_activities + dst, written by the call (cells without a
+ *     pair: count 0, min UINT64_MAX, max 0). start, end: device arrays of
+ *     n_activities entries.
+ *   cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ * The only working memory is a fixed array inside the library (about 7 MB per
+ * GPU that loads it, held until the process exits); the call allocates nothing
+ * and returns after the stream has finished its work. All calls share that
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller. The first call on a device looks up the array's device address with
+ * that device current; make it before any stream capture. */
+int pm4g_dfg_noalloc(const int32_t *case_id, const int32_t *activity, const int64_t *ts_ns,
+                     int64_t n_events, int32_t n_activities, void *cuda_stream, uint64_t *count,
+                     uint64_t *sum_lo, uint64_t *sum_hi, uint64_t *min, uint64_t *max,
+                     uint64_t *start, uint64_t *end);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *pm4g_last_error(void);
 

@@ -77,6 +77,7 @@ lib.pm4g_variants_free.argtypes = [ctypes.POINTER(_Variants)]
 lib.pm4g_filter.argtypes = [_P, ctypes.POINTER(_FilterSpec), ctypes.POINTER(_P)]
 lib.pm4g_last_error.restype = ctypes.c_char_p
 lib.pm4g_last_error.argtypes = []
+lib.pm4g_dfg_noalloc.argtypes = [_P, _P, _P, _i64, _i32, _P] + [_P] * 7
 
 
 class Pm4gError(RuntimeError):
@@ -282,3 +283,29 @@ def pm4g_filter(log: int, attr_set=None, t_lo: int = -(2**63), t_hi: int = 2**63
     h = _P()
     _check(lib.pm4g_filter(log, ctypes.byref(spec), ctypes.byref(h)), "pm4g_filter")
     return h.value
+
+
+def pm4g_dfg_noalloc(case_id, activity, ts_ns, n_activities: int, stream: int | None = None) -> dict:
+    """Allocation-free DFG of a small log, for callers that cannot allocate
+    device memory at call time (graph capture, fixed-budget serving, foreign
+    memory pools): the library call uses only its fixed internal scratch. The
+    inputs are CUDA tensors; the dense outputs (count, sum_lo, sum_hi, min, max
+    over n_activities^2 cells; start, end) are CUDA int64 tensors allocated
+    here, on the caller's side, and filled by the call."""
+    import torch
+    for x in (case_id, activity, ts_ns):
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.is_contiguous() and x.dim() == 1):
+            raise TypeError("pm4g_dfg_noalloc takes contiguous 1-D CUDA tensors")
+    n = case_id.numel()
+    if activity.numel() != n or ts_ns.numel() != n:
+        raise ValueError("columns differ in length")
+    A = int(n_activities)
+    dev = case_id.device
+    out = {k: torch.empty(A * A, dtype=torch.int64, device=dev) for k in ("count", "sum_lo", "sum_hi", "min", "max")}
+    out["start"] = torch.empty(A, dtype=torch.int64, device=dev)
+    out["end"] = torch.empty(A, dtype=torch.int64, device=dev)
+    _check(lib.pm4g_dfg_noalloc(case_id.data_ptr(), activity.data_ptr(), ts_ns.data_ptr(), n, A, stream,
+                                *(out[k].data_ptr() for k in ("count", "sum_lo", "sum_hi", "min", "max", "start",
+                                                              "end"))),
+           "pm4g_dfg_noalloc")
+    return out
