@@ -717,7 +717,7 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
       }
       {
         KTime t(c, "scan");
-        k_bucket_colprefix<<<(L->nb + 255) / 256, 256, 0, c->stream>>>(mat, L->nb, p_ctas, total);
+        k_bucket_colprefix<<<(L->nb + 31) / 32, 256, 0, c->stream>>>(mat, L->nb, p_ctas, total);
         if (fail(check_launch(c, "k_bucket_colprefix"))) break;
       }
       if (fail(scan_u32(c, total, L->bucket_off.p, L->nb))) break;
@@ -741,7 +741,7 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           {
             KTime t(c, "scan");
             const int64_t k = (int64_t)p_ctas * nc;
-            k_bucket_colprefix<<<(nc + 255) / 256, 256, 0, c->stream>>>(mat1, nc, p_ctas, total);
+            k_bucket_colprefix<<<(nc + 31) / 32, 256, 0, c->stream>>>(mat1, nc, p_ctas, total);
             if (fail(check_launch(c, "k_bucket_colprefix"))) break;
             k_add_base<<<(unsigned)((k + 255) / 256), 256, 0, c->stream>>>(mat1, p_ctas, nc, L->bucket_off.p, fbits);
             if (fail(check_launch(c, "k_add_base"))) break;

@@ -49,10 +49,11 @@ __device__ __forceinline__ uint64_t ts_key(int64_t ts) { return (uint64_t)ts ^ 0
 
 // ---------------------------------------------------------------------------
 // Hashing. fmix64 is the 64-bit finalizer of MurmurHash3 (Austin Appleby,
-// public domain). A case's variant hash is the wrap-around sum over its events
-// of fmix64 applied to (activity, position in case, seed): order-sensitive
-// through the position, and computable by any thread for any event. It only
-// accelerates grouping; equality of sequences is always verified.
+// public domain). A case's variant hash sums, over its events, the term fmix64
+// of (activity, position in case, seed): its low words and its high words
+// each in a 32-bit wrap-around sum. It is order-sensitive through the
+// position, and any thread can add any event's term. It only accelerates
+// grouping; equality of sequences is always verified.
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   k ^= k >> 33;

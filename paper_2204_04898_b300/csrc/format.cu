@@ -99,19 +99,31 @@ __global__ void __launch_bounds__(1024) k_bucket_hist(FormatArgs a, uint32_t b_l
 }
 
 // Per bucket: exclusive prefix of the counts over CTAs (in place) and the
-// bucket total.
-__global__ void k_bucket_colprefix(uint32_t *__restrict__ mat, uint32_t nb, int p_ctas,
-                                   uint32_t *__restrict__ total) {
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+// bucket total. A block handles 32 buckets; its 8 warps split the CTA range so
+// that no thread walks more than an eighth of it serially.
+__global__ void __launch_bounds__(256) k_bucket_colprefix(uint32_t *__restrict__ mat, uint32_t nb, int p_ctas,
+                                                          uint32_t *__restrict__ total) {
+  __shared__ uint32_t s_part[8][33];
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t b = blockIdx.x * 32 + lane;
+  const int per = (p_ctas + 7) / 8;
+  const int p0 = min(p_ctas, (int)w * per), p1 = min(p_ctas, p0 + per);
+  uint32_t s = 0;
+  if (b < nb)
+    for (int p = p0; p < p1; ++p) s += mat[(int64_t)p * nb + b];
+  s_part[w][lane] = s;
+  __syncthreads();
   uint32_t acc = 0;
-  for (int p = 0; p < p_ctas; ++p) {
-    uint32_t *q = mat + (int64_t)p * nb + b;
-    const uint32_t v = *q;
-    *q = acc;
-    acc += v;
+  for (uint32_t ww = 0; ww < w; ++ww) acc += s_part[ww][lane];
+  if (b < nb) {
+    for (int p = p0; p < p1; ++p) {
+      uint32_t *q = mat + (int64_t)p * nb + b;
+      const uint32_t v = *q;
+      *q = acc;
+      acc += v;
+    }
+    if (w == 7) total[b] = acc;
   }
-  total[b] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -254,14 +266,15 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   uint16_t *dig = reinterpret_cast<uint16_t *>(sm + (size_t)kPartTile * 16);
   uint16_t *wh = reinterpret_cast<uint16_t *>(sm + (size_t)kPartTile * 18);
   uint32_t *cur = reinterpret_cast<uint32_t *>(sm + (size_t)kPartTile * 18 + part_wh_bytes(nbins));
-  uint32_t *tst = cur + nbins;   // tile start of every digit, nbins + 1
+  uint32_t *tst = cur + nbins;     // tile start of every digit, nbins + 1
   uint32_t *sw = tst + nbins + 1;  // block-scan scratch, 32 words
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  int64_t i0, i1;
+  // item indices fit 32 bits (at most 2^31 - 1 events)
+  uint32_t i0, i1;
   if (kLevel == 1) {
-    i0 = (int64_t)blockIdx.x * a.chunk;
-    i1 = min(a.n, i0 + a.chunk);
+    i0 = (uint32_t)((int64_t)blockIdx.x * a.chunk);
+    i1 = (uint32_t)min(a.n, (int64_t)i0 + a.chunk);
     for (uint32_t d = tid; d < nbins; d += kPartThreads) cur[d] = a.cur1[(int64_t)blockIdx.x * nbins + d];
   } else {
     const uint32_t b0 = blockIdx.x << a.fbits;
@@ -270,15 +283,19 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     i1 = a.bucket_off[b1];
     for (uint32_t d = tid; d < nbins; d += kPartThreads) cur[d] = b0 + d < a.nb ? a.bucket_off[b0 + d] : 0u;
   }
+  for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) wh[j] = 0;
   __syncthreads();
   const uint32_t fmask = (1u << a.fbits) - 1;
+  const int shift1 = a.clb + a.fbits;
   bool bad = false;
-  for (int64_t base = i0; base < i1; base += kPartTile) {
+  uint16_t *myh = wh + warp * nbins;
+  for (uint32_t base = i0; base < i1; base += kPartTile) {
     uint4 rec[kPartItems];
     uint32_t dg[kPartItems];
+    const uint32_t wbase = base + (uint32_t)warp * (32 * kPartItems) + lane;
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
-      const int64_t i = base + warp * (32 * kPartItems) + r * 32 + lane;
+      const uint32_t i = wbase + r * 32;
       dg[r] = 0xFFFFFFFFu;
       rec[r] = make_uint4(0, 0, 0, 0);
       if (i < i1) {
@@ -289,29 +306,27 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
             bad = true;
             act = 0;
           }
-          rec[r] = make_rec(slot & kSlotLoMask, act, a.act_bits, (uint32_t)i, __ldcs(a.ts + i));
-          dg[r] = slot >> (a.clb + a.fbits);
+          rec[r] = make_rec(slot & kSlotLoMask, act, a.act_bits, i, __ldcs(a.ts + i));
+          dg[r] = slot >> shift1;
         } else {
           rec[r] = __ldcs(a.rec_in + i);
           dg[r] = ((rec[r].x >> a.act_bits) >> a.clb) & fmask;
         }
       }
     }
-    for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) wh[j] = 0;
-    __syncthreads();
+    // stable ranks: per-warp counts in item order (rounds, then lanes)
     uint32_t rk[kPartItems];
-    uint16_t *myh = wh + warp * nbins;
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
       const uint32_t peers = __match_any_sync(kFull, dg[r]);
       const int leader = __ffs(peers) - 1;
-      uint32_t b = 0;
+      uint32_t bb = 0;
       if (lane == leader && dg[r] != 0xFFFFFFFFu) {
-        b = myh[dg[r]];
-        myh[dg[r]] = (uint16_t)(b + __popc(peers));
+        bb = myh[dg[r]];
+        myh[dg[r]] = (uint16_t)(bb + __popc(peers));
       }
-      b = __shfl_sync(kFull, b, leader);
-      rk[r] = b + __popc(peers & lanemask_lt());
+      bb = __shfl_sync(kFull, bb, leader);
+      rk[r] = bb + __popc(peers & lanemask_lt());
       __syncwarp();
     }
     __syncthreads();
@@ -342,11 +357,13 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
       }
     }
     __syncthreads();
+    // write the runs; clear the per-warp counts for the next tile meanwhile
     const uint32_t cnt = tst[nbins];
     for (uint32_t j = tid; j < cnt; j += kPartThreads) {
       const uint32_t d = dig[j];
       a.rec_out[cur[d] + (j - tst[d])] = stg[j];
     }
+    for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) wh[j] = 0;
     __syncthreads();
     if ((uint32_t)tid < nbins) cur[tid] += tst[tid + 1] - tst[tid];
     __syncthreads();

@@ -107,7 +107,7 @@ struct SegArgs {
 };
 
 struct SegSmem {
-  size_t rec, tlo, chash, idx, hw, rng, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;
+  size_t rec, tlo, chash, idx, hw, rng, flg, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;
 };
 
 constexpr int kSegThreads = 512;
@@ -134,6 +134,8 @@ __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, in
   o += seg_align((size_t)kSegWarps * ((ncl + 1) & ~1) * 2, 16);
   L.rng = o;
   o += (size_t)(2 * ncl + 4) * 4;
+  L.flg = o;
+  o += seg_align((size_t)ncl, 16);
   L.ccnt = o;
   o += (size_t)(ncl + 1) * 4;
   L.cstart = o;

@@ -53,14 +53,6 @@ __device__ __forceinline__ void global_edge_group(const DfgTable &g, uint32_t ke
   global_sum(g, key, lo, hi);
 }
 
-// 64-bit wrap-around add into two 32-bit shared words (low, high).
-__device__ __forceinline__ void smem_add64(uint32_t *lo, uint32_t *hi, uint64_t v) {
-  const uint32_t l = (uint32_t)v;
-  const uint32_t old = atomicAdd(lo, l);
-  const uint32_t h = (uint32_t)(v >> 32) + (old + l < old ? 1u : 0u);
-  if (h) atomicAdd(hi, h);
-}
-
 struct SmemSink {
   uint32_t *tkey, *tcnt, *tminh, *tmaxh;
   uint32_t *tl, *tm;  // low and middle 32-bit words of the slot's sum
@@ -127,7 +119,12 @@ struct SmemSink {
     if (en) atomicAdd(&en[act], 1u);
     else atomicAdd(&a->g_end[act], 1ull);
   }
-  __device__ __forceinline__ void hash_add(uint32_t c, uint64_t v) { smem_add64(&hl[c], &hh[c], v); }
+  // The case hash is two independent 32-bit wrap-around sums (low and high
+  // words of the event terms), so each term is two fire-and-forget adds.
+  __device__ __forceinline__ void hash_add(uint32_t c, uint64_t v) {
+    atomicAdd(&hl[c], (uint32_t)v);
+    atomicAdd(&hh[c], (uint32_t)(v >> 32));
+  }
 };
 
 struct GlobalSink {
@@ -141,7 +138,9 @@ struct GlobalSink {
   __device__ __forceinline__ void start(uint32_t act) { atomicAdd(&a->g_start[act], 1ull); }
   __device__ __forceinline__ void end(uint32_t act) { atomicAdd(&a->g_end[act], 1ull); }
   __device__ __forceinline__ void hash_add(uint32_t c, uint64_t v) {
-    atomicAdd((unsigned long long *)&a->hash[slot_base + c], (unsigned long long)v);
+    uint32_t *h = reinterpret_cast<uint32_t *>(&a->hash[slot_base + c]);  // little endian: low word first
+    atomicAdd(&h[0], (uint32_t)v);
+    atomicAdd(&h[1], (uint32_t)(v >> 32));
   }
 };
 
@@ -276,6 +275,7 @@ struct SegShared {
   uint16_t *idx;
   uint32_t *ccnt, *cstart;
   uint32_t *hl, *hh;
+  uint8_t *flg;  // per case: events out of (timestamp, row) order
 };
 
 // Processes the n_r records now in S.rec, all of bucket b with case slots in
@@ -293,6 +293,7 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   for (int c = tid; c < ncl; c += kSegThreads) {
     S.hl[c] = 0;
     S.hh[c] = 0;
+    S.flg[c] = 0;
   }
   __syncthreads();
   // stable counting sort by case slot
@@ -342,26 +343,29 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   }
   __syncthreads();
   // flag the cases whose events are out of (timestamp, row) order; hw is free
-  uint16_t *unsorted = hw;
-  for (int c = tid; c < ncl; c += kSegThreads) unsorted[c] = 0;
-  __syncthreads();
+  // (S.flg was cleared with the per-case sums at the start of the range)
+  bool any = false;
   for (uint32_t p = tid + 1; p < n_r; p += kSegThreads) {
     const uint4 x = S.rec[S.idx[p - 1]], y = S.rec[S.idx[p]];
     const uint32_t cx = (x.x >> a.act_bits) & cmask, cy = (y.x >> a.act_bits) & cmask;
-    if (cx == cy && !kr_less(ts_key(rec_ts(x)), x.y, ts_key(rec_ts(y)), y.y)) unsorted[cy] = 1;
+    if (cx == cy && !kr_less(ts_key(rec_ts(x)), x.y, ts_key(rec_ts(y)), y.y)) {
+      S.flg[cy] = 1;
+      any = true;
+    }
   }
-  __syncthreads();
-  for (uint32_t c = c_a + warp; c < c_b; c += kSegWarps) {
-    if (!unsorted[c]) continue;
-    const uint32_t s0 = S.cstart[c], L = S.ccnt[c];
-    if (L <= 32) sort_case<1>(S.rec, S.idx, s0, L);
-    else if (L <= 64) sort_case<2>(S.rec, S.idx, s0, L);
-    else if (L <= 128) sort_case<4>(S.rec, S.idx, s0, L);
-    else if (L <= 256) sort_case<8>(S.rec, S.idx, s0, L);
-    else sort_case<16>(S.rec, S.idx, s0, L);
-    ++n_sorted;
+  if (__syncthreads_or(any)) {
+    for (uint32_t c = c_a + warp; c < c_b; c += kSegWarps) {
+      if (!S.flg[c]) continue;
+      const uint32_t s0 = S.cstart[c], L = S.ccnt[c];
+      if (L <= 32) sort_case<1>(S.rec, S.idx, s0, L);
+      else if (L <= 64) sort_case<2>(S.rec, S.idx, s0, L);
+      else if (L <= 128) sort_case<4>(S.rec, S.idx, s0, L);
+      else if (L <= 256) sort_case<8>(S.rec, S.idx, s0, L);
+      else sort_case<16>(S.rec, S.idx, s0, L);
+      ++n_sorted;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // every ordered position, 32 per warp at a time
   const uint64_t slot_base = (uint64_t)b << a.clb;
   {
@@ -406,6 +410,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   S.cstart = reinterpret_cast<uint32_t *>(smem + L.cstart);
   S.hl = reinterpret_cast<uint32_t *>(smem + L.chash);
   S.hh = S.hl + ncl;
+  S.flg = smem + L.flg;
   uint32_t *tl = reinterpret_cast<uint32_t *>(smem + L.tlo);
   uint32_t *tm = tl + a.tbl_slots;
   uint16_t *hw = reinterpret_cast<uint16_t *>(smem + L.hw);

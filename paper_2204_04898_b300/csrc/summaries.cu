@@ -86,7 +86,13 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
     } else {
       h = 0;
       const int32_t *q = a.act_s + a.off[s];
-      for (uint32_t k = 0; k < L; ++k) h += event_hash((uint32_t)q[k], k, round);
+      uint32_t hl = 0, hh = 0;  // same combination as the segment pass: two 32-bit sums
+      for (uint32_t k = 0; k < L; ++k) {
+        const uint64_t t = event_hash((uint32_t)q[k], k, round);
+        hl += (uint32_t)t;
+        hh += (uint32_t)(t >> 32);
+      }
+      h = ((uint64_t)hh << 32) | hl;
     }
     const unsigned long long key = variant_key(h, L, a.bits);
     uint32_t g = (uint32_t)fmix64(key ^ round) & a.tmask;
