@@ -38,10 +38,38 @@ FALLBACK_HBM_GBS = 6400.0
 # in case-grouped order (12 B/event), read them back (12 B/event), write the
 # case-to-variant id (4 B/case). Split by the kernel that does each part.
 ALG_BYTES = {
-    "bucket_scatter": (28.0, 0.0),  # (per event, per case)
+    "partition": (28.0, 0.0),  # (per event, per case), over the kernel's launches in one step
+    "bucket_scatter": (28.0, 0.0),
     "segment": (12.0, 0.0),
     "variants": (0.0, 4.0),
 }
+# Source file of each timed kernel: a DRAM-traffic figure recorded under
+# profiles/ is used only while this file is unchanged since the capture.
+KERNEL_SOURCE = {"segment": "segment.cu", "partition": "format.cu", "bucket_scatter": "format.cu",
+                 "variants": "summaries.cu"}
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary
+    (profiles/<kernel>_<workload>.md, lines 'source_sha256: ...' and
+    'dram_bytes_per_launch: ...'), or None if absent or stale."""
+    import hashlib
+    src = KERNEL_SOURCE.get(kernel)
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not src or not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2204_04898_b300", "csrc", src), "rb").read()).hexdigest()
+    fields = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip().lstrip("-* `").rstrip("`")] = v.strip().strip("`")
+    if fields.get("source_sha256") != sha:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def parse():
@@ -306,7 +334,7 @@ def main():
                    "l2": "inputs (16 B/event, %.1f GB) larger than L2; no flush" % (16 * N / 1e9),
                    "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": recorded_traffic(dom, spec.name), "peak_kind": peak_kind,
                      "alg_bytes_per_launch": per_launch, "launch_ms": launch_ms,
                      "path_alg_bytes": b_alg, "path_frac": b_alg / (ms_max * 1e-3) / 1e9 / peak},
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kt.items(), key=lambda x: -x[1][1])},

@@ -767,10 +767,16 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           pa.nbins = 1u << fbits;
           pa.rec_in = tmp;
           pa.rec_out = L->rec.p;
+          pa.mat = mat;
+          pa.p_ctas = p_ctas;
+          // split coarse buckets at row-chunk boundaries into about four
+          // waves of units, so that no short last wave idles most SMs
+          pa.splits = (int)std::max<int64_t>(
+              1, std::min<int64_t>(p_ctas, (8 * (int64_t)c->num_sms + nc - 1) / (int64_t)nc));
           {
             KTime t(c, "partition");
             c->launches++;
-            if (launch_partition(2, pa, nc, c->stream) != cudaSuccess) {
+            if (launch_partition(2, pa, nc * (unsigned)pa.splits, c->stream) != cudaSuccess) {
               set_error("launch of k_partition<2> failed: %s", cudaGetErrorString(cudaGetLastError()));
               fail(PM4G_ECUDA);
               break;

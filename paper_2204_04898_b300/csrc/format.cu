@@ -277,11 +277,17 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     i1 = (uint32_t)min(a.n, (int64_t)i0 + a.chunk);
     for (uint32_t d = tid; d < nbins; d += kPartThreads) cur[d] = a.cur1[(int64_t)blockIdx.x * nbins + d];
   } else {
-    const uint32_t b0 = blockIdx.x << a.fbits;
-    const uint32_t b1 = min(a.nb, b0 + (1u << a.fbits));
-    i0 = a.bucket_off[b0];
-    i1 = a.bucket_off[b1];
-    for (uint32_t d = tid; d < nbins; d += kPartThreads) cur[d] = b0 + d < a.nb ? a.bucket_off[b0 + d] : 0u;
+    // unit (C, j): the part of coarse bucket C that level 1 wrote from row
+    // chunks [p0, p1); its records of final bucket b go after those that
+    // chunks before p0 contributed to b (the CTA-major prefix in mat)
+    const uint32_t C = blockIdx.x / a.splits, j = blockIdx.x % a.splits;
+    const int p0 = (int)((int64_t)j * a.p_ctas / a.splits), p1 = (int)((int64_t)(j + 1) * a.p_ctas / a.splits);
+    const uint32_t nc = (a.nb + (1u << a.fbits) - 1) >> a.fbits;
+    const uint32_t b0 = C << a.fbits;
+    i0 = a.cur1[(int64_t)p0 * nc + C];
+    i1 = p1 < a.p_ctas ? a.cur1[(int64_t)p1 * nc + C] : a.bucket_off[min(a.nb, b0 + (1u << a.fbits))];
+    for (uint32_t d = tid; d < nbins; d += kPartThreads)
+      cur[d] = b0 + d < a.nb ? a.bucket_off[b0 + d] + a.mat[(int64_t)p0 * a.nb + b0 + d] : 0u;
   }
   for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) wh[j] = 0;
   __syncthreads();

@@ -45,7 +45,10 @@ struct PartArgs {
   const uint4 *rec_in;
   const uint32_t *bucket_off;
   uint32_t nb;
-  const uint32_t *cur1;
+  const uint32_t *cur1;      // level 1 cursors: CTA-major coarse prefixes plus coarse starts
+  const uint32_t *mat;       // level 2: CTA-major prefixes of the final-bucket counts
+  int p_ctas;                // row chunks of level 1
+  int splits;                // level 2: units per coarse bucket
   uint4 *rec_out;
   uint32_t *err_flags;
 };
