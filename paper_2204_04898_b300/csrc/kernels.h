@@ -113,7 +113,7 @@ struct SegSmem {
   size_t rec, tlo, chash, idx, hw, rng, flg, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;
 };
 
-constexpr int kSegThreads = 512;
+constexpr int kSegThreads = 1024;
 constexpr int kSegWarps = kSegThreads / 32;
 
 __host__ __device__ inline size_t seg_align(size_t x, size_t a) { return (x + a - 1) / a * a; }

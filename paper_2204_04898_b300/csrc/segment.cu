@@ -4,7 +4,9 @@
 // DFG, start/end activities and the per-case variant features follow from
 // consecutive events of a case).
 //
-// One persistent CTA per SM takes buckets from a work counter. For a bucket it
+// One persistent 32-warp CTA per SM takes buckets from a work counter (the
+// register budget is 64 per thread, which the sort paths below respect). For a
+// bucket it
 //  1. loads the bucket's 16-byte records into shared memory (a bucket larger
 //     than the on-chip capacity is processed in case-slot ranges that fit,
 //     streaming the bucket once per range);
@@ -12,7 +14,8 @@
 //     contiguous record ranges, then placement in record order, so each case
 //     keeps the order the scatter wrote, which is row order for most cases;
 //  3. flags every case whose events are not in (timestamp, row) order and
-//     sorts only those, one warp per case (warp bitonic sort);
+//     sorts only those, one warp per case (warp bitonic sort in registers of
+//     up to 128 events; longer cases merge sorted 128-event chunks by rank);
 //  4. walks the ordered positions 32 at a time per warp: writes the activity
 //     sequence, counts start/end activities, forms the directly-follows pair
 //     (a_i, a_{i+1}) with duration ts_{i+1} - ts_i and aggregates it, and sums
@@ -270,6 +273,48 @@ __device__ __forceinline__ void sort_case(const uint4 *rec_s, uint16_t *idx_s, u
   __syncwarp();
 }
 
+// Cases of 129..kMaxCaseSmem events: each 128-event chunk is sorted in
+// registers, then every element moves to its rank, which is its position in
+// its own chunk plus the number of smaller elements in each other chunk
+// (binary search; (timestamp, row) keys are unique because rows are). All
+// ranks are computed before any index is overwritten.
+constexpr int kLongPerLane = kMaxCaseSmem / 32;
+__device__ __forceinline__ void sort_long_case(const uint4 *rec_s, uint16_t *idx_s, uint32_t s0, uint32_t L) {
+  for (uint32_t c0 = 0; c0 < L; c0 += 128) sort_case<4>(rec_s, idx_s, s0 + c0, min(128u, L - c0));
+  const int lane = (int)lane_id();
+  uint32_t pk[kLongPerLane];  // index (low 16 bits) and its rank (high 16 bits)
+#pragma unroll
+  for (int e = 0; e < kLongPerLane; ++e) {
+    const uint32_t i = (uint32_t)(lane + 32 * e);
+    pk[e] = 0;
+    if (i < L) {
+      const uint32_t v = idx_s[s0 + i];
+      const uint4 r = rec_s[v];
+      const uint64_t key = ts_key(rec_ts(r));
+      const uint32_t own = i >> 7;
+      uint32_t rank = i & 127u;
+      for (uint32_t j = 0; j * 128 < L; ++j) {
+        if (j == own) continue;
+        const uint16_t *chunk = idx_s + s0 + j * 128;
+        uint32_t lo = 0, hi = min(128u, L - j * 128);
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          const uint4 q = rec_s[chunk[mid]];
+          if (kr_less(ts_key(rec_ts(q)), q.y, key, r.y)) lo = mid + 1;
+          else hi = mid;
+        }
+        rank += lo;
+      }
+      pk[e] = v | (rank << 16);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < kLongPerLane; ++e)
+    if ((uint32_t)(lane + 32 * e) < L) idx_s[s0 + (pk[e] >> 16)] = (uint16_t)(pk[e] & 0xFFFFu);
+  __syncwarp();
+}
+
 struct SegShared {
   uint4 *rec;
   uint16_t *idx;
@@ -360,8 +405,7 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
       if (L <= 32) sort_case<1>(S.rec, S.idx, s0, L);
       else if (L <= 64) sort_case<2>(S.rec, S.idx, s0, L);
       else if (L <= 128) sort_case<4>(S.rec, S.idx, s0, L);
-      else if (L <= 256) sort_case<8>(S.rec, S.idx, s0, L);
-      else sort_case<16>(S.rec, S.idx, s0, L);
+      else sort_long_case(S.rec, S.idx, s0, L);
       ++n_sorted;
     }
     __syncthreads();

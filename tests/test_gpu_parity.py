@@ -107,6 +107,24 @@ def test_long_cases_take_global_path(pm4g, ctx):
     check_log(pm4g, ctx, case, act, ts, 7)
 
 
+@pytest.mark.parametrize("ts_range", [8, 10**9])
+def test_on_chip_sort_lengths(pm4g, ctx, ts_range):
+    """Shuffled cases of every on-chip sort size class (1..32, ..64, ..128 in
+    registers; 129..512 merged from 128-event chunks), with timestamp ties
+    broken by row when the range is small."""
+    rng = np.random.default_rng(7)
+    base = np.array([1, 2, 31, 32, 33, 64, 65, 127, 128, 129, 130, 200, 255, 256, 257, 300, 383, 384, 385,
+                     450, 511, 512], np.int64)
+    lens = np.concatenate([base, rng.integers(100, 513, 60)])
+    case = np.repeat(rng.permutation(lens.size).astype(np.int32) * 5, lens)
+    n = case.size
+    p = rng.permutation(n)
+    case = case[p]
+    act = rng.integers(0, 11, n).astype(np.int32)
+    ts = rng.integers(-ts_range, ts_range, n).astype(np.int64)
+    check_log(pm4g, ctx, case, act, ts, 11)
+
+
 def test_forced_small_buckets(pm4g, ctx):
     """A tiny on-chip capacity sends most buckets down the global path."""
     pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TEST_BUCKET_CAP, 64)
