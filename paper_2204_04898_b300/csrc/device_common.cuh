@@ -39,6 +39,16 @@ __device__ __forceinline__ void st_evict_last(uint4 *p, uint4 v, uint64_t pol) {
                "r"(v.z), "r"(v.w), "l"(pol)
                : "memory");
 }
+// Asks the copy engine to bring [p, p + bytes) into L2 (a hint: nothing is
+// written, and the range lies inside an allocation). p must be 16-byte
+// aligned and bytes a multiple of 16; issued in 32 KB pieces.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  const char *c = static_cast<const char *>(p);
+  for (uint32_t o = 0; o < bytes; o += 32768u) {
+    const uint32_t sz = min(32768u, bytes - o);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + o), "r"(sz) : "memory");
+  }
+}
 __device__ __forceinline__ uint32_t rec_case_lo(uint4 r, int act_bits) { return r.x >> act_bits; }
 __device__ __forceinline__ uint32_t rec_act(uint4 r, uint32_t act_mask) { return r.x & act_mask; }
 __device__ __forceinline__ int64_t rec_ts(uint4 r) {

@@ -295,27 +295,46 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   const int shift1 = a.clb + a.fbits;
   bool bad = false;
   uint16_t *myh = wh + warp * nbins;
+  // The tile loop is software-pipelined: the loads of tile t + 1 are issued
+  // before the runs of tile t are written, so they are in flight meanwhile.
+  // Level 1 holds the raw columns (case id, activity, timestamp) in rec until
+  // the record is formed.
+  uint4 rec[kPartItems];
+  auto load_tile = [&](uint32_t base) {
+    const uint32_t wb = base + (uint32_t)warp * (32 * kPartItems) + lane;
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+      const uint32_t i = wb + r * 32;
+      if (i < i1) {
+        if (kLevel == 1) {
+          const uint64_t t = (uint64_t)__ldcs(a.ts + i);
+          rec[r] = make_uint4((uint32_t)__ldcs(a.case_id + i), (uint32_t)__ldcs(a.activity + i), (uint32_t)t,
+                              (uint32_t)(t >> 32));
+        } else {
+          rec[r] = __ldcs(a.rec_in + i);
+        }
+      }
+    }
+  };
+  if (i0 < i1) load_tile(i0);
   for (uint32_t base = i0; base < i1; base += kPartTile) {
-    uint4 rec[kPartItems];
     uint32_t dg[kPartItems];
     const uint32_t wbase = base + (uint32_t)warp * (32 * kPartItems) + lane;
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
       const uint32_t i = wbase + r * 32;
       dg[r] = 0xFFFFFFFFu;
-      rec[r] = make_uint4(0, 0, 0, 0);
       if (i < i1) {
         if (kLevel == 1) {
-          const uint32_t slot = (uint32_t)__ldcs(a.case_id + i) - (uint32_t)a.min_case;
-          uint32_t act = (uint32_t)__ldcs(a.activity + i);
+          const uint32_t slot = rec[r].x - (uint32_t)a.min_case;
+          uint32_t act = rec[r].y;
           if (act >= (uint32_t)a.n_act) {
             bad = true;
             act = 0;
           }
-          rec[r] = make_rec(slot & kSlotLoMask, act, a.act_bits, i, __ldcs(a.ts + i));
+          rec[r] = make_uint4(((slot & kSlotLoMask) << a.act_bits) | act, i, rec[r].z, rec[r].w);
           dg[r] = slot >> shift1;
         } else {
-          rec[r] = __ldcs(a.rec_in + i);
           dg[r] = ((rec[r].x >> a.act_bits) >> a.clb) & fmask;
         }
       }
@@ -363,6 +382,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
       }
     }
     __syncthreads();
+    if (base + kPartTile < i1) load_tile(base + kPartTile);
     // write the runs; clear the per-warp counts for the next tile meanwhile
     const uint32_t cnt = tst[nbins];
     for (uint32_t j = tid; j < cnt; j += kPartThreads) {

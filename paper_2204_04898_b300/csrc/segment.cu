@@ -488,13 +488,20 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
                 (uint32_t)__clz((uint32_t)a.tbl_slots) + 1u, a.tbl_mode,
                 a_s ? st : nullptr, a_s ? en : nullptr, S.hl, S.hh, &a};
   uint32_t n_sorted = 0;
+  // Buckets are claimed one ahead (misc[0] and misc[1] alternate between the
+  // current and the next claim): while a bucket is processed, lane 0 of the
+  // last warp claims the next one and starts moving its records into L2.
+  if (tid == 0) misc[0] = atomicAdd(a.work, 1u);
   __syncthreads();
 
-  for (;;) {
-    if (tid == 0) misc[0] = atomicAdd(a.work, 1u);
-    __syncthreads();
-    const uint32_t b = misc[0];
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t b = misc[it & 1];
     if (b >= a.nb) break;
+    if (tid == kSegThreads - 32) {
+      const uint32_t nx = atomicAdd(a.work, 1u);
+      misc[(it & 1) ^ 1] = nx;
+      if (nx < a.nb) prefetch_l2(a.rec + a.bucket_off[nx], (a.bucket_off[nx + 1] - a.bucket_off[nx]) * 16u);
+    }
     const uint32_t lo = a.bucket_off[b];
     const uint32_t n = a.bucket_off[b + 1] - lo;
     const uint4 *src = a.rec + lo;
