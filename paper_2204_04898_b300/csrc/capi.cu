@@ -195,7 +195,7 @@ static SegConfig seg_config(Ctx *c, int clb, int32_t A) {
   }
   const size_t fixed = seg_smem_layout(0, ncl, s.a_s, s.tbl_slots, s.tbl_mode).total + 64;
   int64_t cap = ((int64_t)c->smem_optin - (int64_t)fixed) / 18;
-  cap = std::min<int64_t>(cap, 65535);
+  cap = std::min<int64_t>(cap, std::min(65535, kSegThreads * kSegChunks));
   cap = cap / 32 * 32;
   if (c->test_bucket_cap > 0) cap = std::min<int64_t>(cap, c->test_bucket_cap);
   s.cap = (int)std::max<int64_t>(cap, 0);

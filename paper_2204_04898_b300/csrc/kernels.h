@@ -115,6 +115,7 @@ struct SegSmem {
 
 constexpr int kSegThreads = 1024;
 constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kSegChunks = 7;  // records a thread holds in registers: capacity <= kSegThreads * kSegChunks
 
 __host__ __device__ inline size_t seg_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -7,12 +7,14 @@
 // One persistent 32-warp CTA per SM takes buckets from a work counter (the
 // register budget is 64 per thread, which the sort paths below respect). For a
 // bucket it
-//  1. loads the bucket's 16-byte records into shared memory (a bucket larger
-//     than the on-chip capacity is processed in case-slot ranges that fit,
-//     streaming the bucket once per range);
-//  2. counting-sorts them by case slot, stably: per-warp counts over
-//     contiguous record ranges, then placement in record order, so each case
-//     keeps the order the scatter wrote, which is row order for most cases;
+//  1. loads the bucket's 16-byte records into registers, each warp a
+//     contiguous run of them (a bucket larger than the on-chip capacity is
+//     processed in case-slot ranges that fit, streaming the bucket once per
+//     range);
+//  2. counting-sorts them by case slot, stably: per-warp counts over the
+//     warps' runs, then each record goes from registers straight to its
+//     ordered position in shared memory, in record order, so each case keeps
+//     the order the scatter wrote, which is row order for most cases;
 //  3. flags every case whose events are not in (timestamp, row) order and
 //     sorts only those, one warp per case (warp bitonic sort in registers of
 //     up to 128 events; longer cases merge sorted 128-event chunks by rank);
@@ -323,17 +325,32 @@ struct SegShared {
   uint8_t *flg;  // per case: events out of (timestamp, row) order
 };
 
-// Processes the n_r records now in S.rec, all of bucket b with case slots in
-// [c_a, c_b); their ordered positions start at out_base in the bucketed log.
-// Returns false (having written nothing) if a case is too long to sort on chip.
+// Processes n_r records of bucket b, all with case slots in [c_a, c_b); their
+// ordered positions start at out_base in the bucketed log. The records are
+// read from global memory (src) or, when from_smem, from S.rec, where a case
+// range of an oversized bucket was compacted. Each warp holds a contiguous
+// run of them in registers while they are counted, and then writes each one
+// straight to its ordered position in S.rec, so every later step reads S.rec
+// in order. Returns false (having written nothing) if a case is too long to
+// sort on chip.
 template <bool kExport>
 __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared &S, uint16_t *hw, uint32_t *misc,
-                              uint32_t b, uint32_t n_r, uint32_t c_a, uint32_t c_b, int64_t out_base,
-                              uint32_t act_mask, uint32_t &n_sorted) {
+                              const uint4 *src, bool from_smem, uint32_t b, uint32_t n_r, uint32_t c_a,
+                              uint32_t c_b, int64_t out_base, uint32_t act_mask, uint32_t &n_sorted) {
   const int ncl = 1 << a.clb;
   const int hws = (ncl + 1) & ~1;  // per-warp row of 16-bit counts, 4-byte aligned
   const uint32_t cmask = (uint32_t)ncl - 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // warp w owns records [w_lo, w_hi), chunk k of it is w_lo + 32k + lane
+  const uint32_t per = ((n_r + kSegWarps - 1) / kSegWarps + 31) & ~31u;  // at most 32 * kSegChunks
+  const uint32_t w_lo = min(n_r, (uint32_t)warp * per), w_hi = min(n_r, w_lo + per);
+  uint4 r[kSegChunks];
+#pragma unroll
+  for (int k = 0; k < kSegChunks; ++k) {
+    const uint32_t i = w_lo + 32u * k + lane;
+    r[k] = make_uint4(0, 0, 0, 0);
+    if (i < w_hi) r[k] = from_smem ? S.rec[i] : __ldcs(src + i);
+  }
   for (int j = tid; j < kSegWarps * hws; j += kSegThreads) hw[j] = 0;
   for (int c = tid; c < ncl; c += kSegThreads) {
     S.hl[c] = 0;
@@ -342,18 +359,18 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   }
   __syncthreads();
   // stable counting sort by case slot
-  const uint32_t per = ((n_r + kSegWarps - 1) / kSegWarps + 31) & ~31u;
-  const uint32_t w_lo = min(n_r, (uint32_t)warp * per), w_hi = min(n_r, w_lo + per);
   uint16_t *myh = hw + warp * hws;
   // myh holds 16-bit counts, two per 32-bit word (no count reaches 2^16)
   uint32_t *myw = reinterpret_cast<uint32_t *>(myh);
-  for (uint32_t j = w_lo; j < w_hi; j += 32) {
-    const uint32_t i = j + lane;
-    const bool v = i < w_hi;
-    const uint32_t c = v ? ((S.rec[i].x >> a.act_bits) & cmask) : 0xFFFFFFFFu;
-    uint32_t run;
-    const uint32_t head = run_head(c, run);
-    if (v && (uint32_t)lane == head) atomicAdd(&myw[c >> 1], run << (16 * (c & 1)));
+#pragma unroll
+  for (int k = 0; k < kSegChunks; ++k) {
+    if (w_lo + 32u * k < w_hi) {
+      const bool v = w_lo + 32u * k + lane < w_hi;
+      const uint32_t c = v ? ((r[k].x >> a.act_bits) & cmask) : 0xFFFFFFFFu;
+      uint32_t run;
+      const uint32_t head = run_head(c, run);
+      if (v && (uint32_t)lane == head) atomicAdd(&myw[c >> 1], run << (16 * (c & 1)));
+    }
   }
   __syncthreads();
   {
@@ -375,30 +392,37 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
     if (tid == 0) S.cstart[ncl] = n_r;
     if (__syncthreads_or(tot > (uint32_t)kMaxCaseSmem)) return false;
   }
-  for (uint32_t j = w_lo; j < w_hi; j += 32) {
-    const uint32_t i = j + lane;
-    const bool v = i < w_hi;
-    const uint32_t c = v ? ((S.rec[i].x >> a.act_bits) & cmask) : 0xFFFFFFFFu;
-    uint32_t run;
-    const uint32_t head = run_head(c, run);
-    uint32_t base = 0;
-    if (v && (uint32_t)lane == head) base = (atomicAdd(&myw[c >> 1], run << (16 * (c & 1))) >> (16 * (c & 1))) & 0xFFFFu;
-    base = __shfl_sync(kFull, base, (int)head);
-    if (v) S.idx[base + ((uint32_t)lane - head)] = (uint16_t)i;
+#pragma unroll
+  for (int k = 0; k < kSegChunks; ++k) {
+    if (w_lo + 32u * k < w_hi) {
+      const bool v = w_lo + 32u * k + lane < w_hi;
+      const uint32_t c = v ? ((r[k].x >> a.act_bits) & cmask) : 0xFFFFFFFFu;
+      uint32_t run;
+      const uint32_t head = run_head(c, run);
+      uint32_t base = 0;
+      if (v && (uint32_t)lane == head)
+        base = (atomicAdd(&myw[c >> 1], run << (16 * (c & 1))) >> (16 * (c & 1))) & 0xFFFFu;
+      base = __shfl_sync(kFull, base, (int)head);
+      if (v) S.rec[base + ((uint32_t)lane - head)] = r[k];
+    }
   }
   __syncthreads();
-  // flag the cases whose events are out of (timestamp, row) order; hw is free
-  // (S.flg was cleared with the per-case sums at the start of the range)
+  // flag the cases whose events are out of (timestamp, row) order (S.flg was
+  // cleared with the per-case sums at the start of the range)
   bool any = false;
   for (uint32_t p = tid + 1; p < n_r; p += kSegThreads) {
-    const uint4 x = S.rec[S.idx[p - 1]], y = S.rec[S.idx[p]];
+    const uint4 x = S.rec[p - 1], y = S.rec[p];
     const uint32_t cx = (x.x >> a.act_bits) & cmask, cy = (y.x >> a.act_bits) & cmask;
     if (cx == cy && !kr_less(ts_key(rec_ts(x)), x.y, ts_key(rec_ts(y)), y.y)) {
       S.flg[cy] = 1;
       any = true;
     }
   }
+  const uint64_t slot_base = (uint64_t)b << a.clb;
   if (__syncthreads_or(any)) {
+    // the flagged cases are ordered through the index S.idx (identity elsewhere)
+    for (uint32_t p = tid; p < n_r; p += kSegThreads) S.idx[p] = (uint16_t)p;
+    __syncthreads();
     for (uint32_t c = c_a + warp; c < c_b; c += kSegWarps) {
       if (!S.flg[c]) continue;
       const uint32_t s0 = S.cstart[c], L = S.ccnt[c];
@@ -409,17 +433,18 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
       ++n_sorted;
     }
     __syncthreads();
-  }
-  // every ordered position, 32 per warp at a time
-  const uint64_t slot_base = (uint64_t)b << a.clb;
-  {
     auto fetch = [&](int p) { return S.rec[S.idx[p]]; };
+    for (uint32_t base = (uint32_t)warp * 32; base < n_r; base += kSegThreads)
+      process_warp_tile<kExport>(a, sink, fetch, S.cstart, (int)(base + lane), (int)n_r, out_base, slot_base,
+                                 act_mask);
+  } else {
+    auto fetch = [&](int p) { return S.rec[p]; };
     for (uint32_t base = (uint32_t)warp * 32; base < n_r; base += kSegThreads)
       process_warp_tile<kExport>(a, sink, fetch, S.cstart, (int)(base + lane), (int)n_r, out_base, slot_base,
                                  act_mask);
   }
   __syncthreads();
-  // per-case outputs
+  // per-case outputs (the first event of a sorted case is found through S.idx)
   if (!kExport) {
     uint32_t present = 0;
     for (uint32_t c = c_a + tid; c < c_b; c += kSegThreads) {
@@ -428,7 +453,10 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
         const uint32_t Lc = S.ccnt[c];
         a.len[slot] = Lc;
         a.hash[slot] = Lc ? (((uint64_t)S.hh[c] << 32) | S.hl[c]) : 0ull;
-        if (a.cattr) a.cattr[slot] = (Lc && a.attr_in) ? a.attr_in[S.rec[S.idx[S.cstart[c]]].y] : 0;
+        if (a.cattr) {
+          const uint32_t q = S.cstart[c];
+          a.cattr[slot] = (Lc && a.attr_in) ? a.attr_in[S.rec[S.flg[c] ? S.idx[q] : q].y] : 0;
+        }
         present += Lc ? 1u : 0u;
       }
     }
@@ -507,16 +535,8 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
     const uint4 *src = a.rec + lo;
     bool ok = true;
     if (n <= (uint32_t)a.cap) {
-      for (uint32_t i0 = tid; i0 < n; i0 += 4 * kSegThreads) {
-        uint4 v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (i0 + k * kSegThreads < n) v[k] = __ldcs(src + i0 + k * kSegThreads);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (i0 + k * kSegThreads < n) S.rec[i0 + k * kSegThreads] = v[k];
-      }
-      ok = process_range<kExport>(a, sink, S, hw, misc, b, n, 0, (uint32_t)ncl, (int64_t)lo, act_mask, n_sorted);
+      ok = process_range<kExport>(a, sink, S, hw, misc, src, false, b, n, 0, (uint32_t)ncl, (int64_t)lo, act_mask,
+                                  n_sorted);
     } else {
       // too large for one pass: split the case slots into ranges that fit
       for (int c = tid; c < ncl; c += kSegThreads) S.ccnt[c] = 0;
@@ -564,8 +584,8 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
           cnt += tot;
         }
         __syncthreads();
-        ok = process_range<kExport>(a, sink, S, hw, misc, b, cnt, c_a, c_b, (int64_t)lo + pos_a, act_mask,
-                                    n_sorted);
+        ok = process_range<kExport>(a, sink, S, hw, misc, src, true, b, cnt, c_a, c_b, (int64_t)lo + pos_a,
+                                    act_mask, n_sorted);
       }
     }
     if (!ok) {
