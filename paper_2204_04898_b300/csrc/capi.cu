@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "device_common.cuh"
@@ -40,24 +41,64 @@ int check_launch(Ctx *c, const char *what) {
   return PM4G_OK;
 }
 
+// Without a caller-supplied allocator, device memory comes from the stream-
+// ordered pool, and blocks the context frees are kept in its cache: a later
+// request of the same rounded size reuses one at once. Reuse is safe because
+// every kernel and copy of the context runs on its one stream, in order. The
+// cache is emptied when the pool cannot satisfy a request, and when it would
+// exceed its limit the freed block goes back to the pool.
+static size_t cache_round(size_t bytes) {
+  if (bytes <= 4096) return (bytes + 255) & ~(size_t)255;
+  size_t p2 = 4096;
+  while (p2 < bytes) p2 <<= 1;
+  const size_t g = p2 >> 4;  // sizes round up by at most 1/16
+  return (bytes + g - 1) / g * g;
+}
+
+static void cache_flush(Ctx *c) {
+  for (auto &kv : c->cache) cudaFreeAsync(kv.second, c->stream);
+  c->cache.clear();
+  c->cached_bytes = 0;
+}
+
 void *dalloc(Ctx *c, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (c->has_alloc) return c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+  const size_t key = cache_round(bytes);
+  auto it = c->cache.find(key);
+  if (it != c->cache.end()) {
+    void *p = it->second;
+    c->cache.erase(it);
+    c->cached_bytes -= key;
+    return p;
+  }
   void *p = nullptr;
-  if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+  if (cudaMallocAsync(&p, key, c->stream) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    if (c->cache.empty()) return nullptr;
+    cache_flush(c);
+    if (cudaMallocAsync(&p, key, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
   }
   return p;
 }
 
 void dfree(Ctx *c, void *p, size_t bytes) {
   if (!p) return;
+  if (bytes == 0) bytes = 16;
   if (c->has_alloc) {
     c->alloc.free(p, bytes, (void *)c->stream, c->alloc.user);
     return;
   }
-  cudaFreeAsync(p, c->stream);
+  const size_t key = cache_round(bytes);
+  if (c->cached_bytes + key <= c->cache_limit) {
+    c->cache.emplace(key, p);
+    c->cached_bytes += key;
+  } else {
+    cudaFreeAsync(p, c->stream);
+  }
 }
 
 static cudaEvent_t get_event(Ctx *c) {
@@ -166,11 +207,74 @@ static void release_log(pm4g_log *L) {
   delete L;
 }
 
+// Pinned host staging owned by the context (grown on demand): device-to-host
+// copies land there asynchronously, so a batch of them costs one
+// synchronisation; the bytes then move to their destinations on the host.
+static char *pinned(Ctx *c, size_t bytes) {
+  if (bytes <= c->pin_bytes) return (char *)c->pin;
+  if (c->pin) {
+    cudaStreamSynchronize(c->stream);
+    cudaFreeHost(c->pin);
+    c->pin = nullptr;
+    c->pin_bytes = 0;
+  }
+  size_t want = (size_t)1 << 20;
+  while (want < bytes) want <<= 1;
+  if (cudaHostAlloc(&c->pin, want, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    c->pin = nullptr;
+    return nullptr;
+  }
+  c->pin_bytes = want;
+  return (char *)c->pin;
+}
+
+// A batch of device-to-host copies through the staging area. The caller
+// states an upper bound of the batch's bytes (each copy adds up to 15 bytes of
+// alignment) before the first add.
+struct D2HBatch {
+  Ctx *c;
+  char *base = nullptr;
+  size_t cap = 0, used = 0;
+  int st = PM4G_OK;
+  std::vector<std::tuple<void *, size_t, size_t>> items;
+  D2HBatch(Ctx *ctx, size_t bound) : c(ctx), cap(bound) {
+    base = pinned(c, std::max<size_t>(bound, 16));
+    if (!base) {
+      set_error("out of pinned host memory for results");
+      st = PM4G_ENOMEM;
+    }
+  }
+  void add(void *dst, const void *src, size_t bytes) {
+    if (st != PM4G_OK || bytes == 0) return;
+    used = (used + 15) & ~(size_t)15;
+    if (used + bytes > cap) {
+      set_error("internal: result staging bound exceeded");
+      st = PM4G_ECUDA;
+      return;
+    }
+    const cudaError_t e = cudaMemcpyAsync(base + used, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) {
+      set_error("device-to-host copy failed: %s", cudaGetErrorString(e));
+      st = PM4G_ECUDA;
+      return;
+    }
+    items.emplace_back(dst, used, bytes);
+    used += bytes;
+  }
+  int finish() {
+    if (st != PM4G_OK) return st;
+    PM4G_CK(cudaStreamSynchronize(c->stream));
+    for (auto &it : items) memcpy(std::get<0>(it), base + std::get<1>(it), std::get<2>(it));
+    return PM4G_OK;
+  }
+};
+
 static int d2h(Ctx *c, void *dst, const void *src, size_t bytes) {
   if (!bytes) return PM4G_OK;
-  PM4G_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
-  PM4G_CK(cudaStreamSynchronize(c->stream));
-  return PM4G_OK;
+  D2HBatch b(c, bytes);
+  b.add(dst, src, bytes);
+  return b.finish();
 }
 
 // ---------------------------------------------------------------------------
@@ -433,6 +537,11 @@ int pm4g_ctx_create(pm4g_ctx **out, int device, void *cuda_stream, const pm4g_al
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
   }
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) c->cache_limit = tot / 2;
+    cudaGetLastError();
+  }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   *out = c;
@@ -448,6 +557,9 @@ int pm4g_ctx_destroy(pm4g_ctx *c) {
     cudaEventDestroy(p.b);
   }
   for (auto e : c->free_events) cudaEventDestroy(e);
+  cache_flush(c);
+  cudaStreamSynchronize(c->stream);
+  if (c->pin) cudaFreeHost(c->pin);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return PM4G_OK;
@@ -712,7 +824,7 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         }
         KTime t(c, "scan");
         const int64_t k = (int64_t)p_ctas * nc;
-        k_coarse_counts<<<(unsigned)((k + 255) / 256), 256, 0, c->stream>>>(mat, L->nb, p_ctas, fbits, nc, mat1);
+        k_coarse_counts<<<(unsigned)((k * 32 + 255) / 256), 256, 0, c->stream>>>(mat, L->nb, p_ctas, fbits, nc, mat1);
         if (fail(check_launch(c, "k_coarse_counts"))) break;
       }
       {
@@ -940,18 +1052,18 @@ static int ensure_edges(pm4g_log *L) {
   L->h_start.resize(A);
   L->h_end.resize(A);
   L->h_freq.resize(A);
-  cudaStream_t s = c->stream;
-  PM4G_CK(cudaMemcpyAsync(L->e_src.data(), src, E * 4, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->e_dst.data(), dst, E * 4, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->e_cnt.data(), o[0], E * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->e_lo.data(), o[1], E * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->e_hi.data(), o[2], E * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->e_min.data(), o[3], E * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->e_max.data(), o[4], E * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->h_start.data(), L->ends.p, A * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->h_end.data(), L->ends.p + A, A * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(L->h_freq.data(), freq, A * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaStreamSynchronize(s));
+  D2HBatch hb(c, (size_t)E * 48 + (size_t)A * 24 + 10 * 16);
+  hb.add(L->e_src.data(), src, E * 4);
+  hb.add(L->e_dst.data(), dst, E * 4);
+  hb.add(L->e_cnt.data(), o[0], E * 8);
+  hb.add(L->e_lo.data(), o[1], E * 8);
+  hb.add(L->e_hi.data(), o[2], E * 8);
+  hb.add(L->e_min.data(), o[3], E * 8);
+  hb.add(L->e_max.data(), o[4], E * 8);
+  hb.add(L->h_start.data(), L->ends.p, A * 8);
+  hb.add(L->h_end.data(), L->ends.p + A, A * 8);
+  hb.add(L->h_freq.data(), freq, A * 8);
+  PM4G_TRY(hb.finish());
   L->edges_ready = true;
   return PM4G_OK;
 }
@@ -1218,11 +1330,13 @@ int pm4g_variants(pm4g_log *L, int64_t top_k, uint32_t flags, pm4g_variants_t *o
     return PM4G_ENOMEM;
   }
   cudaStream_t s = c->stream;
-  PM4G_CK(cudaMemcpyAsync(out->count, oc, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(out->min_case, om, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(hoff.data(), oo, ((size_t)k + 1) * 4, cudaMemcpyDeviceToHost, s));
-  PM4G_CK(cudaMemcpyAsync(out->acts, oa, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
-  if (flags & PM4G_VARIANTS_CASES) {
+  const bool want_cases = (flags & PM4G_VARIANTS_CASES) != 0;
+  D2HBatch hb(c, (size_t)k * 16 + 4 + (size_t)total * 4 + (want_cases ? (size_t)L->C * 8 : 0) + 6 * 16);
+  hb.add(out->count, oc, (size_t)k * 8);
+  hb.add(out->min_case, om, (size_t)k * 4);
+  hb.add(hoff.data(), oo, ((size_t)k + 1) * 4);
+  hb.add(out->acts, oa, (size_t)total * 4);
+  if (want_cases) {
     const uint64_t R = L->R;
     uint32_t *pf = S.get<uint32_t>(R), *pp = S.get<uint32_t>(R + 1);
     int32_t *cid = S.get<int32_t>(L->C), *cv = S.get<int32_t>(L->C);
@@ -1240,10 +1354,16 @@ int pm4g_variants(pm4g_log *L, int64_t top_k, uint32_t flags, pm4g_variants_t *o
       pm4g_variants_free(out);
       return PM4G_ENOMEM;
     }
-    PM4G_CK(cudaMemcpyAsync(out->case_ids, cid, L->C * 4, cudaMemcpyDeviceToHost, s));
-    PM4G_CK(cudaMemcpyAsync(out->case_variant, cv, L->C * 4, cudaMemcpyDeviceToHost, s));
+    hb.add(out->case_ids, cid, L->C * 4);
+    hb.add(out->case_variant, cv, L->C * 4);
   }
-  PM4G_CK(cudaStreamSynchronize(s));
+  {
+    const int st = hb.finish();
+    if (st != PM4G_OK) {
+      pm4g_variants_free(out);
+      return st;
+    }
+  }
   for (size_t i = 0; i <= k; ++i) out->off[i] = hoff[i];
   return PM4G_OK;
 }

@@ -56,6 +56,14 @@ struct Ctx {
   std::map<std::string, std::pair<int64_t, double>> totals;
   int64_t live_logs = 0;
   int64_t launches = 0;  // kernels launched by this context
+  // pinned host staging for device-to-host results
+  void *pin = nullptr;
+  size_t pin_bytes = 0;
+  // device blocks freed by this context, kept for reuse in stream order
+  // (rounded size -> blocks); every kernel of the context runs on its stream
+  std::multimap<size_t, void *> cache;
+  size_t cached_bytes = 0;
+  size_t cache_limit = 0;
 };
 
 // Device memory through the context's allocator (stream ordered).

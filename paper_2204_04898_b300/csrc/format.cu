@@ -108,15 +108,30 @@ __global__ void __launch_bounds__(256) k_bucket_colprefix(uint32_t *__restrict__
   const uint32_t b = blockIdx.x * 32 + lane;
   const int per = (p_ctas + 7) / 8;
   const int p0 = min(p_ctas, (int)w * per), p1 = min(p_ctas, p0 + per);
+  // the rows are independent loads: unrolled so that many are in flight
   uint32_t s = 0;
-  if (b < nb)
-    for (int p = p0; p < p1; ++p) s += mat[(int64_t)p * nb + b];
+  if (b < nb) {
+#pragma unroll 8
+    for (int p = p0; p < p1; ++p) s += __ldcg(mat + (int64_t)p * nb + b);
+  }
   s_part[w][lane] = s;
   __syncthreads();
   uint32_t acc = 0;
   for (uint32_t ww = 0; ww < w; ++ww) acc += s_part[ww][lane];
   if (b < nb) {
-    for (int p = p0; p < p1; ++p) {
+    constexpr int kU = 8;
+    int p = p0;
+    for (; p + kU <= p1; p += kU) {
+      uint32_t v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) v[u] = __ldcg(mat + (int64_t)(p + u) * nb + b);
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        mat[(int64_t)(p + u) * nb + b] = acc;
+        acc += v[u];
+      }
+    }
+    for (; p < p1; ++p) {
       uint32_t *q = mat + (int64_t)p * nb + b;
       const uint32_t v = *q;
       *q = acc;
@@ -414,16 +429,20 @@ cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaSt
 
 // Coarse count matrix: mat1[p][C] = sum of mat[p][b] over the final buckets b
 // of coarse bucket C.
+// One warp per (p, C): the warp reads the 2^fbits counts coalesced and sums
+// them with a warp reduction.
 __global__ void k_coarse_counts(const uint32_t *__restrict__ mat, uint32_t nb, int p_ctas, int fbits, uint32_t nc,
                                 uint32_t *__restrict__ mat1) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (int64_t)p_ctas * nc) return;
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (k >= (int64_t)p_ctas * nc) return;  // warp-uniform
   const int64_t p = k / nc;
   const uint32_t C = (uint32_t)(k % nc);
   const uint32_t b0 = C << fbits, b1 = min(nb, b0 + (1u << fbits));
   uint32_t s = 0;
-  for (uint32_t b = b0; b < b1; ++b) s += mat[p * nb + b];
-  mat1[p * nc + C] = s;
+  for (uint32_t b = b0 + lane; b < b1; b += 32) s += __ldcg(mat + p * nb + b);
+  s = __reduce_add_sync(0xFFFFFFFFu, s);
+  if (lane == 0) mat1[p * nc + C] = s;
 }
 
 // Adds the coarse bucket's first position to every CTA's prefix.
