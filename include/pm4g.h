@@ -201,6 +201,53 @@ typedef struct {
 } pm4g_filter_spec;
 int pm4g_filter(pm4g_log *log, const pm4g_filter_spec *spec, pm4g_log **out);
 
+/* Batched drill-down (Section 1, drill-down; Section 3, filters then the
+ * frequency and performance DFG): for each of n_sub sub-logs, the results that
+ * pm4g_filter(log, spec_i) followed by pm4g_perf_dfg and pm4g_start_end on the
+ * sub-log would give, computed in one pass over the resident log without
+ * forming the sub-logs.
+ *   Sub-log i: attribute values attr_vals[attr_off[i] .. attr_off[i+1]) (any
+ *   order, repeats allowed; none = no attribute filter), window [t_lo[i],
+ *   t_hi[i]] and mode[i] (PM4G_TW_*), as in pm4g_filter_spec. All spec arrays
+ *   are host arrays; attr_off has n_sub + 1 entries, attr_off[0] = 0 and
+ *   non-decreasing. A log loaded without case_attr accepts only empty lists.
+ * Results (host arrays owned by the library, freed with pm4g_batch_dfg_free):
+ *   n_events[i], n_cases[i]: size of sub-log i;
+ *   edge_off[n_sub + 1]: sub-log i's edges are rows edge_off[i] ..
+ *   edge_off[i+1] of src, dst, count, sum_lo, sum_hi, min, max, mean, in
+ *   ascending (src, dst) order, with pm4g_perf_dfg's meaning;
+ *   start, end, freq: n_sub x n_activities, row i for sub-log i.
+ * Errors: PM4G_EINVAL for a malformed spec (n_sub < 0, bad offsets or mode,
+ * attribute lists on a log without case_attr), PM4G_ENOMEM, PM4G_ECUDA. */
+typedef struct {
+  int32_t n_sub;
+  const int64_t *attr_off;
+  const int32_t *attr_vals;
+  const int64_t *t_lo;
+  const int64_t *t_hi;
+  const int32_t *mode;
+} pm4g_batch_spec;
+typedef struct {
+  int32_t n_sub;
+  int32_t n_activities;
+  int64_t *n_events;  /* [n_sub] */
+  int64_t *n_cases;   /* [n_sub] */
+  int64_t *edge_off;  /* [n_sub + 1] */
+  int32_t *src;
+  int32_t *dst;
+  uint64_t *count;
+  uint64_t *sum_lo;
+  uint64_t *sum_hi;
+  uint64_t *min;
+  uint64_t *max;
+  double *mean;
+  uint64_t *start;    /* [n_sub * n_activities] */
+  uint64_t *end;
+  uint64_t *freq;
+} pm4g_batch_dfg_t;
+int pm4g_batch_dfg(pm4g_log *log, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out);
+int pm4g_batch_dfg_free(pm4g_batch_dfg_t *res);
+
 /* Allocation-free frequency/performance DFG and start/end counts of a small
  * log. The paper has no counterpart: this serves callers that cannot allocate
  * device memory when they need the summary (code running under CUDA graph

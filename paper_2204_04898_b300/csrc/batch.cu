@@ -1,0 +1,665 @@
+// Batched drill-down (Section 1: drill-down into sub-logs; Section 3: the
+// attribute and timestamp filters followed by the frequency and performance
+// DFG and the start/end activities).
+//
+// A sub-log keeps the cases whose attribute is in its set and, by its window
+// mode, the events (EVENTS) or whole cases (CONTAINED, INTERSECTING) that meet
+// its window. A case's kept events are a contiguous run of its events in
+// (timestamp, row) order, because the window is a closed timestamp interval.
+// So the sub-log's directly-follows pairs are exactly the resident log's pairs
+// whose two events are both kept, and every sub-log result can be computed
+// from the resident formatted log without forming the sub-log.
+//
+// The resident log gets a drill-down index once: timestamps in formatted
+// order (ts_s; activities are act_s), case offsets, the present cases ordered
+// by (attribute, slot) with event prefixes, the distinct attribute values with
+// their case ranges (host copy), and the map from a pair (a, b) to the index
+// of edge (a, b) among the resident log's edges (any sub-log edge is one).
+//
+// A call plans work items on the host: each sub-log becomes one or more items,
+// an item being a list of case ranges of the attribute order with at most
+// about W events; items run largest first. One persistent CTA per SM takes
+// items from a counter. For an item it aggregates the pairs of its cases in a
+// shared-memory table keyed by edge index (the segment pass's table, hashed),
+// counts start/end activities in shared memory, and at the end of the item
+// adds its table and counts to the sub-log's dense accumulators (one row of
+// E entries per sub-log, E = the resident log's edge count). A compaction
+// then lists each sub-log's edges with a non-zero count in edge order, which
+// is (src, dst) order.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "device_common.cuh"
+#include "engine.h"
+#include "kernels.h"
+#include "sink.cuh"
+#include "variants.h"
+
+using namespace pm4g;
+
+namespace pm4g {
+namespace {
+
+constexpr int kBtThreads = 1024;
+constexpr int kBtWarps = kBtThreads / 32;
+constexpr int kBtSlots = 8192;  // shared edge table (hashed)
+
+struct BatchArgs {
+  const uint32_t *aslots;  // present slots in (attribute, slot) order
+  const uint32_t *off;     // first formatted position of each slot
+  const uint32_t *len;     // events of each slot
+  const int32_t *act_s;
+  const int64_t *ts_s;
+  const uint32_t *emap;  // A * A -> edge index
+  uint32_t n_act;
+  uint32_t n_edges;
+  const uint4 *items;   // {sub, first range, end range, 0}
+  uint32_t n_items;
+  const uint2 *ranges;  // [k0, k1) of aslots
+  uint32_t *work;
+  const int64_t *t_lo, *t_hi;
+  const int32_t *mode;
+  DfgTable acc;                   // each array: n_sub rows of n_edges
+  unsigned long long *start, *end;  // n_sub rows of n_act
+  unsigned long long *n_ev, *n_cs;  // n_sub
+};
+
+__host__ __device__ inline size_t bt_smem_bytes(uint32_t n_act) {
+  return (size_t)kBtSlots * 24 + (size_t)n_act * 8 + 64;
+}
+
+// Kept run [j0, j1) of one case of L events at formatted position o.
+__device__ __forceinline__ void kept_run(const BatchArgs &a, uint32_t o, uint32_t L, int mode, int64_t t_lo,
+                                         int64_t t_hi, uint32_t &j0, uint32_t &j1) {
+  j0 = 0;
+  j1 = L;
+  if (mode == PM4G_TW_NONE || L == 0) return;
+  if (mode == PM4G_TW_EVENTS) {
+    // timestamps are non-decreasing along the case: count those below t_lo
+    // and those at most t_hi
+    const int lane = (int)lane_id();
+    uint32_t below = 0, upto = 0;
+    for (uint32_t base = 0; base < L; base += 32) {
+      const uint32_t j = base + (uint32_t)lane;
+      const int64_t t = j < L ? a.ts_s[o + j] : 0;
+      below += __popc(__ballot_sync(kFull, j < L && t < t_lo));
+      upto += __popc(__ballot_sync(kFull, j < L && t <= t_hi));
+    }
+    j0 = below;
+    j1 = max(upto, below);
+    return;
+  }
+  const int64_t first = a.ts_s[o], last = a.ts_s[o + L - 1];
+  const bool keep = mode == PM4G_TW_CASES_CONTAINED ? (first >= t_lo && last <= t_hi)
+                                                    : (first <= t_hi && last >= t_lo);
+  if (!keep) j1 = 0;
+}
+
+__global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tl = reinterpret_cast<uint32_t *>(smem);
+  uint32_t *tm = tl + kBtSlots;
+  uint32_t *tkey = tm + kBtSlots;
+  uint32_t *tcnt = tkey + kBtSlots;
+  uint32_t *tminh = tcnt + kBtSlots;
+  uint32_t *tmaxh = tminh + kBtSlots;
+  uint32_t *st = tmaxh + kBtSlots;
+  uint32_t *en = st + a.n_act;
+  uint32_t *misc = en + a.n_act;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t A = a.n_act;
+  for (;;) {
+    if (tid == 0) misc[0] = atomicAdd(a.work, 1u);
+    for (int i = tid; i < kBtSlots; i += kBtThreads) {
+      tkey[i] = kEmptyKey;
+      tcnt[i] = 0;
+      tl[i] = 0;
+      tm[i] = 0;
+      tminh[i] = 0xFFFFFFFFu;
+      tmaxh[i] = 0;
+    }
+    for (uint32_t i = tid; i < A; i += kBtThreads) {
+      st[i] = 0;
+      en[i] = 0;
+    }
+    __syncthreads();
+    const uint32_t it = misc[0];
+    if (it >= a.n_items) break;
+    const uint4 item = a.items[it];
+    const uint32_t sub = item.x;
+    const int mode = a.mode[sub];
+    const int64_t t_lo = a.t_lo[sub], t_hi = a.t_hi[sub];
+    const uint64_t row = (uint64_t)sub * a.n_edges;
+    const DfgTable g{a.acc.cnt + row, a.acc.lo + row, a.acc.hi + row, a.acc.mn + row, a.acc.mx + row};
+    SmemSink sink{tkey, tcnt, tminh, tmaxh, tl, tm, (uint32_t)(kBtSlots - 1),
+                  (uint32_t)__clz((uint32_t)kBtSlots) + 1u, 1, st, en, nullptr, nullptr, g,
+                  a.start + (uint64_t)sub * A, a.end + (uint64_t)sub * A};
+    sink.probes = 16;
+    uint64_t ev = 0, cs = 0;
+    for (uint32_t r = item.y; r < item.z; ++r) {
+      const uint2 rg = a.ranges[r];
+      for (uint32_t k = rg.x + (uint32_t)warp; k < rg.y; k += kBtWarps) {
+        const uint32_t slot = a.aslots[k];
+        const uint32_t o = a.off[slot], L = a.len[slot];
+        uint32_t j0, j1;
+        kept_run(a, o, L, mode, t_lo, t_hi, j0, j1);
+        if (j1 <= j0) continue;
+        ev += j1 - j0;
+        cs += 1;
+        for (uint32_t base = j0; base < j1; base += 32) {
+          const uint32_t j = base + (uint32_t)lane;
+          const bool valid = j < j1;
+          uint32_t act = 0;
+          int64_t ts = 0;
+          if (valid) {
+            act = (uint32_t)a.act_s[o + j];
+            ts = a.ts_s[o + j];
+          }
+          if (valid && j == j0) sink.start(act);
+          if (valid && j + 1 == j1) sink.end(act);
+          uint32_t nact = __shfl_down_sync(kFull, act, 1);
+          int64_t nts = __shfl_down_sync(kFull, ts, 1);
+          const bool has_edge = valid && j + 1 < j1;
+          if (lane == 31 && has_edge) {
+            nact = (uint32_t)a.act_s[o + j + 1];
+            nts = a.ts_s[o + j + 1];
+          }
+          const uint32_t e = has_edge ? a.emap[act * A + nact] : 0u;
+          aggregate_edges(sink, has_edge, e, (uint64_t)nts - (uint64_t)ts);
+        }
+      }
+    }
+    // lane 0 of every warp holds the warp's case and event counts
+    if (lane == 0 && cs) {
+      atomicAdd(&a.n_ev[sub], (unsigned long long)ev);
+      atomicAdd(&a.n_cs[sub], (unsigned long long)cs);
+    }
+    __syncthreads();
+    for (int s = tid; s < kBtSlots; s += kBtThreads) {
+      const uint32_t c = tcnt[s];
+      if (c) global_edge_group(g, tkey[s], c, tl[s] | ((uint64_t)tm[s] << 32), 0);
+    }
+    for (uint32_t i = tid; i < A; i += kBtThreads) {
+      if (st[i]) atomicAdd(&sink.g_start[i], (unsigned long long)st[i]);
+      if (en[i]) atomicAdd(&sink.g_end[i], (unsigned long long)en[i]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- drill-down index ----
+__global__ void k_dd_present_keys(const uint32_t *__restrict__ len, uint64_t R, const uint32_t *__restrict__ pos,
+                                  const int32_t *__restrict__ cattr, uint32_t *keys, uint32_t *vals) {
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < R; s += (uint64_t)gridDim.x * blockDim.x) {
+    if (!len[s]) continue;
+    const uint32_t p = pos[s];
+    keys[p] = cattr ? ((uint32_t)cattr[s] ^ 0x80000000u) : 0x80000000u;  // signed order
+    vals[p] = (uint32_t)s;
+  }
+}
+__global__ void k_dd_lens(const uint32_t *__restrict__ aslots, const uint32_t *__restrict__ len, uint32_t C,
+                          uint32_t *out) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < C; k += gridDim.x * blockDim.x) out[k] = len[aslots[k]];
+}
+__global__ void k_dd_heads(const uint32_t *__restrict__ keys, uint32_t C, uint32_t *flags) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < C; k += gridDim.x * blockDim.x)
+    flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
+}
+__global__ void k_dd_groups(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ flags,
+                            const uint32_t *__restrict__ pos, const uint32_t *__restrict__ apre, uint32_t C,
+                            int32_t *vals, uint32_t *lo, uint32_t *ev) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < C; k += gridDim.x * blockDim.x) {
+    if (!flags[k]) continue;
+    const uint32_t u = pos[k];
+    vals[u] = (int32_t)(keys[k] ^ 0x80000000u);
+    lo[u] = k;
+    ev[u] = apre[k];
+  }
+}
+__global__ void k_dd_emap(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos, int64_t cells,
+                          uint32_t n_act, uint32_t *emap, int32_t *pair, uint32_t E) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x) {
+    if (flags[i]) {
+      const uint32_t e = pos[i];
+      emap[i] = e;
+      pair[e] = (int32_t)(i / n_act);
+      pair[E + e] = (int32_t)(i % n_act);
+    } else {
+      emap[i] = 0xFFFFFFFFu;
+    }
+  }
+}
+
+// ---- outputs ----
+__global__ void k_bt_flags(const unsigned long long *__restrict__ cnt, uint64_t n, uint32_t *flags) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    flags[i] = cnt[i] ? 1u : 0u;
+}
+__global__ void k_bt_compact(DfgTable acc, const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos,
+                             uint64_t n, uint32_t E, uint32_t A, const int32_t *__restrict__ pair, int32_t *src,
+                             int32_t *dst, unsigned long long *cnt, unsigned long long *lo, unsigned long long *hi,
+                             unsigned long long *mn, unsigned long long *mx, unsigned long long *freq) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (!flags[i]) continue;
+    const uint32_t p = pos[i];
+    const uint32_t e = (uint32_t)(i % E);
+    const uint64_t q = i / E;
+    src[p] = pair[e];
+    dst[p] = pair[E + e];
+    cnt[p] = acc.cnt[i];
+    lo[p] = acc.lo[i];
+    hi[p] = acc.hi[i];
+    mn[p] = acc.mn[i];
+    mx[p] = acc.mx[i];
+    atomicAdd(&freq[q * A + (uint32_t)pair[e]], acc.cnt[i]);  // out-edges of src
+  }
+}
+__global__ void k_bt_offsets(const uint32_t *__restrict__ pos, uint32_t Qg, uint32_t E, int64_t *off) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= Qg; q += gridDim.x * blockDim.x)
+    off[q] = pos[(uint64_t)q * E];
+}
+__global__ void k_bt_add(unsigned long long *freq, const unsigned long long *__restrict__ end, uint64_t n) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    freq[i] += end[i];
+}
+
+// Builds the drill-down index of L (once).
+int ensure_drilldown(pm4g_log *L) {
+  if (L->dd_ready) return PM4G_OK;
+  Ctx *c = L->ctx;
+  const uint32_t C = (uint32_t)L->C;
+  PM4G_TRY(ensure_offsets(L));
+  PM4G_TRY(alloc_buf(c, L->ts_s, (size_t)L->n));
+  PM4G_TRY(run_export(L, nullptr, nullptr, L->ts_s.p, nullptr));
+  // present cases in (attribute, slot) order
+  PM4G_TRY(alloc_buf(c, L->aslots, C));
+  PM4G_TRY(alloc_buf(c, L->apre, (size_t)C + 1));
+  {
+    Scratch S(c);
+    const uint64_t R = L->R;
+    uint32_t *pf = S.get<uint32_t>(R), *pp = S.get<uint32_t>(R + 1);
+    uint32_t *keys = S.get<uint32_t>(C), *k2 = S.get<uint32_t>(C), *v2 = S.get<uint32_t>(C);
+    uint32_t *lens = S.get<uint32_t>(C), *hf = S.get<uint32_t>(C), *hp = S.get<uint32_t>((size_t)C + 1);
+    if (!pf || !pp || !keys || !k2 || !v2 || !lens || !hf || !hp) {
+      set_error("drill-down index: out of device memory");
+      return PM4G_ENOMEM;
+    }
+    const unsigned gR = grid_for((int64_t)R, 256, 65535), gC = grid_for((int64_t)C, 256, 65535);
+    k_present_flags<<<gR, 256, 0, c->stream>>>(L->len.p, R, pf);
+    PM4G_TRY(check_launch(c, "k_present_flags"));
+    PM4G_TRY(scan_u32(c, pf, pp, (int64_t)R));
+    k_dd_present_keys<<<gR, 256, 0, c->stream>>>(L->len.p, R, pp, L->has_attr ? L->cattr.p : nullptr, keys,
+                                                  L->aslots.p);
+    PM4G_TRY(check_launch(c, "k_dd_present_keys"));
+    if (L->has_attr && C > 1) PM4G_TRY(radix_sort_u32(c, keys, L->aslots.p, k2, v2, C, 0, 32));
+    k_dd_lens<<<gC, 256, 0, c->stream>>>(L->aslots.p, L->len.p, C, lens);
+    PM4G_TRY(check_launch(c, "k_dd_lens"));
+    PM4G_TRY(scan_u32(c, lens, L->apre.p, C));
+    k_dd_heads<<<gC, 256, 0, c->stream>>>(keys, C, hf);
+    PM4G_TRY(check_launch(c, "k_dd_heads"));
+    PM4G_TRY(scan_u32(c, hf, hp, C));
+    uint32_t U = 0;
+    PM4G_TRY(d2h(c, &U, hp + C, 4));
+    int32_t *gv = S.get<int32_t>(U);
+    uint32_t *glo = S.get<uint32_t>(U), *gev = S.get<uint32_t>(U);
+    if (!gv || !glo || !gev) return PM4G_ENOMEM;
+    if (C) {
+      k_dd_groups<<<gC, 256, 0, c->stream>>>(keys, hf, hp, L->apre.p, C, gv, glo, gev);
+      PM4G_TRY(check_launch(c, "k_dd_groups"));
+    }
+    L->attr_vals.assign(U, 0);
+    L->attr_lo.assign((size_t)U + 1, C);
+    L->attr_ev.assign((size_t)U + 1, (uint32_t)L->n);
+    D2HBatch hb(c, (size_t)U * 12 + 64);
+    hb.add(L->attr_vals.data(), gv, (size_t)U * 4);
+    hb.add(L->attr_lo.data(), glo, (size_t)U * 4);
+    hb.add(L->attr_ev.data(), gev, (size_t)U * 4);
+    PM4G_TRY(hb.finish());
+  }
+  // edge index of every directly-follows pair of the resident log
+  {
+    Scratch S(c);
+    const int64_t cells = (int64_t)L->A * L->A;
+    uint32_t *flags = S.get<uint32_t>(cells), *pos = S.get<uint32_t>(cells + 1);
+    if (!flags || !pos) return PM4G_ENOMEM;
+    k_dfg_flags<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(L->dfg.p, cells, flags);
+    PM4G_TRY(check_launch(c, "k_dfg_flags"));
+    PM4G_TRY(scan_u32(c, flags, pos, cells));
+    uint32_t E = 0;
+    PM4G_TRY(d2h(c, &E, pos + cells, 4));
+    L->n_edges = E;
+    PM4G_TRY(alloc_buf(c, L->emap, (size_t)cells));
+    PM4G_TRY(alloc_buf(c, L->e_pair, 2 * (size_t)E));
+    k_dd_emap<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(flags, pos, cells, (uint32_t)L->A, L->emap.p,
+                                                                 L->e_pair.p, E);
+    PM4G_TRY(check_launch(c, "k_dd_emap"));
+  }
+  L->dd_ready = true;
+  return PM4G_OK;
+}
+
+struct Plan {
+  std::vector<uint4> items;   // {sub (group-local), r0, r1, events}
+  std::vector<uint2> ranges;
+};
+
+}  // namespace
+}  // namespace pm4g
+
+int pm4g_batch_dfg_free(pm4g_batch_dfg_t *r) {
+  if (!r) return PM4G_OK;
+  free(r->n_events);
+  free(r->n_cases);
+  free(r->edge_off);
+  free(r->src);
+  free(r->dst);
+  free(r->count);
+  free(r->sum_lo);
+  free(r->sum_hi);
+  free(r->min);
+  free(r->max);
+  free(r->mean);
+  free(r->start);
+  free(r->end);
+  free(r->freq);
+  memset(r, 0, sizeof(*r));
+  return PM4G_OK;
+}
+
+int pm4g_batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out) {
+  if (!L || !spec || !out) {
+    set_error("pm4g_batch_dfg: NULL argument");
+    return PM4G_EINVAL;
+  }
+  memset(out, 0, sizeof(*out));
+  const int32_t Q = spec->n_sub;
+  if (Q < 0 || (Q > 0 && (!spec->attr_off || !spec->t_lo || !spec->t_hi || !spec->mode))) {
+    set_error("pm4g_batch_dfg: bad spec (n_sub < 0 or NULL arrays)");
+    return PM4G_EINVAL;
+  }
+  if (Q > 0 && spec->attr_off[0] != 0) {
+    set_error("pm4g_batch_dfg: attr_off[0] must be 0");
+    return PM4G_EINVAL;
+  }
+  for (int32_t i = 0; i < Q; ++i) {
+    if (spec->attr_off[i + 1] < spec->attr_off[i]) {
+      set_error("pm4g_batch_dfg: attr_off decreases at sub-log %d", i);
+      return PM4G_EINVAL;
+    }
+    if (spec->mode[i] < PM4G_TW_NONE || spec->mode[i] > PM4G_TW_CASES_INTERSECTING) {
+      set_error("pm4g_batch_dfg: bad window mode %d at sub-log %d", spec->mode[i], i);
+      return PM4G_EINVAL;
+    }
+    if (spec->attr_off[i + 1] > spec->attr_off[i] && !L->has_attr) {
+      set_error("pm4g_batch_dfg: attribute filter on a log loaded without case_attr");
+      return PM4G_EINVAL;
+    }
+  }
+  if (Q > 0 && spec->attr_off[Q] > 0 && !spec->attr_vals) {
+    set_error("pm4g_batch_dfg: attr_vals is NULL");
+    return PM4G_EINVAL;
+  }
+  Ctx *c = L->ctx;
+  PM4G_CK(cudaSetDevice(c->device));
+  const uint32_t A = (uint32_t)L->A;
+  out->n_sub = Q;
+  out->n_activities = (int32_t)A;
+  out->n_events = (int64_t *)calloc(std::max(Q, 1), 8);
+  out->n_cases = (int64_t *)calloc(std::max(Q, 1), 8);
+  out->edge_off = (int64_t *)calloc((size_t)Q + 1, 8);
+  out->start = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
+  out->end = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
+  out->freq = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
+  if (!out->n_events || !out->n_cases || !out->edge_off || !out->start || !out->end || !out->freq) {
+    pm4g_batch_dfg_free(out);
+    return PM4G_ENOMEM;
+  }
+  if (Q == 0 || L->C == 0) {
+    out->src = (int32_t *)malloc(4);
+    out->dst = (int32_t *)malloc(4);
+    out->count = (uint64_t *)malloc(8);
+    out->sum_lo = (uint64_t *)malloc(8);
+    out->sum_hi = (uint64_t *)malloc(8);
+    out->min = (uint64_t *)malloc(8);
+    out->max = (uint64_t *)malloc(8);
+    out->mean = (double *)malloc(8);
+    return PM4G_OK;
+  }
+  int st = ensure_drilldown(L);
+  if (st != PM4G_OK) {
+    pm4g_batch_dfg_free(out);
+    return st;
+  }
+  const uint32_t E = L->n_edges;
+  const uint32_t C = (uint32_t)L->C;
+  // per sub-log: its case ranges and their events
+  std::vector<std::vector<uint2>> sub_ranges(Q);
+  std::vector<std::vector<uint32_t>> sub_ev(Q);
+  uint64_t total_ev = 0;
+  for (int32_t i = 0; i < Q; ++i) {
+    const int64_t a0 = spec->attr_off[i], a1 = spec->attr_off[i + 1];
+    if (a1 == a0) {
+      sub_ranges[i].push_back(make_uint2(0, C));
+      sub_ev[i].push_back((uint32_t)L->n);
+      total_ev += (uint64_t)L->n;
+      continue;
+    }
+    std::vector<int32_t> v(spec->attr_vals + a0, spec->attr_vals + a1);
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    for (int32_t x : v) {
+      const auto it = std::lower_bound(L->attr_vals.begin(), L->attr_vals.end(), x);
+      if (it == L->attr_vals.end() || *it != x) continue;
+      const size_t u = (size_t)(it - L->attr_vals.begin());
+      sub_ranges[i].push_back(make_uint2(L->attr_lo[u], L->attr_lo[u + 1]));
+      sub_ev[i].push_back(L->attr_ev[u + 1] - L->attr_ev[u]);
+      total_ev += L->attr_ev[u + 1] - L->attr_ev[u];
+    }
+  }
+  // sub-log groups whose accumulators fit the memory budget
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  const size_t per_sub = (size_t)E * 40 + (size_t)A * 16 + 16 + (size_t)E * 8;
+  const size_t budget = std::max<size_t>(std::min<size_t>(fr / 3, (size_t)8 << 30), per_sub);
+  const int32_t Qg_max = (int32_t)std::max<size_t>(1, std::min<size_t>((size_t)Q, budget / per_sub));
+  const uint64_t W = std::max<uint64_t>(1 << 15, total_ev / ((uint64_t)c->num_sms * 4) + 1);
+  std::vector<int32_t> h_src, h_dst;
+  std::vector<uint64_t> h_cnt, h_lo, h_hi, h_mn, h_mx;
+  std::vector<int64_t> h_off;
+  for (int32_t q0 = 0; q0 < Q && st == PM4G_OK; q0 += Qg_max) {
+    const int32_t Qg = std::min(Qg_max, Q - q0);
+    Plan P;
+    for (int32_t q = 0; q < Qg; ++q) {
+      const int32_t i = q0 + q;
+      uint32_t r_first = (uint32_t)P.ranges.size();
+      uint64_t ev = 0;
+      auto close = [&]() {
+        if ((uint32_t)P.ranges.size() > r_first)
+          P.items.push_back(make_uint4((uint32_t)q, r_first, (uint32_t)P.ranges.size(), (uint32_t)std::min<uint64_t>(ev, 0xFFFFFFFFu)));
+        r_first = (uint32_t)P.ranges.size();
+        ev = 0;
+      };
+      for (size_t r = 0; r < sub_ranges[i].size(); ++r) {
+        const uint2 rg = sub_ranges[i][r];
+        const uint64_t rev = sub_ev[i][r];
+        const uint32_t ncase = rg.y - rg.x;
+        if (ncase == 0) continue;
+        // split a large range into pieces of about W events
+        const uint64_t pieces = std::max<uint64_t>(1, (rev + W - 1) / W);
+        const uint32_t step = (uint32_t)((ncase + pieces - 1) / pieces);
+        for (uint32_t k = rg.x; k < rg.y; k += step) {
+          const uint32_t k1 = std::min(rg.y, k + step);
+          const uint64_t pev = rev * (k1 - k) / ncase;
+          if (ev > 0 && ev + pev > W) close();
+          P.ranges.push_back(make_uint2(k, k1));
+          ev += pev;
+        }
+      }
+      close();
+    }
+    std::stable_sort(P.items.begin(), P.items.end(), [](const uint4 &x, const uint4 &y) { return x.w > y.w; });
+    const uint64_t cellsg = (uint64_t)Qg * E;
+    Scratch S(c);
+    unsigned long long *acc = S.get<unsigned long long>(5 * cellsg);
+    unsigned long long *se = S.get<unsigned long long>(3 * (size_t)Qg * A);  // start, end, freq
+    unsigned long long *cnts = S.get<unsigned long long>(2 * (size_t)Qg);
+    uint4 *ditems = S.get<uint4>(P.items.size());
+    uint2 *dranges = S.get<uint2>(P.ranges.size());
+    uint32_t *dwork = S.get<uint32_t>(1);
+    int64_t *dtlo = S.get<int64_t>(Qg), *dthi = S.get<int64_t>(Qg);
+    int32_t *dmode = S.get<int32_t>(Qg);
+    if (!acc || !se || !cnts || !ditems || !dranges || !dwork || !dtlo || !dthi || !dmode) {
+      set_error("pm4g_batch_dfg: out of device memory");
+      st = PM4G_ENOMEM;
+      break;
+    }
+    cudaStream_t s = c->stream;
+    if (cudaMemsetAsync(acc, 0, 3 * cellsg * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(acc + 3 * cellsg, 0xFF, cellsg * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(acc + 4 * cellsg, 0, cellsg * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(se, 0, 3 * (size_t)Qg * A * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(cnts, 0, 2 * (size_t)Qg * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(dwork, 0, 4, s) != cudaSuccess ||
+        (!P.items.empty() &&
+         cudaMemcpyAsync(ditems, P.items.data(), P.items.size() * sizeof(uint4), cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+        (!P.ranges.empty() &&
+         cudaMemcpyAsync(dranges, P.ranges.data(), P.ranges.size() * sizeof(uint2), cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+        cudaMemcpyAsync(dtlo, spec->t_lo + q0, (size_t)Qg * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dthi, spec->t_hi + q0, (size_t)Qg * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dmode, spec->mode + q0, (size_t)Qg * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("pm4g_batch_dfg: copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+      st = PM4G_ECUDA;
+      break;
+    }
+    BatchArgs a{};
+    a.aslots = L->aslots.p;
+    a.off = L->off.p;
+    a.len = L->len.p;
+    a.act_s = L->act_s.p;
+    a.ts_s = L->ts_s.p;
+    a.emap = L->emap.p;
+    a.n_act = A;
+    a.n_edges = E;
+    a.items = ditems;
+    a.n_items = (uint32_t)P.items.size();
+    a.ranges = dranges;
+    a.work = dwork;
+    a.t_lo = dtlo;
+    a.t_hi = dthi;
+    a.mode = dmode;
+    a.acc = DfgTable{acc, acc + cellsg, acc + 2 * cellsg, acc + 3 * cellsg, acc + 4 * cellsg};
+    a.start = se;
+    a.end = se + (size_t)Qg * A;
+    a.n_ev = cnts;
+    a.n_cs = cnts + Qg;
+    unsigned long long *freq = se + 2 * (size_t)Qg * A;
+    if (!P.items.empty()) {
+      const size_t smem = bt_smem_bytes(A);
+      if (cudaFuncSetAttribute(k_batch_dfg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        set_error("pm4g_batch_dfg: shared memory attribute: %s", cudaGetErrorString(cudaGetLastError()));
+        st = PM4G_ECUDA;
+        break;
+      }
+      KTime t(c, "batch");
+      c->launches++;
+      k_batch_dfg<<<std::min<unsigned>(a.n_items, (unsigned)c->num_sms), kBtThreads, smem, s>>>(a);
+      if ((st = check_launch(c, "k_batch_dfg")) != PM4G_OK) break;
+    }
+    // compaction of the group's edges, sub-log by sub-log in edge order
+    uint32_t *flags = S.get<uint32_t>(cellsg), *pos = S.get<uint32_t>(cellsg + 1);
+    int64_t *doff = S.get<int64_t>((size_t)Qg + 1);
+    if (!flags || !pos || !doff) {
+      st = PM4G_ENOMEM;
+      break;
+    }
+    const unsigned gN = grid_for((int64_t)cellsg, 256, 65535);
+    {
+      KTime t(c, "batch");
+      k_bt_flags<<<gN, 256, 0, s>>>(acc, cellsg, flags);
+      if ((st = check_launch(c, "k_bt_flags")) != PM4G_OK) break;
+    }
+    if ((st = scan_u32(c, flags, pos, (int64_t)cellsg)) != PM4G_OK) break;
+    uint32_t Eg = 0;
+    if ((st = d2h(c, &Eg, pos + cellsg, 4)) != PM4G_OK) break;
+    int32_t *osrc = S.get<int32_t>(Eg), *odst = S.get<int32_t>(Eg);
+    unsigned long long *o5 = S.get<unsigned long long>(5 * (size_t)Eg);
+    if (!osrc || !odst || !o5) {
+      st = PM4G_ENOMEM;
+      break;
+    }
+    {
+      KTime t(c, "batch");
+      k_bt_compact<<<gN, 256, 0, s>>>(a.acc, flags, pos, cellsg, E, A, L->e_pair.p, osrc, odst, o5, o5 + Eg,
+                                      o5 + 2 * (size_t)Eg, o5 + 3 * (size_t)Eg, o5 + 4 * (size_t)Eg, freq);
+      if ((st = check_launch(c, "k_bt_compact")) != PM4G_OK) break;
+      k_bt_add<<<grid_for((int64_t)Qg * A, 256, 65535), 256, 0, s>>>(freq, a.end, (uint64_t)Qg * A);
+      if ((st = check_launch(c, "k_bt_add")) != PM4G_OK) break;
+      k_bt_offsets<<<grid_for((int64_t)Qg + 1, 256, 65535), 256, 0, s>>>(pos, (uint32_t)Qg, E, doff);
+      if ((st = check_launch(c, "k_bt_offsets")) != PM4G_OK) break;
+    }
+    const size_t base = h_src.size();
+    h_src.resize(base + Eg);
+    h_dst.resize(base + Eg);
+    h_cnt.resize(base + Eg);
+    h_lo.resize(base + Eg);
+    h_hi.resize(base + Eg);
+    h_mn.resize(base + Eg);
+    h_mx.resize(base + Eg);
+    std::vector<int64_t> goff((size_t)Qg + 1);
+    std::vector<unsigned long long> gcnt(2 * (size_t)Qg);
+    D2HBatch hb(c, (size_t)Eg * 48 + (size_t)Qg * (3 * A * 8 + 32) + 16 * 16);
+    hb.add(h_src.data() + base, osrc, (size_t)Eg * 4);
+    hb.add(h_dst.data() + base, odst, (size_t)Eg * 4);
+    hb.add(h_cnt.data() + base, o5, (size_t)Eg * 8);
+    hb.add(h_lo.data() + base, o5 + Eg, (size_t)Eg * 8);
+    hb.add(h_hi.data() + base, o5 + 2 * (size_t)Eg, (size_t)Eg * 8);
+    hb.add(h_mn.data() + base, o5 + 3 * (size_t)Eg, (size_t)Eg * 8);
+    hb.add(h_mx.data() + base, o5 + 4 * (size_t)Eg, (size_t)Eg * 8);
+    hb.add(out->start + (size_t)q0 * A, a.start, (size_t)Qg * A * 8);
+    hb.add(out->end + (size_t)q0 * A, a.end, (size_t)Qg * A * 8);
+    hb.add(out->freq + (size_t)q0 * A, freq, (size_t)Qg * A * 8);
+    hb.add(goff.data(), doff, ((size_t)Qg + 1) * 8);
+    hb.add(gcnt.data(), cnts, 2 * (size_t)Qg * 8);
+    if ((st = hb.finish()) != PM4G_OK) break;
+    for (int32_t q = 0; q < Qg; ++q) {
+      out->n_events[q0 + q] = (int64_t)gcnt[q];
+      out->n_cases[q0 + q] = (int64_t)gcnt[Qg + q];
+      out->edge_off[q0 + q] = (int64_t)base + goff[q];
+    }
+    out->edge_off[q0 + Qg] = (int64_t)base + goff[Qg];
+  }
+  if (st != PM4G_OK) {
+    pm4g_batch_dfg_free(out);
+    return st;
+  }
+  const size_t Et = h_src.size();
+  out->src = (int32_t *)malloc(std::max<size_t>(Et, 1) * 4);
+  out->dst = (int32_t *)malloc(std::max<size_t>(Et, 1) * 4);
+  out->count = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
+  out->sum_lo = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
+  out->sum_hi = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
+  out->min = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
+  out->max = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
+  out->mean = (double *)malloc(std::max<size_t>(Et, 1) * 8);
+  if (!out->src || !out->dst || !out->count || !out->sum_lo || !out->sum_hi || !out->min || !out->max || !out->mean) {
+    pm4g_batch_dfg_free(out);
+    return PM4G_ENOMEM;
+  }
+  if (Et) {
+    memcpy(out->src, h_src.data(), Et * 4);
+    memcpy(out->dst, h_dst.data(), Et * 4);
+    memcpy(out->count, h_cnt.data(), Et * 8);
+    memcpy(out->sum_lo, h_lo.data(), Et * 8);
+    memcpy(out->sum_hi, h_hi.data(), Et * 8);
+    memcpy(out->min, h_mn.data(), Et * 8);
+    memcpy(out->max, h_mx.data(), Et * 8);
+  }
+  // means as in pm4g_perf_dfg: the exact sum converted once, one division
+  for (size_t k = 0; k < Et; ++k) {
+    const u128 sm = ((u128)h_hi[k] << 64) | (u128)h_lo[k];
+    out->mean[k] = (double)sm / (double)h_cnt[k];
+  }
+  return PM4G_OK;
+}

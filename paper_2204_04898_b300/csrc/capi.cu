@@ -127,63 +127,37 @@ KTime::~KTime() {
   }
 }
 
+char *pinned(Ctx *c, size_t bytes) {
+  if (bytes <= c->pin_bytes) return (char *)c->pin;
+  if (c->pin) {
+    cudaStreamSynchronize(c->stream);
+    cudaFreeHost(c->pin);
+    c->pin = nullptr;
+    c->pin_bytes = 0;
+  }
+  size_t want = (size_t)1 << 20;
+  while (want < bytes) want <<= 1;
+  if (cudaHostAlloc(&c->pin, want, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    c->pin = nullptr;
+    return nullptr;
+  }
+  c->pin_bytes = want;
+  return (char *)c->pin;
+}
+
+int d2h(Ctx *c, void *dst, const void *src, size_t bytes) {
+  if (!bytes) return PM4G_OK;
+  D2HBatch b(c, bytes);
+  b.add(dst, src, bytes);
+  return b.finish();
+}
+
 }  // namespace pm4g
 
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
-struct pm4g_ctx : public pm4g::Ctx {};
-
-struct pm4g_log {
-  Ctx *ctx = nullptr;
-  int64_t n = 0;
-  int32_t A = 1;
-  int64_t C = 0;
-  int32_t min_case = 0;
-  uint64_t R = 0;  // case slots
-  int clb = 0;
-  int act_bits = 0;
-  uint32_t nb = 0;
-  bool has_attr = false;
-  DBuf<uint4> rec;
-  DBuf<uint32_t> bucket_off;
-  DBuf<int32_t> act_s;
-  DBuf<uint32_t> len;
-  DBuf<uint64_t> hash;
-  DBuf<int32_t> cattr;
-  DBuf<int32_t> uniq;  // sorted distinct case ids when renumbered
-  DBuf<unsigned long long> dfg;  // 5 * A * A: cnt, lo, hi, min, max
-  DBuf<unsigned long long> ends; // 2 * A: start, end
-  // caches
-  bool edges_ready = false;
-  std::vector<int32_t> e_src, e_dst;
-  std::vector<uint64_t> e_cnt, e_lo, e_hi, e_min, e_max, h_start, h_end, h_freq;
-  bool span_ready = false;
-  DBuf<int64_t> span;  // first_ts[R], last_ts[R]
-  bool var_ready = false;
-  uint32_t V = 0;
-  DBuf<uint32_t> off, rep_slots, order, vcount, rep_of;
-  DBuf<int32_t> cvar;
-};
-
-template <class T>
-static int alloc_buf(Ctx *c, DBuf<T> &b, size_t n) {
-  b.n = n;
-  b.p = (T *)dalloc(c, (n ? n : 1) * sizeof(T));
-  if (!b.p) {
-    set_error("device allocation of %zu bytes failed", (n ? n : 1) * sizeof(T));
-    return PM4G_ENOMEM;
-  }
-  return PM4G_OK;
-}
-
-template <class T>
-static void free_buf(Ctx *c, DBuf<T> &b) {
-  if (b.p) dfree(c, b.p, (b.n ? b.n : 1) * sizeof(T));
-  b.p = nullptr;
-  b.n = 0;
-}
-
 static void release_log(pm4g_log *L) {
   if (!L) return;
   Ctx *c = L->ctx;
@@ -203,79 +177,16 @@ static void release_log(pm4g_log *L) {
   free_buf(c, L->vcount);
   free_buf(c, L->rep_of);
   free_buf(c, L->cvar);
+  free_buf(c, L->ts_s);
+  free_buf(c, L->aslots);
+  free_buf(c, L->apre);
+  free_buf(c, L->emap);
+  free_buf(c, L->e_pair);
   c->live_logs--;
   delete L;
 }
 
-// Pinned host staging owned by the context (grown on demand): device-to-host
-// copies land there asynchronously, so a batch of them costs one
-// synchronisation; the bytes then move to their destinations on the host.
-static char *pinned(Ctx *c, size_t bytes) {
-  if (bytes <= c->pin_bytes) return (char *)c->pin;
-  if (c->pin) {
-    cudaStreamSynchronize(c->stream);
-    cudaFreeHost(c->pin);
-    c->pin = nullptr;
-    c->pin_bytes = 0;
-  }
-  size_t want = (size_t)1 << 20;
-  while (want < bytes) want <<= 1;
-  if (cudaHostAlloc(&c->pin, want, cudaHostAllocDefault) != cudaSuccess) {
-    cudaGetLastError();
-    c->pin = nullptr;
-    return nullptr;
-  }
-  c->pin_bytes = want;
-  return (char *)c->pin;
-}
 
-// A batch of device-to-host copies through the staging area. The caller
-// states an upper bound of the batch's bytes (each copy adds up to 15 bytes of
-// alignment) before the first add.
-struct D2HBatch {
-  Ctx *c;
-  char *base = nullptr;
-  size_t cap = 0, used = 0;
-  int st = PM4G_OK;
-  std::vector<std::tuple<void *, size_t, size_t>> items;
-  D2HBatch(Ctx *ctx, size_t bound) : c(ctx), cap(bound) {
-    base = pinned(c, std::max<size_t>(bound, 16));
-    if (!base) {
-      set_error("out of pinned host memory for results");
-      st = PM4G_ENOMEM;
-    }
-  }
-  void add(void *dst, const void *src, size_t bytes) {
-    if (st != PM4G_OK || bytes == 0) return;
-    used = (used + 15) & ~(size_t)15;
-    if (used + bytes > cap) {
-      set_error("internal: result staging bound exceeded");
-      st = PM4G_ECUDA;
-      return;
-    }
-    const cudaError_t e = cudaMemcpyAsync(base + used, src, bytes, cudaMemcpyDeviceToHost, c->stream);
-    if (e != cudaSuccess) {
-      set_error("device-to-host copy failed: %s", cudaGetErrorString(e));
-      st = PM4G_ECUDA;
-      return;
-    }
-    items.emplace_back(dst, used, bytes);
-    used += bytes;
-  }
-  int finish() {
-    if (st != PM4G_OK) return st;
-    PM4G_CK(cudaStreamSynchronize(c->stream));
-    for (auto &it : items) memcpy(std::get<0>(it), base + std::get<1>(it), std::get<2>(it));
-    return PM4G_OK;
-  }
-};
-
-static int d2h(Ctx *c, void *dst, const void *src, size_t bytes) {
-  if (!bytes) return PM4G_OK;
-  D2HBatch b(c, bytes);
-  b.add(dst, src, bytes);
-  return b.finish();
-}
 
 // ---------------------------------------------------------------------------
 // segment pass configuration
@@ -494,7 +405,7 @@ static int choose_clb(Ctx *c, int64_t n, uint64_t R, int32_t A, int act_bits) {
 const char *pm4g_last_error(void) { return pm4g::g_err; }
 
 const char *pm4g_kernel_names(void) {
-  return "stats,bucket_hist,bucket_scatter,partition,segment,fallback,scan,radix_sort,filter,variants,dfg";
+  return "stats,bucket_hist,bucket_scatter,partition,segment,fallback,scan,radix_sort,filter,variants,dfg,export,batch";
 }
 
 int pm4g_ctx_create(pm4g_ctx **out, int device, void *cuda_stream, const pm4g_allocator *alloc) {
@@ -956,22 +867,17 @@ int pm4g_log_free(pm4g_log *L) {
   return PM4G_OK;
 }
 
-int pm4g_log_export(pm4g_log *L, int32_t *case_out, int32_t *act_out, int64_t *ts_out, int64_t *row_out) {
-  if (!L) {
-    set_error("pm4g_log_export: log is NULL");
-    return PM4G_EINVAL;
-  }
+// Runs the segment pass in export mode: the formatted log in (case,
+// timestamp, row) order into the given device arrays (any may be NULL).
+int pm4g::run_export(pm4g_log *L, int32_t *ec, int32_t *ea, int64_t *et, int64_t *er) {
   Ctx *c = L->ctx;
-  PM4G_CK(cudaSetDevice(c->device));
   if (L->n == 0) return PM4G_OK;
   Scratch S(c);
-  int32_t *ec = S.get<int32_t>(L->n), *ea = S.get<int32_t>(L->n);
-  int64_t *et = S.get<int64_t>(L->n), *er = S.get<int64_t>(L->n);
   uint32_t *ctr = S.get<uint32_t>(4);
   uint32_t *ovf = S.get<uint32_t>(L->nb);
   unsigned long long *dummy = S.get<unsigned long long>(1);
-  if (!ec || !ea || !et || !er || !ctr || !ovf || !dummy) {
-    set_error("pm4g_log_export: out of device memory");
+  if (!ctr || !ovf || !dummy) {
+    set_error("export: out of device memory");
     return PM4G_ENOMEM;
   }
   PM4G_CK(cudaMemsetAsync(ctr, 0, 16, c->stream));
@@ -997,12 +903,38 @@ int pm4g_log_export(pm4g_log *L, int32_t *case_out, int32_t *act_out, int64_t *t
     for (uint32_t b = 0; b < n_ovf; ++b) list[b] = b;
   }
   for (uint32_t b : list) PM4G_TRY(fallback_bucket(L, a, b, true));
+  return PM4G_OK;
+}
+
+int pm4g_log_export(pm4g_log *L, int32_t *case_out, int32_t *act_out, int64_t *ts_out, int64_t *row_out) {
+  if (!L) {
+    set_error("pm4g_log_export: log is NULL");
+    return PM4G_EINVAL;
+  }
+  Ctx *c = L->ctx;
+  PM4G_CK(cudaSetDevice(c->device));
+  if (L->n == 0) return PM4G_OK;
+  Scratch S(c);
+  int32_t *ec = S.get<int32_t>(L->n), *ea = S.get<int32_t>(L->n);
+  int64_t *et = S.get<int64_t>(L->n), *er = S.get<int64_t>(L->n);
+  if (!ec || !ea || !et || !er) {
+    set_error("pm4g_log_export: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  PM4G_TRY(run_export(L, ec, ea, et, er));
   if (case_out) PM4G_CK(cudaMemcpyAsync(case_out, ec, L->n * 4, cudaMemcpyDeviceToHost, c->stream));
   if (act_out) PM4G_CK(cudaMemcpyAsync(act_out, ea, L->n * 4, cudaMemcpyDeviceToHost, c->stream));
   if (ts_out) PM4G_CK(cudaMemcpyAsync(ts_out, et, L->n * 8, cudaMemcpyDeviceToHost, c->stream));
   if (row_out) PM4G_CK(cudaMemcpyAsync(row_out, er, L->n * 8, cudaMemcpyDeviceToHost, c->stream));
   PM4G_CK(cudaStreamSynchronize(c->stream));
   return PM4G_OK;
+}
+
+// Case offsets: exclusive prefix of the per-slot lengths (R + 1 entries).
+int pm4g::ensure_offsets(pm4g_log *L) {
+  if (L->off.p) return PM4G_OK;
+  PM4G_TRY(alloc_buf(L->ctx, L->off, L->R + 1));
+  return scan_u32(L->ctx, L->len.p, L->off.p, (int64_t)L->R);
 }
 
 // ---------------------------------------------------------------------------
@@ -1172,11 +1104,10 @@ static int ensure_variants(pm4g_log *L) {
   if (L->var_ready) return PM4G_OK;
   Ctx *c = L->ctx;
   const uint64_t R = L->R;
-  PM4G_TRY(alloc_buf(c, L->off, R + 1));
+  PM4G_TRY(ensure_offsets(L));
   PM4G_TRY(alloc_buf(c, L->vcount, R));
   PM4G_TRY(alloc_buf(c, L->rep_of, R));
   PM4G_TRY(alloc_buf(c, L->cvar, R));
-  PM4G_TRY(scan_u32(c, L->len.p, L->off.p, (int64_t)R));
   if (L->C == 0) {
     L->V = 0;
     PM4G_TRY(alloc_buf(c, L->rep_slots, 0));

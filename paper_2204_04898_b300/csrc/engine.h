@@ -6,8 +6,10 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pm4g.h"
@@ -105,6 +107,84 @@ struct KTime {
 
 int check_launch(Ctx *c, const char *what);
 
+// Device arrays of a log or context, through the context's allocator.
+template <class T>
+inline int alloc_buf(Ctx *c, DBuf<T> &b, size_t n) {
+  b.n = n;
+  b.p = (T *)dalloc(c, (n ? n : 1) * sizeof(T));
+  if (!b.p) {
+    set_error("device allocation of %zu bytes failed", (n ? n : 1) * sizeof(T));
+    return PM4G_ENOMEM;
+  }
+  return PM4G_OK;
+}
+
+template <class T>
+inline void free_buf(Ctx *c, DBuf<T> &b) {
+  if (b.p) dfree(c, b.p, (b.n ? b.n : 1) * sizeof(T));
+  b.p = nullptr;
+  b.n = 0;
+}
+
+// Pinned host staging owned by the context (grown on demand): device-to-host
+// copies land there asynchronously, so a batch of them costs one
+// synchronisation; the bytes then move to their destinations on the host.
+char *pinned(Ctx *c, size_t bytes);
+
+// A batch of device-to-host copies through the staging area. The caller
+// states an upper bound of the batch's bytes (each copy adds up to 15 bytes of
+// alignment) before the first add; nothing else may use the staging area
+// until finish().
+struct D2HBatch {
+  Ctx *c;
+  char *base = nullptr;
+  size_t cap = 0, used = 0;
+  int st = PM4G_OK;
+  std::vector<std::tuple<void *, size_t, size_t>> items;
+  D2HBatch(Ctx *ctx, size_t bound) : c(ctx), cap(bound) {
+    base = pinned(c, bound < 16 ? 16 : bound);
+    if (!base) {
+      set_error("out of pinned host memory for results");
+      st = PM4G_ENOMEM;
+    }
+  }
+  void add(void *dst, const void *src, size_t bytes) {
+    if (st != PM4G_OK || bytes == 0) return;
+    used = (used + 15) & ~(size_t)15;
+    if (used + bytes > cap) {
+      set_error("internal: result staging bound exceeded");
+      st = PM4G_ECUDA;
+      return;
+    }
+    const cudaError_t e = cudaMemcpyAsync(base + used, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) {
+      set_error("device-to-host copy failed: %s", cudaGetErrorString(e));
+      st = PM4G_ECUDA;
+      return;
+    }
+    items.emplace_back(dst, used, bytes);
+    used += bytes;
+  }
+  int finish() {
+    if (st != PM4G_OK) return st;
+    PM4G_CK(cudaStreamSynchronize(c->stream));
+    for (auto &it : items) memcpy(std::get<0>(it), base + std::get<1>(it), std::get<2>(it));
+    return PM4G_OK;
+  }
+};
+
+// One device-to-host copy, synchronised.
+int d2h(Ctx *c, void *dst, const void *src, size_t bytes);
+
+}  // namespace pm4g
+struct pm4g_log;
+namespace pm4g {
+// Log helpers (capi.cu): the formatted log in export order into device arrays
+// (any may be NULL), and the per-slot case offsets L->off.
+int run_export(pm4g_log *L, int32_t *ec, int32_t *ea, int64_t *et, int64_t *er);
+int ensure_offsets(pm4g_log *L);
+
+
 // ---- primitives (prims.cu) ----
 // Exclusive scan of n uint32 values; out must hold n + 1 entries, out[n] = total.
 int scan_u32(Ctx *c, const uint32_t *in, uint32_t *out, int64_t n);
@@ -131,3 +211,50 @@ inline unsigned grid_for(int64_t n, int per_block, unsigned cap = 1u << 20) {
 }
 
 }  // namespace pm4g
+
+// Handles of the C ABI.
+struct pm4g_ctx : public pm4g::Ctx {};
+
+struct pm4g_log {
+  pm4g::Ctx *ctx = nullptr;
+  int64_t n = 0;
+  int32_t A = 1;
+  int64_t C = 0;
+  int32_t min_case = 0;
+  uint64_t R = 0;  // case slots
+  int clb = 0;
+  int act_bits = 0;
+  uint32_t nb = 0;
+  bool has_attr = false;
+  pm4g::DBuf<uint4> rec;
+  pm4g::DBuf<uint32_t> bucket_off;
+  pm4g::DBuf<int32_t> act_s;
+  pm4g::DBuf<uint32_t> len;
+  pm4g::DBuf<uint64_t> hash;
+  pm4g::DBuf<int32_t> cattr;
+  pm4g::DBuf<int32_t> uniq;  // sorted distinct case ids when renumbered
+  pm4g::DBuf<unsigned long long> dfg;  // 5 * A * A: cnt, lo, hi, min, max
+  pm4g::DBuf<unsigned long long> ends; // 2 * A: start, end
+  // caches
+  bool edges_ready = false;
+  std::vector<int32_t> e_src, e_dst;
+  std::vector<uint64_t> e_cnt, e_lo, e_hi, e_min, e_max, h_start, h_end, h_freq;
+  bool span_ready = false;
+  pm4g::DBuf<int64_t> span;  // first_ts[R], last_ts[R]
+  bool var_ready = false;
+  uint32_t V = 0;
+  pm4g::DBuf<uint32_t> off, rep_slots, order, vcount, rep_of;
+  pm4g::DBuf<int32_t> cvar;
+  // drill-down index (batched drill-down; built on first use)
+  bool dd_ready = false;
+  pm4g::DBuf<int64_t> ts_s;       // timestamps in (case, timestamp, row) order
+  pm4g::DBuf<uint32_t> aslots;    // present case slots ordered by (attribute, slot)
+  pm4g::DBuf<uint32_t> apre;      // events before each entry of aslots (C + 1)
+  std::vector<int32_t> attr_vals; // distinct attribute values, ascending
+  std::vector<uint32_t> attr_lo;  // their first entry in aslots (one more at the end)
+  std::vector<uint32_t> attr_ev;  // events before that entry
+  pm4g::DBuf<uint32_t> emap;      // A * A: edge index of a directly-follows pair, or ~0
+  pm4g::DBuf<int32_t> e_pair;     // 2 * E: src and dst of every edge, (src, dst) order
+  uint32_t n_edges = 0;
+};
+

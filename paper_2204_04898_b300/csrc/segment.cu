@@ -39,98 +39,11 @@
 #include "device_common.cuh"
 #include "engine.h"
 #include "kernels.h"
+#include "sink.cuh"
 
 namespace pm4g {
 
 namespace {
-
-constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
-
-__device__ __forceinline__ void global_sum(const DfgTable &g, uint32_t key, uint64_t lo, uint64_t hi) {
-  const unsigned long long old = atomicAdd(&g.lo[key], (unsigned long long)lo);
-  const unsigned long long h2 = hi + (old + lo < old ? 1ull : 0ull);
-  if (h2) atomicAdd(&g.hi[key], h2);
-}
-
-__device__ __forceinline__ void global_edge_group(const DfgTable &g, uint32_t key, uint32_t cnt, uint64_t lo,
-                                                  uint64_t hi) {
-  atomicAdd(&g.cnt[key], (unsigned long long)cnt);
-  global_sum(g, key, lo, hi);
-}
-
-struct SmemSink {
-  uint32_t *tkey, *tcnt, *tminh, *tmaxh;
-  uint32_t *tl, *tm;  // low and middle 32-bit words of the slot's sum
-  uint32_t mask;
-  uint32_t shift;  // 32 - log2(slots), for the multiplicative slot hash
-  int mode;
-  uint32_t *st, *en;
-  uint32_t *hl, *hh;  // per-case sequence hash, low and high words
-  const SegArgs *a;
-
-  __device__ __forceinline__ int find(uint32_t key) {
-    if (mode == 0) return (int)key;
-    uint32_t h = (key * 0x9E3779B1u) >> shift;
-    for (int it = 0; it < 64; ++it) {
-      const uint32_t k = *(volatile uint32_t *)&tkey[h];
-      if (k == key) return (int)h;
-      if (k == kEmptyKey) {
-        const uint32_t old = atomicCAS(&tkey[h], kEmptyKey, key);
-        if (old == kEmptyKey || old == key) return (int)h;
-      }
-      h = (h + 1) & mask;
-    }
-    return -1;
-  }
-  // The shared sum of a slot is two 32-bit words (low, middle) updated with
-  // native 32-bit atomics; every carry out of bit 63 goes to the global high
-  // word at once.
-  __device__ __forceinline__ void edge_group(uint32_t key, uint32_t cnt, u128 sum, uint64_t mn, uint64_t mx) {
-    const uint64_t lo64 = (uint64_t)sum;
-    uint64_t top = (uint64_t)(sum >> 64);
-    const int s = find(key);
-    if (s >= 0) {
-      atomicAdd(&tcnt[s], cnt);
-      const uint32_t l = (uint32_t)lo64;
-      const uint32_t old_l = atomicAdd(&tl[s], l);
-      const uint64_t madd = (lo64 >> 32) + (old_l + l < old_l ? 1u : 0u);
-      if (madd >> 32) {
-        top += 1;
-      } else if (madd) {
-        const uint32_t old_m = atomicAdd(&tm[s], (uint32_t)madd);
-        if (old_m + (uint32_t)madd < old_m) top += 1;
-      }
-      if (top) atomicAdd(&a->g.hi[key], (unsigned long long)top);
-      const uint32_t mnh = (uint32_t)(mn >> 32), mxh = (uint32_t)(mx >> 32);
-      if (mnh <= *(volatile uint32_t *)&tminh[s]) {
-        atomicMin(&tminh[s], mnh);
-        atomicMin(&a->g.mn[key], (unsigned long long)mn);
-      }
-      if (mxh >= *(volatile uint32_t *)&tmaxh[s]) {
-        atomicMax(&tmaxh[s], mxh);
-        atomicMax(&a->g.mx[key], (unsigned long long)mx);
-      }
-    } else {
-      global_edge_group(a->g, key, cnt, lo64, top);
-      atomicMin(&a->g.mn[key], (unsigned long long)mn);
-      atomicMax(&a->g.mx[key], (unsigned long long)mx);
-    }
-  }
-  __device__ __forceinline__ void start(uint32_t act) {
-    if (st) atomicAdd(&st[act], 1u);
-    else atomicAdd(&a->g_start[act], 1ull);
-  }
-  __device__ __forceinline__ void end(uint32_t act) {
-    if (en) atomicAdd(&en[act], 1u);
-    else atomicAdd(&a->g_end[act], 1ull);
-  }
-  // The case hash is two independent 32-bit wrap-around sums (low and high
-  // words of the event terms), so each term is two fire-and-forget adds.
-  __device__ __forceinline__ void hash_add(uint32_t c, uint64_t v) {
-    atomicAdd(&hl[c], (uint32_t)v);
-    atomicAdd(&hh[c], (uint32_t)(v >> 32));
-  }
-};
 
 struct GlobalSink {
   const SegArgs *a;
@@ -148,49 +61,6 @@ struct GlobalSink {
     atomicAdd(&h[1], (uint32_t)(v >> 32));
   }
 };
-
-// Aggregates the warp's directly-follows pairs with full-warp operations.
-// Up to twice, the pending lanes whose edge equals the first pending lane's
-// edge are reduced together (count, exact 128-bit sum, min, max; non-members
-// add neutral values) when there are at least two of them. Then a single pass
-// updates the sink: each group through its first lane, every other pending
-// lane on its own.
-template <class Sink>
-__device__ __forceinline__ void aggregate_edges(Sink &sink, bool has_edge, uint32_t key, uint64_t d) {
-  const int lane = (int)lane_id();
-  uint32_t rem = __ballot_sync(kFull, has_edge);
-  if (rem == 0) return;
-  const uint32_t hi = (uint32_t)(d >> 32), lo = (uint32_t)d;
-  uint32_t u_cnt = 1;
-  u128 u_sum = (u128)d;
-  uint64_t u_mn = d, u_mx = d;
-  bool leader = false;
-#pragma unroll
-  for (int round = 0; round < 2; ++round) {
-    if (rem == 0) break;
-    const int src = __ffs(rem) - 1;
-    const uint32_t cand = __shfl_sync(kFull, key, src);
-    const bool mem = ((rem >> lane) & 1u) && key == cand;
-    const uint32_t grp = __ballot_sync(kFull, mem);
-    if (__popc(grp) < 2) break;
-    const uint32_t s0 = __reduce_add_sync(kFull, mem ? (uint32_t)(d & 0x3FFFFF) : 0u);
-    const uint32_t s1 = __reduce_add_sync(kFull, mem ? (uint32_t)((d >> 22) & 0x3FFFFF) : 0u);
-    const uint32_t s2 = __reduce_add_sync(kFull, mem ? (uint32_t)(d >> 44) : 0u);
-    const uint32_t mnh = __reduce_min_sync(kFull, mem ? hi : 0xFFFFFFFFu);
-    const uint32_t mnl = __reduce_min_sync(kFull, (mem && hi == mnh) ? lo : 0xFFFFFFFFu);
-    const uint32_t mxh = __reduce_max_sync(kFull, mem ? hi : 0u);
-    const uint32_t mxl = __reduce_max_sync(kFull, (mem && hi == mxh) ? lo : 0u);
-    if (lane == src) {
-      u_cnt = (uint32_t)__popc(grp);
-      u_sum = (u128)s0 + ((u128)s1 << 22) + ((u128)s2 << 44);
-      u_mn = ((uint64_t)mnh << 32) | mnl;
-      u_mx = ((uint64_t)mxh << 32) | mxl;
-      leader = true;
-    }
-    rem &= ~grp;
-  }
-  if (leader || ((rem >> lane) & 1u)) sink.edge_group(key, u_cnt, u_sum, u_mn, u_mx);
-}
 
 // One warp handles 32 consecutive ordered positions p = base + lane of a
 // bucket. fetch(p) returns the record at ordered position p; cstart[c] is the
@@ -216,10 +86,10 @@ __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, 
   if (kExport) {
     if (valid) {
       const uint64_t slot = slot_base + c;
-      a.act_s[out_base + p] = (int32_t)act;
-      a.ex_case[out_base + p] = a.uniq ? a.uniq[slot] : (int32_t)((uint32_t)a.min_case + (uint32_t)slot);
-      a.ex_ts[out_base + p] = ts;
-      a.ex_row[out_base + p] = (int64_t)r.y;
+      if (a.act_s) a.act_s[out_base + p] = (int32_t)act;
+      if (a.ex_case) a.ex_case[out_base + p] = a.uniq ? a.uniq[slot] : (int32_t)((uint32_t)a.min_case + (uint32_t)slot);
+      if (a.ex_ts) a.ex_ts[out_base + p] = ts;
+      if (a.ex_row) a.ex_row[out_base + p] = (int64_t)r.y;
     }
     return;
   }
@@ -514,7 +384,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   }
   SmemSink sink{tkey, tcnt, tminh, tmaxh, tl, tm, (uint32_t)(a.tbl_slots - 1),
                 (uint32_t)__clz((uint32_t)a.tbl_slots) + 1u, a.tbl_mode,
-                a_s ? st : nullptr, a_s ? en : nullptr, S.hl, S.hh, &a};
+                a_s ? st : nullptr, a_s ? en : nullptr, S.hl, S.hh, a.g, a.g_start, a.g_end};
   uint32_t n_sorted = 0;
   // Buckets are claimed one ahead (misc[0] and misc[1] alternate between the
   // current and the next claim): while a bucket is processed, lane 0 of the

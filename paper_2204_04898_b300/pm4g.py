@@ -51,6 +51,17 @@ class _FilterSpec(ctypes.Structure):
     _fields_ = [("attr_set", _P), ("n_attr", _i32), ("t_lo", _i64), ("t_hi", _i64), ("mode", _i32)]
 
 
+class _BatchSpec(ctypes.Structure):
+    _fields_ = [("n_sub", _i32), ("attr_off", _P), ("attr_vals", _P), ("t_lo", _P), ("t_hi", _P),
+                ("mode", _P)]
+
+
+class _BatchDfg(ctypes.Structure):
+    _fields_ = [("n_sub", _i32), ("n_activities", _i32), ("n_events", _P), ("n_cases", _P),
+                ("edge_off", _P), ("src", _P), ("dst", _P), ("count", _P), ("sum_lo", _P), ("sum_hi", _P),
+                ("min", _P), ("max", _P), ("mean", _P), ("start", _P), ("end", _P), ("freq", _P)]
+
+
 LIBRARY = _build.LIB
 if not os.path.exists(LIBRARY):
     raise ImportError(f"{LIBRARY} is missing: build it with `python -m paper_2204_04898_b300.build`")
@@ -75,6 +86,8 @@ lib.pm4g_start_end.argtypes = [_P, _P, _P, _P]
 lib.pm4g_variants.argtypes = [_P, _i64, _u32, ctypes.POINTER(_Variants)]
 lib.pm4g_variants_free.argtypes = [ctypes.POINTER(_Variants)]
 lib.pm4g_filter.argtypes = [_P, ctypes.POINTER(_FilterSpec), ctypes.POINTER(_P)]
+lib.pm4g_batch_dfg.argtypes = [_P, ctypes.POINTER(_BatchSpec), ctypes.POINTER(_BatchDfg)]
+lib.pm4g_batch_dfg_free.argtypes = [ctypes.POINTER(_BatchDfg)]
 lib.pm4g_last_error.restype = ctypes.c_char_p
 lib.pm4g_last_error.argtypes = []
 lib.pm4g_dfg_noalloc.argtypes = [_P, _P, _P, _i64, _i32, _P] + [_P] * 7
@@ -283,6 +296,62 @@ def pm4g_filter(log: int, attr_set=None, t_lo: int = -(2**63), t_hi: int = 2**63
     h = _P()
     _check(lib.pm4g_filter(log, ctypes.byref(spec), ctypes.byref(h)), "pm4g_filter")
     return h.value
+
+
+@dataclass
+class BatchDfg:
+    """Per-sub-log results of pm4g_batch_dfg; sub-log i's edges are rows
+    edge_off[i]:edge_off[i+1] of the edge arrays."""
+    n_events: np.ndarray   # int64[Q]
+    n_cases: np.ndarray    # int64[Q]
+    edge_off: np.ndarray   # int64[Q+1]
+    src: np.ndarray
+    dst: np.ndarray
+    count: np.ndarray
+    sum_lo: np.ndarray
+    sum_hi: np.ndarray
+    min: np.ndarray
+    max: np.ndarray
+    mean: np.ndarray
+    start: np.ndarray      # uint64[Q, A]
+    end: np.ndarray
+    freq: np.ndarray
+
+    def sub(self, i: int) -> dict:
+        a, b = int(self.edge_off[i]), int(self.edge_off[i + 1])
+        return {k: getattr(self, k)[a:b] for k in ("src", "dst", "count", "sum_lo", "sum_hi", "min", "max", "mean")}
+
+
+def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes) -> BatchDfg:
+    """Batched drill-down: sub-log i keeps the cases whose attribute is in
+    attr_sets[i] (empty or None: all) and applies window [t_lo[i], t_hi[i]]
+    with mode modes[i]."""
+    Q = len(t_lo)
+    sets = [np.asarray(x if x is not None else [], np.int32).ravel() for x in attr_sets]
+    if len(sets) != Q or len(t_hi) != Q or len(modes) != Q:
+        raise ValueError("spec lists differ in length")
+    off = np.zeros(Q + 1, np.int64)
+    off[1:] = np.cumsum([x.size for x in sets])
+    vals = np.ascontiguousarray(np.concatenate(sets) if Q else np.empty(0, np.int32), np.int32)
+    tl = np.ascontiguousarray(t_lo, np.int64)
+    th = np.ascontiguousarray(t_hi, np.int64)
+    md = np.ascontiguousarray(modes, np.int32)
+    spec = _BatchSpec(Q, off.ctypes.data, vals.ctypes.data if vals.size else None, tl.ctypes.data,
+                      th.ctypes.data, md.ctypes.data)
+    r = _BatchDfg()
+    _check(lib.pm4g_batch_dfg(log, ctypes.byref(spec), ctypes.byref(r)), "pm4g_batch_dfg")
+    try:
+        A = r.n_activities
+        eo = _np(r.edge_off, Q + 1, np.int64)
+        E = int(eo[-1]) if Q else 0
+        u = np.uint64
+        return BatchDfg(_np(r.n_events, Q, np.int64), _np(r.n_cases, Q, np.int64), eo,
+                        _np(r.src, E, np.int32), _np(r.dst, E, np.int32), _np(r.count, E, u),
+                        _np(r.sum_lo, E, u), _np(r.sum_hi, E, u), _np(r.min, E, u), _np(r.max, E, u),
+                        _np(r.mean, E, np.float64), _np(r.start, Q * A, u).reshape(Q, A),
+                        _np(r.end, Q * A, u).reshape(Q, A), _np(r.freq, Q * A, u).reshape(Q, A))
+    finally:
+        lib.pm4g_batch_dfg_free(ctypes.byref(r))
 
 
 def pm4g_dfg_noalloc(case_id, activity, ts_ns, n_activities: int, stream: int | None = None) -> dict:

@@ -1,0 +1,165 @@
+"""Batched drill-down (pm4g_batch_dfg) against the CPU oracle, bit-exact: for
+every sub-log of a batch, the oracle filters the rows (attribute set, window,
+mode) and summarises the sub-log; the batch's sizes, edges (count, 128-bit
+sum, min, max, mean bits) and start/end/freq rows must equal it. All calls go
+through the C ABI."""
+
+import numpy as np
+import pytest
+
+import oracle
+import pm4g_synth as synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm4g():
+    from paper_2204_04898_b300 import pm4g as m
+    return m
+
+
+@pytest.fixture()
+def ctx(pm4g):
+    c = pm4g.pm4g_ctx_create(0)
+    yield c
+    pm4g.pm4g_ctx_destroy(c)
+
+
+def _load(pm4g, ctx, L, with_attr=True):
+    import torch
+    cols = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (L.case_id, L.activity, L.ts_ns)]
+    attr = torch.from_numpy(np.ascontiguousarray(L.case_attr)).cuda() if with_attr else None
+    return pm4g.pm4g_load_log(ctx, *cols, case_attr=attr, n_activities=L.n_activities)
+
+
+def _check_batch(B, L, specs, with_attr=True):
+    A = L.n_activities
+    assert B.edge_off.shape[0] == len(specs) + 1
+    for i, (aset, lo, hi, mode) in enumerate(specs):
+        rows = oracle.filter_rows(L.case_id, L.activity, L.ts_ns, L.case_attr if with_attr else None, A,
+                                  aset, lo, hi, mode)
+        R = oracle.summarize(L.case_id[rows], L.activity[rows], L.ts_ns[rows], A)
+        assert B.n_events[i] == rows.shape[0], f"sub-log {i}: n_events"
+        assert B.n_cases[i] == R.n_cases, f"sub-log {i}: n_cases"
+        s = B.sub(i)
+        for name, got, want in (("src", s["src"], R.src), ("dst", s["dst"], R.dst), ("count", s["count"], R.count),
+                                ("sum_lo", s["sum_lo"], R.sum_lo), ("sum_hi", s["sum_hi"], R.sum_hi),
+                                ("min", s["min"], R.min), ("max", s["max"], R.max)):
+            assert np.array_equal(got, want), f"sub-log {i}: {name} differs"
+        assert np.array_equal(s["mean"].view(np.uint64), R.mean.view(np.uint64)), f"sub-log {i}: mean"
+        assert np.array_equal(B.start[i], R.start), f"sub-log {i}: start"
+        assert np.array_equal(B.end[i], R.end), f"sub-log {i}: end"
+        assert np.array_equal(B.freq[i], R.freq), f"sub-log {i}: freq"
+
+
+def _random_specs(L, rng, n, max_attrs=200):
+    t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+    specs = []
+    for _ in range(n):
+        k = int(rng.integers(0, max_attrs))
+        aset = rng.integers(-5, 4100, k).astype(np.int32)  # values outside the log's range too
+        if k and rng.random() < 0.3:
+            aset = np.concatenate([aset, aset[: k // 2]])  # repeats
+        lo = t0 + int(rng.uniform(-0.1, 0.8) * (t1 - t0))
+        hi = lo + int(rng.uniform(-0.05, 0.7) * (t1 - t0))  # sometimes hi < lo
+        specs.append((aset, lo, hi, int(rng.integers(0, 4))))
+    return specs
+
+
+def _run(pm4g, log, specs):
+    return pm4g.pm4g_batch_dfg(log, [s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs],
+                               [s[3] for s in specs])
+
+
+def test_batch_random_subsets(pm4g, ctx):
+    L = synth.generate(synth.drilldown_log(8000))
+    log = _load(pm4g, ctx, L)
+    try:
+        t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+        specs = [(np.empty(0, np.int32), t0, t1, m) for m in range(4)]       # whole log, every mode
+        specs += [(np.empty(0, np.int32), t1 + 1, t1 + 10, 1)]               # window after the log
+        specs += [(np.array([5000], np.int32), t0, t1, 0)]                    # absent attribute
+        specs += _random_specs(L, np.random.default_rng(11), 60)
+        _check_batch(_run(pm4g, log, specs), L, specs)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_batch_equals_plain_filter_calls(pm4g, ctx):
+    """The batch gives what pm4g_filter + the DFG queries give, sub-log by sub-log."""
+    L = synth.generate(synth.drilldown_log(5000))
+    log = _load(pm4g, ctx, L)
+    try:
+        specs = _random_specs(L, np.random.default_rng(12), 12)
+        B = _run(pm4g, log, specs)
+        for i, (aset, lo, hi, mode) in enumerate(specs):
+            f = pm4g.pm4g_filter(log, np.unique(aset), lo, hi, mode)
+            try:
+                p = pm4g.pm4g_perf_dfg(f)
+                st, en, fr = pm4g.pm4g_start_end(f, L.n_activities)
+                s = B.sub(i)
+                assert pm4g.pm4g_log_info(f) == (B.n_events[i], B.n_cases[i])
+                for k in ("src", "dst", "count", "sum_lo", "sum_hi", "min", "max"):
+                    assert np.array_equal(getattr(p, k), s[k]), k
+                assert np.array_equal(st, B.start[i]) and np.array_equal(en, B.end[i])
+                assert np.array_equal(fr, B.freq[i])
+            finally:
+                pm4g.pm4g_log_free(f)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_batch_large_subsets_split_into_items(pm4g, ctx):
+    """Sub-logs far larger than one work item (the whole log, wide windows)
+    are split across CTAs and merged exactly; long cases and the sorted-case
+    path are in the mix."""
+    L = synth.generate(synth.large_log(60_000))
+    rng = np.random.default_rng(13)
+    L.case_attr = (L.case_id.astype(np.int64) * 7919 % 50).astype(np.int32)
+    log = _load(pm4g, ctx, L)
+    try:
+        t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+        specs = [(np.empty(0, np.int32), t0, t1, 0), (np.empty(0, np.int32), t0, (t0 + t1) // 2, 1),
+                 (np.arange(0, 50, 2, dtype=np.int32), t0 + (t1 - t0) // 4, t1, 3)]
+        specs += _random_specs(L, rng, 8, max_attrs=40)
+        _check_batch(_run(pm4g, log, specs), L, specs)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_batch_without_attributes(pm4g, ctx):
+    L = synth.generate(synth.single_log(3000))
+    log = _load(pm4g, ctx, L, with_attr=False)
+    try:
+        t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+        specs = [(np.empty(0, np.int32), t0 + (t1 - t0) // 3, t1 - (t1 - t0) // 3, m) for m in range(4)]
+        _check_batch(_run(pm4g, log, specs), L, specs, with_attr=False)
+        with pytest.raises(pm4g.Pm4gError) as e:
+            _run(pm4g, log, [(np.array([1], np.int32), t0, t1, 0)])
+        assert e.value.status == pm4g.EINVAL
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_batch_edge_cases(pm4g, ctx):
+    L = synth.generate(synth.drilldown_log(500))
+    log = _load(pm4g, ctx, L)
+    try:
+        B = _run(pm4g, log, [])
+        assert B.edge_off.tolist() == [0] and B.src.size == 0
+        with pytest.raises(pm4g.Pm4gError) as e:
+            _run(pm4g, log, [(np.empty(0, np.int32), 0, 1, 7)])
+        assert e.value.status == pm4g.EINVAL
+    finally:
+        pm4g.pm4g_log_free(log)
+    # an empty log: every sub-log is empty
+    e = np.empty(0, np.int32)
+    L0 = synth.EventLog(e, e, np.empty(0, np.int64), e, 3)
+    log = _load(pm4g, ctx, L0)
+    try:
+        B = _run(pm4g, log, [(np.empty(0, np.int32), 0, 10, 1), (np.empty(0, np.int32), 0, 10, 0)])
+        assert B.n_events.tolist() == [0, 0] and B.edge_off.tolist() == [0, 0, 0]
+        assert B.start.shape == (2, 3) and not B.start.any()
+    finally:
+        pm4g.pm4g_log_free(log)
