@@ -10,6 +10,15 @@ One step = pm4g_load_log (device-resident columns) + pm4g_dfg + pm4g_perf_dfg +
 pm4g_start_end + pm4g_variants(top_k) + pm4g_log_free. Prints one JSON line.
 Under torchrun every rank processes its own copy of the workload (replicas;
 weak scaling); value = events of all ranks / max rank time.
+
+    python bench.py --mode drilldown [--views 4096] [--plain-views 4096]
+
+Drill-down: a resident drilldown_log (100M events, A = 2000, case attributes)
+and 4096 drill-down views (attribute set + time window, EVENTS mode). One step
+= one pm4g_batch_dfg call over all views (filter + frequency/performance DFG +
+start/end per view, results on the host); value = sub-log events / step time.
+The same views through plain calls (pm4g_filter + pm4g_perf_dfg +
+pm4g_start_end + pm4g_log_free per view) are timed once beside it.
 """
 
 from __future__ import annotations
@@ -84,6 +93,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cases", type=int, default=1_000_000)
+    p.add_argument("--mode", default="single", choices=["single", "drilldown"])
+    p.add_argument("--views", type=int, default=4096)
+    p.add_argument("--plain-views", type=int, default=4096, help="views timed through plain calls")
     return p.parse_args()
 
 
@@ -200,8 +212,194 @@ def run_reference(args):
         dist.barrier()
 
 
+DD_METRIC = "sub-log events/s for filter+DFG+perf-DFG+start/end over drill-down views (batched)"
+
+
+def drilldown_workload(args):
+    spec = synth.drilldown_log(args.cases) if args.cases else synth.drilldown_log()
+    return spec
+
+
+def oracle_views(oracle, L, views):
+    """Filter then summarise every view with the oracle; returns the sub-log events."""
+    n = 0
+    for v in views:
+        rows = oracle.filter_rows(L.case_id, L.activity, L.ts_ns, L.case_attr, L.n_activities, v.attr_set,
+                                  v.t_lo, v.t_hi, 1)
+        oracle.summarize(L.case_id[rows], L.activity[rows], L.ts_ns[rows], L.n_activities)
+        n += rows.shape[0]
+    return n
+
+
+def run_reference_drilldown(args):
+    """The CPU oracle (filter, then summarise) on a bounded sample of views."""
+    import oracle
+    rank, world, _ = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    spec = drilldown_workload(args)
+    small = spec.scaled(max(2000, min(spec.n_cases, args.cpu_sample_cases // 4)))
+    L = synth.generate(small)
+    views = synth.drilldown_specs(L, n_views=8, lo_events=1e3, hi_events=max(2e3, L.n_events / 4))
+    times, ev = [], 0
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        n = oracle_views(oracle, L, views)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+            ev += n
+    total = sum(times)
+    value = ev / total
+    sample = f"{len(views)} views of a {small.name} law log with {small.n_cases} cases ({L.n_events} events) per step"
+    line = {"impl": "reference", "metric": DD_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": "drilldown_views", "n_cases": small.n_cases,
+                                            "n_events": L.n_events, "n_activities": small.n_activities,
+                                            "n_views": len(views)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_drilldown(args):
+    import torch
+    from paper_2204_04898_b300 import pm4g
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    spec = drilldown_workload(args)
+    t_gen = time.perf_counter()
+    L = synth.generate(spec, pinned=True)
+    t_gen = time.perf_counter() - t_gen
+    A = L.n_activities
+    views = synth.drilldown_specs(L, n_views=args.views)
+    sets = [v.attr_set for v in views]
+    lo = [v.t_lo for v in views]
+    hi = [v.t_hi for v in views]
+    modes = [pm4g.TW_EVENTS] * len(views)
+    dev = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns, L.case_attr)]
+    stream = torch.cuda.Stream()
+    ctx = pm4g.pm4g_ctx_create(local, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    log = pm4g.pm4g_load_log(ctx, *dev[:3], case_attr=dev[3], n_activities=A)
+    torch.cuda.synchronize()
+    load_ms = 1e3 * (time.perf_counter() - t)
+    buf = pm4g.BatchBuffers(len(views), A, 0)  # page-locked result buffers, reused every step
+    t = time.perf_counter()
+    B = pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf)  # first call builds the drill-down index
+    first_ms = 1e3 * (time.perf_counter() - t)
+    sub_events = int(B.n_events.sum())
+    out_edges = int(B.edge_off[-1])
+    for _ in range(max(0, args.warmup - 1)):
+        pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf)
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 1)
+    pm4g.pm4g_ctx_timing_reset(ctx)
+    launches0 = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t
+    dev_ms = ev0.elapsed_time(ev1) / args.steps
+    wall_ms = 1e3 * wall / args.steps
+    n_b, batch_ms = pm4g.pm4g_ctx_timing(ctx, "batch")
+    launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0] - launches0
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
+    ms = dev_ms
+    if dist is not None:
+        t_ = torch.tensor([ms, wall_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        ms, wall_ms = float(t_[0]), float(t_[1])
+    value = sub_events * world * 1e3 / ms
+    # plain calls over the first plain-views views
+    P = min(args.plain_views, len(views))
+    plain = None
+    if P > 0:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pev = 0
+        for i in range(P):
+            f = pm4g.pm4g_filter(log, sets[i], lo[i], hi[i], pm4g.TW_EVENTS)
+            try:
+                pm4g.pm4g_perf_dfg(f)
+                pm4g.pm4g_start_end(f, A)
+                pev += pm4g.pm4g_log_info(f)[0]
+            finally:
+                pm4g.pm4g_log_free(f)
+        torch.cuda.synchronize()
+        pt = time.perf_counter() - t
+        plain = {"value": pev / pt, "unit": UNIT, "views": P, "ms_per_view": 1e3 * pt / P,
+                 "calls": "pm4g_filter + pm4g_perf_dfg + pm4g_start_end + pm4g_log_free per view"}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        small = spec.scaled(max(2000, min(spec.n_cases, args.cpu_sample_cases // 4)))
+        S = synth.generate(small)
+        sv = synth.drilldown_specs(S, n_views=8, lo_events=1e3, hi_events=max(2e3, S.n_events / 4))
+        t = time.perf_counter()
+        n = oracle_views(oracle, S, sv)
+        dt = time.perf_counter() - t
+        cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(sv)} views of a {small.name} law log with {small.n_cases} cases "
+                         f"({S.n_events} events), one run, {dt:.1f} s on 1 of {os.cpu_count()} host cores"}
+    res_bytes = out_edges * (4 + 4 + 5 * 8 + 8) + len(views) * (3 * A * 8 + 24)
+    spec_bytes = sum(x.size for x in sets) * 4 + len(views) * (8 + 8 + 8 + 4)
+    pm4g.pm4g_log_free(log)
+    pm4g.pm4g_ctx_destroy(ctx)
+    if rank != 0:
+        return
+    peak, peak_kind = peaks()
+    per_launch = 12.0 * sub_events  # activity + timestamp of every sub-log event
+    kernel_ms = batch_ms / max(1, args.steps)
+    achieved = per_launch / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else 0.0
+    line = {
+        "metric": DD_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "drilldown_views", "log": spec.name, "n_events": L.n_events,
+                   "n_cases": spec.n_cases, "n_activities": A, "n_views": len(views), "mode": "EVENTS",
+                   "sub_log_events": sub_events, "out_edges": out_edges,
+                   "l2": "resident log %.1f GB of activity+timestamp, larger than L2; no flush" % (12 * L.n_events / 1e9),
+                   "load_ms": round(load_ms, 1), "first_call_ms_with_index": round(first_ms, 1),
+                   "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
+        "wall_ms_per_step": wall_ms,
+        "plain": plain,
+        "roofline": {"bound": "hbm", "kernel": "batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": per_launch, "launch_ms": kernel_ms},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "e2e": {"value": sub_events * world * 1e3 / wall_ms, "unit": UNIT, "h2d_bytes_per_step": int(spec_bytes),
+                "d2h_bytes_per_step": int(res_bytes)},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "drilldown":
+        return run_reference_drilldown(args) if args.impl == "reference" else run_drilldown(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch

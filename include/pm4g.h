@@ -40,7 +40,7 @@ extern "C" {
 /* Status codes */
 #define PM4G_OK 0
 #define PM4G_EINVAL (-1)   /* null pointer, negative size, bad mode or option */
-#define PM4G_ERANGE (-2)   /* an activity code outside [0, n_activities) */
+#define PM4G_ERANGE (-2)   /* an activity code outside [0, n_activities); results larger than caller buffers */
 #define PM4G_ENOMEM (-3)   /* the allocator returned NULL */
 #define PM4G_ECUDA (-4)    /* a CUDA runtime call failed */
 #define PM4G_ETIMEOUT (-5) /* a bounded device wait gave up */
@@ -119,6 +119,8 @@ int pm4g_load_log(pm4g_ctx *ctx, const int32_t *case_id, const int32_t *activity
 
 /* Number of events and of cases (distinct case ids) of a log. */
 int pm4g_log_info(const pm4g_log *log, int64_t *n_events, int64_t *n_cases);
+/* The n_activities the log was loaded with. */
+int pm4g_log_activities(const pm4g_log *log, int32_t *n_activities);
 
 /* Releases a log and its device memory. NULL is accepted. */
 int pm4g_log_free(pm4g_log *log);
@@ -247,6 +249,17 @@ typedef struct {
 } pm4g_batch_dfg_t;
 int pm4g_batch_dfg(pm4g_log *log, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out);
 int pm4g_batch_dfg_free(pm4g_batch_dfg_t *res);
+/* The same results written into caller-owned host arrays, which may be
+ * page-locked and reused from call to call (no allocation, one copy from the
+ * device): every pointer of out must be set, n_events/n_cases to n_sub
+ * entries, edge_off to n_sub + 1, start/end/freq to n_sub * n_activities and
+ * the eight edge arrays to edge_capacity entries (their pointers may be NULL
+ * when edge_capacity is 0). n_sub and n_activities are filled in. If the
+ * batch has more edges than edge_capacity, the call returns PM4G_ERANGE with
+ * every other result written and edge_off[n_sub] = the edges needed; the edge
+ * arrays then hold no complete result. Never free out with
+ * pm4g_batch_dfg_free. */
+int pm4g_batch_dfg_into(pm4g_log *log, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out, int64_t edge_capacity);
 
 /* Allocation-free frequency/performance DFG and start/end counts of a small
  * log. The paper has no counterpart: this serves callers that cannot allocate

@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -240,20 +241,23 @@ __global__ void k_bt_flags(const unsigned long long *__restrict__ cnt, uint64_t 
 __global__ void k_bt_compact(DfgTable acc, const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos,
                              uint64_t n, uint32_t E, uint32_t A, const int32_t *__restrict__ pair, int32_t *src,
                              int32_t *dst, unsigned long long *cnt, unsigned long long *lo, unsigned long long *hi,
-                             unsigned long long *mn, unsigned long long *mx, unsigned long long *freq) {
+                             unsigned long long *mn, unsigned long long *mx, double *mean,
+                             unsigned long long *freq) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     if (!flags[i]) continue;
     const uint32_t p = pos[i];
     const uint32_t e = (uint32_t)(i % E);
     const uint64_t q = i / E;
+    const unsigned long long c = acc.cnt[i], l = acc.lo[i], h = acc.hi[i];
     src[p] = pair[e];
     dst[p] = pair[E + e];
-    cnt[p] = acc.cnt[i];
-    lo[p] = acc.lo[i];
-    hi[p] = acc.hi[i];
+    cnt[p] = c;
+    lo[p] = l;
+    hi[p] = h;
     mn[p] = acc.mn[i];
     mx[p] = acc.mx[i];
-    atomicAdd(&freq[q * A + (uint32_t)pair[e]], acc.cnt[i]);  // out-edges of src
+    mean[p] = edge_mean(h, l, c);
+    atomicAdd(&freq[q * A + (uint32_t)pair[e]], c);  // out-edges of src
   }
 }
 __global__ void k_bt_offsets(const uint32_t *__restrict__ pos, uint32_t Qg, uint32_t E, int64_t *off) {
@@ -368,12 +372,17 @@ int pm4g_batch_dfg_free(pm4g_batch_dfg_t *r) {
   return PM4G_OK;
 }
 
-int pm4g_batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out) {
+// The batched drill-down. With caller buffers (cap >= 0) the results go
+// straight into out's arrays, edges only while they fit cap (the required
+// count is reported through edge_off either way); otherwise the library
+// allocates every array.
+static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out, int64_t cap) {
   if (!L || !spec || !out) {
     set_error("pm4g_batch_dfg: NULL argument");
     return PM4G_EINVAL;
   }
-  memset(out, 0, sizeof(*out));
+  const bool caller = cap >= 0;
+  if (!caller) memset(out, 0, sizeof(*out));
   const int32_t Q = spec->n_sub;
   if (Q < 0 || (Q > 0 && (!spec->attr_off || !spec->t_lo || !spec->t_hi || !spec->mode))) {
     set_error("pm4g_batch_dfg: bad spec (n_sub < 0 or NULL arrays)");
@@ -406,32 +415,64 @@ int pm4g_batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *o
   const uint32_t A = (uint32_t)L->A;
   out->n_sub = Q;
   out->n_activities = (int32_t)A;
-  out->n_events = (int64_t *)calloc(std::max(Q, 1), 8);
-  out->n_cases = (int64_t *)calloc(std::max(Q, 1), 8);
-  out->edge_off = (int64_t *)calloc((size_t)Q + 1, 8);
-  out->start = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
-  out->end = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
-  out->freq = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
-  if (!out->n_events || !out->n_cases || !out->edge_off || !out->start || !out->end || !out->freq) {
-    pm4g_batch_dfg_free(out);
-    return PM4G_ENOMEM;
+  if (caller) {
+    if (!out->n_events || !out->n_cases || !out->edge_off || (Q > 0 && (!out->start || !out->end || !out->freq)) ||
+        (cap > 0 && (!out->src || !out->dst || !out->count || !out->sum_lo || !out->sum_hi || !out->min ||
+                     !out->max || !out->mean))) {
+      set_error("pm4g_batch_dfg_into: NULL result array");
+      return PM4G_EINVAL;
+    }
+    memset(out->edge_off, 0, ((size_t)Q + 1) * 8);
+    if (Q > 0) {
+      memset(out->n_events, 0, (size_t)Q * 8);
+      memset(out->n_cases, 0, (size_t)Q * 8);
+      memset(out->start, 0, (size_t)Q * A * 8);
+      memset(out->end, 0, (size_t)Q * A * 8);
+      memset(out->freq, 0, (size_t)Q * A * 8);
+    }
+  } else {
+    out->n_events = (int64_t *)calloc(std::max(Q, 1), 8);
+    out->n_cases = (int64_t *)calloc(std::max(Q, 1), 8);
+    out->edge_off = (int64_t *)calloc((size_t)Q + 1, 8);
+    out->start = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
+    out->end = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
+    out->freq = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
+    if (!out->n_events || !out->n_cases || !out->edge_off || !out->start || !out->end || !out->freq) {
+      pm4g_batch_dfg_free(out);
+      return PM4G_ENOMEM;
+    }
   }
+  auto fail_out = [&](int code) {
+    if (!caller) pm4g_batch_dfg_free(out);
+    return code;
+  };
+  size_t Et = 0;  // edges so far
+  // room for n edges in the result arrays
+  auto room = [&](size_t n) {
+    if (caller) return n <= (size_t)cap;
+    const size_t m = std::max<size_t>(n, 1);
+    bool ok = true;
+    auto re = [&](auto *&p, size_t el) {
+      void *q = realloc(p, m * el);
+      if (!q) ok = false;
+      else p = (std::remove_reference_t<decltype(p)>)q;
+    };
+    re(out->src, 4);
+    re(out->dst, 4);
+    re(out->count, 8);
+    re(out->sum_lo, 8);
+    re(out->sum_hi, 8);
+    re(out->min, 8);
+    re(out->max, 8);
+    re(out->mean, 8);
+    return ok;
+  };
   if (Q == 0 || L->C == 0) {
-    out->src = (int32_t *)malloc(4);
-    out->dst = (int32_t *)malloc(4);
-    out->count = (uint64_t *)malloc(8);
-    out->sum_lo = (uint64_t *)malloc(8);
-    out->sum_hi = (uint64_t *)malloc(8);
-    out->min = (uint64_t *)malloc(8);
-    out->max = (uint64_t *)malloc(8);
-    out->mean = (double *)malloc(8);
+    if (!room(0)) return fail_out(PM4G_ENOMEM);
     return PM4G_OK;
   }
   int st = ensure_drilldown(L);
-  if (st != PM4G_OK) {
-    pm4g_batch_dfg_free(out);
-    return st;
-  }
+  if (st != PM4G_OK) return fail_out(st);
   const uint32_t E = L->n_edges;
   const uint32_t C = (uint32_t)L->C;
   // per sub-log: its case ranges and their events
@@ -465,9 +506,7 @@ int pm4g_batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *o
   const size_t budget = std::max<size_t>(std::min<size_t>(fr / 3, (size_t)8 << 30), per_sub);
   const int32_t Qg_max = (int32_t)std::max<size_t>(1, std::min<size_t>((size_t)Q, budget / per_sub));
   const uint64_t W = std::max<uint64_t>(1 << 15, total_ev / ((uint64_t)c->num_sms * 4) + 1);
-  std::vector<int32_t> h_src, h_dst;
-  std::vector<uint64_t> h_cnt, h_lo, h_hi, h_mn, h_mx;
-  std::vector<int64_t> h_off;
+  bool overflow = false;
   for (int32_t q0 = 0; q0 < Q && st == PM4G_OK; q0 += Qg_max) {
     const int32_t Qg = std::min(Qg_max, Q - q0);
     Plan P;
@@ -585,44 +624,58 @@ int pm4g_batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *o
     if ((st = d2h(c, &Eg, pos + cellsg, 4)) != PM4G_OK) break;
     int32_t *osrc = S.get<int32_t>(Eg), *odst = S.get<int32_t>(Eg);
     unsigned long long *o5 = S.get<unsigned long long>(5 * (size_t)Eg);
-    if (!osrc || !odst || !o5) {
+    double *omean = S.get<double>(Eg);
+    if (!osrc || !odst || !o5 || !omean) {
       st = PM4G_ENOMEM;
       break;
     }
     {
       KTime t(c, "batch");
       k_bt_compact<<<gN, 256, 0, s>>>(a.acc, flags, pos, cellsg, E, A, L->e_pair.p, osrc, odst, o5, o5 + Eg,
-                                      o5 + 2 * (size_t)Eg, o5 + 3 * (size_t)Eg, o5 + 4 * (size_t)Eg, freq);
+                                      o5 + 2 * (size_t)Eg, o5 + 3 * (size_t)Eg, o5 + 4 * (size_t)Eg, omean, freq);
       if ((st = check_launch(c, "k_bt_compact")) != PM4G_OK) break;
       k_bt_add<<<grid_for((int64_t)Qg * A, 256, 65535), 256, 0, s>>>(freq, a.end, (uint64_t)Qg * A);
       if ((st = check_launch(c, "k_bt_add")) != PM4G_OK) break;
       k_bt_offsets<<<grid_for((int64_t)Qg + 1, 256, 65535), 256, 0, s>>>(pos, (uint32_t)Qg, E, doff);
       if ((st = check_launch(c, "k_bt_offsets")) != PM4G_OK) break;
     }
-    const size_t base = h_src.size();
-    h_src.resize(base + Eg);
-    h_dst.resize(base + Eg);
-    h_cnt.resize(base + Eg);
-    h_lo.resize(base + Eg);
-    h_hi.resize(base + Eg);
-    h_mn.resize(base + Eg);
-    h_mx.resize(base + Eg);
+    const size_t base = Et;
+    const bool fits = !overflow && room(base + Eg);
+    if (!fits) {
+      if (!caller) {
+        st = PM4G_ENOMEM;
+        break;
+      }
+      overflow = true;  // keep counting to report the size needed
+    }
     std::vector<int64_t> goff((size_t)Qg + 1);
     std::vector<unsigned long long> gcnt(2 * (size_t)Qg);
-    D2HBatch hb(c, (size_t)Eg * 48 + (size_t)Qg * (3 * A * 8 + 32) + 16 * 16);
-    hb.add(h_src.data() + base, osrc, (size_t)Eg * 4);
-    hb.add(h_dst.data() + base, odst, (size_t)Eg * 4);
-    hb.add(h_cnt.data() + base, o5, (size_t)Eg * 8);
-    hb.add(h_lo.data() + base, o5 + Eg, (size_t)Eg * 8);
-    hb.add(h_hi.data() + base, o5 + 2 * (size_t)Eg, (size_t)Eg * 8);
-    hb.add(h_mn.data() + base, o5 + 3 * (size_t)Eg, (size_t)Eg * 8);
-    hb.add(h_mx.data() + base, o5 + 4 * (size_t)Eg, (size_t)Eg * 8);
-    hb.add(out->start + (size_t)q0 * A, a.start, (size_t)Qg * A * 8);
-    hb.add(out->end + (size_t)q0 * A, a.end, (size_t)Qg * A * 8);
-    hb.add(out->freq + (size_t)q0 * A, freq, (size_t)Qg * A * 8);
-    hb.add(goff.data(), doff, ((size_t)Qg + 1) * 8);
-    hb.add(gcnt.data(), cnts, 2 * (size_t)Qg * 8);
-    if ((st = hb.finish()) != PM4G_OK) break;
+    cudaError_t ce = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+      if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    };
+    if (fits) {
+      cp(out->src + base, osrc, (size_t)Eg * 4);
+      cp(out->dst + base, odst, (size_t)Eg * 4);
+      cp(out->count + base, o5, (size_t)Eg * 8);
+      cp(out->sum_lo + base, o5 + Eg, (size_t)Eg * 8);
+      cp(out->sum_hi + base, o5 + 2 * (size_t)Eg, (size_t)Eg * 8);
+      cp(out->min + base, o5 + 3 * (size_t)Eg, (size_t)Eg * 8);
+      cp(out->max + base, o5 + 4 * (size_t)Eg, (size_t)Eg * 8);
+      cp(out->mean + base, omean, (size_t)Eg * 8);
+    }
+    cp(out->start + (size_t)q0 * A, a.start, (size_t)Qg * A * 8);
+    cp(out->end + (size_t)q0 * A, a.end, (size_t)Qg * A * 8);
+    cp(out->freq + (size_t)q0 * A, freq, (size_t)Qg * A * 8);
+    cp(goff.data(), doff, ((size_t)Qg + 1) * 8);
+    cp(gcnt.data(), cnts, 2 * (size_t)Qg * 8);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+      set_error("pm4g_batch_dfg: result copy failed: %s", cudaGetErrorString(ce));
+      st = PM4G_ECUDA;
+      break;
+    }
+    Et = base + Eg;
     for (int32_t q = 0; q < Qg; ++q) {
       out->n_events[q0 + q] = (int64_t)gcnt[q];
       out->n_cases[q0 + q] = (int64_t)gcnt[Qg + q];
@@ -630,36 +683,23 @@ int pm4g_batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *o
     }
     out->edge_off[q0 + Qg] = (int64_t)base + goff[Qg];
   }
-  if (st != PM4G_OK) {
-    pm4g_batch_dfg_free(out);
-    return st;
-  }
-  const size_t Et = h_src.size();
-  out->src = (int32_t *)malloc(std::max<size_t>(Et, 1) * 4);
-  out->dst = (int32_t *)malloc(std::max<size_t>(Et, 1) * 4);
-  out->count = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
-  out->sum_lo = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
-  out->sum_hi = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
-  out->min = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
-  out->max = (uint64_t *)malloc(std::max<size_t>(Et, 1) * 8);
-  out->mean = (double *)malloc(std::max<size_t>(Et, 1) * 8);
-  if (!out->src || !out->dst || !out->count || !out->sum_lo || !out->sum_hi || !out->min || !out->max || !out->mean) {
-    pm4g_batch_dfg_free(out);
-    return PM4G_ENOMEM;
-  }
-  if (Et) {
-    memcpy(out->src, h_src.data(), Et * 4);
-    memcpy(out->dst, h_dst.data(), Et * 4);
-    memcpy(out->count, h_cnt.data(), Et * 8);
-    memcpy(out->sum_lo, h_lo.data(), Et * 8);
-    memcpy(out->sum_hi, h_hi.data(), Et * 8);
-    memcpy(out->min, h_mn.data(), Et * 8);
-    memcpy(out->max, h_mx.data(), Et * 8);
-  }
-  // means as in pm4g_perf_dfg: the exact sum converted once, one division
-  for (size_t k = 0; k < Et; ++k) {
-    const u128 sm = ((u128)h_hi[k] << 64) | (u128)h_lo[k];
-    out->mean[k] = (double)sm / (double)h_cnt[k];
+  if (st == PM4G_OK && !caller && !room(Et)) st = PM4G_ENOMEM;  // arrays exist even with no edges
+  if (st != PM4G_OK) return fail_out(st);
+  if (overflow) {
+    set_error("pm4g_batch_dfg_into: %zu edges do not fit the %lld given", Et, (long long)cap);
+    return PM4G_ERANGE;
   }
   return PM4G_OK;
+}
+
+int pm4g_batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out) {
+  return batch_dfg(L, spec, out, -1);
+}
+
+int pm4g_batch_dfg_into(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out, int64_t edge_capacity) {
+  if (edge_capacity < 0) {
+    set_error("pm4g_batch_dfg_into: negative edge capacity");
+    return PM4G_EINVAL;
+  }
+  return batch_dfg(L, spec, out, edge_capacity);
 }

@@ -850,6 +850,15 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
   return PM4G_OK;
 }
 
+int pm4g_log_activities(const pm4g_log *L, int32_t *n_activities) {
+  if (!L || !n_activities) {
+    set_error("pm4g_log_activities: NULL argument");
+    return PM4G_EINVAL;
+  }
+  *n_activities = L->A;
+  return PM4G_OK;
+}
+
 int pm4g_log_info(const pm4g_log *L, int64_t *n_events, int64_t *n_cases) {
   if (!L) {
     set_error("pm4g_log_info: log is NULL");

@@ -93,6 +93,49 @@ __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 }
 
 // ---------------------------------------------------------------------------
+// Mean of a performance-DFG edge: the exact 128-bit duration sum converted to
+// double with round-to-nearest-even (IEEE 754), divided by the count (also
+// converted), so that it equals (double)sum / (double)count computed on the
+// host. The conversion keeps the top 53 significant bits and rounds on the
+// bits below them: above half up, below half down, exactly half to even.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double u128_to_double_rn(uint64_t hi, uint64_t lo) {
+  if (hi == 0) return __ull2double_rn(lo);
+  const int nbits = 128 - __clzll((long long)hi);  // 65..128 significant bits
+  const int shift = nbits - 53;                    // 12..75 low bits dropped
+  uint64_t mant;     // the top 53 bits
+  bool above, half;  // dropped bits compared with half of the last kept bit
+  if (shift < 64) {
+    mant = (hi << (64 - shift)) | (lo >> shift);
+    const uint64_t rem = lo & ((1ull << shift) - 1), h = 1ull << (shift - 1);
+    above = rem > h;
+    half = rem == h;
+  } else {
+    const int s2 = shift - 64;  // 0..11 dropped bits of hi, then all of lo
+    mant = hi >> s2;
+    if (s2 == 0) {
+      above = lo > (1ull << 63);
+      half = lo == (1ull << 63);
+    } else {
+      const uint64_t remh = hi & ((1ull << s2) - 1), hh = 1ull << (s2 - 1);
+      above = remh > hh || (remh == hh && lo != 0);
+      half = remh == hh && lo == 0;
+    }
+  }
+  if (above || (half && (mant & 1ull))) ++mant;
+  int e = shift;
+  if (mant >> 53) {  // rounding carried into a 54th bit
+    mant >>= 1;
+    ++e;
+  }
+  // mant < 2^53 converts exactly; scaling by 2^e (e <= 76) is exact
+  return (double)mant * __longlong_as_double((long long)(1023 + e) << 52);
+}
+__device__ __forceinline__ double edge_mean(uint64_t sum_hi, uint64_t sum_lo, uint64_t count) {
+  return u128_to_double_rn(sum_hi, sum_lo) / __ull2double_rn(count);
+}
+
+// ---------------------------------------------------------------------------
 // Warp helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }

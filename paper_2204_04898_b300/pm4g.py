@@ -76,6 +76,7 @@ lib.pm4g_kernel_names.restype = ctypes.c_char_p
 lib.pm4g_kernel_names.argtypes = []
 lib.pm4g_load_log.argtypes = [_P, _P, _P, _P, _P, _i64, _i32, _u32, ctypes.POINTER(_P)]
 lib.pm4g_log_info.argtypes = [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+lib.pm4g_log_activities.argtypes = [_P, ctypes.POINTER(_i32)]
 lib.pm4g_log_free.argtypes = [_P]
 lib.pm4g_log_export.argtypes = [_P, _P, _P, _P, _P]
 lib.pm4g_dfg.argtypes = [_P, ctypes.POINTER(_Dfg)]
@@ -88,6 +89,7 @@ lib.pm4g_variants_free.argtypes = [ctypes.POINTER(_Variants)]
 lib.pm4g_filter.argtypes = [_P, ctypes.POINTER(_FilterSpec), ctypes.POINTER(_P)]
 lib.pm4g_batch_dfg.argtypes = [_P, ctypes.POINTER(_BatchSpec), ctypes.POINTER(_BatchDfg)]
 lib.pm4g_batch_dfg_free.argtypes = [ctypes.POINTER(_BatchDfg)]
+lib.pm4g_batch_dfg_into.argtypes = [_P, ctypes.POINTER(_BatchSpec), ctypes.POINTER(_BatchDfg), _i64]
 lib.pm4g_last_error.restype = ctypes.c_char_p
 lib.pm4g_last_error.argtypes = []
 lib.pm4g_dfg_noalloc.argtypes = [_P, _P, _P, _i64, _i32, _P] + [_P] * 7
@@ -201,6 +203,12 @@ def pm4g_log_info(log: int) -> tuple[int, int]:
     ne, nc = _i64(), _i64()
     _check(lib.pm4g_log_info(log, ctypes.byref(ne), ctypes.byref(nc)), "pm4g_log_info")
     return ne.value, nc.value
+
+
+def pm4g_log_activities(log: int) -> int:
+    a = _i32()
+    _check(lib.pm4g_log_activities(log, ctypes.byref(a)), "pm4g_log_activities")
+    return a.value
 
 
 def pm4g_log_free(log: int) -> None:
@@ -322,10 +330,46 @@ class BatchDfg:
         return {k: getattr(self, k)[a:b] for k in ("src", "dst", "count", "sum_lo", "sum_hi", "min", "max", "mean")}
 
 
-def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes) -> BatchDfg:
+class BatchBuffers:
+    """Reusable host arrays for pm4g_batch_dfg_into, page-locked through torch
+    when it is available (then the device writes them directly). Results
+    returned with these buffers are views, valid until their next use."""
+
+    def __init__(self, n_sub: int = 0, n_act: int = 0, edges: int = 0):
+        self.n_sub = self.n_act = self.edges = -1
+        self.ensure(n_sub, n_act, edges)
+
+    @staticmethod
+    def _alloc(n, dtype):
+        try:
+            import torch
+            tdt = {np.int32: torch.int32, np.int64: torch.int64, np.uint64: torch.uint64,
+                   np.float64: torch.float64}[dtype]
+            return torch.empty(max(n, 1), dtype=tdt, pin_memory=torch.cuda.is_available()).numpy()
+        except (ImportError, KeyError):
+            return np.empty(max(n, 1), dtype)
+
+    def ensure(self, n_sub: int, n_act: int, edges: int) -> None:
+        if n_sub > self.n_sub or n_act > self.n_act or n_sub * n_act > max(self.n_sub, 0) * max(self.n_act, 0):
+            self.n_sub, self.n_act = max(n_sub, self.n_sub), max(n_act, self.n_act)
+            q, qa = self.n_sub, self.n_sub * self.n_act
+            self.n_events, self.n_cases = self._alloc(q, np.int64), self._alloc(q, np.int64)
+            self.edge_off = self._alloc(q + 1, np.int64)
+            self.start, self.end, self.freq = (self._alloc(qa, np.uint64) for _ in range(3))
+        if edges > self.edges:
+            self.edges = int(edges * 1.25) + 1024
+            e = self.edges
+            self.src, self.dst = self._alloc(e, np.int32), self._alloc(e, np.int32)
+            (self.count, self.sum_lo, self.sum_hi, self.min,
+             self.max) = (self._alloc(e, np.uint64) for _ in range(5))
+            self.mean = self._alloc(e, np.float64)
+
+
+def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers | None = None) -> BatchDfg:
     """Batched drill-down: sub-log i keeps the cases whose attribute is in
     attr_sets[i] (empty or None: all) and applies window [t_lo[i], t_hi[i]]
-    with mode modes[i]."""
+    with mode modes[i]. With `out`, results are written into those reusable
+    buffers (pm4g_batch_dfg_into) and returned as views of them."""
     Q = len(t_lo)
     sets = [np.asarray(x if x is not None else [], np.int32).ravel() for x in attr_sets]
     if len(sets) != Q or len(t_hi) != Q or len(modes) != Q:
@@ -338,6 +382,8 @@ def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes) -> BatchDfg:
     md = np.ascontiguousarray(modes, np.int32)
     spec = _BatchSpec(Q, off.ctypes.data, vals.ctypes.data if vals.size else None, tl.ctypes.data,
                       th.ctypes.data, md.ctypes.data)
+    if out is not None:
+        return _batch_into(log, spec, Q, out)
     r = _BatchDfg()
     _check(lib.pm4g_batch_dfg(log, ctypes.byref(spec), ctypes.byref(r)), "pm4g_batch_dfg")
     try:
@@ -352,6 +398,31 @@ def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes) -> BatchDfg:
                         _np(r.end, Q * A, u).reshape(Q, A), _np(r.freq, Q * A, u).reshape(Q, A))
     finally:
         lib.pm4g_batch_dfg_free(ctypes.byref(r))
+
+
+def pm4g_batch_dfg_into(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers) -> BatchDfg:
+    """pm4g_batch_dfg into caller-owned reusable buffers."""
+    return pm4g_batch_dfg(log, attr_sets, t_lo, t_hi, modes, out=out)
+
+
+def _batch_into(log, spec, Q, out: BatchBuffers) -> BatchDfg:
+    A = pm4g_log_activities(log)
+    out.ensure(Q, A, 0)
+    for _ in range(2):
+        r = _BatchDfg(Q, A, *(x.ctypes.data for x in (out.n_events, out.n_cases, out.edge_off, out.src, out.dst,
+                                                    out.count, out.sum_lo, out.sum_hi, out.min, out.max,
+                                                    out.mean, out.start, out.end, out.freq)))
+        st = lib.pm4g_batch_dfg_into(log, ctypes.byref(spec), ctypes.byref(r), out.edges)
+        if st == ERANGE:  # more edges than the buffers hold: grow and run again
+            out.ensure(Q, A, int(out.edge_off[Q]))
+            continue
+        _check(st, "pm4g_batch_dfg_into")
+        E = int(out.edge_off[Q])
+        return BatchDfg(out.n_events[:Q], out.n_cases[:Q], out.edge_off[:Q + 1], out.src[:E], out.dst[:E],
+                        out.count[:E], out.sum_lo[:E], out.sum_hi[:E], out.min[:E], out.max[:E], out.mean[:E],
+                        out.start[:Q * A].reshape(Q, A), out.end[:Q * A].reshape(Q, A),
+                        out.freq[:Q * A].reshape(Q, A))
+    raise Pm4gError(ERANGE, "pm4g_batch_dfg_into")
 
 
 def pm4g_dfg_noalloc(case_id, activity, ts_ns, n_activities: int, stream: int | None = None) -> dict:

@@ -163,3 +163,76 @@ def test_batch_edge_cases(pm4g, ctx):
         assert B.start.shape == (2, 3) and not B.start.any()
     finally:
         pm4g.pm4g_log_free(log)
+
+
+def test_batch_means_of_sums_beyond_64_bits(pm4g, ctx):
+    """Edge (0, 0) sums above 2^64 whose low bits sit at, just below and just
+    above the rounding boundary of the double conversion (round to nearest,
+    ties to even, carry into a new bit): the batch's means are computed on the
+    device and must have the oracle's (host) bits."""
+    rng = np.random.default_rng(14)
+    spans = []
+    for d in (0, 1, 2, 3, 1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097):
+        spans.append((1 << 63) + d)
+        spans.append((1 << 64) - 1 - d)
+    spans += [int(x) for x in rng.integers(1 << 62, (1 << 63) - 1, 20, dtype=np.int64)]
+    K = len(spans)
+    case = np.repeat(np.arange(K, dtype=np.int32), 2)
+    ts = np.empty(2 * K, np.int64)
+    for k, s in enumerate(spans):
+        lo = -(1 << 63) + (k % 3)  # span < 2^64 fits between the int64 extremes
+        ts[2 * k] = lo
+        ts[2 * k + 1] = lo + s if lo + s < (1 << 63) else (1 << 63) - 1
+    act = np.zeros(2 * K, np.int32)
+    attr = np.repeat(np.arange(K, dtype=np.int32), 2)
+    L = synth.EventLog(case, act, ts, attr, 1)
+    log = _load(pm4g, ctx, L)
+    try:
+        specs = []
+        for _ in range(40):
+            k = int(rng.integers(2, 12))
+            specs.append((rng.choice(K, k, replace=False).astype(np.int32), -(1 << 63), (1 << 63) - 1, 0))
+        specs.append((np.arange(K, dtype=np.int32), -(1 << 63), (1 << 63) - 1, 0))
+        _check_batch(_run(pm4g, log, specs), L, specs)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_batch_into_reused_buffers(pm4g, ctx):
+    """Caller-owned buffers: identical results, a too-small edge capacity
+    reports PM4G_ERANGE with the size needed (the binding then grows and
+    retries), and buffers are reused across calls."""
+    L = synth.generate(synth.drilldown_log(4000))
+    log = _load(pm4g, ctx, L)
+    try:
+        specs = _random_specs(L, np.random.default_rng(15), 20)
+        args = ([s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs], [s[3] for s in specs])
+        B1 = pm4g.pm4g_batch_dfg(log, *args)
+        buf = pm4g.BatchBuffers(1, 1, 8)
+        for _ in range(2):
+            B2 = pm4g.pm4g_batch_dfg_into(log, *args, out=buf)
+            for k in ("n_events", "n_cases", "edge_off", "src", "dst", "count", "sum_lo", "sum_hi", "min", "max",
+                      "start", "end", "freq"):
+                assert np.array_equal(getattr(B1, k), getattr(B2, k)), k
+            assert np.array_equal(B1.mean.view(np.uint64), B2.mean.view(np.uint64))
+        # the raw call with room for one edge
+        import ctypes
+        Q, A = len(specs), L.n_activities
+        small = pm4g.BatchBuffers(Q, A, 1)
+        small.edges = 1
+        off = np.zeros(Q + 1, np.int64)
+        off[1:] = np.cumsum([s[0].size for s in specs])
+        vals = np.ascontiguousarray(np.concatenate([s[0] for s in specs]), np.int32)
+        tl, th = np.array(args[1], np.int64), np.array(args[2], np.int64)
+        md = np.array(args[3], np.int32)
+        spec = pm4g._BatchSpec(Q, off.ctypes.data, vals.ctypes.data, tl.ctypes.data, th.ctypes.data, md.ctypes.data)
+        r = pm4g._BatchDfg(Q, A, *(x.ctypes.data for x in (small.n_events, small.n_cases, small.edge_off, small.src,
+                                                             small.dst, small.count, small.sum_lo, small.sum_hi,
+                                                             small.min, small.max, small.mean, small.start,
+                                                             small.end, small.freq)))
+        st = pm4g.lib.pm4g_batch_dfg_into(log, ctypes.byref(spec), ctypes.byref(r), 1)
+        assert st == pm4g.ERANGE
+        assert int(small.edge_off[Q]) == int(B1.edge_off[-1]) > 1
+        assert np.array_equal(small.n_events[:Q], B1.n_events)
+    finally:
+        pm4g.pm4g_log_free(log)
