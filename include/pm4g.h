@@ -228,6 +228,7 @@ typedef struct {
   const int64_t *t_lo;
   const int64_t *t_hi;
   const int32_t *mode;
+  int64_t var_top_k; /* variants per sub-log: 0 none, < 0 all, else the first var_top_k */
 } pm4g_batch_spec;
 typedef struct {
   int32_t n_sub;
@@ -246,6 +247,19 @@ typedef struct {
   uint64_t *start;    /* [n_sub * n_activities] */
   uint64_t *end;
   uint64_t *freq;
+  /* Variants of each sub-log (pm4g_variants' order and meaning) when
+   * spec->var_top_k != 0: sub-log i has n_variants[i] variants, of which rows
+   * var_off[i] .. var_off[i+1] are returned; row r has var_count[r] cases, the
+   * smallest case id var_min_case[r] and the activity sequence
+   * var_acts[var_seq_off[r] .. var_seq_off[r+1]). */
+  int64_t *n_variants;   /* [n_sub] */
+  int64_t *var_off;      /* [n_sub + 1] */
+  uint64_t *var_count;
+  int32_t *var_min_case;
+  int64_t *var_seq_off;  /* [rows + 1] */
+  int32_t *var_acts;
+  int64_t var_capacity;  /* pm4g_batch_dfg_into: rows var_count/var_min_case hold (var_seq_off one more) */
+  int64_t acts_capacity; /* pm4g_batch_dfg_into: entries var_acts holds */
 } pm4g_batch_dfg_t;
 int pm4g_batch_dfg(pm4g_log *log, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out);
 int pm4g_batch_dfg_free(pm4g_batch_dfg_t *res);
@@ -254,9 +268,13 @@ int pm4g_batch_dfg_free(pm4g_batch_dfg_t *res);
  * device): every pointer of out must be set, n_events/n_cases to n_sub
  * entries, edge_off to n_sub + 1, start/end/freq to n_sub * n_activities and
  * the eight edge arrays to edge_capacity entries (their pointers may be NULL
- * when edge_capacity is 0). n_sub and n_activities are filled in. If the
- * batch has more edges than edge_capacity, the call returns PM4G_ERANGE with
- * every other result written and edge_off[n_sub] = the edges needed; the edge
+ * when edge_capacity is 0); with variants, n_variants to n_sub, var_off to
+ * n_sub + 1 and the variant arrays to out->var_capacity / acts_capacity. n_sub
+ * and n_activities are filled in. If the batch has more edges than
+ * edge_capacity, or more variant rows or activities than the variant
+ * capacities, the call returns PM4G_ERANGE with the sizes written
+ * (edge_off[n_sub] = edges needed, var_off[n_sub] = rows needed, var_seq_off
+ * unchanged and acts_capacity set to the activities needed); the overflowing
  * arrays then hold no complete result. Never free out with
  * pm4g_batch_dfg_free. */
 int pm4g_batch_dfg_into(pm4g_log *log, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out, int64_t edge_capacity);

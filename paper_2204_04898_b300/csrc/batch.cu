@@ -65,6 +65,11 @@ struct BatchArgs {
   DfgTable acc;                   // each array: n_sub rows of n_edges
   unsigned long long *start, *end;  // n_sub rows of n_act
   unsigned long long *n_ev, *n_cs;  // n_sub
+  // variant records (NULL rlen: no variants): one per (sub-log, case of its
+  // ranges) at rbase[range] + position in the range; rlen 0 = nothing kept
+  const uint32_t *rbase;
+  uint32_t *rq, *rslot, *rpos, *rlen;
+  uint64_t *rhash;
 };
 
 __host__ __device__ inline size_t bt_smem_bytes(uint32_t n_act) {
@@ -144,11 +149,16 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
       for (uint32_t k = rg.x + (uint32_t)warp; k < rg.y; k += kBtWarps) {
         const uint32_t slot = a.aslots[k];
         const uint32_t o = a.off[slot], L = a.len[slot];
+        const uint32_t rec = a.rlen ? a.rbase[r] + (k - rg.x) : 0u;
         uint32_t j0, j1;
         kept_run(a, o, L, mode, t_lo, t_hi, j0, j1);
-        if (j1 <= j0) continue;
+        if (j1 <= j0) {
+          if (a.rlen && lane == 0) a.rlen[rec] = 0;
+          continue;
+        }
         ev += j1 - j0;
         cs += 1;
+        uint32_t hl = 0, hh = 0;  // sequence hash of the kept run (as the segment pass forms it)
         for (uint32_t base = j0; base < j1; base += 32) {
           const uint32_t j = base + (uint32_t)lane;
           const bool valid = j < j1;
@@ -169,6 +179,22 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
           }
           const uint32_t e = has_edge ? a.emap[act * A + nact] : 0u;
           aggregate_edges(sink, has_edge, e, (uint64_t)nts - (uint64_t)ts);
+          if (a.rlen && valid) {
+            const uint64_t t = event_hash(act, j - j0, 0);
+            hl += (uint32_t)t;
+            hh += (uint32_t)(t >> 32);
+          }
+        }
+        if (a.rlen) {
+          hl = __reduce_add_sync(kFull, hl);
+          hh = __reduce_add_sync(kFull, hh);
+          if (lane == 0) {
+            a.rq[rec] = sub;
+            a.rslot[rec] = slot;
+            a.rpos[rec] = o + j0;
+            a.rlen[rec] = j1 - j0;
+            a.rhash[rec] = ((uint64_t)hh << 32) | hl;
+          }
         }
       }
     }
@@ -269,6 +295,81 @@ __global__ void k_bt_add(unsigned long long *freq, const unsigned long long *__r
     freq[i] += end[i];
 }
 
+// ---- variants of the sub-logs ----
+__global__ void k_bv_flags(const uint32_t *__restrict__ rlen, uint32_t n, uint32_t *flags) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    flags[i] = rlen[i] ? 1u : 0u;
+}
+// kept records keyed by (sub-log, case slot), so that sorting puts each
+// sub-log's cases in ascending case order
+__global__ void k_bv_keys(const uint32_t *__restrict__ rlen, const uint32_t *__restrict__ rq,
+                          const uint32_t *__restrict__ rslot, const uint32_t *__restrict__ pos, uint32_t n,
+                          uint64_t *keys, uint32_t *idx) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (!rlen[i]) continue;
+    const uint32_t p = pos[i];
+    keys[p] = ((uint64_t)rq[i] << 32) | rslot[i];
+    idx[p] = i;
+  }
+}
+__global__ void k_bv_gather(const uint32_t *__restrict__ idx, uint32_t n, const uint32_t *__restrict__ rq,
+                            const uint32_t *__restrict__ rslot, const uint32_t *__restrict__ rpos,
+                            const uint32_t *__restrict__ rlen, const uint64_t *__restrict__ rhash, uint32_t *sq,
+                            uint32_t *sslot, uint32_t *spos, uint32_t *slen, uint64_t *shash) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const uint32_t i = idx[p];
+    sq[p] = rq[i];
+    sslot[p] = rslot[i];
+    spos[p] = rpos[i];
+    slen[p] = rlen[i];
+    shash[p] = rhash[i];
+  }
+}
+// after the sort by count: the sub-log of each representative, for the
+// stable second sort
+__global__ void k_bv_qkeys(const uint32_t *__restrict__ order, const uint32_t *__restrict__ rep_idx,
+                           const uint32_t *__restrict__ sq, uint32_t V, uint32_t *qk, uint32_t *vq) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < V; t += gridDim.x * blockDim.x) {
+    const uint32_t q = sq[rep_idx[order[t]]];
+    qk[t] = q;
+    atomicAdd(&vq[q], 1u);
+  }
+}
+__global__ void k_bv_take(const uint32_t *__restrict__ vq, uint32_t Qg, int64_t top_k, uint32_t *take) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < Qg; q += gridDim.x * blockDim.x)
+    take[q] = (top_k < 0 || (uint64_t)vq[q] <= (uint64_t)top_k) ? vq[q] : (uint32_t)top_k;
+}
+// output rows: the first take[q] representatives of every sub-log, in
+// (count desc, smallest case asc) order
+__global__ void k_bv_head(const uint32_t *__restrict__ order, const uint32_t *__restrict__ qk,
+                          const uint32_t *__restrict__ vstart, const uint32_t *__restrict__ take,
+                          const uint32_t *__restrict__ row0, const uint32_t *__restrict__ rep_idx,
+                          const uint32_t *__restrict__ vcount, const uint32_t *__restrict__ sslot,
+                          const uint32_t *__restrict__ slen, uint32_t V, int32_t min_case,
+                          const int32_t *__restrict__ uniq, unsigned long long *o_count, int32_t *o_min,
+                          uint32_t *o_len, uint32_t *o_rep) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < V; t += gridDim.x * blockDim.x) {
+    const uint32_t q = qk[t], i = t - vstart[q];
+    if (i >= take[q]) continue;
+    const uint32_t row = row0[q] + i, r = rep_idx[order[t]];
+    const uint32_t slot = sslot[r];
+    o_count[row] = vcount[r];
+    o_min[row] = uniq ? uniq[slot] : (int32_t)((uint32_t)min_case + slot);
+    o_len[row] = slen[r];
+    o_rep[row] = r;
+  }
+}
+__global__ void k_bv_acts(const uint32_t *__restrict__ o_rep, const uint32_t *__restrict__ seq,
+                          const uint32_t *__restrict__ spos, const uint32_t *__restrict__ slen,
+                          const int32_t *__restrict__ act_s, uint32_t rows, int32_t *o_acts) {
+  for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
+    const uint32_t r = o_rep[row], L = slen[r];
+    const int32_t *src = act_s + spos[r];
+    int32_t *dst = o_acts + seq[row];
+    for (uint32_t k = 0; k < L; ++k) dst[k] = src[k];
+  }
+}
+
 // Builds the drill-down index of L (once).
 int ensure_drilldown(pm4g_log *L) {
   if (L->dd_ready) return PM4G_OK;
@@ -347,6 +448,8 @@ int ensure_drilldown(pm4g_log *L) {
 struct Plan {
   std::vector<uint4> items;   // {sub (group-local), r0, r1, events}
   std::vector<uint2> ranges;
+  std::vector<uint32_t> rbase;  // first variant record of each range
+  uint32_t n_rec = 0;
 };
 
 }  // namespace
@@ -368,6 +471,12 @@ int pm4g_batch_dfg_free(pm4g_batch_dfg_t *r) {
   free(r->start);
   free(r->end);
   free(r->freq);
+  free(r->n_variants);
+  free(r->var_off);
+  free(r->var_count);
+  free(r->var_min_case);
+  free(r->var_seq_off);
+  free(r->var_acts);
   memset(r, 0, sizeof(*r));
   return PM4G_OK;
 }
@@ -415,12 +524,22 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
   const uint32_t A = (uint32_t)L->A;
   out->n_sub = Q;
   out->n_activities = (int32_t)A;
+  const bool want_var = spec->var_top_k != 0;
   if (caller) {
     if (!out->n_events || !out->n_cases || !out->edge_off || (Q > 0 && (!out->start || !out->end || !out->freq)) ||
         (cap > 0 && (!out->src || !out->dst || !out->count || !out->sum_lo || !out->sum_hi || !out->min ||
-                     !out->max || !out->mean))) {
-      set_error("pm4g_batch_dfg_into: NULL result array");
+                     !out->max || !out->mean)) ||
+        (want_var && (!out->n_variants || !out->var_off || !out->var_seq_off || out->var_capacity < 0 ||
+                      out->acts_capacity < 0 ||
+                      (out->var_capacity > 0 && (!out->var_count || !out->var_min_case)) ||
+                      (out->acts_capacity > 0 && !out->var_acts)))) {
+      set_error("pm4g_batch_dfg_into: NULL result array or negative capacity");
       return PM4G_EINVAL;
+    }
+    if (want_var) {
+      memset(out->var_off, 0, ((size_t)Q + 1) * 8);
+      out->var_seq_off[0] = 0;
+      if (Q > 0) memset(out->n_variants, 0, (size_t)Q * 8);
     }
     memset(out->edge_off, 0, ((size_t)Q + 1) * 8);
     if (Q > 0) {
@@ -437,11 +556,16 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     out->start = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
     out->end = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
     out->freq = (uint64_t *)calloc(std::max<size_t>((size_t)Q * A, 1), 8);
-    if (!out->n_events || !out->n_cases || !out->edge_off || !out->start || !out->end || !out->freq) {
+    out->n_variants = (int64_t *)calloc(std::max(Q, 1), 8);
+    out->var_off = (int64_t *)calloc((size_t)Q + 1, 8);
+    out->var_seq_off = (int64_t *)calloc(1, 8);
+    if (!out->n_events || !out->n_cases || !out->edge_off || !out->start || !out->end || !out->freq ||
+        !out->n_variants || !out->var_off || !out->var_seq_off) {
       pm4g_batch_dfg_free(out);
       return PM4G_ENOMEM;
     }
   }
+  const int64_t var_cap = caller ? out->var_capacity : -1, acts_cap = caller ? out->acts_capacity : -1;
   auto fail_out = [&](int code) {
     if (!caller) pm4g_batch_dfg_free(out);
     return code;
@@ -467,8 +591,24 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     re(out->mean, 8);
     return ok;
   };
+  size_t Vt = 0, At = 0;  // variant rows and their activities so far
+  // room for n variant rows with m activities
+  auto room_var = [&](size_t n, size_t m) {
+    if (caller) return (int64_t)n <= var_cap && (int64_t)m <= acts_cap;
+    bool ok = true;
+    auto re = [&](auto *&p, size_t cnt, size_t el) {
+      void *q = realloc(p, std::max<size_t>(cnt, 1) * el);
+      if (!q) ok = false;
+      else p = (std::remove_reference_t<decltype(p)>)q;
+    };
+    re(out->var_count, n, 8);
+    re(out->var_min_case, n, 4);
+    re(out->var_seq_off, n + 1, 8);
+    re(out->var_acts, m, 4);
+    return ok;
+  };
   if (Q == 0 || L->C == 0) {
-    if (!room(0)) return fail_out(PM4G_ENOMEM);
+    if (!room(0) || (!caller && !room_var(0, 0))) return fail_out(PM4G_ENOMEM);
     return PM4G_OK;
   }
   int st = ensure_drilldown(L);
@@ -499,16 +639,38 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       total_ev += L->attr_ev[u + 1] - L->attr_ev[u];
     }
   }
-  // sub-log groups whose accumulators fit the memory budget
+  // groups of consecutive sub-logs whose accumulators (and variant records)
+  // fit the memory budget
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
-  const size_t per_sub = (size_t)E * 40 + (size_t)A * 16 + 16 + (size_t)E * 8;
+  const size_t per_sub = (size_t)E * 40 + (size_t)A * 24 + 64 + (size_t)E * 8;
+  const size_t rec_bytes = want_var ? 128 : 0;  // records, their sort and the variant table, per case
   const size_t budget = std::max<size_t>(std::min<size_t>(fr / 3, (size_t)8 << 30), per_sub);
-  const int32_t Qg_max = (int32_t)std::max<size_t>(1, std::min<size_t>((size_t)Q, budget / per_sub));
+  std::vector<std::pair<int32_t, int32_t>> groups;
+  {
+    int32_t g0 = 0;
+    size_t mem = 0;
+    uint64_t recs = 0;
+    for (int32_t i = 0; i < Q; ++i) {
+      uint64_t ci = 0;
+      for (const uint2 &rg : sub_ranges[i]) ci += rg.y - rg.x;
+      const size_t m = per_sub + (size_t)ci * rec_bytes;
+      if (i > g0 && (mem + m > budget || (want_var && recs + ci > (1ull << 31)))) {
+        groups.emplace_back(g0, i - g0);
+        g0 = i;
+        mem = 0;
+        recs = 0;
+      }
+      mem += m;
+      recs += ci;
+    }
+    groups.emplace_back(g0, Q - g0);
+  }
   const uint64_t W = std::max<uint64_t>(1 << 15, total_ev / ((uint64_t)c->num_sms * 4) + 1);
   bool overflow = false;
-  for (int32_t q0 = 0; q0 < Q && st == PM4G_OK; q0 += Qg_max) {
-    const int32_t Qg = std::min(Qg_max, Q - q0);
+  for (const auto &grp : groups) {
+    if (st != PM4G_OK) break;
+    const int32_t q0 = grp.first, Qg = grp.second;
     Plan P;
     for (int32_t q = 0; q < Qg; ++q) {
       const int32_t i = q0 + q;
@@ -533,6 +695,8 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
           const uint64_t pev = rev * (k1 - k) / ncase;
           if (ev > 0 && ev + pev > W) close();
           P.ranges.push_back(make_uint2(k, k1));
+          P.rbase.push_back(P.n_rec);
+          P.n_rec += k1 - k;
           ev += pev;
         }
       }
@@ -549,6 +713,26 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     uint32_t *dwork = S.get<uint32_t>(1);
     int64_t *dtlo = S.get<int64_t>(Qg), *dthi = S.get<int64_t>(Qg);
     int32_t *dmode = S.get<int32_t>(Qg);
+    uint32_t *drbase = nullptr, *rq = nullptr, *rslot = nullptr, *rpos = nullptr, *rlen = nullptr;
+    uint64_t *rhash = nullptr;
+    if (want_var) {
+      drbase = S.get<uint32_t>(P.rbase.size());
+      rq = S.get<uint32_t>(P.n_rec);
+      rslot = S.get<uint32_t>(P.n_rec);
+      rpos = S.get<uint32_t>(P.n_rec);
+      rlen = S.get<uint32_t>(P.n_rec);
+      rhash = S.get<uint64_t>(P.n_rec);
+      if (!drbase || !rq || !rslot || !rpos || !rlen || !rhash) {
+        set_error("pm4g_batch_dfg: out of device memory for variant records");
+        st = PM4G_ENOMEM;
+        break;
+      }
+      if (!P.rbase.empty() && cudaMemcpyAsync(drbase, P.rbase.data(), P.rbase.size() * 4, cudaMemcpyHostToDevice,
+                                              c->stream) != cudaSuccess) {
+        st = PM4G_ECUDA;
+        break;
+      }
+    }
     if (!acc || !se || !cnts || !ditems || !dranges || !dwork || !dtlo || !dthi || !dmode) {
       set_error("pm4g_batch_dfg: out of device memory");
       st = PM4G_ENOMEM;
@@ -593,6 +777,12 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     a.end = se + (size_t)Qg * A;
     a.n_ev = cnts;
     a.n_cs = cnts + Qg;
+    a.rbase = drbase;
+    a.rq = rq;
+    a.rslot = rslot;
+    a.rpos = rpos;
+    a.rlen = rlen;
+    a.rhash = rhash;
     unsigned long long *freq = se + 2 * (size_t)Qg * A;
     if (!P.items.empty()) {
       const size_t smem = bt_smem_bytes(A);
@@ -639,6 +829,138 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       k_bt_offsets<<<grid_for((int64_t)Qg + 1, 256, 65535), 256, 0, s>>>(pos, (uint32_t)Qg, E, doff);
       if ((st = check_launch(c, "k_bt_offsets")) != PM4G_OK) break;
     }
+    // variants of the group's sub-logs
+    uint32_t rows_g = 0, acts_g = 0;
+    uint32_t *vq = nullptr, *row0 = nullptr, *o_seq = nullptr;
+    unsigned long long *o_count = nullptr;
+    int32_t *o_min = nullptr, *o_acts = nullptr;
+    if (want_var) {
+      const uint32_t NR = P.n_rec;
+      uint32_t *kf = S.get<uint32_t>(NR), *kp = S.get<uint32_t>((size_t)NR + 1);
+      vq = S.get<uint32_t>(Qg);
+      row0 = S.get<uint32_t>((size_t)Qg + 1);
+      uint32_t *take = S.get<uint32_t>(Qg), *vstart = S.get<uint32_t>((size_t)Qg + 1);
+      if (!kf || !kp || !vq || !row0 || !take || !vstart) {
+        st = PM4G_ENOMEM;
+        break;
+      }
+      const unsigned gR = grid_for((int64_t)NR, 256, 65535);
+      if (NR) {
+        KTime t(c, "variants");
+        k_bv_flags<<<gR, 256, 0, s>>>(rlen, NR, kf);
+        if ((st = check_launch(c, "k_bv_flags")) != PM4G_OK) break;
+      }
+      if ((st = scan_u32(c, kf, kp, (int64_t)NR)) != PM4G_OK) break;
+      uint32_t NK = 0;
+      if ((st = d2h(c, &NK, kp + NR, 4)) != PM4G_OK) break;
+      uint64_t *k64 = S.get<uint64_t>(NK), *k64b = S.get<uint64_t>(NK);
+      uint32_t *idx = S.get<uint32_t>(NK), *idxb = S.get<uint32_t>(NK);
+      uint32_t *sq = S.get<uint32_t>(NK), *sslot = S.get<uint32_t>(NK), *spos = S.get<uint32_t>(NK);
+      uint32_t *slen = S.get<uint32_t>(NK), *rep_of = S.get<uint32_t>(NK), *vcount = S.get<uint32_t>(NK);
+      uint64_t *shash = S.get<uint64_t>(NK);
+      uint32_t *rf = S.get<uint32_t>(NK), *rp = S.get<uint32_t>((size_t)NK + 1);
+      if (!k64 || !k64b || !idx || !idxb || !sq || !sslot || !spos || !slen || !rep_of || !vcount || !shash || !rf ||
+          !rp) {
+        set_error("pm4g_batch_dfg: out of device memory for variants");
+        st = PM4G_ENOMEM;
+        break;
+      }
+      const unsigned gK = grid_for((int64_t)NK, 256, 65535);
+      if (NK) {
+        {
+          KTime t(c, "variants");
+          k_bv_keys<<<gR, 256, 0, s>>>(rlen, rq, rslot, kp, NR, k64, idx);
+          if ((st = check_launch(c, "k_bv_keys")) != PM4G_OK) break;
+        }
+        const int qb = bits_for((uint64_t)std::max(Qg - 1, 0));
+        if ((st = radix_sort_u64(c, k64, idx, k64b, idxb, NK, 0, 32 + qb)) != PM4G_OK) break;
+        KTime t(c, "variants");
+        k_bv_gather<<<gK, 256, 0, s>>>(idx, NK, rq, rslot, rpos, rlen, rhash, sq, sslot, spos, slen, shash);
+        if ((st = check_launch(c, "k_bv_gather")) != PM4G_OK) break;
+      }
+      VarArgs va{};
+      va.n_slots = NK;
+      va.len = slen;
+      va.hash = shash;
+      va.off = spos;
+      va.act_s = L->act_s.p;
+      va.bits = c->test_hash_bits;
+      va.rep_of = rep_of;
+      va.vcount = vcount;
+      va.cls = sq;
+      if (NK && (st = group_variants(c, va, NK)) != PM4G_OK) break;
+      if (NK) {
+        KTime t(c, "variants");
+        k_rep_flags<<<gK, 256, 0, s>>>(va, rf);
+        if ((st = check_launch(c, "k_rep_flags")) != PM4G_OK) break;
+      }
+      if ((st = scan_u32(c, rf, rp, (int64_t)NK)) != PM4G_OK) break;
+      uint32_t V = 0;
+      if ((st = d2h(c, &V, rp + NK, 4)) != PM4G_OK) break;
+      uint32_t *rep_idx = S.get<uint32_t>(V), *ck = S.get<uint32_t>(V), *ckb = S.get<uint32_t>(V);
+      uint32_t *order = S.get<uint32_t>(V), *orderb = S.get<uint32_t>(V), *qk = S.get<uint32_t>(V);
+      if (!rep_idx || !ck || !ckb || !order || !orderb || !qk) {
+        st = PM4G_ENOMEM;
+        break;
+      }
+      if (cudaMemsetAsync(vq, 0, (size_t)Qg * 4, s) != cudaSuccess) {
+        st = PM4G_ECUDA;
+        break;
+      }
+      if (V) {
+        const int cbits = bits_for((uint64_t)NK);
+        const uint32_t cmask = cbits >= 32 ? 0xFFFFFFFFu : ((1u << cbits) - 1);
+        {
+          KTime t(c, "variants");
+          k_rep_compact<<<gK, 256, 0, s>>>(va, rf, rp, cmask, rep_idx, ck, order);
+          if ((st = check_launch(c, "k_rep_compact")) != PM4G_OK) break;
+        }
+        // (sub-log asc, count desc, smallest case asc): stable sort by count,
+        // then by sub-log; representatives start in (sub-log, case) order
+        if ((st = radix_sort_u32(c, ck, order, ckb, orderb, V, 0, cbits)) != PM4G_OK) break;
+        {
+          KTime t(c, "variants");
+          k_bv_qkeys<<<grid_for(V, 256, 65535), 256, 0, s>>>(order, rep_idx, sq, V, qk, vq);
+          if ((st = check_launch(c, "k_bv_qkeys")) != PM4G_OK) break;
+        }
+        const int qb = bits_for((uint64_t)std::max(Qg - 1, 0));
+        if (qb > 0 && (st = radix_sort_u32(c, qk, order, ckb, orderb, V, 0, qb)) != PM4G_OK) break;
+      }
+      if ((st = scan_u32(c, vq, vstart, Qg)) != PM4G_OK) break;
+      {
+        KTime t(c, "variants");
+        k_bv_take<<<grid_for(Qg, 256, 65535), 256, 0, s>>>(vq, (uint32_t)Qg, spec->var_top_k, take);
+        if ((st = check_launch(c, "k_bv_take")) != PM4G_OK) break;
+      }
+      if ((st = scan_u32(c, take, row0, Qg)) != PM4G_OK) break;
+      if ((st = d2h(c, &rows_g, row0 + Qg, 4)) != PM4G_OK) break;
+      o_count = S.get<unsigned long long>(rows_g);
+      o_min = S.get<int32_t>(rows_g);
+      uint32_t *o_len = S.get<uint32_t>(rows_g), *o_rep = S.get<uint32_t>(rows_g);
+      o_seq = S.get<uint32_t>((size_t)rows_g + 1);
+      if (!o_count || !o_min || !o_len || !o_rep || !o_seq) {
+        st = PM4G_ENOMEM;
+        break;
+      }
+      if (V) {
+        KTime t(c, "variants");
+        k_bv_head<<<grid_for(V, 256, 65535), 256, 0, s>>>(order, qk, vstart, take, row0, rep_idx, vcount, sslot, slen,
+                                                          V, L->min_case, L->uniq.p, o_count, o_min, o_len, o_rep);
+        if ((st = check_launch(c, "k_bv_head")) != PM4G_OK) break;
+      }
+      if ((st = scan_u32(c, o_len, o_seq, rows_g)) != PM4G_OK) break;
+      if ((st = d2h(c, &acts_g, o_seq + rows_g, 4)) != PM4G_OK) break;
+      o_acts = S.get<int32_t>(acts_g);
+      if (!o_acts) {
+        st = PM4G_ENOMEM;
+        break;
+      }
+      if (rows_g) {
+        KTime t(c, "variants");
+        k_bv_acts<<<grid_for(rows_g, 256, 65535), 256, 0, s>>>(o_rep, o_seq, spos, slen, L->act_s.p, rows_g, o_acts);
+        if ((st = check_launch(c, "k_bv_acts")) != PM4G_OK) break;
+      }
+    }
     const size_t base = Et;
     const bool fits = !overflow && room(base + Eg);
     if (!fits) {
@@ -669,6 +991,28 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     cp(out->freq + (size_t)q0 * A, freq, (size_t)Qg * A * 8);
     cp(goff.data(), doff, ((size_t)Qg + 1) * 8);
     cp(gcnt.data(), cnts, 2 * (size_t)Qg * 8);
+    std::vector<uint32_t> gvq, grow0, gseq;
+    bool vfits = false;
+    const size_t vbase = Vt, abase = At;
+    if (want_var) {
+      vfits = !overflow && room_var(vbase + rows_g, abase + acts_g);
+      if (!vfits && !caller) {
+        st = PM4G_ENOMEM;
+        break;
+      }
+      if (!vfits) overflow = true;
+      gvq.resize(Qg);
+      grow0.resize((size_t)Qg + 1);
+      cp(gvq.data(), vq, (size_t)Qg * 4);
+      cp(grow0.data(), row0, ((size_t)Qg + 1) * 4);
+      if (vfits) {
+        gseq.resize((size_t)rows_g + 1);
+        cp(gseq.data(), o_seq, ((size_t)rows_g + 1) * 4);
+        cp(out->var_count + vbase, o_count, (size_t)rows_g * 8);
+        cp(out->var_min_case + vbase, o_min, (size_t)rows_g * 4);
+        cp(out->var_acts + abase, o_acts, (size_t)acts_g * 4);
+      }
+    }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) {
       set_error("pm4g_batch_dfg: result copy failed: %s", cudaGetErrorString(ce));
@@ -682,11 +1026,23 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       out->edge_off[q0 + q] = (int64_t)base + goff[q];
     }
     out->edge_off[q0 + Qg] = (int64_t)base + goff[Qg];
+    if (want_var) {
+      for (int32_t q = 0; q < Qg; ++q) {
+        out->n_variants[q0 + q] = gvq[q];
+        out->var_off[q0 + q] = (int64_t)vbase + grow0[q];
+      }
+      out->var_off[q0 + Qg] = (int64_t)vbase + grow0[Qg];
+      if (vfits)
+        for (uint32_t r = 0; r <= rows_g; ++r) out->var_seq_off[vbase + r] = (int64_t)abase + gseq[r];
+      Vt = vbase + rows_g;
+      At = abase + acts_g;
+    }
   }
-  if (st == PM4G_OK && !caller && !room(Et)) st = PM4G_ENOMEM;  // arrays exist even with no edges
+  if (st == PM4G_OK && !caller && (!room(Et) || !room_var(Vt, At))) st = PM4G_ENOMEM;  // arrays exist even when empty
   if (st != PM4G_OK) return fail_out(st);
   if (overflow) {
-    set_error("pm4g_batch_dfg_into: %zu edges do not fit the %lld given", Et, (long long)cap);
+    if (want_var) out->acts_capacity = (int64_t)At;
+    set_error("pm4g_batch_dfg_into: %zu edges, %zu variant rows, %zu activities do not fit the buffers", Et, Vt, At);
     return PM4G_ERANGE;
   }
   return PM4G_OK;

@@ -1109,53 +1109,31 @@ static uint64_t next_pow2(uint64_t x) {
   return p;
 }
 
-static int ensure_variants(pm4g_log *L) {
-  if (L->var_ready) return PM4G_OK;
-  Ctx *c = L->ctx;
-  const uint64_t R = L->R;
-  PM4G_TRY(ensure_offsets(L));
-  PM4G_TRY(alloc_buf(c, L->vcount, R));
-  PM4G_TRY(alloc_buf(c, L->rep_of, R));
-  PM4G_TRY(alloc_buf(c, L->cvar, R));
-  if (L->C == 0) {
-    L->V = 0;
-    PM4G_TRY(alloc_buf(c, L->rep_slots, 0));
-    PM4G_TRY(alloc_buf(c, L->order, 0));
-    L->var_ready = true;
-    return PM4G_OK;
-  }
+int pm4g::group_variants(Ctx *c, VarArgs a, uint64_t n_items) {
+  const uint64_t R = a.n_slots;
   Scratch S(c);
-  const uint64_t T = next_pow2(std::max<uint64_t>(2 * (uint64_t)L->C, 1024));
+  const uint64_t T = next_pow2(std::max<uint64_t>(2 * n_items, 1024));
   unsigned long long *tkey = S.get<unsigned long long>(T);
   uint32_t *tcnt = S.get<uint32_t>(T), *tmin = S.get<uint32_t>(T);
   uint32_t *grp = S.get<uint32_t>(R);
   uint8_t *isbad = S.get<uint8_t>(R);
-  uint32_t *listA = S.get<uint32_t>(L->C), *listB = S.get<uint32_t>(L->C);
+  uint32_t *listA = S.get<uint32_t>(n_items), *listB = S.get<uint32_t>(n_items);
   uint32_t *n_bad = S.get<uint32_t>(1);
   if (!tkey || !tcnt || !tmin || !grp || !isbad || !listA || !listB || !n_bad) {
     set_error("variants: out of device memory");
     return PM4G_ENOMEM;
   }
-  VarArgs a{};
-  a.n_slots = R;
-  a.len = L->len.p;
-  a.hash = L->hash.p;
-  a.off = L->off.p;
-  a.act_s = L->act_s.p;
-  a.bits = c->test_hash_bits;
   a.tkey = tkey;
   a.tcnt = tcnt;
   a.tmin = tmin;
   a.grp = grp;
-  a.rep_of = L->rep_of.p;
-  a.vcount = L->vcount.p;
   a.isbad = isbad;
   const uint32_t *list = nullptr;
   uint32_t n_list = 0;
   uint32_t *out_list = listA;
   for (uint32_t round = 0;; ++round) {
     const uint64_t items = list ? n_list : R;
-    const uint64_t Tr = next_pow2(std::max<uint64_t>(2 * (list ? n_list : (uint64_t)L->C), 1024));
+    const uint64_t Tr = next_pow2(std::max<uint64_t>(2 * (list ? n_list : n_items), 1024));
     a.tmask = (uint32_t)(Tr - 1);
     PM4G_CK(cudaMemsetAsync(tkey, 0, Tr * 8, c->stream));
     PM4G_CK(cudaMemsetAsync(tcnt, 0, Tr * 4, c->stream));
@@ -1180,6 +1158,35 @@ static int ensure_variants(pm4g_log *L) {
     n_list = nb;
     out_list = (out_list == listA) ? listB : listA;
   }
+  return PM4G_OK;
+}
+
+static int ensure_variants(pm4g_log *L) {
+  if (L->var_ready) return PM4G_OK;
+  Ctx *c = L->ctx;
+  const uint64_t R = L->R;
+  PM4G_TRY(ensure_offsets(L));
+  PM4G_TRY(alloc_buf(c, L->vcount, R));
+  PM4G_TRY(alloc_buf(c, L->rep_of, R));
+  PM4G_TRY(alloc_buf(c, L->cvar, R));
+  if (L->C == 0) {
+    L->V = 0;
+    PM4G_TRY(alloc_buf(c, L->rep_slots, 0));
+    PM4G_TRY(alloc_buf(c, L->order, 0));
+    L->var_ready = true;
+    return PM4G_OK;
+  }
+  Scratch S(c);
+  VarArgs a{};
+  a.n_slots = R;
+  a.len = L->len.p;
+  a.hash = L->hash.p;
+  a.off = L->off.p;
+  a.act_s = L->act_s.p;
+  a.bits = c->test_hash_bits;
+  a.rep_of = L->rep_of.p;
+  a.vcount = L->vcount.p;
+  PM4G_TRY(group_variants(c, a, (uint64_t)L->C));
   // rank representatives by (count desc, smallest case asc)
   uint32_t *flags = S.get<uint32_t>(R), *pos = S.get<uint32_t>(R + 1);
   if (!flags || !pos) return PM4G_ENOMEM;

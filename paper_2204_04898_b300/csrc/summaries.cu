@@ -94,6 +94,7 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
       }
       h = ((uint64_t)hh << 32) | hl;
     }
+    if (a.cls) h ^= fmix64(((uint64_t)a.cls[s] << 1) | 1u);  // keys of different classes differ
     const unsigned long long key = variant_key(h, L, a.bits);
     uint32_t g = (uint32_t)fmix64(key ^ round) & a.tmask;
     for (uint32_t it = 0; it <= a.tmask; ++it) {
@@ -122,7 +123,7 @@ __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, u
     bool same = true;
     if (rep != s) {
       const uint32_t L = a.len[s];
-      same = a.len[rep] == L;
+      same = a.len[rep] == L && (!a.cls || a.cls[rep] == a.cls[s]);
       if (same) {
         const int32_t *x = a.act_s + a.off[s];
         const int32_t *y = a.act_s + a.off[rep];

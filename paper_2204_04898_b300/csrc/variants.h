@@ -21,7 +21,14 @@ struct VarArgs {
   uint32_t *rep_of;
   uint32_t *vcount;
   uint8_t *isbad;
+  const uint32_t *cls;     // optional class of each slot (batched sub-logs): a variant never spans two classes
 };
+
+// Groups the items of `a` (slots with len > 0, or the whole list) by exact
+// sequence: fills a.rep_of (smallest slot of the item's group) and a.vcount
+// (group size, at the representative). n_items bounds the present slots.
+struct Ctx;
+int group_variants(Ctx *c, VarArgs a, uint64_t n_items);
 
 __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t round);
 __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out, uint32_t *n_bad);

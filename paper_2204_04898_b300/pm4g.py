@@ -53,13 +53,15 @@ class _FilterSpec(ctypes.Structure):
 
 class _BatchSpec(ctypes.Structure):
     _fields_ = [("n_sub", _i32), ("attr_off", _P), ("attr_vals", _P), ("t_lo", _P), ("t_hi", _P),
-                ("mode", _P)]
+                ("mode", _P), ("var_top_k", _i64)]
 
 
 class _BatchDfg(ctypes.Structure):
     _fields_ = [("n_sub", _i32), ("n_activities", _i32), ("n_events", _P), ("n_cases", _P),
                 ("edge_off", _P), ("src", _P), ("dst", _P), ("count", _P), ("sum_lo", _P), ("sum_hi", _P),
-                ("min", _P), ("max", _P), ("mean", _P), ("start", _P), ("end", _P), ("freq", _P)]
+                ("min", _P), ("max", _P), ("mean", _P), ("start", _P), ("end", _P), ("freq", _P),
+                ("n_variants", _P), ("var_off", _P), ("var_count", _P), ("var_min_case", _P),
+                ("var_seq_off", _P), ("var_acts", _P), ("var_capacity", _i64), ("acts_capacity", _i64)]
 
 
 LIBRARY = _build.LIB
@@ -324,10 +326,23 @@ class BatchDfg:
     start: np.ndarray      # uint64[Q, A]
     end: np.ndarray
     freq: np.ndarray
+    n_variants: np.ndarray | None = None   # int64[Q] (with variants)
+    var_off: np.ndarray | None = None      # int64[Q+1]
+    var_count: np.ndarray | None = None
+    var_min_case: np.ndarray | None = None
+    var_seq_off: np.ndarray | None = None  # int64[rows+1]
+    var_acts: np.ndarray | None = None
 
     def sub(self, i: int) -> dict:
         a, b = int(self.edge_off[i]), int(self.edge_off[i + 1])
         return {k: getattr(self, k)[a:b] for k in ("src", "dst", "count", "sum_lo", "sum_hi", "min", "max", "mean")}
+
+    def sub_variants(self, i: int) -> tuple[np.ndarray, np.ndarray, list]:
+        """(counts, smallest case ids, sequences) of sub-log i's returned variants."""
+        a, b = int(self.var_off[i]), int(self.var_off[i + 1])
+        so = self.var_seq_off
+        seqs = [tuple(int(x) for x in self.var_acts[so[r]:so[r + 1]]) for r in range(a, b)]
+        return self.var_count[a:b], self.var_min_case[a:b], seqs
 
 
 class BatchBuffers:
@@ -335,9 +350,9 @@ class BatchBuffers:
     when it is available (then the device writes them directly). Results
     returned with these buffers are views, valid until their next use."""
 
-    def __init__(self, n_sub: int = 0, n_act: int = 0, edges: int = 0):
-        self.n_sub = self.n_act = self.edges = -1
-        self.ensure(n_sub, n_act, edges)
+    def __init__(self, n_sub: int = 0, n_act: int = 0, edges: int = 0, var_rows: int = 0, var_acts: int = 0):
+        self.n_sub = self.n_act = self.edges = self.var_rows = self.var_acts_cap = -1
+        self.ensure(n_sub, n_act, edges, var_rows, var_acts)
 
     @staticmethod
     def _alloc(n, dtype):
@@ -349,13 +364,22 @@ class BatchBuffers:
         except (ImportError, KeyError):
             return np.empty(max(n, 1), dtype)
 
-    def ensure(self, n_sub: int, n_act: int, edges: int) -> None:
+    def ensure(self, n_sub: int, n_act: int, edges: int, var_rows: int = 0, var_acts: int = 0) -> None:
         if n_sub > self.n_sub or n_act > self.n_act or n_sub * n_act > max(self.n_sub, 0) * max(self.n_act, 0):
             self.n_sub, self.n_act = max(n_sub, self.n_sub), max(n_act, self.n_act)
             q, qa = self.n_sub, self.n_sub * self.n_act
             self.n_events, self.n_cases = self._alloc(q, np.int64), self._alloc(q, np.int64)
             self.edge_off = self._alloc(q + 1, np.int64)
             self.start, self.end, self.freq = (self._alloc(qa, np.uint64) for _ in range(3))
+            self.n_variants, self.var_off = self._alloc(q, np.int64), self._alloc(q + 1, np.int64)
+        if var_rows > self.var_rows:
+            self.var_rows = int(var_rows * 1.25) + 1024
+            self.var_count = self._alloc(self.var_rows, np.uint64)
+            self.var_min_case = self._alloc(self.var_rows, np.int32)
+            self.var_seq_off = self._alloc(self.var_rows + 1, np.int64)
+        if var_acts > self.var_acts_cap:
+            self.var_acts_cap = int(var_acts * 1.25) + 4096
+            self.var_acts = self._alloc(self.var_acts_cap, np.int32)
         if edges > self.edges:
             self.edges = int(edges * 1.25) + 1024
             e = self.edges
@@ -365,11 +389,13 @@ class BatchBuffers:
             self.mean = self._alloc(e, np.float64)
 
 
-def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers | None = None) -> BatchDfg:
+def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers | None = None,
+                   var_top_k: int = 0) -> BatchDfg:
     """Batched drill-down: sub-log i keeps the cases whose attribute is in
     attr_sets[i] (empty or None: all) and applies window [t_lo[i], t_hi[i]]
-    with mode modes[i]. With `out`, results are written into those reusable
-    buffers (pm4g_batch_dfg_into) and returned as views of them."""
+    with mode modes[i]; var_top_k != 0 adds each sub-log's variants (< 0: all).
+    With `out`, results are written into those reusable buffers
+    (pm4g_batch_dfg_into) and returned as views of them."""
     Q = len(t_lo)
     sets = [np.asarray(x if x is not None else [], np.int32).ravel() for x in attr_sets]
     if len(sets) != Q or len(t_hi) != Q or len(modes) != Q:
@@ -381,9 +407,9 @@ def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers | N
     th = np.ascontiguousarray(t_hi, np.int64)
     md = np.ascontiguousarray(modes, np.int32)
     spec = _BatchSpec(Q, off.ctypes.data, vals.ctypes.data if vals.size else None, tl.ctypes.data,
-                      th.ctypes.data, md.ctypes.data)
+                      th.ctypes.data, md.ctypes.data, int(var_top_k))
     if out is not None:
-        return _batch_into(log, spec, Q, out)
+        return _batch_into(log, spec, Q, out, var_top_k)
     r = _BatchDfg()
     _check(lib.pm4g_batch_dfg(log, ctypes.byref(spec), ctypes.byref(r)), "pm4g_batch_dfg")
     try:
@@ -391,37 +417,57 @@ def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers | N
         eo = _np(r.edge_off, Q + 1, np.int64)
         E = int(eo[-1]) if Q else 0
         u = np.uint64
-        return BatchDfg(_np(r.n_events, Q, np.int64), _np(r.n_cases, Q, np.int64), eo,
-                        _np(r.src, E, np.int32), _np(r.dst, E, np.int32), _np(r.count, E, u),
-                        _np(r.sum_lo, E, u), _np(r.sum_hi, E, u), _np(r.min, E, u), _np(r.max, E, u),
-                        _np(r.mean, E, np.float64), _np(r.start, Q * A, u).reshape(Q, A),
-                        _np(r.end, Q * A, u).reshape(Q, A), _np(r.freq, Q * A, u).reshape(Q, A))
+        B = BatchDfg(_np(r.n_events, Q, np.int64), _np(r.n_cases, Q, np.int64), eo,
+                     _np(r.src, E, np.int32), _np(r.dst, E, np.int32), _np(r.count, E, u),
+                     _np(r.sum_lo, E, u), _np(r.sum_hi, E, u), _np(r.min, E, u), _np(r.max, E, u),
+                     _np(r.mean, E, np.float64), _np(r.start, Q * A, u).reshape(Q, A),
+                     _np(r.end, Q * A, u).reshape(Q, A), _np(r.freq, Q * A, u).reshape(Q, A))
+        if var_top_k:
+            vo = _np(r.var_off, Q + 1, np.int64)
+            rows = int(vo[-1]) if Q else 0
+            so = _np(r.var_seq_off, rows + 1, np.int64)
+            B.n_variants, B.var_off, B.var_seq_off = _np(r.n_variants, Q, np.int64), vo, so
+            B.var_count, B.var_min_case = _np(r.var_count, rows, u), _np(r.var_min_case, rows, np.int32)
+            B.var_acts = _np(r.var_acts, int(so[-1]), np.int32)
+        return B
     finally:
         lib.pm4g_batch_dfg_free(ctypes.byref(r))
 
 
-def pm4g_batch_dfg_into(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers) -> BatchDfg:
+def pm4g_batch_dfg_into(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers,
+                        var_top_k: int = 0) -> BatchDfg:
     """pm4g_batch_dfg into caller-owned reusable buffers."""
-    return pm4g_batch_dfg(log, attr_sets, t_lo, t_hi, modes, out=out)
+    return pm4g_batch_dfg(log, attr_sets, t_lo, t_hi, modes, out=out, var_top_k=var_top_k)
 
 
-def _batch_into(log, spec, Q, out: BatchBuffers) -> BatchDfg:
+def _batch_into(log, spec, Q, out: BatchBuffers, var_top_k: int) -> BatchDfg:
     A = pm4g_log_activities(log)
-    out.ensure(Q, A, 0)
+    out.ensure(Q, A, 0, 1, 1)
     for _ in range(2):
         r = _BatchDfg(Q, A, *(x.ctypes.data for x in (out.n_events, out.n_cases, out.edge_off, out.src, out.dst,
                                                     out.count, out.sum_lo, out.sum_hi, out.min, out.max,
-                                                    out.mean, out.start, out.end, out.freq)))
+                                                    out.mean, out.start, out.end, out.freq, out.n_variants,
+                                                    out.var_off, out.var_count, out.var_min_case,
+                                                    out.var_seq_off, out.var_acts)),
+                      out.var_rows, out.var_acts_cap)
         st = lib.pm4g_batch_dfg_into(log, ctypes.byref(spec), ctypes.byref(r), out.edges)
-        if st == ERANGE:  # more edges than the buffers hold: grow and run again
-            out.ensure(Q, A, int(out.edge_off[Q]))
+        if st == ERANGE:  # more than the buffers hold: grow to the reported sizes and run again
+            out.ensure(Q, A, int(out.edge_off[Q]), int(out.var_off[Q]) if var_top_k else 0,
+                       int(r.acts_capacity) if var_top_k else 0)
             continue
         _check(st, "pm4g_batch_dfg_into")
         E = int(out.edge_off[Q])
-        return BatchDfg(out.n_events[:Q], out.n_cases[:Q], out.edge_off[:Q + 1], out.src[:E], out.dst[:E],
-                        out.count[:E], out.sum_lo[:E], out.sum_hi[:E], out.min[:E], out.max[:E], out.mean[:E],
-                        out.start[:Q * A].reshape(Q, A), out.end[:Q * A].reshape(Q, A),
-                        out.freq[:Q * A].reshape(Q, A))
+        B = BatchDfg(out.n_events[:Q], out.n_cases[:Q], out.edge_off[:Q + 1], out.src[:E], out.dst[:E],
+                     out.count[:E], out.sum_lo[:E], out.sum_hi[:E], out.min[:E], out.max[:E], out.mean[:E],
+                     out.start[:Q * A].reshape(Q, A), out.end[:Q * A].reshape(Q, A),
+                     out.freq[:Q * A].reshape(Q, A))
+        if var_top_k:
+            rows = int(out.var_off[Q])
+            B.n_variants, B.var_off = out.n_variants[:Q], out.var_off[:Q + 1]
+            B.var_count, B.var_min_case = out.var_count[:rows], out.var_min_case[:rows]
+            B.var_seq_off = out.var_seq_off[:rows + 1]
+            B.var_acts = out.var_acts[:int(out.var_seq_off[rows])]
+        return B
     raise Pm4gError(ERANGE, "pm4g_batch_dfg_into")
 
 

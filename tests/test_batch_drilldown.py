@@ -33,7 +33,7 @@ def _load(pm4g, ctx, L, with_attr=True):
     return pm4g.pm4g_load_log(ctx, *cols, case_attr=attr, n_activities=L.n_activities)
 
 
-def _check_batch(B, L, specs, with_attr=True):
+def _check_batch(B, L, specs, with_attr=True, top_k=0):
     A = L.n_activities
     assert B.edge_off.shape[0] == len(specs) + 1
     for i, (aset, lo, hi, mode) in enumerate(specs):
@@ -51,6 +51,13 @@ def _check_batch(B, L, specs, with_attr=True):
         assert np.array_equal(B.start[i], R.start), f"sub-log {i}: start"
         assert np.array_equal(B.end[i], R.end), f"sub-log {i}: end"
         assert np.array_equal(B.freq[i], R.freq), f"sub-log {i}: freq"
+        if top_k:
+            assert B.n_variants[i] == R.n_variants, f"sub-log {i}: n_variants"
+            k = R.n_variants if top_k < 0 else min(top_k, R.n_variants)
+            cnt, mnc, seqs = B.sub_variants(i)
+            assert np.array_equal(cnt, R.var_count[:k]), f"sub-log {i}: variant counts"
+            assert np.array_equal(mnc, R.var_min_case[:k]), f"sub-log {i}: variant min case"
+            assert seqs == R.variant_seqs()[:k], f"sub-log {i}: variant sequences"
 
 
 def _random_specs(L, rng, n, max_attrs=200):
@@ -67,9 +74,9 @@ def _random_specs(L, rng, n, max_attrs=200):
     return specs
 
 
-def _run(pm4g, log, specs):
+def _run(pm4g, log, specs, top_k=0):
     return pm4g.pm4g_batch_dfg(log, [s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs],
-                               [s[3] for s in specs])
+                               [s[3] for s in specs], var_top_k=top_k)
 
 
 def test_batch_random_subsets(pm4g, ctx):
@@ -234,5 +241,56 @@ def test_batch_into_reused_buffers(pm4g, ctx):
         assert st == pm4g.ERANGE
         assert int(small.edge_off[Q]) == int(B1.edge_off[-1]) > 1
         assert np.array_equal(small.n_events[:Q], B1.n_events)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+@pytest.mark.parametrize("top_k", [-1, 1, 3])
+def test_batch_variants(pm4g, ctx, top_k):
+    """Per-sub-log variants (counts, smallest case ids, sequences, order, top-k)
+    computed in the same batch."""
+    L = synth.generate(synth.drilldown_log(6000))
+    log = _load(pm4g, ctx, L)
+    try:
+        t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+        specs = [(np.empty(0, np.int32), t0, t1, 0), (np.empty(0, np.int32), t0, (t0 + t1) // 2, 1)]
+        specs += _random_specs(L, np.random.default_rng(16), 30)
+        _check_batch(_run(pm4g, log, specs, top_k), L, specs, top_k=top_k)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_batch_variants_repeated_sequences(pm4g, ctx):
+    """Few activities, so many cases share sequences within and across
+    sub-logs (a variant must never merge two sub-logs); forced hash collisions
+    take the verification rounds."""
+    L = synth.generate(synth.single_log(4000))
+    L.case_attr = (L.case_id.astype(np.int64) % 7).astype(np.int32)
+    log = _load(pm4g, ctx, L)
+    try:
+        t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+        specs = [(np.array([a], np.int32), t0, t1, 0) for a in range(7)]
+        specs += [(np.array([0, 1], np.int32), t0 + (t1 - t0) // 5, t1, 1), (np.empty(0, np.int32), t0, t1, 3)]
+        _check_batch(_run(pm4g, log, specs, -1), L, specs, top_k=-1)
+        pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TEST_HASH_BITS, 3)
+        _check_batch(_run(pm4g, log, specs, 5), L, specs, top_k=5)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_batch_variants_into_buffers(pm4g, ctx):
+    """Variants through caller buffers, starting too small (grow and retry)."""
+    L = synth.generate(synth.drilldown_log(3000))
+    log = _load(pm4g, ctx, L)
+    try:
+        specs = _random_specs(L, np.random.default_rng(17), 15)
+        args = ([s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs], [s[3] for s in specs])
+        B1 = pm4g.pm4g_batch_dfg(log, *args, var_top_k=-1)
+        buf = pm4g.BatchBuffers(1, 1, 4, 2, 2)
+        B2 = pm4g.pm4g_batch_dfg_into(log, *args, out=buf, var_top_k=-1)
+        for k in ("n_variants", "var_off", "var_count", "var_min_case", "var_seq_off", "var_acts", "edge_off",
+                  "count"):
+            assert np.array_equal(getattr(B1, k), getattr(B2, k)), k
+        _check_batch(B2, L, specs, top_k=-1)
     finally:
         pm4g.pm4g_log_free(log)
