@@ -212,7 +212,7 @@ def run_reference(args):
         dist.barrier()
 
 
-DD_METRIC = "sub-log events/s for filter+DFG+perf-DFG+start/end over drill-down views (batched)"
+DD_METRIC = "sub-log events/s for filter+DFG+perf-DFG+start/end+variants over drill-down views (batched)"
 
 
 def drilldown_workload(args):
@@ -298,12 +298,14 @@ def run_drilldown(args):
     load_ms = 1e3 * (time.perf_counter() - t)
     buf = pm4g.BatchBuffers(len(views), A, 0)  # page-locked result buffers, reused every step
     t = time.perf_counter()
-    B = pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf)  # first call builds the drill-down index
+    vk = args.top_k
+    B = pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf, var_top_k=vk)  # first call builds the index
     first_ms = 1e3 * (time.perf_counter() - t)
     sub_events = int(B.n_events.sum())
     out_edges = int(B.edge_off[-1])
+    out_vars = int(B.var_off[-1])
     for _ in range(max(0, args.warmup - 1)):
-        pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf)
+        pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf, var_top_k=vk)
     pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 1)
     pm4g.pm4g_ctx_timing_reset(ctx)
     launches0 = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
@@ -316,13 +318,14 @@ def run_drilldown(args):
         t = time.perf_counter()
         ev0.record(stream)
         for _ in range(args.steps):
-            pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf)
+            pm4g.pm4g_batch_dfg(log, sets, lo, hi, modes, out=buf, var_top_k=vk)
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t
     dev_ms = ev0.elapsed_time(ev1) / args.steps
     wall_ms = 1e3 * wall / args.steps
     n_b, batch_ms = pm4g.pm4g_ctx_timing(ctx, "batch")
+    var_ms = pm4g.pm4g_ctx_timing(ctx, "variants")[1] / max(1, args.steps)
     launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0] - launches0
     pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
     ms = dev_ms
@@ -343,13 +346,14 @@ def run_drilldown(args):
             try:
                 pm4g.pm4g_perf_dfg(f)
                 pm4g.pm4g_start_end(f, A)
+                pm4g.pm4g_variants(f, top_k=vk)
                 pev += pm4g.pm4g_log_info(f)[0]
             finally:
                 pm4g.pm4g_log_free(f)
         torch.cuda.synchronize()
         pt = time.perf_counter() - t
         plain = {"value": pev / pt, "unit": UNIT, "views": P, "ms_per_view": 1e3 * pt / P,
-                 "calls": "pm4g_filter + pm4g_perf_dfg + pm4g_start_end + pm4g_log_free per view"}
+                 "calls": "pm4g_filter + pm4g_perf_dfg + pm4g_start_end + pm4g_variants + pm4g_log_free per view"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -378,13 +382,14 @@ def run_drilldown(args):
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": "drilldown_views", "log": spec.name, "n_events": L.n_events,
                    "n_cases": spec.n_cases, "n_activities": A, "n_views": len(views), "mode": "EVENTS",
-                   "sub_log_events": sub_events, "out_edges": out_edges,
+                   "sub_log_events": sub_events, "out_edges": out_edges, "var_top_k": vk,
+                   "out_variants": out_vars, "variants_ms_per_step": round(var_ms, 3),
                    "l2": "resident log %.1f GB of activity+timestamp, larger than L2; no flush" % (12 * L.n_events / 1e9),
                    "load_ms": round(load_ms, 1), "first_call_ms_with_index": round(first_ms, 1),
                    "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
         "wall_ms_per_step": wall_ms,
         "plain": plain,
-        "roofline": {"bound": "hbm", "kernel": "batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": "batch_dfg", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "alg_bytes_per_launch": per_launch, "launch_ms": kernel_ms},
         "gpu_launches": int(launches),
