@@ -93,7 +93,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cases", type=int, default=1_000_000)
-    p.add_argument("--mode", default="single", choices=["single", "drilldown"])
+    p.add_argument("--mode", default="single", choices=["single", "drilldown", "serve"])
+    p.add_argument("--rates", default="100,300,1000,3000,10000", help="serve: Poisson request rates (req/s)")
+    p.add_argument("--seconds", type=float, default=3.0, help="serve: seconds of arrivals per rate")
     p.add_argument("--views", type=int, default=4096)
     p.add_argument("--plain-views", type=int, default=4096, help="views timed through plain calls")
     return p.parse_args()
@@ -401,8 +403,117 @@ def run_drilldown(args):
     print(json.dumps(line), flush=True)
 
 
+SERVE_METRIC = "served events/s (filter+DFG views and uploads) under a Poisson request mix; p50/p99 request ms"
+
+
+def run_serve(args):
+    """Serving: a resident serving_log, Poisson arrivals of 70 % filter+DFG,
+    20 % variants top-10, 10 % uploads of LogUniform(10k, 50M)-event logs of
+    the workload-3 law, at each rate; latency from arrival to result on host."""
+    import torch
+    from paper_2204_04898_b300 import pm4g
+    from paper_2204_04898_b300.serve import GpuEngine, Request, Server, latency_summary
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    spec = synth.serving_log(args.cases) if args.cases else synth.serving_log()
+    t_gen = time.perf_counter()
+    L = synth.generate(spec, pinned=True)
+    A = L.n_activities
+    rng = np.random.default_rng(20220416)
+    # upload pool: sizes LogUniform(10k, 50M), workload-3 law, page-locked host columns
+    pool = []
+    for k, n in enumerate(np.exp(rng.uniform(np.log(1e4), np.log(5e7), 6))):
+        cases = max(500, int(n / 20.66))
+        u = synth.generate(synth.very_large_log(cases).scaled(cases, f"upload{k}"), pinned=True)
+        pool.append(u)
+    views = synth.drilldown_specs(L, n_views=2048, seed=20220417)
+    t_gen = time.perf_counter() - t_gen
+    ctx = pm4g.pm4g_ctx_create(local)
+    cols = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns, L.case_attr)]
+    t = time.perf_counter()
+    log = pm4g.pm4g_load_log(ctx, *cols[:3], case_attr=cols[3], n_activities=A)
+    load_ms = 1e3 * (time.perf_counter() - t)
+    del cols
+    torch.cuda.empty_cache()
+    eng = GpuEngine(pm4g, local, log, ctx, upload_slots=2)
+    # warm: drill-down index, variant table, upload contexts
+    eng.batch_dfg([Request("dfg", attr_set=views[0].attr_set, t_lo=views[0].t_lo, t_hi=views[0].t_hi)])
+    eng.variants(10)
+    eng.upload(Request("upload", columns=(pool[0].case_id, pool[0].activity, pool[0].ts_ns), n_activities=A), 0)
+    srv = Server(eng, upload_slots=2)
+    per_rate = []
+    with ClockSampler(local) as clk:
+        for rate in [float(x) for x in args.rates.split(",") if x]:
+            n = max(1, int(rng.poisson(rate * args.seconds)))
+            arrivals = np.sort(rng.uniform(0, args.seconds, n))
+            kinds = rng.choice(3, n, p=[0.7, 0.2, 0.1])
+            reqs = []
+            for kd in kinds:
+                if kd == 0:
+                    v = views[int(rng.integers(len(views)))]
+                    reqs.append(Request("dfg", attr_set=v.attr_set, t_lo=v.t_lo, t_hi=v.t_hi, mode=pm4g.TW_EVENTS))
+                elif kd == 1:
+                    reqs.append(Request("variants", top_k=10))
+                else:
+                    u = pool[int(rng.integers(len(pool)))]
+                    reqs.append(Request("upload", columns=(u.case_id, u.activity, u.ts_ns), n_activities=A))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for r, at in zip(reqs, arrivals):
+                d = t0 + at - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                r.t_arrival = t0 + at
+                srv.submit(r)
+            for r in reqs:
+                r.done.wait(600)
+            t_end = max(r.t_done for r in reqs)
+            ok = [r for r in reqs if r.done.is_set() and r.error is None]
+            ev = sum(r.result["n_events"] for r in ok if r.kind in ("dfg", "upload"))
+            h2d = sum(16 * r.columns[0].shape[0] for r in ok if r.kind == "upload")
+            d2h = sum(sum(v.nbytes for v in r.result.values() if isinstance(v, np.ndarray)) for r in ok)
+            entry = {"rate": rate, "requests": n, "completed": len(ok),
+                     "errors": sum(1 for r in reqs if r.error is not None),
+                     "events_per_s": ev / (t_end - t0), "wall_s": t_end - t0,
+                     "all": latency_summary(reqs),
+                     "dfg": latency_summary([r for r in reqs if r.kind == "dfg"]),
+                     "variants": latency_summary([r for r in reqs if r.kind == "variants"]),
+                     "upload": latency_summary([r for r in reqs if r.kind == "upload"]),
+                     "dfg_batches": len(srv.batches), "upload_h2d_bytes": h2d, "d2h_bytes": d2h,
+                     "error_samples": sorted({f"{r.kind}: {r.error!r}"[:200] for r in reqs if r.error is not None})[:3]}
+            srv.batches.clear()
+            per_rate.append(entry)
+    srv.close()
+    launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
+    eng.close()
+    pm4g.pm4g_log_free(log)
+    pm4g.pm4g_ctx_destroy(ctx)
+    top = per_rate[-1]
+    line = {
+        "metric": SERVE_METRIC, "value": top["events_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(per_rate),
+        "warmup": 1, "ms_per_step": 1e3 * top["wall_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "serving_mix", "log": spec.name, "n_events": L.n_events, "n_cases": spec.n_cases,
+                   "n_activities": A, "mix": "70% filter+DFG (EVENTS), 20% variants top-10, 10% upload",
+                   "upload_events": [int(u.n_events) for u in pool], "seconds_per_rate": args.seconds,
+                   "load_ms": round(load_ms, 1), "generate_s": round(t_gen, 1),
+                   "l2": "resident log larger than L2; no flush"},
+        "rates": per_rate,
+        "p50_ms": top["all"].get("p50_ms"), "p99_ms": top["all"].get("p99_ms"),
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        # every latency above is end to end (arrival to result on the host)
+        "e2e": {"value": top["events_per_s"], "unit": UNIT, "h2d_bytes_per_step": int(top["upload_h2d_bytes"]),
+                "d2h_bytes_per_step": int(top["d2h_bytes"])},
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "serve":
+        return run_serve(args)
     if args.mode == "drilldown":
         return run_reference_drilldown(args) if args.impl == "reference" else run_drilldown(args)
     if args.impl == "reference":

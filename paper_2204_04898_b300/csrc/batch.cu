@@ -786,7 +786,7 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     unsigned long long *freq = se + 2 * (size_t)Qg * A;
     if (!P.items.empty()) {
       const size_t smem = bt_smem_bytes(A);
-      if (cudaFuncSetAttribute(k_batch_dfg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      if (cudaFuncSetAttribute(k_batch_dfg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max()) != cudaSuccess) {
         set_error("pm4g_batch_dfg: shared memory attribute: %s", cudaGetErrorString(cudaGetLastError()));
         st = PM4G_ECUDA;
         break;

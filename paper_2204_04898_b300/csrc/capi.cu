@@ -710,8 +710,8 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
       fa.rec = L->rec.p;
       fa.err_flags = err;
       const uint32_t nbs_max = (uint32_t)std::min<int64_t>(((int64_t)c->smem_optin - 1024) / 4, 1 << 20);
-      cudaFuncSetAttribute(k_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, nbs_max * 4);
-      cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, nbs_max * 4);
+      cudaFuncSetAttribute(k_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
+      cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
       for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
         const uint32_t nbs = std::min(nbs_max, L->nb - b0);
         KTime t(c, "bucket_hist");
@@ -781,8 +781,8 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           {
             KTime t(c, "partition");
             c->launches++;
-            if (launch_partition(1, pa, (unsigned)p_ctas, c->stream) != cudaSuccess) {
-              set_error("launch of k_partition<1> failed: %s", cudaGetErrorString(cudaGetLastError()));
+            if (const cudaError_t le = launch_partition(1, pa, (unsigned)p_ctas, c->stream)) {
+              set_error("launch of k_partition<1> failed: %s", cudaGetErrorString(le));
               fail(PM4G_ECUDA);
               break;
             }
@@ -799,8 +799,8 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           {
             KTime t(c, "partition");
             c->launches++;
-            if (launch_partition(2, pa, nc * (unsigned)pa.splits, c->stream) != cudaSuccess) {
-              set_error("launch of k_partition<2> failed: %s", cudaGetErrorString(cudaGetLastError()));
+            if (const cudaError_t le = launch_partition(2, pa, nc * (unsigned)pa.splits, c->stream)) {
+              set_error("launch of k_partition<2> failed: %s", cudaGetErrorString(le));
               fail(PM4G_ECUDA);
               break;
             }
@@ -817,8 +817,8 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           pa.rec_out = L->rec.p;
           KTime t(c, "partition");
           c->launches++;
-          if (launch_partition(1, pa, (unsigned)p_ctas, c->stream) != cudaSuccess) {
-            set_error("launch of k_partition<1> failed: %s", cudaGetErrorString(cudaGetLastError()));
+          if (const cudaError_t le = launch_partition(1, pa, (unsigned)p_ctas, c->stream)) {
+            set_error("launch of k_partition<1> failed: %s", cudaGetErrorString(le));
             fail(PM4G_ECUDA);
             break;
           }

@@ -107,6 +107,17 @@ struct KTime {
 
 int check_launch(Ctx *c, const char *what);
 
+// A kernel's dynamic shared-memory limit is one setting per function, shared by
+// every thread and context of the process, so it is always set to the
+// device's opt-in maximum (a launch still uses only what it asks for):
+// concurrent calls with different needs cannot undo each other's setting.
+inline int smem_optin_max() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
 // Device arrays of a log or context, through the context's allocator.
 template <class T>
 inline int alloc_buf(Ctx *c, DBuf<T> &b, size_t n) {

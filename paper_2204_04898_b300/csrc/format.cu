@@ -416,11 +416,11 @@ cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaSt
   const size_t smem = part_smem_bytes(a.nbins);
   cudaError_t e;
   if (level == 1) {
-    e = cudaFuncSetAttribute(k_partition<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_partition<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
     if (e != cudaSuccess) return e;
     k_partition<1><<<grid, kPartThreads, smem, s>>>(a);
   } else {
-    e = cudaFuncSetAttribute(k_partition<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_partition<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
     if (e != cudaSuccess) return e;
     k_partition<2><<<grid, kPartThreads, smem, s>>>(a);
   }

@@ -479,11 +479,11 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
 cudaError_t launch_segment(bool exp, const SegArgs &a, unsigned grid, size_t smem, cudaStream_t s) {
   cudaError_t e;
   if (exp) {
-    e = cudaFuncSetAttribute(k_segment<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_segment<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
     if (e != cudaSuccess) return e;
     k_segment<true><<<grid, kSegThreads, smem, s>>>(a);
   } else {
-    e = cudaFuncSetAttribute(k_segment<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_segment<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
     if (e != cudaSuccess) return e;
     k_segment<false><<<grid, kSegThreads, smem, s>>>(a);
   }

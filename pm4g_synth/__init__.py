@@ -143,7 +143,9 @@ def drilldown_log(n_cases: int = 4_850_000) -> LogSpec:
 
 
 def serving_log(n_cases: int = 10_000_000) -> LogSpec:
-    return replace(very_large_log(n_cases), name="serving_log", seed=BASE_SEED + 5)
+    """Workload-3 law with its own seed and a uniform case attribute in
+    [0, 4096), for filter(attribute set, window) requests."""
+    return replace(very_large_log(n_cases), name="serving_log", seed=BASE_SEED + 5, n_attr_values=4096)
 
 
 WORKLOADS = {
