@@ -1112,20 +1112,18 @@ static uint64_t next_pow2(uint64_t x) {
 int pm4g::group_variants(Ctx *c, VarArgs a, uint64_t n_items) {
   const uint64_t R = a.n_slots;
   Scratch S(c);
-  const uint64_t T = next_pow2(std::max<uint64_t>(2 * n_items, 1024));
-  unsigned long long *tkey = S.get<unsigned long long>(T);
-  uint32_t *tcnt = S.get<uint32_t>(T), *tmin = S.get<uint32_t>(T);
+  // table of about 1.5 slots per item (load at most 2/3), a power of two
+  const uint64_t T = next_pow2(std::max<uint64_t>(n_items + n_items / 2, 1024));
+  VarSlot *tab = S.get<VarSlot>(T);
   uint32_t *grp = S.get<uint32_t>(R);
   uint8_t *isbad = S.get<uint8_t>(R);
   uint32_t *listA = S.get<uint32_t>(n_items), *listB = S.get<uint32_t>(n_items);
   uint32_t *n_bad = S.get<uint32_t>(1);
-  if (!tkey || !tcnt || !tmin || !grp || !isbad || !listA || !listB || !n_bad) {
+  if (!tab || !grp || !isbad || !listA || !listB || !n_bad) {
     set_error("variants: out of device memory");
     return PM4G_ENOMEM;
   }
-  a.tkey = tkey;
-  a.tcnt = tcnt;
-  a.tmin = tmin;
+  a.tab = tab;
   a.grp = grp;
   a.isbad = isbad;
   const uint32_t *list = nullptr;
@@ -1133,11 +1131,10 @@ int pm4g::group_variants(Ctx *c, VarArgs a, uint64_t n_items) {
   uint32_t *out_list = listA;
   for (uint32_t round = 0;; ++round) {
     const uint64_t items = list ? n_list : R;
-    const uint64_t Tr = next_pow2(std::max<uint64_t>(2 * (list ? n_list : n_items), 1024));
+    const uint64_t ni = list ? n_list : n_items;
+    const uint64_t Tr = next_pow2(std::max<uint64_t>(ni + ni / 2, 1024));
     a.tmask = (uint32_t)(Tr - 1);
-    PM4G_CK(cudaMemsetAsync(tkey, 0, Tr * 8, c->stream));
-    PM4G_CK(cudaMemsetAsync(tcnt, 0, Tr * 4, c->stream));
-    PM4G_CK(cudaMemsetAsync(tmin, 0xFF, Tr * 4, c->stream));
+    PM4G_CK(cudaMemsetAsync(tab, 0, Tr * sizeof(VarSlot), c->stream));
     PM4G_CK(cudaMemsetAsync(n_bad, 0, 4, c->stream));
     const unsigned g = grid_for((int64_t)items, 256, 65535);
     KTime t(c, "variants");

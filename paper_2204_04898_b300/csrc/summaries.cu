@@ -98,17 +98,17 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
     const unsigned long long key = variant_key(h, L, a.bits);
     uint32_t g = (uint32_t)fmix64(key ^ round) & a.tmask;
     for (uint32_t it = 0; it <= a.tmask; ++it) {
-      const unsigned long long k = *(volatile unsigned long long *)&a.tkey[g];
+      const unsigned long long k = *(volatile unsigned long long *)&a.tab[g].key;
       if (k == key) break;
       if (k == 0) {
-        const unsigned long long old = atomicCAS(&a.tkey[g], 0ull, key);
+        const unsigned long long old = atomicCAS(&a.tab[g].key, 0ull, key);
         if (old == 0 || old == key) break;
       }
       g = (g + 1) & a.tmask;
     }
     a.grp[s] = g;
-    atomicAdd(&a.tcnt[g], 1u);
-    atomicMin(&a.tmin[g], s);
+    atomicAdd(&a.tab[g].cnt, 1u);
+    atomicMax(&a.tab[g].nmin, ~s);
   }
 }
 
@@ -119,7 +119,7 @@ __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, u
     uint32_t s;
     if (!var_item(a, list, n_list, i, s)) continue;
     const uint32_t g = a.grp[s];
-    const uint32_t rep = a.tmin[g];
+    const uint32_t rep = ~a.tab[g].nmin;
     bool same = true;
     if (rep != s) {
       const uint32_t L = a.len[s];
@@ -136,7 +136,7 @@ __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, u
     }
     a.isbad[s] = same ? 0 : 1;
     if (!same) {
-      atomicSub(&a.tcnt[g], 1u);
+      atomicSub(&a.tab[g].cnt, 1u);
       bad_out[atomicAdd(n_bad, 1u)] = s;
     }
   }
@@ -149,9 +149,9 @@ __global__ void k_var_final(VarArgs a, const uint32_t *list, uint32_t n_list) {
     if (!var_item(a, list, n_list, i, s)) continue;
     if (a.isbad[s]) continue;
     const uint32_t g = a.grp[s];
-    const uint32_t rep = a.tmin[g];
+    const uint32_t rep = ~a.tab[g].nmin;
     a.rep_of[s] = rep;
-    if (rep == s) a.vcount[s] = a.tcnt[g];
+    if (rep == s) a.vcount[s] = a.tab[g].cnt;
   }
 }
 

@@ -6,6 +6,15 @@
 
 namespace pm4g {
 
+// One slot of the grouping table (16 bytes, one sector): the group key, its
+// member count and the bitwise complement of its smallest slot (so that an
+// all-zero slot is empty and atomicMax keeps the smallest slot).
+struct __align__(16) VarSlot {
+  unsigned long long key;
+  uint32_t cnt;
+  uint32_t nmin;
+};
+
 struct VarArgs {
   uint64_t n_slots;
   const uint32_t *len;     // per case slot, 0 = no case
@@ -13,9 +22,7 @@ struct VarArgs {
   const uint32_t *off;     // per case slot, first position in the ordered log
   const int32_t *act_s;    // activity of every event in (case, ts, row) order
   int bits;                // key truncation (tests only), 0 = full key
-  unsigned long long *tkey;
-  uint32_t *tcnt;
-  uint32_t *tmin;
+  VarSlot *tab;
   uint32_t tmask;
   uint32_t *grp;
   uint32_t *rep_of;
