@@ -317,7 +317,10 @@ static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) 
 
 // Runs the segment pass over a bucketed log: fills act_s, len, hash, the DFG
 // table, the endpoint counts and (at load) the per-case attribute; sets C.
-static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr) {
+// err_in (optional): a device word to read back with the pass's own counters
+// (one synchronisation for both); its value goes to *err_out.
+static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, const uint32_t *err_in = nullptr,
+                       uint32_t *err_out = nullptr) {
   Ctx *c = L->ctx;
   const size_t cells = (size_t)L->A * L->A;
   PM4G_TRY(alloc_buf(c, L->act_s, L->n));
@@ -339,15 +342,21 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr) {
     return PM4G_OK;
   }
   Scratch S(c);
-  uint32_t *ctr = S.get<uint32_t>(4);  // work, n_ovf
-  unsigned long long *n_cases = S.get<unsigned long long>(2);  // cases, sorted windows
+  // status block: counters {work, n_ovf, -, -}, {cases, sorted windows}, caller's word
+  struct Status {
+    uint32_t ctr[4];
+    unsigned long long nc[2];
+    uint32_t err[4];
+  };
+  Status *blk = S.get<Status>(1);
   uint32_t *ovf = S.get<uint32_t>(L->nb);
-  if (!ctr || !n_cases || !ovf) {
+  if (!blk || !ovf) {
     set_error("segment pass: out of device memory");
     return PM4G_ENOMEM;
   }
-  PM4G_CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), c->stream));
-  PM4G_CK(cudaMemsetAsync(n_cases, 0, 2 * sizeof(unsigned long long), c->stream));
+  uint32_t *ctr = blk->ctr;
+  unsigned long long *n_cases = blk->nc;
+  PM4G_CK(cudaMemsetAsync(blk, 0, sizeof(Status), c->stream));
   const SegConfig sc = seg_config(c, L->clb, L->A);
   SegArgs a = seg_args(L, sc, ctr, ovf, ctr + 1, n_cases);
   a.n_sorted = n_cases + 1;
@@ -366,19 +375,21 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr) {
     const uint32_t nbv = L->nb;
     PM4G_CK(cudaMemcpyAsync(ctr + 1, &nbv, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
   }
-  uint32_t n_ovf = 0;
-  PM4G_TRY(d2h(c, &n_ovf, ctr + 1, sizeof(uint32_t)));
+  if (err_in) PM4G_CK(cudaMemcpyAsync(blk->err, err_in, 4, cudaMemcpyDeviceToDevice, c->stream));
+  Status h{};
+  PM4G_TRY(d2h(c, &h, blk, sizeof(Status)));
+  if (err_out) *err_out = h.err[0];
+  const uint32_t n_ovf = h.ctr[1];
   if (n_ovf) {
     std::vector<uint32_t> list(n_ovf);
     PM4G_TRY(d2h(c, list.data(), ovf, n_ovf * sizeof(uint32_t)));
     std::sort(list.begin(), list.end());
     for (uint32_t b : list) PM4G_TRY(fallback_bucket(L, a, b, false));
+    PM4G_TRY(d2h(c, h.nc, n_cases, sizeof(h.nc)));  // the global path adds its cases
   }
-  unsigned long long nc[2] = {0, 0};
-  PM4G_TRY(d2h(c, nc, n_cases, sizeof(nc)));
-  L->C = (int64_t)nc[0];
+  L->C = (int64_t)h.nc[0];
   auto &sw = c->totals["sorted_windows"];
-  sw.first += (int64_t)nc[1];
+  sw.first += (int64_t)h.nc[1];
   return PM4G_OK;
 }
 
@@ -832,9 +843,8 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         }
       }
       if (st) break;
-      if (fail(run_segment(L, dattr, L->has_attr))) break;
       uint32_t errv = 0;
-      if (fail(d2h(c, &errv, err, 4))) break;
+      if (fail(run_segment(L, dattr, L->has_attr, err, &errv))) break;
       if (errv & 1u) {
         set_error("pm4g_load_log: activity code outside [0, %d)", A);
         fail(PM4G_ERANGE);
