@@ -49,11 +49,11 @@ constexpr int kBtSlots = 8192;  // shared edge table (hashed)
 
 struct BatchArgs {
   const uint32_t *aslots;  // present slots in (attribute, slot) order
-  const uint32_t *off;     // first formatted position of each slot
-  const uint32_t *len;     // events of each slot
+  const uint32_t *aoff;    // first formatted position of each entry of aslots
+  const uint32_t *alen;    // events of each entry of aslots
   const int32_t *act_s;
   const int64_t *ts_s;
-  const uint32_t *emap;  // A * A -> edge index
+  const uint32_t *eidx_s;  // edge index of each event's pair with the next event of its case
   uint32_t n_act;
   uint32_t n_edges;
   const uint4 *items;   // {sub, first range, end range, 0}
@@ -147,8 +147,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
     for (uint32_t r = item.y; r < item.z; ++r) {
       const uint2 rg = a.ranges[r];
       for (uint32_t k = rg.x + (uint32_t)warp; k < rg.y; k += kBtWarps) {
-        const uint32_t slot = a.aslots[k];
-        const uint32_t o = a.off[slot], L = a.len[slot];
+        const uint32_t o = a.aoff[k], L = a.alen[k];
         const uint32_t rec = a.rlen ? a.rbase[r] + (k - rg.x) : 0u;
         uint32_t j0, j1;
         kept_run(a, o, L, mode, t_lo, t_hi, j0, j1);
@@ -162,22 +161,19 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
         for (uint32_t base = j0; base < j1; base += 32) {
           const uint32_t j = base + (uint32_t)lane;
           const bool valid = j < j1;
-          uint32_t act = 0;
+          const bool first = valid && j == j0, last = valid && j + 1 == j1;
+          const bool has_edge = valid && !last;
+          uint32_t act = 0, e = 0;
           int64_t ts = 0;
           if (valid) {
-            act = (uint32_t)a.act_s[o + j];
             ts = a.ts_s[o + j];
+            if (a.rlen || first || last) act = (uint32_t)a.act_s[o + j];
+            if (has_edge) e = a.eidx_s[o + j];
           }
-          if (valid && j == j0) sink.start(act);
-          if (valid && j + 1 == j1) sink.end(act);
-          uint32_t nact = __shfl_down_sync(kFull, act, 1);
+          if (first) sink.start(act);
+          if (last) sink.end(act);
           int64_t nts = __shfl_down_sync(kFull, ts, 1);
-          const bool has_edge = valid && j + 1 < j1;
-          if (lane == 31 && has_edge) {
-            nact = (uint32_t)a.act_s[o + j + 1];
-            nts = a.ts_s[o + j + 1];
-          }
-          const uint32_t e = has_edge ? a.emap[act * A + nact] : 0u;
+          if (lane == 31 && has_edge) nts = a.ts_s[o + j + 1];
           aggregate_edges(sink, has_edge, e, (uint64_t)nts - (uint64_t)ts);
           if (a.rlen && valid) {
             const uint64_t t = event_hash(act, j - j0, 0);
@@ -190,7 +186,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
           hh = __reduce_add_sync(kFull, hh);
           if (lane == 0) {
             a.rq[rec] = sub;
-            a.rslot[rec] = slot;
+            a.rslot[rec] = a.aslots[k];
             a.rpos[rec] = o + j0;
             a.rlen[rec] = j1 - j0;
             a.rhash[rec] = ((uint64_t)hh << 32) | hl;
@@ -255,6 +251,35 @@ __global__ void k_dd_emap(const uint32_t *__restrict__ flags, const uint32_t *__
       pair[E + e] = (int32_t)(i % n_act);
     } else {
       emap[i] = 0xFFFFFFFFu;
+    }
+  }
+}
+
+__global__ void k_dd_case_cols(const uint32_t *__restrict__ aslots, const uint32_t *__restrict__ off,
+                               const uint32_t *__restrict__ len, uint32_t C, uint32_t *aoff, uint32_t *alen) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < C; k += gridDim.x * blockDim.x) {
+    const uint32_t s = aslots[k];
+    aoff[k] = off[s];
+    alen[k] = len[s];
+  }
+}
+// One warp per case: the edge index of every event's pair with the next
+// event of its case (~0 for the case's last event).
+__global__ void k_dd_eidx(const uint32_t *__restrict__ aoff, const uint32_t *__restrict__ alen, uint32_t C,
+                          const int32_t *__restrict__ act_s, const uint32_t *__restrict__ emap, uint32_t A,
+                          uint32_t *eidx) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t k = w0; k < C; k += nw) {
+    const uint32_t o = aoff[k], L = alen[k];
+    for (uint32_t base = 0; base < L; base += 32) {
+      const uint32_t j = base + lane;
+      const uint32_t act = j < L ? (uint32_t)act_s[o + j] : 0u;
+      uint32_t nact = __shfl_down_sync(kFull, act, 1);
+      if (lane == 31 && j + 1 < L) nact = (uint32_t)act_s[o + j + 1];
+      if (j + 1 < L) eidx[o + j] = emap[act * A + nact];
+      else if (j + 1 == L) eidx[o + j] = 0xFFFFFFFFu;
     }
   }
 }
@@ -328,12 +353,27 @@ __global__ void k_bv_gather(const uint32_t *__restrict__ idx, uint32_t n, const 
 // after the sort by count: the sub-log of each representative, for the
 // stable second sort
 __global__ void k_bv_qkeys(const uint32_t *__restrict__ order, const uint32_t *__restrict__ rep_idx,
-                           const uint32_t *__restrict__ sq, uint32_t V, uint32_t *qk, uint32_t *vq) {
+                           const uint32_t *__restrict__ sq, uint32_t V, uint32_t *qk) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < V; t += gridDim.x * blockDim.x)
+    qk[t] = sq[rep_idx[order[t]]];
+}
+// after the sort by sub-log: each sub-log's first representative and count
+// (absent sub-logs keep 0 from the memset)
+__global__ void k_bv_bounds(const uint32_t *__restrict__ qk, uint32_t V, uint32_t *vbeg, uint32_t *vq) {
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < V; t += gridDim.x * blockDim.x) {
-    const uint32_t q = sq[rep_idx[order[t]]];
-    qk[t] = q;
-    atomicAdd(&vq[q], 1u);
+    const uint32_t q = qk[t];
+    if (t == 0 || qk[t - 1] != q) vbeg[q] = t;
+    if (t + 1 == V || qk[t + 1] != q) vq[q] = t + 1;  // end, made a count below
   }
+}
+__global__ void k_bv_counts(const uint32_t *__restrict__ vbeg, uint32_t Qg, uint32_t *vq) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < Qg; q += gridDim.x * blockDim.x)
+    if (vq[q]) vq[q] -= vbeg[q];
+}
+// sequence offsets of the output rows as 64-bit positions in the call's result
+__global__ void k_bv_seq64(const uint32_t *__restrict__ seq, uint32_t n, int64_t base, int64_t *out) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    out[r] = base + (int64_t)seq[r];
 }
 __global__ void k_bv_take(const uint32_t *__restrict__ vq, uint32_t Qg, int64_t top_k, uint32_t *take) {
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < Qg; q += gridDim.x * blockDim.x)
@@ -440,6 +480,19 @@ int ensure_drilldown(pm4g_log *L) {
     k_dd_emap<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(flags, pos, cells, (uint32_t)L->A, L->emap.p,
                                                                  L->e_pair.p, E);
     PM4G_TRY(check_launch(c, "k_dd_emap"));
+  }
+  // per-entry case columns in attribute order, and the edge index of every pair
+  PM4G_TRY(alloc_buf(c, L->aoff, C));
+  PM4G_TRY(alloc_buf(c, L->alen, C));
+  PM4G_TRY(alloc_buf(c, L->eidx_s, (size_t)L->n));
+  if (C) {
+    k_dd_case_cols<<<grid_for((int64_t)C, 256, 65535), 256, 0, c->stream>>>(L->aslots.p, L->off.p, L->len.p, C,
+                                                                            L->aoff.p, L->alen.p);
+    PM4G_TRY(check_launch(c, "k_dd_case_cols"));
+    k_dd_eidx<<<grid_for((int64_t)C * 32, 256, 65535), 256, 0, c->stream>>>(L->aoff.p, L->alen.p, C, L->act_s.p,
+                                                                            L->emap.p, (uint32_t)L->A,
+                                                                            L->eidx_s.p);
+    PM4G_TRY(check_launch(c, "k_dd_eidx"));
   }
   L->dd_ready = true;
   return PM4G_OK;
@@ -645,7 +698,7 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
   cudaMemGetInfo(&fr, &tot);
   const size_t per_sub = (size_t)E * 40 + (size_t)A * 24 + 64 + (size_t)E * 8;
   const size_t rec_bytes = want_var ? 128 : 0;  // records, their sort and the variant table, per case
-  const size_t budget = std::max<size_t>(std::min<size_t>(fr / 3, (size_t)8 << 30), per_sub);
+  const size_t budget = std::max<size_t>(std::min<size_t>(fr / 3, (size_t)32 << 30), per_sub);
   std::vector<std::pair<int32_t, int32_t>> groups;
   {
     int32_t g0 = 0;
@@ -758,11 +811,11 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     }
     BatchArgs a{};
     a.aslots = L->aslots.p;
-    a.off = L->off.p;
-    a.len = L->len.p;
+    a.aoff = L->aoff.p;
+    a.alen = L->alen.p;
     a.act_s = L->act_s.p;
     a.ts_s = L->ts_s.p;
-    a.emap = L->emap.p;
+    a.eidx_s = L->eidx_s.p;
     a.n_act = A;
     a.n_edges = E;
     a.items = ditems;
@@ -832,6 +885,7 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     // variants of the group's sub-logs
     uint32_t rows_g = 0, acts_g = 0;
     uint32_t *vq = nullptr, *row0 = nullptr, *o_seq = nullptr;
+    int64_t *o_seq64 = nullptr;
     unsigned long long *o_count = nullptr;
     int32_t *o_min = nullptr, *o_acts = nullptr;
     if (want_var) {
@@ -903,7 +957,8 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
         st = PM4G_ENOMEM;
         break;
       }
-      if (cudaMemsetAsync(vq, 0, (size_t)Qg * 4, s) != cudaSuccess) {
+      if (cudaMemsetAsync(vq, 0, (size_t)Qg * 4, s) != cudaSuccess ||
+          cudaMemsetAsync(vstart, 0, ((size_t)Qg + 1) * 4, s) != cudaSuccess) {
         st = PM4G_ECUDA;
         break;
       }
@@ -920,13 +975,17 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
         if ((st = radix_sort_u32(c, ck, order, ckb, orderb, V, 0, cbits)) != PM4G_OK) break;
         {
           KTime t(c, "variants");
-          k_bv_qkeys<<<grid_for(V, 256, 65535), 256, 0, s>>>(order, rep_idx, sq, V, qk, vq);
+          k_bv_qkeys<<<grid_for(V, 256, 65535), 256, 0, s>>>(order, rep_idx, sq, V, qk);
           if ((st = check_launch(c, "k_bv_qkeys")) != PM4G_OK) break;
         }
         const int qb = bits_for((uint64_t)std::max(Qg - 1, 0));
         if (qb > 0 && (st = radix_sort_u32(c, qk, order, ckb, orderb, V, 0, qb)) != PM4G_OK) break;
+        KTime t(c, "variants");
+        k_bv_bounds<<<grid_for(V, 256, 65535), 256, 0, s>>>(qk, V, vstart, vq);
+        if ((st = check_launch(c, "k_bv_bounds")) != PM4G_OK) break;
+        k_bv_counts<<<grid_for(Qg, 256, 65535), 256, 0, s>>>(vstart, (uint32_t)Qg, vq);
+        if ((st = check_launch(c, "k_bv_counts")) != PM4G_OK) break;
       }
-      if ((st = scan_u32(c, vq, vstart, Qg)) != PM4G_OK) break;
       {
         KTime t(c, "variants");
         k_bv_take<<<grid_for(Qg, 256, 65535), 256, 0, s>>>(vq, (uint32_t)Qg, spec->var_top_k, take);
@@ -938,7 +997,8 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       o_min = S.get<int32_t>(rows_g);
       uint32_t *o_len = S.get<uint32_t>(rows_g), *o_rep = S.get<uint32_t>(rows_g);
       o_seq = S.get<uint32_t>((size_t)rows_g + 1);
-      if (!o_count || !o_min || !o_len || !o_rep || !o_seq) {
+      o_seq64 = S.get<int64_t>((size_t)rows_g + 1);
+      if (!o_count || !o_min || !o_len || !o_rep || !o_seq || !o_seq64) {
         st = PM4G_ENOMEM;
         break;
       }
@@ -991,7 +1051,7 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     cp(out->freq + (size_t)q0 * A, freq, (size_t)Qg * A * 8);
     cp(goff.data(), doff, ((size_t)Qg + 1) * 8);
     cp(gcnt.data(), cnts, 2 * (size_t)Qg * 8);
-    std::vector<uint32_t> gvq, grow0, gseq;
+    std::vector<uint32_t> gvq, grow0;
     bool vfits = false;
     const size_t vbase = Vt, abase = At;
     if (want_var) {
@@ -1006,8 +1066,12 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       cp(gvq.data(), vq, (size_t)Qg * 4);
       cp(grow0.data(), row0, ((size_t)Qg + 1) * 4);
       if (vfits) {
-        gseq.resize((size_t)rows_g + 1);
-        cp(gseq.data(), o_seq, ((size_t)rows_g + 1) * 4);
+        if (rows_g + 1 > 0) {
+          k_bv_seq64<<<grid_for((int64_t)rows_g + 1, 256, 65535), 256, 0, s>>>(o_seq, rows_g + 1, (int64_t)abase,
+                                                                              o_seq64);
+          if (ce == cudaSuccess) ce = cudaGetLastError();
+        }
+        cp(out->var_seq_off + vbase, o_seq64, ((size_t)rows_g + 1) * 8);
         cp(out->var_count + vbase, o_count, (size_t)rows_g * 8);
         cp(out->var_min_case + vbase, o_min, (size_t)rows_g * 4);
         cp(out->var_acts + abase, o_acts, (size_t)acts_g * 4);
@@ -1032,8 +1096,6 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
         out->var_off[q0 + q] = (int64_t)vbase + grow0[q];
       }
       out->var_off[q0 + Qg] = (int64_t)vbase + grow0[Qg];
-      if (vfits)
-        for (uint32_t r = 0; r <= rows_g; ++r) out->var_seq_off[vbase + r] = (int64_t)abase + gseq[r];
       Vt = vbase + rows_g;
       At = abase + acts_g;
     }

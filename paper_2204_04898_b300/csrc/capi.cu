@@ -180,6 +180,9 @@ static void release_log(pm4g_log *L) {
   free_buf(c, L->ts_s);
   free_buf(c, L->aslots);
   free_buf(c, L->apre);
+  free_buf(c, L->aoff);
+  free_buf(c, L->alen);
+  free_buf(c, L->eidx_s);
   free_buf(c, L->emap);
   free_buf(c, L->e_pair);
   c->live_logs--;

@@ -261,6 +261,8 @@ struct pm4g_log {
   pm4g::DBuf<int64_t> ts_s;       // timestamps in (case, timestamp, row) order
   pm4g::DBuf<uint32_t> aslots;    // present case slots ordered by (attribute, slot)
   pm4g::DBuf<uint32_t> apre;      // events before each entry of aslots (C + 1)
+  pm4g::DBuf<uint32_t> aoff, alen; // first formatted position and length of each entry of aslots
+  pm4g::DBuf<uint32_t> eidx_s;     // edge index of the pair (event, next event of its case), ~0 at case ends
   std::vector<int32_t> attr_vals; // distinct attribute values, ascending
   std::vector<uint32_t> attr_lo;  // their first entry in aslots (one more at the end)
   std::vector<uint32_t> attr_ev;  // events before that entry

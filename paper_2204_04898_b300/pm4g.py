@@ -389,25 +389,38 @@ class BatchBuffers:
             self.mean = self._alloc(e, np.float64)
 
 
-def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers | None = None,
-                   var_top_k: int = 0) -> BatchDfg:
+class BatchSpec:
+    """The views of a batch as the flat arrays of pm4g_batch_spec (attribute
+    lists in CSR form, windows, modes); build once and pass to pm4g_batch_dfg
+    as many times as needed."""
+
+    def __init__(self, attr_sets, t_lo, t_hi, modes):
+        self.Q = Q = len(t_lo)
+        sets = [np.asarray(x if x is not None else [], np.int32).ravel() for x in attr_sets]
+        if len(sets) != Q or len(t_hi) != Q or len(modes) != Q:
+            raise ValueError("spec lists differ in length")
+        self.off = np.zeros(Q + 1, np.int64)
+        self.off[1:] = np.cumsum([x.size for x in sets])
+        self.vals = np.ascontiguousarray(np.concatenate(sets) if Q else np.empty(0, np.int32), np.int32)
+        self.tl = np.ascontiguousarray(t_lo, np.int64)
+        self.th = np.ascontiguousarray(t_hi, np.int64)
+        self.md = np.ascontiguousarray(modes, np.int32)
+
+    def struct(self, var_top_k: int) -> _BatchSpec:
+        return _BatchSpec(self.Q, self.off.ctypes.data, self.vals.ctypes.data if self.vals.size else None,
+                          self.tl.ctypes.data, self.th.ctypes.data, self.md.ctypes.data, int(var_top_k))
+
+
+def pm4g_batch_dfg(log: int, attr_sets=None, t_lo=None, t_hi=None, modes=None, out: BatchBuffers | None = None,
+                   var_top_k: int = 0, spec: BatchSpec | None = None) -> BatchDfg:
     """Batched drill-down: sub-log i keeps the cases whose attribute is in
     attr_sets[i] (empty or None: all) and applies window [t_lo[i], t_hi[i]]
-    with mode modes[i]; var_top_k != 0 adds each sub-log's variants (< 0: all).
-    With `out`, results are written into those reusable buffers
-    (pm4g_batch_dfg_into) and returned as views of them."""
-    Q = len(t_lo)
-    sets = [np.asarray(x if x is not None else [], np.int32).ravel() for x in attr_sets]
-    if len(sets) != Q or len(t_hi) != Q or len(modes) != Q:
-        raise ValueError("spec lists differ in length")
-    off = np.zeros(Q + 1, np.int64)
-    off[1:] = np.cumsum([x.size for x in sets])
-    vals = np.ascontiguousarray(np.concatenate(sets) if Q else np.empty(0, np.int32), np.int32)
-    tl = np.ascontiguousarray(t_lo, np.int64)
-    th = np.ascontiguousarray(t_hi, np.int64)
-    md = np.ascontiguousarray(modes, np.int32)
-    spec = _BatchSpec(Q, off.ctypes.data, vals.ctypes.data if vals.size else None, tl.ctypes.data,
-                      th.ctypes.data, md.ctypes.data, int(var_top_k))
+    with mode modes[i] (or the views of a prepared `spec`); var_top_k != 0 adds
+    each sub-log's variants (< 0: all). With `out`, results are written into
+    those reusable buffers (pm4g_batch_dfg_into) and returned as views of them."""
+    bs = spec if spec is not None else BatchSpec(attr_sets, t_lo, t_hi, modes)
+    Q = bs.Q
+    spec = bs.struct(var_top_k)
     if out is not None:
         return _batch_into(log, spec, Q, out, var_top_k)
     r = _BatchDfg()
@@ -434,10 +447,10 @@ def pm4g_batch_dfg(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers | N
         lib.pm4g_batch_dfg_free(ctypes.byref(r))
 
 
-def pm4g_batch_dfg_into(log: int, attr_sets, t_lo, t_hi, modes, out: BatchBuffers,
-                        var_top_k: int = 0) -> BatchDfg:
+def pm4g_batch_dfg_into(log: int, attr_sets=None, t_lo=None, t_hi=None, modes=None, out: BatchBuffers = None,
+                        var_top_k: int = 0, spec: BatchSpec | None = None) -> BatchDfg:
     """pm4g_batch_dfg into caller-owned reusable buffers."""
-    return pm4g_batch_dfg(log, attr_sets, t_lo, t_hi, modes, out=out, var_top_k=var_top_k)
+    return pm4g_batch_dfg(log, attr_sets, t_lo, t_hi, modes, out=out, var_top_k=var_top_k, spec=spec)
 
 
 def _batch_into(log, spec, Q, out: BatchBuffers, var_top_k: int) -> BatchDfg:
