@@ -177,6 +177,7 @@ static void release_log(pm4g_log *L) {
   free_buf(c, L->vcount);
   free_buf(c, L->rep_of);
   free_buf(c, L->cvar);
+  free_buf(c, L->status);
   free_buf(c, L->ts_s);
   free_buf(c, L->aslots);
   free_buf(c, L->apre);
@@ -248,6 +249,7 @@ static SegArgs seg_args(pm4g_log *L, const SegConfig &sc, uint32_t *work, uint32
   a.g.mx = L->dfg.p + 4 * cells;
   a.g_start = L->ends.p;
   a.g_end = L->ends.p + L->A;
+  a.order_flags = L->status.p;  // NULL for a filtered log: its cases are checked
   a.ovf = ovf;
   a.n_ovf = n_ovf;
   a.n_cases = n_cases;
@@ -696,14 +698,15 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
       const int p_ctas = (int)((n + chunk - 1) / chunk);
       uint32_t *mat = S.get<uint32_t>((size_t)p_ctas * L->nb);
       uint32_t *total = S.get<uint32_t>(L->nb);
-      uint32_t *err = S.get<uint32_t>(1);
-      if (!mat || !total || !err) {
+      if (!mat || !total) {
         set_error("pm4g_load_log: out of device memory for the bucket matrix");
         fail(PM4G_ENOMEM);
         break;
       }
       if (fail(alloc_buf(c, L->bucket_off, (size_t)L->nb + 1))) break;
       if (fail(alloc_buf(c, L->rec, n))) break;
+      if (fail(alloc_buf(c, L->status, 1))) break;
+      uint32_t *err = L->status.p;
       if (cudaMemsetAsync(err, 0, 4, c->stream) != cudaSuccess) {
         fail(PM4G_ECUDA);
         break;
@@ -838,6 +841,11 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           }
         }
       } else {
+        // the record scatter may reorder a case's events: the segment pass checks them all
+        if (cudaMemsetAsync(err, 2, 1, c->stream) != cudaSuccess) {
+          fail(PM4G_ECUDA);
+          break;
+        }
         for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
           const uint32_t nbs = std::min(nbs_max, L->nb - b0);
           KTime t(c, "bucket_scatter");

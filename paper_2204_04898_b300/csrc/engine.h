@@ -246,6 +246,11 @@ struct pm4g_log {
   pm4g::DBuf<int32_t> uniq;  // sorted distinct case ids when renumbered
   pm4g::DBuf<unsigned long long> dfg;  // 5 * A * A: cnt, lo, hi, min, max
   pm4g::DBuf<unsigned long long> ends; // 2 * A: start, end
+  // one device word: bit 0 an activity outside [0, A) was seen; bit 1 the
+  // bucketed records of a case may not be in (timestamp, row) order (clear
+  // only when the loaded timestamps never decrease in row order and the
+  // records were bucketed stably)
+  pm4g::DBuf<uint32_t> status;
   // caches
   bool edges_ready = false;
   std::vector<int32_t> e_src, e_dst;

@@ -332,12 +332,22 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     }
   };
   if (i0 < i1) load_tile(i0);
+  bool desc = false;  // level 1: a timestamp below the previous row's
   for (uint32_t base = i0; base < i1; base += kPartTile) {
     uint32_t dg[kPartItems];
     const uint32_t wbase = base + (uint32_t)warp * (32 * kPartItems) + lane;
+    int64_t t_last = 0;  // previous round's timestamp (lane 31's is the row before this round's lane 0)
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
       const uint32_t i = wbase + r * 32;
+      if (kLevel == 1) {
+        const int64_t t = (int64_t)(((uint64_t)rec[r].w << 32) | rec[r].z);
+        int64_t tp = __shfl_up_sync(kFull, t, 1);
+        const int64_t t31 = __shfl_sync(kFull, t_last, 31);
+        if (lane == 0) tp = r > 0 ? t31 : (i > 0 && i < i1 ? a.ts[i - 1] : t);
+        if (i < i1 && i > 0 && tp > t) desc = true;
+        t_last = t;
+      }
       dg[r] = 0xFFFFFFFFu;
       if (i < i1) {
         if (kLevel == 1) {
@@ -409,7 +419,10 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     if ((uint32_t)tid < nbins) cur[tid] += tst[tid + 1] - tst[tid];
     __syncthreads();
   }
-  if (kLevel == 1 && __any_sync(kFull, bad) && lane == 0) atomicOr(a.err_flags, 1u);
+  if (kLevel == 1) {
+    const bool any_bad = __any_sync(kFull, bad), any_desc = __any_sync(kFull, desc);
+    if (lane == 0 && (any_bad || any_desc)) atomicOr(a.err_flags, (any_bad ? 1u : 0u) | (any_desc ? 2u : 0u));
+  }
 }
 
 cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s) {

@@ -107,6 +107,7 @@ struct SegArgs {
   int64_t *ex_row;
   int32_t min_case;
   const int32_t *uniq;
+  const uint32_t *order_flags;  // optional: bit 1 clear = every case's records are in (timestamp, row) order
 };
 
 struct SegSmem {

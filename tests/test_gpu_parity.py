@@ -261,3 +261,29 @@ def test_filter_chain_and_reuse(pm4g, ctx):
     finally:
         for h in (f2, f1, log):
             pm4g.pm4g_log_free(h)
+
+
+@pytest.mark.parametrize("where", ["first", "warp", "tile", "chunk", "last", "none"])
+def test_time_sorted_input_fast_path(pm4g, ctx, where):
+    """Rows sorted by timestamp let the segment pass skip its order check; one
+    descent anywhere (at a warp, tile or row-chunk boundary of the partition,
+    or at the ends) must be seen, and the case it puts out of order sorted."""
+    L = synth.generate(synth.very_large_log(20000))
+    n = L.n_events
+    case, act, ts = L.case_id.copy(), L.activity.copy(), L.ts_ns.copy()
+    assert np.all(np.diff(ts) >= 0)
+    chunk = ((n + 2 * 148 - 1) // (2 * 148) + 3) // 4 * 4
+    target = {"first": 1, "warp": 256, "tile": 4096, "chunk": chunk, "last": n - 1, "none": None}[where]
+    if target is not None:
+        # the first row at or after target whose case has an earlier event: its
+        # timestamp drops just below that earlier event's, so exactly one
+        # descent appears (at that row) and its case is out of order
+        first_row = {}
+        for r in range(n):
+            first_row.setdefault(int(case[r]), r)
+        pos = next(r for r in range(target, n) if first_row[int(case[r])] < r)
+        q = max(r for r in range(pos) if case[r] == case[pos])
+        ts[pos] = ts[q] - 1
+        d = np.nonzero(np.diff(ts) < 0)[0]
+        assert d.tolist() == [pos - 1]
+    check_log(pm4g, ctx, case, act, ts, L.n_activities)
