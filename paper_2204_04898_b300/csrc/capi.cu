@@ -994,12 +994,13 @@ static int ensure_edges(pm4g_log *L) {
   int32_t *src = S.get<int32_t>(E), *dst = S.get<int32_t>(E);
   unsigned long long *o[5];
   for (auto &p : o) p = S.get<unsigned long long>(E);
-  if (!src || !dst || !o[0] || !o[1] || !o[2] || !o[3] || !o[4]) return PM4G_ENOMEM;
+  double *mean = S.get<double>(E);
+  if (!src || !dst || !o[0] || !o[1] || !o[2] || !o[3] || !o[4] || !mean) return PM4G_ENOMEM;
   DfgTable t{L->dfg.p, L->dfg.p + cells, L->dfg.p + 2 * cells, L->dfg.p + 3 * cells, L->dfg.p + 4 * cells};
   {
     KTime tk(c, "dfg");
     k_dfg_compact<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(t, cells, A, flags, pos, src, dst, o[0], o[1],
-                                                                     o[2], o[3], o[4]);
+                                                                     o[2], o[3], o[4], mean);
     PM4G_TRY(check_launch(c, "k_dfg_compact"));
     k_freq<<<A, 256, 0, c->stream>>>(t.cnt, L->ends.p + A, A, freq);
     PM4G_TRY(check_launch(c, "k_freq"));
@@ -1011,10 +1012,11 @@ static int ensure_edges(pm4g_log *L) {
   L->e_hi.resize(E);
   L->e_min.resize(E);
   L->e_max.resize(E);
+  L->e_mean.resize(E);
   L->h_start.resize(A);
   L->h_end.resize(A);
   L->h_freq.resize(A);
-  D2HBatch hb(c, (size_t)E * 48 + (size_t)A * 24 + 10 * 16);
+  D2HBatch hb(c, (size_t)E * 56 + (size_t)A * 24 + 11 * 16);
   hb.add(L->e_src.data(), src, E * 4);
   hb.add(L->e_dst.data(), dst, E * 4);
   hb.add(L->e_cnt.data(), o[0], E * 8);
@@ -1022,6 +1024,7 @@ static int ensure_edges(pm4g_log *L) {
   hb.add(L->e_hi.data(), o[2], E * 8);
   hb.add(L->e_min.data(), o[3], E * 8);
   hb.add(L->e_max.data(), o[4], E * 8);
+  hb.add(L->e_mean.data(), mean, E * 8);
   hb.add(L->h_start.data(), L->ends.p, A * 8);
   hb.add(L->h_end.data(), L->ends.p + A, A * 8);
   hb.add(L->h_freq.data(), freq, A * 8);
@@ -1082,14 +1085,10 @@ int pm4g_perf_dfg(pm4g_log *L, pm4g_perf_dfg_t *out) {
   out->sum_hi = host_copy(L->e_hi);
   out->min = host_copy(L->e_min);
   out->max = host_copy(L->e_max);
-  out->mean = (double *)malloc(std::max<size_t>(E, 1) * sizeof(double));
+  out->mean = host_copy(L->e_mean);  // formed on the device from the exact sums
   if (!out->src || !out->dst || !out->count || !out->sum_lo || !out->sum_hi || !out->min || !out->max || !out->mean) {
     pm4g_perf_dfg_free(out);
     return PM4G_ENOMEM;
-  }
-  for (size_t k = 0; k < E; ++k) {
-    const u128 s = ((u128)L->e_hi[k] << 64) | (u128)L->e_lo[k];
-    out->mean[k] = (double)s / (double)L->e_cnt[k];
   }
   return PM4G_OK;
 }

@@ -255,6 +255,7 @@ struct pm4g_log {
   bool edges_ready = false;
   std::vector<int32_t> e_src, e_dst;
   std::vector<uint64_t> e_cnt, e_lo, e_hi, e_min, e_max, h_start, h_end, h_freq;
+  std::vector<double> e_mean;
   bool span_ready = false;
   pm4g::DBuf<int64_t> span;  // first_ts[R], last_ts[R]
   bool var_ready = false;

@@ -212,7 +212,7 @@ __global__ void k_dfg_flags(const unsigned long long *cnt, int64_t cells, uint32
 __global__ void k_dfg_compact(DfgTable g, int64_t cells, uint32_t n_act, const uint32_t *flags,
                               const uint32_t *pos, int32_t *src, int32_t *dst, unsigned long long *cnt,
                               unsigned long long *lo, unsigned long long *hi, unsigned long long *mn,
-                              unsigned long long *mx);
+                              unsigned long long *mx, double *mean);
 __global__ void k_freq(const unsigned long long *cnt, const unsigned long long *end, uint32_t n_act,
                        unsigned long long *freq);
 

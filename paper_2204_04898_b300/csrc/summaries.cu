@@ -22,20 +22,24 @@ __global__ void k_dfg_flags(const unsigned long long *__restrict__ cnt, int64_t 
     flags[i] = cnt[i] ? 1u : 0u;
 }
 
+// Edges with a count, in (src, dst) order, with the mean duration formed from
+// the exact sum (edge_mean: the host formula (double)sum / (double)count).
 __global__ void k_dfg_compact(DfgTable g, int64_t cells, uint32_t n_act, const uint32_t *__restrict__ flags,
                               const uint32_t *__restrict__ pos, int32_t *src, int32_t *dst, unsigned long long *cnt,
                               unsigned long long *lo, unsigned long long *hi, unsigned long long *mn,
-                              unsigned long long *mx) {
+                              unsigned long long *mx, double *mean) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x) {
     if (!flags[i]) continue;
     const uint32_t p = pos[i];
+    const unsigned long long c = g.cnt[i], l = g.lo[i], h = g.hi[i];
     src[p] = (int32_t)(i / n_act);
     dst[p] = (int32_t)(i % n_act);
-    cnt[p] = g.cnt[i];
-    lo[p] = g.lo[i];
-    hi[p] = g.hi[i];
+    cnt[p] = c;
+    lo[p] = l;
+    hi[p] = h;
     mn[p] = g.mn[i];
     mx[p] = g.mx[i];
+    mean[p] = edge_mean(h, l, c);
   }
 }
 
