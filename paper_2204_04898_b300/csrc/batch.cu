@@ -1111,10 +1111,12 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
 }
 
 int pm4g_batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out) {
+  pm4g::ApiRange nvtx_range("pm4g_batch_dfg");
   return batch_dfg(L, spec, out, -1);
 }
 
 int pm4g_batch_dfg_into(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t *out, int64_t edge_capacity) {
+  pm4g::ApiRange nvtx_range("pm4g_batch_dfg_into");
   if (edge_capacity < 0) {
     set_error("pm4g_batch_dfg_into: negative edge capacity");
     return PM4G_EINVAL;

@@ -556,6 +556,7 @@ int pm4g_ctx_timing_reset(pm4g_ctx *c) {
 
 int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, const int64_t *ts_ns,
                   const int32_t *case_attr, int64_t n, int32_t A, uint32_t flags, pm4g_log **out) {
+  pm4g::ApiRange nvtx_range("pm4g_load_log");
   if (!c || !out) {
     set_error("pm4g_load_log: ctx or out is NULL");
     return PM4G_EINVAL;
@@ -891,6 +892,7 @@ int pm4g_log_info(const pm4g_log *L, int64_t *n_events, int64_t *n_cases) {
 }
 
 int pm4g_log_free(pm4g_log *L) {
+  pm4g::ApiRange nvtx_range("pm4g_log_free");
   if (!L) return PM4G_OK;
   cudaSetDevice(L->ctx->device);
   release_log(L);
@@ -937,6 +939,7 @@ int pm4g::run_export(pm4g_log *L, int32_t *ec, int32_t *ea, int64_t *et, int64_t
 }
 
 int pm4g_log_export(pm4g_log *L, int32_t *case_out, int32_t *act_out, int64_t *ts_out, int64_t *row_out) {
+  pm4g::ApiRange nvtx_range("pm4g_log_export");
   if (!L) {
     set_error("pm4g_log_export: log is NULL");
     return PM4G_EINVAL;
@@ -1041,6 +1044,7 @@ static T *host_copy(const std::vector<T> &v) {
 }
 
 int pm4g_dfg(pm4g_log *L, pm4g_dfg_t *out) {
+  pm4g::ApiRange nvtx_range("pm4g_dfg");
   if (!L || !out) {
     set_error("pm4g_dfg: NULL argument");
     return PM4G_EINVAL;
@@ -1069,6 +1073,7 @@ int pm4g_dfg_free(pm4g_dfg_t *r) {
 }
 
 int pm4g_perf_dfg(pm4g_log *L, pm4g_perf_dfg_t *out) {
+  pm4g::ApiRange nvtx_range("pm4g_perf_dfg");
   if (!L || !out) {
     set_error("pm4g_perf_dfg: NULL argument");
     return PM4G_EINVAL;
@@ -1108,6 +1113,7 @@ int pm4g_perf_dfg_free(pm4g_perf_dfg_t *r) {
 }
 
 int pm4g_start_end(pm4g_log *L, uint64_t *start, uint64_t *end, uint64_t *freq) {
+  pm4g::ApiRange nvtx_range("pm4g_start_end");
   if (!L || !start || !end) {
     set_error("pm4g_start_end: NULL argument");
     return PM4G_EINVAL;
@@ -1240,6 +1246,7 @@ static int ensure_variants(pm4g_log *L) {
 }
 
 int pm4g_variants(pm4g_log *L, int64_t top_k, uint32_t flags, pm4g_variants_t *out) {
+  pm4g::ApiRange nvtx_range("pm4g_variants");
   if (!L || !out) {
     set_error("pm4g_variants: NULL argument");
     return PM4G_EINVAL;
@@ -1348,6 +1355,7 @@ int pm4g_variants_free(pm4g_variants_t *r) {
 // filter
 // ---------------------------------------------------------------------------
 int pm4g_filter(pm4g_log *L, const pm4g_filter_spec *spec, pm4g_log **out) {
+  pm4g::ApiRange nvtx_range("pm4g_filter");
   if (!L || !spec || !out) {
     set_error("pm4g_filter: NULL argument");
     return PM4G_EINVAL;

@@ -12,6 +12,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pm4g.h"
 
 namespace pm4g {
@@ -106,6 +108,14 @@ struct KTime {
 };
 
 int check_launch(Ctx *c, const char *what);
+
+// NVTX range over an ABI call (visible to profilers; no cost without one).
+struct ApiRange {
+  explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
+  ApiRange(const ApiRange &) = delete;
+  ApiRange &operator=(const ApiRange &) = delete;
+};
 
 // A kernel's dynamic shared-memory limit is one setting per function, shared by
 // every thread and context of the process, so it is always set to the

@@ -237,6 +237,7 @@ using namespace pm4g;
 int pm4g_dfg_noalloc(const int32_t *case_id, const int32_t *activity, const int64_t *ts_ns, int64_t n_events,
                      int32_t n_activities, void *cuda_stream, uint64_t *count, uint64_t *sum_lo, uint64_t *sum_hi,
                      uint64_t *min, uint64_t *max, uint64_t *start, uint64_t *end) {
+  pm4g::ApiRange nvtx_range("pm4g_dfg_noalloc");
   if (n_events < 0 || n_events > kNoAllocMaxEvents) {
     set_error("pm4g_dfg_noalloc: n_events %lld outside [0, %lld]", (long long)n_events,
               (long long)kNoAllocMaxEvents);
