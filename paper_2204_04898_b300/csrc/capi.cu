@@ -730,11 +730,19 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
       const uint32_t nbs_max = (uint32_t)std::min<int64_t>(((int64_t)c->smem_optin - 1024) / 4, 1 << 20);
       cudaFuncSetAttribute(k_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
       cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
-      for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
-        const uint32_t nbs = std::min(nbs_max, L->nb - b0);
+      if (L->nb > nbs_max && L->nb <= 2 * nbs_max - 2) {
+        // one pass with 16-bit counters instead of two with 32-bit ones
+        cudaFuncSetAttribute(k_bucket_hist16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
         KTime t(c, "bucket_hist");
-        k_bucket_hist<<<p_ctas, 1024, nbs * 4, c->stream>>>(fa, b0, nbs);
-        fail(check_launch(c, "k_bucket_hist"));
+        k_bucket_hist16<<<p_ctas, 1024, ((size_t)(L->nb + 1) / 2 + 1) * 4, c->stream>>>(fa);
+        fail(check_launch(c, "k_bucket_hist16"));
+      } else {
+        for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
+          const uint32_t nbs = std::min(nbs_max, L->nb - b0);
+          KTime t(c, "bucket_hist");
+          k_bucket_hist<<<p_ctas, 1024, nbs * 4, c->stream>>>(fa, b0, nbs);
+          fail(check_launch(c, "k_bucket_hist"));
+        }
       }
       if (st) break;
       // Partition levels: one level when the buckets fit the bins of a pass,

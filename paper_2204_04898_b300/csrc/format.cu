@@ -141,6 +141,53 @@ __global__ void __launch_bounds__(256) k_bucket_colprefix(uint32_t *__restrict__
   }
 }
 
+// The same histogram for all nb buckets in one pass with 16-bit counters (two
+// per shared word), for bucket counts that would need two passes with 32-bit
+// ones. A counter passing 65535 inside one CTA's chunk is detected from the
+// atomic's old value; that CTA then counts its chunk again straight into its
+// global row (exact, slow, and only for chunks where one bucket holds more
+// than 65535 events).
+__global__ void __launch_bounds__(1024) k_bucket_hist16(FormatArgs a) {
+  extern __shared__ uint32_t s_w[];  // (nb + 1) / 2 words of counters, then the overflow word
+  const uint32_t nw = (a.nb + 1) / 2;
+  uint32_t &s_ovf = s_w[nw];
+  for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) s_w[w] = 0;
+  if (threadIdx.x == 0) s_ovf = 0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * a.chunk;
+  const int64_t r1 = min(a.n, r0 + a.chunk);
+  const bool al = ((uintptr_t)a.case_id & 15) == 0;
+  bool ovf = false;
+  for (int64_t i = r0 + (int64_t)threadIdx.x * 4; i < r1; i += (int64_t)blockDim.x * 4) {
+    const int4 q = load4_i32(a.case_id, i, r1, al);
+    const int32_t cc[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (i + k < r1) {
+        const uint32_t b = ((uint32_t)cc[k] - (uint32_t)a.min_case) >> a.clb;
+        if (b < a.nb) {
+          const uint32_t sh = (b & 1u) * 16u;
+          const uint32_t old = atomicAdd(&s_w[b >> 1], 1u << sh);
+          ovf |= ((old >> sh) & 0xFFFFu) == 0xFFFFu;
+        }
+      }
+    }
+  }
+  if (ovf) s_ovf = 1;
+  __syncthreads();
+  uint32_t *row = a.mat + (int64_t)blockIdx.x * a.nb;
+  if (!s_ovf) {
+    for (uint32_t b = threadIdx.x; b < a.nb; b += blockDim.x) row[b] = (s_w[b >> 1] >> ((b & 1u) * 16u)) & 0xFFFFu;
+    return;
+  }
+  for (uint32_t b = threadIdx.x; b < a.nb; b += blockDim.x) row[b] = 0;
+  __syncthreads();
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const uint32_t b = ((uint32_t)a.case_id[i] - (uint32_t)a.min_case) >> a.clb;
+    if (b < a.nb) atomicAdd(&row[b], 1u);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Scatter: every event of buckets [b_lo, b_lo + nbs) goes to its bucket as one
 // 16-byte record. Activity codes outside [0, A) raise the error flag and are

@@ -64,6 +64,7 @@ __global__ void k_add_base(uint32_t *mat1, int p_ctas, uint32_t nc, const uint32
 
 __global__ void k_stats(const int32_t *case_id, int64_t n, int2 *partial);
 __global__ void k_bucket_hist(FormatArgs a, uint32_t b_lo, uint32_t nbs);
+__global__ void k_bucket_hist16(FormatArgs a);
 __global__ void k_bucket_colprefix(uint32_t *mat, uint32_t nb, int p_ctas, uint32_t *total);
 __global__ void k_bucket_scatter(FormatArgs a, uint32_t b_lo, uint32_t nbs);
 __global__ void k_case_keys(const int32_t *case_id, int64_t n, uint32_t *keys, uint32_t *vals);

@@ -287,3 +287,31 @@ def test_time_sorted_input_fast_path(pm4g, ctx, where):
         d = np.nonzero(np.diff(ts) < 0)[0]
         assert d.tolist() == [pos - 1]
     check_log(pm4g, ctx, case, act, ts, L.n_activities)
+
+
+def test_one_pass_16bit_histogram(pm4g, ctx):
+    """Between 57,856 and 115,712 buckets the bucket histogram runs once with
+    16-bit counters (8M events, case ids spread over 16M slots)."""
+    rng = np.random.default_rng(31)
+    n = 8_000_000
+    case = rng.integers(0, 16_000_000, n).astype(np.int32)
+    act = rng.integers(0, 6, n).astype(np.int32)
+    ts = rng.integers(0, 10**12, n).astype(np.int64)
+    check_log(pm4g, ctx, case, act, ts, 6, export=False)
+
+
+def test_16bit_histogram_overflow_recount(pm4g, ctx):
+    """A row chunk holding more than 65,535 events of one bucket makes its CTA
+    count again in 32 bits (24M rows: one 70,000-event case in consecutive rows
+    among single-event cases)."""
+    rng = np.random.default_rng(32)
+    n_small = 24_000_000
+    big = 70_000
+    case = np.arange(n_small, dtype=np.int32)
+    n = n_small + big
+    chunk = ((n + 2 * 148 - 1) // (2 * 148) + 3) // 4 * 4  # the partition's row chunk
+    at = 62 * chunk                                      # the whole run inside chunk 62
+    case = np.concatenate([case[:at], np.full(big, 1_000_003, np.int32), case[at:]])
+    act = rng.integers(0, 5, n).astype(np.int32)
+    ts = rng.integers(0, 10**9, n).astype(np.int64)
+    check_log(pm4g, ctx, case, act, ts, 5, export=False)
