@@ -212,10 +212,16 @@ static SegConfig seg_config(Ctx *c, int clb, int32_t A) {
     s.tbl_mode = 1;
     s.tbl_slots = 4096;
   }
-  const size_t fixed = seg_smem_layout(0, ncl, s.a_s, s.tbl_slots, s.tbl_mode).total + 64;
-  int64_t cap = ((int64_t)c->smem_optin - (int64_t)fixed) / 18;
-  cap = std::min<int64_t>(cap, std::min(65535, kSegThreads * kSegChunks));
-  cap = cap / 32 * 32;
+  // the largest multiple of 32 records whose layout fits the opt-in shared memory
+  int64_t lo = 0, hi = std::min(65535, kSegThreads * kSegChunks) / 32;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (seg_smem_layout((int)(mid * 32), ncl, s.a_s, s.tbl_slots, s.tbl_mode).total + 64 <= (size_t)c->smem_optin)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  int64_t cap = lo * 32;
   if (c->test_bucket_cap > 0) cap = std::min<int64_t>(cap, c->test_bucket_cap);
   s.cap = (int)std::max<int64_t>(cap, 0);
   s.smem = seg_smem_layout(s.cap, ncl, s.a_s, s.tbl_slots, s.tbl_mode).total;
@@ -406,7 +412,7 @@ static int choose_clb(Ctx *c, int64_t n, uint64_t R, int32_t A, int act_bits) {
   for (int clb = 8; clb >= 0; --clb) {  // per-warp case counts hold at most 256 slots
     if (clb + act_bits > 32) continue;
     const SegConfig sc = seg_config(c, clb, A);
-    if (avg * (double)(1 << clb) <= 0.72 * (double)sc.cap) {
+    if (avg * (double)(1 << clb) <= 0.8 * (double)sc.cap) {
       best = clb;
       break;
     }

@@ -112,19 +112,20 @@ struct SegArgs {
 };
 
 struct SegSmem {
-  size_t rec, tlo, chash, idx, hw, rng, flg, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;
+  size_t rec, tlo, chash, hw, rng, flg, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;
 };
 
 constexpr int kSegThreads = 1024;
 constexpr int kSegWarps = kSegThreads / 32;
-constexpr int kSegChunks = 7;  // records a thread holds in registers: capacity <= kSegThreads * kSegChunks
+constexpr int kSegChunks = 8;  // records a thread holds in registers: capacity <= kSegThreads * kSegChunks
 
 __host__ __device__ inline size_t seg_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Shared-memory layout of the segment kernel: cap records of 16 bytes, the
-// ordered index (2 bytes per record), per-warp case counts, per-case arrays,
-// endpoint counts and the edge table (key, count, 64-bit sum, high words of the
-// pushed min and max).
+// per-warp case counts (whose area the ordered index of sorted cases, 2 bytes
+// per record, reuses once the counts are spent), per-case arrays, endpoint
+// counts and the edge table (key, count, 64-bit sum, high words of the pushed
+// minimum and maximum).
 __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, int tbl_slots, int tbl_mode) {
   SegSmem L;
   size_t o = 0;
@@ -134,10 +135,9 @@ __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, in
   o += (size_t)tbl_slots * 8;
   L.chash = o;
   o += (size_t)ncl * 8;
-  L.idx = o;
-  o += seg_align((size_t)cap * 2, 16);
   L.hw = o;
-  o += seg_align((size_t)kSegWarps * ((ncl + 1) & ~1) * 2, 16);
+  const size_t hw_bytes = (size_t)kSegWarps * ((ncl + 1) & ~1) * 2, idx_bytes = (size_t)cap * 2;
+  o += seg_align(hw_bytes > idx_bytes ? hw_bytes : idx_bytes, 16);
   L.rng = o;
   o += (size_t)(2 * ncl + 4) * 4;
   L.flg = o;

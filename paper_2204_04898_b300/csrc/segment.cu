@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   const SegSmem L = seg_smem_layout(a.cap, ncl, a_s, a.tbl_slots, a.tbl_mode);
   SegShared S;
   S.rec = reinterpret_cast<uint4 *>(smem + L.rec);
-  S.idx = reinterpret_cast<uint16_t *>(smem + L.idx);
+  S.idx = reinterpret_cast<uint16_t *>(smem + L.hw);  // shares the per-warp counts' area (dead by the sort)
   S.ccnt = reinterpret_cast<uint32_t *>(smem + L.ccnt);
   S.cstart = reinterpret_cast<uint32_t *>(smem + L.cstart);
   S.hl = reinterpret_cast<uint32_t *>(smem + L.chash);
