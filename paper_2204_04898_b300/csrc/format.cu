@@ -351,7 +351,13 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     for (uint32_t d = tid; d < nbins; d += kPartThreads)
       cur[d] = b0 + d < a.nb ? a.bucket_off[b0 + d] + a.mat[(int64_t)p0 * a.nb + b0 + d] : 0u;
   }
-  for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) wh[j] = 0;
+  // per-warp peer masks of the ranking step; they share the staging tile's
+  // space, which is free from the end of a tile's writes to its staging
+  uint32_t *pm = reinterpret_cast<uint32_t *>(stg);
+  for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) {
+    wh[j] = 0;
+    pm[j] = 0;
+  }
   __syncthreads();
   const uint32_t fmask = (1u << a.fbits) - 1;
   const int shift1 = a.clb + a.fbits;
@@ -362,8 +368,10 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   // Level 1 holds the raw columns (case id, activity, timestamp) in rec until
   // the record is formed.
   uint4 rec[kPartItems];
+  int64_t t_before = 0;  // level 1, lane 0: timestamp of the row before the warp's first row
   auto load_tile = [&](uint32_t base) {
     const uint32_t wb = base + (uint32_t)warp * (32 * kPartItems) + lane;
+    if (kLevel == 1 && lane == 0 && wb > 0 && wb < i1) t_before = a.ts[wb - 1];
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
       const uint32_t i = wb + r * 32;
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
         const int64_t t = (int64_t)(((uint64_t)rec[r].w << 32) | rec[r].z);
         int64_t tp = __shfl_up_sync(kFull, t, 1);
         const int64_t t31 = __shfl_sync(kFull, t_last, 31);
-        if (lane == 0) tp = r > 0 ? t31 : (i > 0 && i < i1 ? a.ts[i - 1] : t);
+        if (lane == 0) tp = r > 0 ? t31 : (i > 0 && i < i1 ? t_before : t);
         if (i < i1 && i > 0 && tp > t) desc = true;
         t_last = t;
       }
@@ -411,20 +419,32 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
         }
       }
     }
-    // stable ranks: per-warp counts in item order (rounds, then lanes)
+    // stable ranks: per-warp counts in item order (rounds, then lanes).
+    // Each round finds the lanes that share a digit by OR-ing the lane bits
+    // into a per-warp mask word of the digit (cheaper than a warp match when
+    // most lanes differ); all of them read the digit's count, and the lowest
+    // lane adds the group's size and clears the mask for the next round.
     uint32_t rk[kPartItems];
+    uint32_t *pmw = pm + warp * nbins;
+    const uint32_t lt = lanemask_lt(), bit = 1u << lane;
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
-      const uint32_t peers = __match_any_sync(kFull, dg[r]);
-      const int leader = __ffs(peers) - 1;
-      uint32_t bb = 0;
-      if (lane == leader && dg[r] != 0xFFFFFFFFu) {
-        bb = myh[dg[r]];
-        myh[dg[r]] = (uint16_t)(bb + __popc(peers));
-      }
-      bb = __shfl_sync(kFull, bb, leader);
-      rk[r] = bb + __popc(peers & lanemask_lt());
+      const uint32_t d = dg[r];
+      const bool v = d != 0xFFFFFFFFu;
+      if (v) atomicOr(&pmw[d], bit);
       __syncwarp();
+      uint32_t peers = 0, bb = 0;
+      if (v) {
+        peers = pmw[d];
+        bb = myh[d];
+      }
+      __syncwarp();
+      if (v && (peers & lt) == 0) {
+        myh[d] = (uint16_t)(bb + __popc(peers));
+        pmw[d] = 0;
+      }
+      __syncwarp();
+      rk[r] = bb + __popc(peers & lt);
     }
     __syncthreads();
     {
@@ -464,6 +484,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) wh[j] = 0;
     __syncthreads();
     if ((uint32_t)tid < nbins) cur[tid] += tst[tid + 1] - tst[tid];
+    for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) pm[j] = 0;
     __syncthreads();
   }
   if (kLevel == 1) {
