@@ -309,7 +309,8 @@ namespace pm4g {
 // scatter whenever the bucket count allows it). Scattered 16-byte stores run
 // about 8x slower than streaming ones on this GPU, so a tile of kPartTile
 // events is first ordered by digit in shared memory and then written out as
-// one contiguous run per digit.
+// one contiguous run per digit, by a bulk copy of the tensor memory
+// accelerator that overlaps the next tile.
 //
 // Level 1 reads the input columns; its digit is the coarse bucket
 // slot >> (clb + fbits), and CTA p owns row chunk p (cursors from the CTA-major
@@ -318,18 +319,18 @@ namespace pm4g {
 // CTA C owns coarse bucket C and its digit is the final bucket inside it,
 // (slot_lo >> clb) & (2^fbits - 1); its cursors are the final bucket offsets.
 // Both levels keep row order within every digit: items of a tile are ranked by
-// warp (warps own consecutive items), then by round, then by lane (match).
+// warp (warps own consecutive items), then by round, then by lane.
 // ---------------------------------------------------------------------------
 template <int kLevel>
 __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const uint32_t nbins = a.nbins;
   uint4 *stg = reinterpret_cast<uint4 *>(sm);
-  uint16_t *dig = reinterpret_cast<uint16_t *>(sm + (size_t)kPartTile * 16);
-  uint16_t *wh = reinterpret_cast<uint16_t *>(sm + (size_t)kPartTile * 18);
-  uint32_t *cur = reinterpret_cast<uint32_t *>(sm + (size_t)kPartTile * 18 + part_wh_bytes(nbins));
-  uint32_t *tst = cur + nbins;     // tile start of every digit, nbins + 1
-  uint32_t *sw = tst + nbins + 1;  // block-scan scratch, 32 words
+  uint16_t *wh = reinterpret_cast<uint16_t *>(sm + (size_t)kPartTile * 16);
+  uint32_t *pm = reinterpret_cast<uint32_t *>(sm + (size_t)kPartTile * 16 + part_wh_bytes(nbins));
+  uint32_t *cur = pm + kPartWarps * nbins;  // next output index of every digit
+  uint32_t *tst = cur + nbins;              // staged start of every digit, nbins + 1
+  uint32_t *sw = tst + nbins + 1;           // block-scan scratch, 32 words
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // item indices fit 32 bits (at most 2^31 - 1 events)
@@ -351,9 +352,6 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     for (uint32_t d = tid; d < nbins; d += kPartThreads)
       cur[d] = b0 + d < a.nb ? a.bucket_off[b0 + d] + a.mat[(int64_t)p0 * a.nb + b0 + d] : 0u;
   }
-  // per-warp peer masks of the ranking step; they share the staging tile's
-  // space, which is free from the end of a tile's writes to its staging
-  uint32_t *pm = reinterpret_cast<uint32_t *>(stg);
   for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) {
     wh[j] = 0;
     pm[j] = 0;
@@ -364,7 +362,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   bool bad = false;
   uint16_t *myh = wh + warp * nbins;
   // The tile loop is software-pipelined: the loads of tile t + 1 are issued
-  // before the runs of tile t are written, so they are in flight meanwhile.
+  // before the runs of tile t are copied out, so both are in flight while
+  // the warps go on to rank tile t + 1.
   // Level 1 holds the raw columns (case id, activity, timestamp) in rec until
   // the record is formed.
   uint4 rec[kPartItems];
@@ -463,30 +462,29 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
         }
       }
       if (tid == 0) tst[nbins] = all;
+      // the previous tile's copies must be done reading the staging tile
+      if ((uint32_t)tid < nbins) bulk_wait_read();
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kPartItems; ++r) {
-      if (dg[r] != 0xFFFFFFFFu) {
-        const uint32_t pos = myh[dg[r]] + rk[r];
-        stg[pos] = rec[r];
-        dig[pos] = (uint16_t)dg[r];
-      }
-    }
+    for (int r = 0; r < kPartItems; ++r)
+      if (dg[r] != 0xFFFFFFFFu) stg[myh[dg[r]] + rk[r]] = rec[r];
+    fence_smem_to_async();
     __syncthreads();
     if (base + kPartTile < i1) load_tile(base + kPartTile);
-    // write the runs; clear the per-warp counts for the next tile meanwhile
-    const uint32_t cnt = tst[nbins];
-    for (uint32_t j = tid; j < cnt; j += kPartThreads) {
-      const uint32_t d = dig[j];
-      a.rec_out[cur[d] + (j - tst[d])] = stg[j];
+    // each digit's run is one bulk copy, issued by the digit's thread; the
+    // copies proceed while the next tile is loaded and ranked
+    if ((uint32_t)tid < nbins) {
+      const uint32_t s0 = tst[tid], cnt = tst[tid + 1] - s0, o = cur[tid];
+      if (cnt) bulk_copy_s2g(a.rec_out + o, stg + s0, cnt * 16u);
+      bulk_commit();
+      cur[tid] = o + cnt;
     }
-    for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) wh[j] = 0;
-    __syncthreads();
-    if ((uint32_t)tid < nbins) cur[tid] += tst[tid + 1] - tst[tid];
-    for (uint32_t j = tid; j < kPartWarps * nbins; j += kPartThreads) pm[j] = 0;
-    __syncthreads();
+    // every warp clears its own counts for the next tile
+    for (uint32_t j = lane; j < nbins; j += 32) myh[j] = 0;
+    __syncwarp();
   }
+  if ((uint32_t)tid < nbins) bulk_wait_all();
   if (kLevel == 1) {
     const bool any_bad = __any_sync(kFull, bad), any_desc = __any_sync(kFull, desc);
     if (lane == 0 && (any_bad || any_desc)) atomicOr(a.err_flags, (any_bad ? 1u : 0u) | (any_desc ? 2u : 0u));

@@ -29,7 +29,7 @@ constexpr int kPartWarps = kPartThreads / 32;
 constexpr int kPartItems = 8;
 constexpr int kPartTile = kPartThreads * kPartItems;
 constexpr uint32_t kPartMaxBins = 512;
-static_assert((size_t)kPartWarps * kPartMaxBins * 4 <= (size_t)kPartTile * 16, "peer masks fit the staging tile");
+static_assert(kPartMaxBins <= (uint32_t)kPartThreads, "one thread per digit");
 
 struct PartArgs {
   const int32_t *case_id;
@@ -55,8 +55,11 @@ struct PartArgs {
 };
 
 __host__ __device__ inline size_t part_wh_bytes(uint32_t nbins) { return ((size_t)kPartWarps * nbins * 2 + 15) / 16 * 16; }
+// staging tile, per-warp 16-bit counts, per-warp peer masks, cursors, staged
+// starts and block-scan scratch
 __host__ __device__ inline size_t part_smem_bytes_hd(uint32_t nbins) {
-  return (size_t)kPartTile * 18 + part_wh_bytes(nbins) + (size_t)(2 * nbins + 1 + 32) * 4;
+  return (size_t)kPartTile * 16 + part_wh_bytes(nbins) + (size_t)kPartWarps * nbins * 4 +
+         (size_t)(2 * nbins + 1 + 32) * 4;
 }
 inline size_t part_smem_bytes(uint32_t nbins) { return part_smem_bytes_hd(nbins); }
 cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s);
