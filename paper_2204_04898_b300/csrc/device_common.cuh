@@ -64,6 +64,12 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 // this thread's committed copies are complete (their writes are visible)
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// L2 prefetch of the 16-byte-aligned interior of [p, p + bytes): it never
+// touches a byte outside the range, whatever the alignment of p.
+__device__ __forceinline__ void prefetch_l2_inner(const void *p, size_t bytes) {
+  const uintptr_t b = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  if (e > b) prefetch_l2(reinterpret_cast<const void *>(b), (uint32_t)(e - b));
+}
 __device__ __forceinline__ uint32_t rec_case_lo(uint4 r, int act_bits) { return r.x >> act_bits; }
 __device__ __forceinline__ uint32_t rec_act(uint4 r, uint32_t act_mask) { return r.x & act_mask; }
 __device__ __forceinline__ int64_t rec_ts(uint4 r) {

@@ -368,7 +368,21 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   // the record is formed.
   uint4 rec[kPartItems];
   int64_t t_before = 0;  // level 1, lane 0: timestamp of the row before the warp's first row
+  // Loading tile t + 1 also starts moving tile t + 2 into L2, so that the
+  // loads of every tile after the first find their data there.
+  auto prefetch_tile = [&](uint32_t base) {
+    if (base >= i1 || warp != kPartWarps - 1 || lane > 2) return;
+    const uint32_t e = min(i1, base + kPartTile);
+    if (kLevel == 1) {
+      if (lane == 0) prefetch_l2_inner(a.case_id + base, (size_t)(e - base) * 4);
+      if (lane == 1) prefetch_l2_inner(a.activity + base, (size_t)(e - base) * 4);
+      if (lane == 2) prefetch_l2_inner(a.ts + base, (size_t)(e - base) * 8);
+    } else if (lane == 0) {
+      prefetch_l2_inner(a.rec_in + base, (size_t)(e - base) * 16);
+    }
+  };
   auto load_tile = [&](uint32_t base) {
+    prefetch_tile(base + kPartTile);
     const uint32_t wb = base + (uint32_t)warp * (32 * kPartItems) + lane;
     if (kLevel == 1 && lane == 0 && wb > 0 && wb < i1) t_before = a.ts[wb - 1];
 #pragma unroll
