@@ -177,6 +177,7 @@ static void release_log(pm4g_log *L) {
   free_buf(c, L->vcount);
   free_buf(c, L->rep_of);
   free_buf(c, L->cvar);
+  free_buf(c, L->rep_pos);
   free_buf(c, L->status);
   free_buf(c, L->ts_s);
   free_buf(c, L->aslots);
@@ -1205,7 +1206,6 @@ static int ensure_variants(pm4g_log *L) {
   PM4G_TRY(ensure_offsets(L));
   PM4G_TRY(alloc_buf(c, L->vcount, R));
   PM4G_TRY(alloc_buf(c, L->rep_of, R));
-  PM4G_TRY(alloc_buf(c, L->cvar, R));
   if (L->C == 0) {
     L->V = 0;
     PM4G_TRY(alloc_buf(c, L->rep_slots, 0));
@@ -1225,8 +1225,9 @@ static int ensure_variants(pm4g_log *L) {
   a.vcount = L->vcount.p;
   PM4G_TRY(group_variants(c, a, (uint64_t)L->C));
   // rank representatives by (count desc, smallest case asc)
-  uint32_t *flags = S.get<uint32_t>(R), *pos = S.get<uint32_t>(R + 1);
-  if (!flags || !pos) return PM4G_ENOMEM;
+  PM4G_TRY(alloc_buf(c, L->rep_pos, R + 1));
+  uint32_t *flags = S.get<uint32_t>(R), *pos = L->rep_pos.p;
+  if (!flags) return PM4G_ENOMEM;
   const unsigned gR = grid_for((int64_t)R, 256, 65535);
   k_rep_flags<<<gR, 256, 0, c->stream>>>(a, flags);
   PM4G_TRY(check_launch(c, "k_rep_flags"));
@@ -1237,8 +1238,7 @@ static int ensure_variants(pm4g_log *L) {
   PM4G_TRY(alloc_buf(c, L->rep_slots, V));
   PM4G_TRY(alloc_buf(c, L->order, V));
   uint32_t *keys = S.get<uint32_t>(V), *k2 = S.get<uint32_t>(V), *v2 = S.get<uint32_t>(V);
-  uint32_t *rank_of = S.get<uint32_t>(V);
-  if (!keys || !k2 || !v2 || !rank_of) return PM4G_ENOMEM;
+  if (!keys || !k2 || !v2) return PM4G_ENOMEM;
   const int cbits = bits_for((uint64_t)L->C);
   const uint32_t cmask = cbits >= 32 ? 0xFFFFFFFFu : ((1u << cbits) - 1);
   {
@@ -1247,15 +1247,33 @@ static int ensure_variants(pm4g_log *L) {
     PM4G_TRY(check_launch(c, "k_rep_compact"));
   }
   PM4G_TRY(radix_sort_u32(c, keys, L->order.p, k2, v2, V, 0, cbits));
-  {
-    KTime t(c, "variants");
-    k_rank_scatter<<<grid_for(V, 256, 65535), 256, 0, c->stream>>>(L->order.p, V, rank_of);
-    PM4G_TRY(check_launch(c, "k_rank_scatter"));
-    k_case_variant<<<gR, 256, 0, c->stream>>>(a, pos, rank_of, L->cvar.p);
-    PM4G_TRY(check_launch(c, "k_case_variant"));
-  }
   PM4G_CK(cudaStreamSynchronize(c->stream));
   L->var_ready = true;
+  return PM4G_OK;
+}
+
+// The variant rank of every case slot (for PM4G_VARIANTS_CASES), from the
+// ranking and the representatives' positions.
+static int ensure_case_variants(pm4g_log *L) {
+  if (L->cvar.p || L->R == 0) return PM4G_OK;
+  Ctx *c = L->ctx;
+  const uint64_t R = L->R;
+  const uint32_t V = L->V;
+  PM4G_TRY(alloc_buf(c, L->cvar, R));
+  if (L->C == 0) return PM4G_OK;  // no case reads it
+  Scratch S(c);
+  uint32_t *rank_of = S.get<uint32_t>(V);
+  if (!rank_of) return PM4G_ENOMEM;
+  VarArgs a{};
+  a.n_slots = R;
+  a.len = L->len.p;
+  a.rep_of = L->rep_of.p;
+  KTime t(c, "variants");
+  k_rank_scatter<<<grid_for(V, 256, 65535), 256, 0, c->stream>>>(L->order.p, V, rank_of);
+  PM4G_TRY(check_launch(c, "k_rank_scatter"));
+  k_case_variant<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(a, L->rep_pos.p, rank_of, L->cvar.p);
+  PM4G_TRY(check_launch(c, "k_case_variant"));
+  PM4G_CK(cudaStreamSynchronize(c->stream));
   return PM4G_OK;
 }
 
@@ -1322,6 +1340,7 @@ int pm4g_variants(pm4g_log *L, int64_t top_k, uint32_t flags, pm4g_variants_t *o
   hb.add(hoff.data(), oo, ((size_t)k + 1) * 4);
   hb.add(out->acts, oa, (size_t)total * 4);
   if (want_cases) {
+    PM4G_TRY(ensure_case_variants(L));
     const uint64_t R = L->R;
     uint32_t *pf = S.get<uint32_t>(R), *pp = S.get<uint32_t>(R + 1);
     int32_t *cid = S.get<int32_t>(L->C), *cv = S.get<int32_t>(L->C);

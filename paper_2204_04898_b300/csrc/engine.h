@@ -271,7 +271,8 @@ struct pm4g_log {
   bool var_ready = false;
   uint32_t V = 0;
   pm4g::DBuf<uint32_t> off, rep_slots, order, vcount, rep_of;
-  pm4g::DBuf<int32_t> cvar;
+  pm4g::DBuf<uint32_t> rep_pos;  // exclusive prefix of the representative flags (the case variants' input)
+  pm4g::DBuf<int32_t> cvar;      // variant rank of every case slot, formed when first asked for
   // drill-down index (batched drill-down; built on first use)
   bool dd_ready = false;
   pm4g::DBuf<int64_t> ts_s;       // timestamps in (case, timestamp, row) order

@@ -116,32 +116,62 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
   }
 }
 
+// Each item is compared with its group's representative, event by event.
+// The comparisons are shared out within the warp: each round, four 8-lane
+// groups take the next four items that need one and read eight consecutive
+// activities of both sequences per step, so a load instruction covers four
+// contiguous 32-byte runs instead of 32 scattered words.
 __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out,
                              uint32_t *n_bad) {
   const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t s;
-    if (!var_item(a, list, n_list, i, s)) continue;
-    const uint32_t g = a.grp[s];
-    const uint32_t rep = ~a.tab[g].nmin;
-    bool same = true;
-    if (rep != s) {
-      const uint32_t L = a.len[s];
-      same = a.len[rep] == L && (!a.cls || a.cls[rep] == a.cls[s]);
-      if (same) {
-        const int32_t *x = a.act_s + a.off[s];
-        const int32_t *y = a.act_s + a.off[rep];
-        for (uint32_t k = 0; k < L; ++k)
-          if (x[k] != y[k]) {
-            same = false;
-            break;
-          }
+  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t w0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); w0 < total; w0 += stride) {
+    uint32_t s = 0, g = 0, L = 0, xo = 0, yo = 0;
+    const bool item = var_item(a, list, n_list, w0 + lane, s);
+    bool same = true, need = false;
+    if (item) {
+      g = a.grp[s];
+      const uint32_t rep = ~a.tab[g].nmin;
+      if (rep != s) {
+        L = a.len[s];
+        same = a.len[rep] == L && (!a.cls || a.cls[rep] == a.cls[s]);
+        need = same && L > 0;
+        if (need) {
+          xo = a.off[s];
+          yo = a.off[rep];
+        }
       }
     }
-    a.isbad[s] = same ? 0 : 1;
-    if (!same) {
-      atomicSub(&a.tab[g].cnt, 1u);
-      bad_out[atomicAdd(n_bad, 1u)] = s;
+    uint32_t todo = __ballot_sync(kFull, need);
+    while (todo) {
+      const uint32_t before = todo;
+      int src = -1;  // the item of this lane's group: the grp-th lowest pending lane
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (todo && j == grp) src = __ffs(todo) - 1;
+        todo &= todo - 1;
+      }
+      const int sl = src < 0 ? 0 : src;
+      const uint32_t Ls = __shfl_sync(kFull, L, sl), xs = __shfl_sync(kFull, xo, sl), ys = __shfl_sync(kFull, yo, sl);
+      bool eq = true;
+      if (src >= 0) {
+#pragma unroll 4
+        for (uint32_t k = gl; k < Ls; k += 8) eq &= a.act_s[xs + k] == a.act_s[ys + k];
+      }
+      const uint32_t ne = __ballot_sync(kFull, !eq);
+      // the pending lanes of this round were taken by groups 0..3 in lane order
+      if ((before >> lane) & 1u) {
+        const int gi = __popc(before & lanemask_lt());
+        if (gi < 4) same = ((ne >> (8 * gi)) & 0xFFu) == 0;
+      }
+    }
+    if (item) {
+      a.isbad[s] = same ? 0 : 1;
+      if (!same) {
+        atomicSub(&a.tab[g].cnt, 1u);
+        bad_out[atomicAdd(n_bad, 1u)] = s;
+      }
     }
   }
 }
