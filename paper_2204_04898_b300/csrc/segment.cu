@@ -233,6 +233,11 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   uint16_t *myh = hw + warp * hws;
   // myh holds 16-bit counts, two per 32-bit word (no count reaches 2^16)
   uint32_t *myw = reinterpret_cast<uint32_t *>(myh);
+  // each record's rank among the warp's earlier records of its case (two
+  // 16-bit ranks per word), kept for the placement below
+  uint32_t lr[(kSegChunks + 1) / 2];
+#pragma unroll
+  for (int k = 0; k < (kSegChunks + 1) / 2; ++k) lr[k] = 0;
 #pragma unroll
   for (int k = 0; k < kSegChunks; ++k) {
     if (w_lo + 32u * k < w_hi) {
@@ -240,7 +245,11 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
       const uint32_t c = v ? ((r[k].x >> a.act_bits) & cmask) : 0xFFFFFFFFu;
       uint32_t run;
       const uint32_t head = run_head(c, run);
-      if (v && (uint32_t)lane == head) atomicAdd(&myw[c >> 1], run << (16 * (c & 1)));
+      uint32_t base = 0;
+      if (v && (uint32_t)lane == head)
+        base = (atomicAdd(&myw[c >> 1], run << (16 * (c & 1))) >> (16 * (c & 1))) & 0xFFFFu;
+      base = __shfl_sync(kFull, base, (int)head);
+      lr[k >> 1] |= (base + ((uint32_t)lane - head)) << (16 * (k & 1));
     }
   }
   __syncthreads();
@@ -263,18 +272,12 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
     if (tid == 0) S.cstart[ncl] = n_r;
     if (__syncthreads_or(tot > (uint32_t)kMaxCaseSmem)) return false;
   }
+  // myh now holds where the warp's records of each case start
 #pragma unroll
   for (int k = 0; k < kSegChunks; ++k) {
-    if (w_lo + 32u * k < w_hi) {
-      const bool v = w_lo + 32u * k + lane < w_hi;
-      const uint32_t c = v ? ((r[k].x >> a.act_bits) & cmask) : 0xFFFFFFFFu;
-      uint32_t run;
-      const uint32_t head = run_head(c, run);
-      uint32_t base = 0;
-      if (v && (uint32_t)lane == head)
-        base = (atomicAdd(&myw[c >> 1], run << (16 * (c & 1))) >> (16 * (c & 1))) & 0xFFFFu;
-      base = __shfl_sync(kFull, base, (int)head);
-      if (v) S.rec[base + ((uint32_t)lane - head)] = r[k];
+    if (w_lo + 32u * k + lane < w_hi) {
+      const uint32_t c = (r[k].x >> a.act_bits) & cmask;
+      S.rec[myh[c] + ((lr[k >> 1] >> (16 * (k & 1))) & 0xFFFFu)] = r[k];
     }
   }
   __syncthreads();
