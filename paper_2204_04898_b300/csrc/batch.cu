@@ -598,9 +598,13 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     if (Q > 0) {
       memset(out->n_events, 0, (size_t)Q * 8);
       memset(out->n_cases, 0, (size_t)Q * 8);
-      memset(out->start, 0, (size_t)Q * A * 8);
-      memset(out->end, 0, (size_t)Q * A * 8);
-      memset(out->freq, 0, (size_t)Q * A * 8);
+      // the endpoint rows are zeroed only where no group copies them (a log
+      // without cases); otherwise every row is written by its group's copy
+      if (L->C == 0) {
+        memset(out->start, 0, (size_t)Q * A * 8);
+        memset(out->end, 0, (size_t)Q * A * 8);
+        memset(out->freq, 0, (size_t)Q * A * 8);
+      }
     }
   } else {
     out->n_events = (int64_t *)calloc(std::max(Q, 1), 8);
@@ -882,6 +886,55 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       k_bt_offsets<<<grid_for((int64_t)Qg + 1, 256, 65535), 256, 0, s>>>(pos, (uint32_t)Qg, E, doff);
       if ((st = check_launch(c, "k_bt_offsets")) != PM4G_OK) break;
     }
+    // The group's edge and endpoint results are final: they are copied out on
+    // the copy stream while the variant kernels run on the context stream.
+    const size_t base = Et;
+    const bool fits = !overflow && room(base + Eg);
+    if (!fits) {
+      if (!caller) {
+        st = PM4G_ENOMEM;
+        break;
+      }
+      overflow = true;  // keep counting to report the size needed
+    }
+    std::vector<int64_t> goff((size_t)Qg + 1);
+    std::vector<unsigned long long> gcnt(2 * (size_t)Qg);
+    cudaError_t ce = cudaSuccess;
+    if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->copy_stream = nullptr;
+      st = PM4G_ECUDA;
+      break;
+    }
+    if (!c->copy_ready && cudaEventCreateWithFlags(&c->copy_ready, cudaEventDisableTiming) != cudaSuccess) {
+      c->copy_ready = nullptr;
+      st = PM4G_ECUDA;
+      break;
+    }
+    cudaStream_t cs = c->copy_stream;
+    ce = cudaEventRecord(c->copy_ready, s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, c->copy_ready, 0);
+    auto cpc = [&](void *dst, const void *src, size_t bytes) {
+      if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, cs);
+    };
+    if (fits) {
+      cpc(out->src + base, osrc, (size_t)Eg * 4);
+      cpc(out->dst + base, odst, (size_t)Eg * 4);
+      cpc(out->count + base, o5, (size_t)Eg * 8);
+      cpc(out->sum_lo + base, o5 + Eg, (size_t)Eg * 8);
+      cpc(out->sum_hi + base, o5 + 2 * (size_t)Eg, (size_t)Eg * 8);
+      cpc(out->min + base, o5 + 3 * (size_t)Eg, (size_t)Eg * 8);
+      cpc(out->max + base, o5 + 4 * (size_t)Eg, (size_t)Eg * 8);
+      cpc(out->mean + base, omean, (size_t)Eg * 8);
+    }
+    cpc(out->start + (size_t)q0 * A, a.start, (size_t)Qg * A * 8);
+    cpc(out->end + (size_t)q0 * A, a.end, (size_t)Qg * A * 8);
+    cpc(out->freq + (size_t)q0 * A, freq, (size_t)Qg * A * 8);
+    // leaving the group by any path waits for these copies before the
+    // group's scratch (their sources) goes back to the block cache
+    struct CopyWait {
+      cudaStream_t cs;
+      ~CopyWait() { cudaStreamSynchronize(cs); }
+    } copy_wait{cs};
     // variants of the group's sub-logs
     uint32_t rows_g = 0, acts_g = 0;
     uint32_t *vq = nullptr, *row0 = nullptr, *o_seq = nullptr;
@@ -1021,34 +1074,9 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
         if ((st = check_launch(c, "k_bv_acts")) != PM4G_OK) break;
       }
     }
-    const size_t base = Et;
-    const bool fits = !overflow && room(base + Eg);
-    if (!fits) {
-      if (!caller) {
-        st = PM4G_ENOMEM;
-        break;
-      }
-      overflow = true;  // keep counting to report the size needed
-    }
-    std::vector<int64_t> goff((size_t)Qg + 1);
-    std::vector<unsigned long long> gcnt(2 * (size_t)Qg);
-    cudaError_t ce = cudaSuccess;
     auto cp = [&](void *dst, const void *src, size_t bytes) {
       if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
     };
-    if (fits) {
-      cp(out->src + base, osrc, (size_t)Eg * 4);
-      cp(out->dst + base, odst, (size_t)Eg * 4);
-      cp(out->count + base, o5, (size_t)Eg * 8);
-      cp(out->sum_lo + base, o5 + Eg, (size_t)Eg * 8);
-      cp(out->sum_hi + base, o5 + 2 * (size_t)Eg, (size_t)Eg * 8);
-      cp(out->min + base, o5 + 3 * (size_t)Eg, (size_t)Eg * 8);
-      cp(out->max + base, o5 + 4 * (size_t)Eg, (size_t)Eg * 8);
-      cp(out->mean + base, omean, (size_t)Eg * 8);
-    }
-    cp(out->start + (size_t)q0 * A, a.start, (size_t)Qg * A * 8);
-    cp(out->end + (size_t)q0 * A, a.end, (size_t)Qg * A * 8);
-    cp(out->freq + (size_t)q0 * A, freq, (size_t)Qg * A * 8);
     cp(goff.data(), doff, ((size_t)Qg + 1) * 8);
     cp(gcnt.data(), cnts, 2 * (size_t)Qg * 8);
     std::vector<uint32_t> gvq, grow0;
@@ -1078,6 +1106,10 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       }
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    {  // the copy stream too, whatever happened (its sources are this group's scratch)
+      const cudaError_t ce2 = cudaStreamSynchronize(cs);
+      if (ce == cudaSuccess) ce = ce2;
+    }
     if (ce != cudaSuccess) {
       set_error("pm4g_batch_dfg: result copy failed: %s", cudaGetErrorString(ce));
       st = PM4G_ECUDA;

@@ -494,6 +494,11 @@ int pm4g_ctx_destroy(pm4g_ctx *c) {
   cache_flush(c);
   cudaStreamSynchronize(c->stream);
   if (c->pin) cudaFreeHost(c->pin);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  if (c->copy_ready) cudaEventDestroy(c->copy_ready);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return PM4G_OK;

@@ -63,6 +63,10 @@ struct Ctx {
   // pinned host staging for device-to-host results
   void *pin = nullptr;
   size_t pin_bytes = 0;
+  // second stream for result copies that overlap later kernels, and the
+  // event that orders it after the context stream (created when first used)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ready = nullptr;
   // device blocks freed by this context, kept for reuse in stream order
   // (rounded size -> blocks); every kernel of the context runs on its stream
   std::multimap<size_t, void *> cache;
