@@ -315,3 +315,74 @@ def test_16bit_histogram_overflow_recount(pm4g, ctx):
     act = rng.integers(0, 5, n).astype(np.int32)
     ts = rng.integers(0, 10**9, n).astype(np.int64)
     check_log(pm4g, ctx, case, act, ts, 5, export=False)
+
+
+def test_unaligned_device_columns(pm4g, ctx):
+    """Columns that start 4, 8 or 12 bytes past a 16-byte boundary (views into
+    larger tensors): the tile prefetches cover only the aligned interior of
+    each range, and the results are those of the aligned columns."""
+    import torch
+    from tests.gpu_util import collect
+    L = synth.generate(synth.large_log(20000))
+    R = oracle.summarize(L.case_id, L.activity, L.ts_ns, L.n_activities)
+    for off in (1, 2, 3):
+        cols = []
+        for x in (L.case_id, L.activity, L.ts_ns):
+            t = torch.from_numpy(x)
+            buf = torch.zeros(x.size + 4, dtype=t.dtype, device="cuda")
+            buf[off:off + x.size] = t.cuda()
+            cols.append(buf[off:off + x.size])
+        assert cols[0].data_ptr() % 16 != 0
+        log = pm4g.pm4g_load_log(ctx, *cols, n_activities=L.n_activities)
+        try:
+            got = collect(pm4g, log, L.n_activities)
+        finally:
+            pm4g.pm4g_log_free(log)
+        assert_same(got, R, L.case_id, L.activity, L.ts_ns)
+
+
+def test_wide_coarse_partition(pm4g, ctx):
+    """32,000 case slots in 32-slot buckets (forced by a small on-chip
+    capacity): 1,000 buckets, a two-level partition with 500 coarse buckets,
+    whose shared memory allows one CTA per SM; buckets over the capacity
+    split into case ranges."""
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TEST_BUCKET_CAP, 1000)
+    rng = np.random.default_rng(8)
+    lens = rng.integers(10, 31, 32000)
+    case = np.repeat(np.arange(32000, dtype=np.int32), lens)
+    n = case.size
+    act = rng.integers(0, 40, n).astype(np.int32)
+    ts = rng.integers(0, 10**13, n).astype(np.int64)
+    order = np.argsort(ts, kind="stable")  # a time-ordered log, cases interleaved
+    check_log(pm4g, ctx, case[order], act[order], ts[order], 40)
+
+
+@pytest.mark.parametrize("bits", [0, 4])
+def test_variants_long_repeated_sequences(pm4g, ctx, bits):
+    """Cases of 40 to 300 events that repeat a few sequences, some of which
+    differ from another only at position 33, in the middle or at the last
+    event: the grouped comparison with the representative has to read past
+    its first steps (with truncated keys every case meets a foreign one)."""
+    if bits:
+        pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TEST_HASH_BITS, bits)
+    rng = np.random.default_rng(5)
+    base = rng.integers(0, 9, 300).astype(np.int32)
+    seqs = []
+    for n in (40, 100, 300):
+        s0 = base[:n].copy()
+        seqs.append(s0)
+        for pos in (33, n // 2, n - 1):
+            s1 = s0.copy()
+            s1[pos] = (s1[pos] + 1) % 9
+            seqs.append(s1)
+    cases, acts, tss = [], [], []
+    cid = 0
+    for _ in range(6):
+        for s in seqs:
+            cases.append(np.full(s.size, cid, np.int32))
+            acts.append(s)
+            tss.append(np.sort(rng.integers(0, 10**12, s.size)))
+            cid += 1
+    case, act, ts = np.concatenate(cases), np.concatenate(acts), np.concatenate(tss).astype(np.int64)
+    p = rng.permutation(case.size)
+    check_log(pm4g, ctx, case[p], act[p], ts[p], 9)
