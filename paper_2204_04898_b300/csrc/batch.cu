@@ -146,8 +146,25 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
     uint64_t ev = 0, cs = 0;
     for (uint32_t r = item.y; r < item.z; ++r) {
       const uint2 rg = a.ranges[r];
-      for (uint32_t k = rg.x + (uint32_t)warp; k < rg.y; k += kBtWarps) {
-        const uint32_t o = a.aoff[k], L = a.alen[k];
+      // Each warp takes cases k, k + kBtWarps, ... of the range; while one
+      // case is processed, the extent of the case two ahead is loaded.
+      uint32_t k = rg.x + (uint32_t)warp;
+      uint32_t o = 0, L = 0, on = 0, Ln = 0, o2 = 0, L2 = 0;  // extents of cases k, k + kBtWarps, k + 2 kBtWarps
+      if (k < rg.y) {
+        o = a.aoff[k];
+        L = a.alen[k];
+      }
+      if (k + kBtWarps < rg.y) {
+        on = a.aoff[k + kBtWarps];
+        Ln = a.alen[k + kBtWarps];
+      }
+      for (; k < rg.y; k += kBtWarps, o = on, L = Ln, on = o2, Ln = L2) {
+        o2 = 0;
+        L2 = 0;
+        if (k + 2 * kBtWarps < rg.y) {
+          o2 = a.aoff[k + 2 * kBtWarps];
+          L2 = a.alen[k + 2 * kBtWarps];
+        }
         const uint32_t rec = a.rlen ? a.rbase[r] + (k - rg.x) : 0u;
         uint32_t j0, j1;
         kept_run(a, o, L, mode, t_lo, t_hi, j0, j1);
