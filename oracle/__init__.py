@@ -7,7 +7,7 @@ and the two share no code.
 ``pm4g_oracle.cpp`` is a plain single-threaded C++17 statement of the
 definitions in Section 3 of the paper (ordering by case, timestamp and row;
 directly-follows pairs; performance aggregates; start/end activities; variants;
-timestamp and attribute filters). This module compiles it with g++ and exposes
+timestamp and attribute filters; paths and case filters). This module compiles it with g++ and exposes
 it through ctypes with numpy arrays.
 """
 
@@ -65,6 +65,11 @@ def _bind(lib):
         getattr(lib, f).restype = None
     lib.oracle_filter.restype = i64
     lib.oracle_filter.argtypes = [_P, _P, _P, _P, i64, i32, _P, i32, i64, i64, i32, _P]
+    lib.oracle_filter_paths.restype = i64
+    lib.oracle_filter_paths.argtypes = [_P, _P, _P, i64, i32, _P, _P, i32, i32, _P]
+    lib.oracle_filter_cases.restype = i64
+    lib.oracle_filter_cases.argtypes = [_P, _P, _P, i64, i32, i64, i64, i64, i64, _P, i32, _P, i32, _P, i32, _P, i32,
+                                        i32, _P]
     return lib
 
 
@@ -190,6 +195,45 @@ def filter_rows(case_id, activity, ts_ns, case_attr, n_activities: int, attr_set
     m = lib.oracle_filter(_ptr(case_id), _ptr(activity), _ptr(ts_ns), _ptr(attr), n,
                           int(n_activities), _ptr(attr_set), int(attr_set.shape[0]), int(t_lo),
                           int(t_hi), int(mode), _ptr(out))
+    if m < 0:
+        raise OracleError(int(m))
+    return out[:m].copy()
+
+
+def filter_paths(case_id, activity, ts_ns, n_activities: int, pairs, exclude: bool = False,
+                 lib=None) -> np.ndarray:
+    """Rows (ascending) kept by the paths filter: events whose (previous
+    activity in the case, activity) is one of `pairs` (or, with exclude, the
+    other events)."""
+    lib = lib or load()
+    case_id, activity, ts_ns = _c(case_id, np.int32), _c(activity, np.int32), _c(ts_ns, np.int64)
+    n = int(case_id.shape[0])
+    pr = np.asarray(pairs, np.int32).reshape(-1, 2)
+    src, dst = _c(pr[:, 0], np.int32), _c(pr[:, 1], np.int32)
+    out = np.empty(max(n, 1), np.int64)
+    m = lib.oracle_filter_paths(_ptr(case_id), _ptr(activity), _ptr(ts_ns), n, int(n_activities), _ptr(src),
+                                _ptr(dst), int(pr.shape[0]), int(bool(exclude)), _ptr(out))
+    if m < 0:
+        raise OracleError(int(m))
+    return out[:m].copy()
+
+
+def filter_cases(case_id, activity, ts_ns, n_activities: int, min_events: int = -1, max_events: int = -1,
+                 min_duration: int = -1, max_duration: int = -1, start_set=(), end_set=(), act_set=(),
+                 variant_set=(), exclude: bool = False, lib=None) -> np.ndarray:
+    """Rows (ascending) kept by the case filters (bounds inclusive, negative =
+    absent; empty set = absent; variant ids are ranks)."""
+    lib = lib or load()
+    case_id, activity, ts_ns = _c(case_id, np.int32), _c(activity, np.int32), _c(ts_ns, np.int64)
+    n = int(case_id.shape[0])
+    sets = [_c(np.asarray(x, np.int32).ravel(), np.int32) for x in (start_set, end_set, act_set, variant_set)]
+    out = np.empty(max(n, 1), np.int64)
+    args = []
+    for x in sets:
+        args += [_ptr(x), int(x.shape[0])]
+    m = lib.oracle_filter_cases(_ptr(case_id), _ptr(activity), _ptr(ts_ns), n, int(n_activities), int(min_events),
+                                int(max_events), int(min_duration), int(max_duration), *args, int(bool(exclude)),
+                                _ptr(out))
     if m < 0:
         raise OracleError(int(m))
     return out[:m].copy()

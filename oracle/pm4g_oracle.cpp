@@ -33,6 +33,18 @@
 //    the events inside the window, CASES_CONTAINED keeps whole cases whose first
 //    and last timestamps are inside, CASES_INTERSECTING keeps whole cases whose
 //    span overlaps the window. The result keeps the original rows.
+//  * Filters on derived results (Section 3, the directly-follows, case and
+//    variant levels; cases_df.py, variants.py, start_end_activities.py and
+//    dfg.py's paths filtering). Paths: an event is kept iff it has a previous
+//    event in its case and the pair (previous activity, its activity) is one of
+//    the given pairs; with exclude, exactly the other events are kept. Cases: a
+//    case is kept iff every given criterion holds (an absent one holds): number
+//    of events in [min_events, max_events]; throughput time (last timestamp
+//    minus first, as an unsigned 64-bit difference) in [min_duration,
+//    max_duration]; first activity in the start set; last activity in the end
+//    set; at least one event whose activity is in the activity set; variant id
+//    (the rank above) in the variant set. With exclude, exactly the other cases
+//    are kept. Either way the result is the kept rows, ascending.
 //
 // Status codes: 0 ok, -1 invalid argument, -2 activity code outside [0, A).
 
@@ -282,6 +294,79 @@ int64_t oracle_filter(const int32_t *case_id, const int32_t *act, const int64_t 
       keep[s[i]] = k ? 1 : 0;
     }
     b = e;
+  }
+  int64_t m = 0;
+  for (int64_t r = 0; r < n; ++r)
+    if (keep[r]) rows_out[m++] = r;
+  return m;
+}
+
+// Paths filter (Section 3, the directly-follows level; dfg.py paths filtering).
+// Writes the kept rows, ascending, to rows_out (capacity n) and returns their
+// number, or a negative status.
+int64_t oracle_filter_paths(const int32_t *case_id, const int32_t *act, const int64_t *ts, int64_t n,
+                            int32_t n_activities, const int32_t *src, const int32_t *dst, int32_t n_pairs,
+                            int32_t exclude, int64_t *rows_out) {
+  int st = validate(case_id, act, ts, n, n_activities);
+  if (st != 0) return st;
+  if (n_pairs < 0 || (n_pairs > 0 && (!src || !dst))) return -1;
+  std::vector<std::pair<int32_t, int32_t>> pairs;
+  for (int32_t k = 0; k < n_pairs; ++k) pairs.emplace_back(src[k], dst[k]);
+  std::vector<int64_t> s = sort_rows(case_id, ts, n);
+  std::vector<char> keep(n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    bool match = false;
+    if (i > 0 && case_id[s[i - 1]] == case_id[s[i]]) {
+      const std::pair<int32_t, int32_t> p(act[s[i - 1]], act[s[i]]);
+      match = std::find(pairs.begin(), pairs.end(), p) != pairs.end();
+    }
+    keep[s[i]] = (match != (exclude != 0)) ? 1 : 0;
+  }
+  int64_t m = 0;
+  for (int64_t r = 0; r < n; ++r)
+    if (keep[r]) rows_out[m++] = r;
+  return m;
+}
+
+// Case filters (Section 3, the case and variant levels). Bounds are inclusive
+// and a negative bound is absent; an empty set is absent. Writes the kept rows,
+// ascending, to rows_out (capacity n) and returns their number, or a negative
+// status.
+int64_t oracle_filter_cases(const int32_t *case_id, const int32_t *act, const int64_t *ts, int64_t n,
+                            int32_t n_activities, int64_t min_events, int64_t max_events,
+                            int64_t min_duration, int64_t max_duration, const int32_t *start_set,
+                            int32_t n_start, const int32_t *end_set, int32_t n_end, const int32_t *act_set,
+                            int32_t n_act, const int32_t *variant_set, int32_t n_variant, int32_t exclude,
+                            int64_t *rows_out) {
+  int st = validate(case_id, act, ts, n, n_activities);
+  if (st != 0) return st;
+  if (n_start < 0 || n_end < 0 || n_act < 0 || n_variant < 0 || (n_start > 0 && !start_set) ||
+      (n_end > 0 && !end_set) || (n_act > 0 && !act_set) || (n_variant > 0 && !variant_set))
+    return -1;
+  Result R;
+  summarize(case_id, act, ts, n, n_activities, R);
+  const std::vector<int64_t> &s = R.sorted_rows;
+  auto in = [](const int32_t *set, int32_t m, int32_t v) { return std::find(set, set + m, v) != set + m; };
+  std::vector<char> keep(n, 0);
+  for (size_t c = 0; c < R.case_ids.size(); ++c) {
+    const int64_t b = R.case_off[c], e = R.case_off[c + 1];
+    const int64_t len = e - b;
+    const uint64_t dur = (uint64_t)ts[s[e - 1]] - (uint64_t)ts[s[b]];
+    bool ok = true;
+    if (min_events >= 0 && len < min_events) ok = false;
+    if (max_events >= 0 && len > max_events) ok = false;
+    if (min_duration >= 0 && dur < (uint64_t)min_duration) ok = false;
+    if (max_duration >= 0 && dur > (uint64_t)max_duration) ok = false;
+    if (n_start > 0 && !in(start_set, n_start, act[s[b]])) ok = false;
+    if (n_end > 0 && !in(end_set, n_end, act[s[e - 1]])) ok = false;
+    if (n_act > 0) {
+      bool any = false;
+      for (int64_t i = b; i < e; ++i) any = any || in(act_set, n_act, act[s[i]]);
+      if (!any) ok = false;
+    }
+    if (n_variant > 0 && !in(variant_set, n_variant, R.case_variant[c])) ok = false;
+    if (exclude) ok = !ok;
+    for (int64_t i = b; i < e; ++i) keep[s[i]] = ok ? 1 : 0;
   }
   int64_t m = 0;
   for (int64_t r = 0; r < n; ++r)

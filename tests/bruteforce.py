@@ -103,3 +103,63 @@ def filter_rows(case, act, ts, attr, attr_set, t_lo, t_hi, mode):
         if ok:
             keep.append(i)
     return keep
+
+
+def _case_members(case, ts, c):
+    """Events of case c in order (by the number of its events preceding each)."""
+    n = len(case)
+    members = [k for k in range(n) if case[k] == c]
+    return sorted(members, key=lambda k: sum(1 for q in members if _before(ts, q, k)))
+
+
+def filter_paths(case, act, ts, pairs, exclude=False):
+    """Rows kept by the paths filter, from the definitions: event j matches iff
+    some event i of its case directly precedes it (precedes it with no event of
+    the case in between) and (act_i, act_j) is one of the pairs."""
+    n = len(case)
+    pset = {tuple(p) for p in pairs}
+    keep = []
+    for j in range(n):
+        match = False
+        for i in range(n):
+            if i == j or case[i] != case[j] or not _before(ts, i, j):
+                continue
+            if any(case[k] == case[j] and k not in (i, j) and _before(ts, i, k) and _before(ts, k, j)
+                   for k in range(n)):
+                continue
+            match = (act[i], act[j]) in pset
+        if match != bool(exclude):
+            keep.append(j)
+    return keep
+
+
+def filter_cases(case, act, ts, min_events=-1, max_events=-1, min_duration=-1, max_duration=-1,
+                 start_set=(), end_set=(), act_set=(), variant_set=(), exclude=False):
+    """Rows kept by the case filters, from the definitions (variant ids are the
+    ranks of summary())."""
+    s = summary(case, act, ts, max(act) + 1 if act else 1)
+    rank = dict(zip(s["cases"], s["case_variant"]))
+    keep = []
+    for c in sorted(set(case)):
+        m = _case_members(case, ts, c)
+        dur = ts[m[-1]] - ts[m[0]]
+        ok = True
+        if min_events >= 0 and len(m) < min_events:
+            ok = False
+        if max_events >= 0 and len(m) > max_events:
+            ok = False
+        if min_duration >= 0 and dur < min_duration:
+            ok = False
+        if max_duration >= 0 and dur > max_duration:
+            ok = False
+        if start_set and act[m[0]] not in start_set:
+            ok = False
+        if end_set and act[m[-1]] not in end_set:
+            ok = False
+        if act_set and not any(act[k] in act_set for k in m):
+            ok = False
+        if variant_set and rank[c] not in variant_set:
+            ok = False
+        if ok != bool(exclude):
+            keep.extend(m)
+    return sorted(keep)

@@ -307,6 +307,80 @@ def check_filters_bruteforce(lib, n_logs=200, seed=9):
             assert got.tolist() == want, (case, ts, attr, aset, t_lo, t_hi, mode, got, want)
 
 
+def check_derived_filters_bruteforce(lib, n_logs=150, seed=13):
+    """Paths and case filters against their definitions on random tiny logs."""
+    rng = np.random.default_rng(seed)
+    for _ in range(n_logs):
+        n = int(rng.integers(0, 10))
+        case = rng.integers(0, 3, n).tolist()
+        act = rng.integers(0, 3, n).tolist()
+        ts = rng.integers(0, 6, n).tolist()
+        pairs = [tuple(rng.integers(0, 3, 2).tolist()) for _ in range(int(rng.integers(0, 4)))]
+        for ex in (False, True):
+            got = oracle.filter_paths(case, act, ts, 3, pairs, exclude=ex, lib=lib)
+            want = bf.filter_paths(case, act, ts, pairs, exclude=ex)
+            assert got.tolist() == want, ("paths", case, act, ts, pairs, ex, got, want)
+        spec = {}
+        for k, hi in (("min_events", 4), ("max_events", 4), ("min_duration", 6), ("max_duration", 6)):
+            if rng.random() < 0.4:
+                spec[k] = int(rng.integers(0, hi))
+        for k in ("start_set", "end_set", "act_set", "variant_set"):
+            if rng.random() < 0.4:
+                spec[k] = sorted(set(rng.integers(0, 3, int(rng.integers(1, 3))).tolist()))
+        for ex in (False, True):
+            got = oracle.filter_cases(case, act, ts, 3, exclude=ex, lib=lib, **spec)
+            want = bf.filter_cases(case, act, ts, exclude=ex, **spec)
+            assert got.tolist() == want, ("cases", case, act, ts, spec, ex, got, want)
+
+
+def check_derived_filters(lib, log, seed=11):
+    """Identities of the paths and case filters on a workload-shaped log."""
+    rng = np.random.default_rng(seed)
+    n, A = log.n_events, log.n_activities
+    args = (log.case_id, log.activity, log.ts_ns, A)
+    R = oracle.summarize(*args, lib=lib)
+    everything = np.arange(n)
+    # exclude is the complement; no criterion keeps every row
+    pairs = [tuple(p) for p in rng.integers(0, A, (5, 2)).tolist()]
+    kp, kx = (oracle.filter_paths(*args, pairs, exclude=e, lib=lib) for e in (False, True))
+    assert np.array_equal(np.sort(np.concatenate([kp, kx])), everything) and np.intersect1d(kp, kx).size == 0
+    assert np.array_equal(oracle.filter_cases(*args, lib=lib), everything)
+    assert oracle.filter_cases(*args, exclude=True, lib=lib).size == 0
+    # every pair keeps exactly the events that have a previous event in their case
+    allp = [(a, b) for a in range(A) for b in range(A)] if A <= 40 else [tuple(e) for e in zip(R.src, R.dst)]
+    rows = oracle.filter_paths(*args, allp, lib=lib)
+    assert rows.size == n - R.n_cases
+    first = R.sorted_rows[np.concatenate([[0], np.cumsum(R.case_len)[:-1]]).astype(np.int64)]
+    assert np.intersect1d(rows, first).size == 0
+    # a path's kept events are as many as the edge's count
+    for k in range(min(5, R.src.size)):
+        assert oracle.filter_paths(*args, [(int(R.src[k]), int(R.dst[k]))], lib=lib).size == int(R.count[k])
+    # exact case sizes; a variant keeps its count of cases
+    L = int(R.case_len[R.case_len.size // 2])
+    kept = oracle.filter_cases(*args, min_events=L, max_events=L, lib=lib)
+    assert kept.size == L * int(np.sum(R.case_len == L))
+    for v in range(min(3, R.n_variants)):
+        kept = oracle.filter_cases(*args, variant_set=[v], lib=lib)
+        assert np.unique(log.case_id[kept]).size == int(R.var_count[v])
+    # start set = every activity keeps everything; the start counts split the cases
+    assert np.array_equal(oracle.filter_cases(*args, start_set=list(range(A)), lib=lib), everything)
+    a0 = int(np.argmax(R.start))
+    assert np.unique(log.case_id[oracle.filter_cases(*args, start_set=[a0], lib=lib)]).size == int(R.start[a0])
+
+
+def check_golden_filters(lib, name):
+    g = load_golden(name)
+    base = load_golden(g["log"])
+    lg = base["log"]
+    args = (lg["case"], lg["activity"], lg["ts"], base["n_activities"])
+    for chk in g["checks"]:
+        if chk["kind"] == "paths":
+            got = oracle.filter_paths(*args, chk["pairs"], exclude=chk["exclude"], lib=lib)
+        else:
+            got = oracle.filter_cases(*args, lib=lib, **chk["spec"])
+        assert got.tolist() == chk["rows"], (chk, got)
+
+
 def load_golden(name):
     with open(os.path.join(GOLDEN, name)) as f:
         return json.load(f)
@@ -347,11 +421,13 @@ def run_all(lib, quick=True):
     check_specials(lib)
     check_big_durations(lib)
     check_filters_bruteforce(lib, n_logs=60 if quick else 300)
+    check_derived_filters_bruteforce(lib, n_logs=60 if quick else 300)
     for name in sorted(os.listdir(GOLDEN)):
         if name.endswith(".json"):
-            check_golden(lib, name)
+            (check_golden_filters if name.startswith("filters_") else check_golden)(lib, name)
     for log in small_logs():
         R = check_invariants(lib, log)
         check_closed_form_sums(lib, log, R)
         check_replication(lib, log, k=2)
         check_filters(lib, log)
+        check_derived_filters(lib, log)

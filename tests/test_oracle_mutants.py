@@ -3,7 +3,10 @@
 The mistakes are the plausible ones: a dropped tie-break, a transposed edge, a
 wrong duration sign, a 64-bit sum, a swapped min/max, wrong end activity,
 reversed variant orders, unsigned case ordering, a filter boundary, the case
-attribute read at the wrong event. The pristine oracle passes every pin."""
+attribute read at the wrong event, a path across cases or reversed, an open
+size bound, a throughput time from the wrong event, the end set read at the
+first event, an activity test that skips the last event. The pristine oracle
+passes every pin."""
 
 import pytest
 
@@ -33,6 +36,17 @@ MUTANTS = {
                         "for (int64_t i = b; i + 1 < e; ++i) R.freq[act[s[i]]] += 1;"),
     "min_case_not_min": ("it->second.min_case = std::min(it->second.min_case, R.case_ids[c]);",
                          "it->second.min_case = std::max(it->second.min_case, R.case_ids[c]);"),
+    "path_crosses_cases": ("if (i > 0 && case_id[s[i - 1]] == case_id[s[i]]) {", "if (i > 0) {"),
+    "path_reversed": ("const std::pair<int32_t, int32_t> p(act[s[i - 1]], act[s[i]]);",
+                      "const std::pair<int32_t, int32_t> p(act[s[i]], act[s[i - 1]]);"),
+    "size_bound_open": ("if (min_events >= 0 && len < min_events) ok = false;",
+                        "if (min_events >= 0 && len <= min_events) ok = false;"),
+    "duration_from_second_event": ("const uint64_t dur = (uint64_t)ts[s[e - 1]] - (uint64_t)ts[s[b]];",
+                                   "const uint64_t dur = (uint64_t)ts[s[e - 1]] - (uint64_t)ts[s[b + (e - b > 1)]];"),
+    "end_set_reads_first": ("if (n_end > 0 && !in(end_set, n_end, act[s[e - 1]])) ok = false;",
+                            "if (n_end > 0 && !in(end_set, n_end, act[s[b]])) ok = false;"),
+    "contains_skips_last": ("for (int64_t i = b; i < e; ++i) any = any || in(act_set, n_act, act[s[i]]);",
+                            "for (int64_t i = b; i + 1 < e; ++i) any = any || in(act_set, n_act, act[s[i]]);"),
 }
 
 

@@ -62,6 +62,15 @@ def test_filters(oracle_lib, logs):
     pins.check_filters_bruteforce(oracle_lib, n_logs=400)
 
 
+def test_derived_filters(oracle_lib, logs):
+    """Paths and case filters: the hand-derived fixture, the definitions on
+    random tiny logs, and identities on workload-shaped logs."""
+    pins.check_golden_filters(oracle_lib, "filters_fine_process.json")
+    pins.check_derived_filters_bruteforce(oracle_lib, n_logs=400)
+    for log in logs:
+        pins.check_derived_filters(oracle_lib, log)
+
+
 def test_filter_then_summarize_keeps_tie_order(oracle_lib):
     # the sub-log keeps original rows, so ties inside a case resolve as before
     case = [1, 1, 1, 2, 2]
