@@ -203,6 +203,43 @@ typedef struct {
 } pm4g_filter_spec;
 int pm4g_filter(pm4g_log *log, const pm4g_filter_spec *spec, pm4g_log **out);
 
+/* Filters on derived results (Section 3: the directly-follows, case and
+ * variant levels; the cases, variants, endpoints and paths-filtering modules).
+ * Each returns a new log (still ordered, original rows kept) owned by the
+ * caller, to be freed with pm4g_log_free; sets are host arrays (repeats
+ * allowed). Errors: PM4G_EINVAL for a NULL log/out, a negative set size with
+ * or a NULL set of positive size, or an activity code outside [0, A) in a set
+ * (variant ids outside [0, n_variants) match no case); PM4G_ENOMEM; PM4G_ECUDA.
+ *
+ * pm4g_filter_paths keeps the events that have a previous event in their case
+ * and whose pair (previous activity, activity) is one of the n_pairs pairs
+ * (src[k], dst[k]); with exclude != 0, exactly the other events.
+ *
+ * pm4g_filter_cases keeps the cases for which every given criterion holds (a
+ * negative bound or an empty set is absent): number of events in [min_events,
+ * max_events]; throughput time, the last timestamp minus the first as an
+ * unsigned 64-bit difference, in [min_duration, max_duration]; first activity
+ * in start_set; last activity in end_set; at least one event with an activity
+ * in act_set; variant id (the rank of pm4g_variants: count descending, then
+ * smallest case id) in variant_set. With exclude != 0, exactly the other
+ * cases. */
+int pm4g_filter_paths(pm4g_log *log, const int32_t *src, const int32_t *dst, int32_t n_pairs, int32_t exclude,
+                      pm4g_log **out);
+typedef struct {
+  int64_t min_events, max_events;
+  int64_t min_duration, max_duration;
+  const int32_t *start_set;
+  int32_t n_start;
+  const int32_t *end_set;
+  int32_t n_end;
+  const int32_t *act_set;
+  int32_t n_act;
+  const int32_t *variant_set;
+  int32_t n_variant;
+  int32_t exclude;
+} pm4g_case_filter;
+int pm4g_filter_cases(pm4g_log *log, const pm4g_case_filter *spec, pm4g_log **out);
+
 /* Batched drill-down (Section 1, drill-down; Section 3, filters then the
  * frequency and performance DFG): for each of n_sub sub-logs, the results that
  * pm4g_filter(log, spec_i) followed by pm4g_perf_dfg and pm4g_start_end on the

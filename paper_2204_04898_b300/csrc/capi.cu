@@ -1392,24 +1392,34 @@ int pm4g_variants_free(pm4g_variants_t *r) {
 // ---------------------------------------------------------------------------
 // filter
 // ---------------------------------------------------------------------------
-int pm4g_filter(pm4g_log *L, const pm4g_filter_spec *spec, pm4g_log **out) {
-  pm4g::ApiRange nvtx_range("pm4g_filter");
-  if (!L || !spec || !out) {
-    set_error("pm4g_filter: NULL argument");
-    return PM4G_EINVAL;
-  }
-  *out = nullptr;
-  if (spec->mode < PM4G_TW_NONE || spec->mode > PM4G_TW_CASES_INTERSECTING || spec->n_attr < 0 ||
-      (spec->n_attr > 0 && !spec->attr_set)) {
-    set_error("pm4g_filter: bad mode or attribute set");
-    return PM4G_EINVAL;
-  }
-  if (spec->n_attr > 0 && !L->has_attr) {
-    set_error("pm4g_filter: the log was loaded without a case attribute");
-    return PM4G_EINVAL;
-  }
+// First and last timestamp of every case slot (cached on the log).
+static int ensure_span(pm4g_log *L) {
+  if (L->span_ready) return PM4G_OK;
   Ctx *c = L->ctx;
-  PM4G_CK(cudaSetDevice(c->device));
+  const uint64_t R = L->R;
+  PM4G_TRY(alloc_buf(c, L->span, 2 * R));
+  FilterArgs fa{};
+  fa.rec = L->rec.p;
+  fa.bucket_off = L->bucket_off.p;
+  fa.nb = L->nb;
+  fa.clb = L->clb;
+  fa.act_bits = L->act_bits;
+  fa.n_slots = R;
+  fa.first_ts = L->span.p;
+  fa.last_ts = L->span.p + R;
+  KTime t(c, "filter");
+  const int ncl = 1 << L->clb;
+  k_case_span<<<std::min<unsigned>(L->nb, 4u * c->num_sms), 256, (size_t)ncl * 16, c->stream>>>(fa);
+  PM4G_TRY(check_launch(c, "k_case_span"));
+  L->span_ready = true;
+  return PM4G_OK;
+}
+
+// A new log holding the records of L that the predicate of `fa` keeps (case_ok
+// per slot with the window, or row_keep per original row), formatted by the
+// segment pass. `fa`'s device arrays must stay valid until this returns.
+static int extract_sublog(pm4g_log *L, FilterArgs fa, pm4g_log **out) {
+  Ctx *c = L->ctx;
   pm4g_log *F = new (std::nothrow) pm4g_log();
   if (!F) return PM4G_ENOMEM;
   F->ctx = c;
@@ -1423,7 +1433,6 @@ int pm4g_filter(pm4g_log *L, const pm4g_filter_spec *spec, pm4g_log **out) {
   F->has_attr = L->has_attr;
   int st = PM4G_OK;
   do {
-    Scratch S(c);
     const uint64_t R = L->R;
     if ((st = alloc_buf(c, F->bucket_off, (size_t)L->nb + 1))) break;
     if (L->has_attr) {
@@ -1449,61 +1458,23 @@ int pm4g_filter(pm4g_log *L, const pm4g_filter_spec *spec, pm4g_log **out) {
       st = run_segment(F, nullptr, false);
       break;
     }
-    const int ncl = 1 << L->clb;
-    if (!L->span_ready) {
-      if ((st = alloc_buf(c, L->span, 2 * R))) break;
-      FilterArgs fa{};
-      fa.rec = L->rec.p;
-      fa.bucket_off = L->bucket_off.p;
-      fa.nb = L->nb;
-      fa.clb = L->clb;
-      fa.act_bits = L->act_bits;
-      fa.n_slots = R;
-      fa.first_ts = L->span.p;
-      fa.last_ts = L->span.p + R;
-      KTime t(c, "filter");
-      k_case_span<<<std::min<unsigned>(L->nb, 4u * c->num_sms), 256, (size_t)ncl * 16, c->stream>>>(fa);
-      if ((st = check_launch(c, "k_case_span"))) break;
-      L->span_ready = true;
-    }
-    std::vector<int32_t> aset(spec->attr_set, spec->attr_set + spec->n_attr);
-    std::sort(aset.begin(), aset.end());
-    aset.erase(std::unique(aset.begin(), aset.end()), aset.end());
-    int32_t *dset = S.get<int32_t>(aset.size());
-    uint8_t *ok = S.get<uint8_t>(R);
+    Scratch S(c);
     uint32_t *kept = S.get<uint32_t>(L->nb);
-    if (!dset || !ok || !kept) {
+    if (!kept) {
       st = PM4G_ENOMEM;
       break;
     }
-    if (!aset.empty() &&
-        cudaMemcpyAsync(dset, aset.data(), aset.size() * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
-      st = PM4G_ECUDA;
-      break;
-    }
-    FilterArgs fa{};
     fa.rec = L->rec.p;
     fa.bucket_off = L->bucket_off.p;
     fa.nb = L->nb;
     fa.clb = L->clb;
     fa.act_bits = L->act_bits;
     fa.n_slots = R;
-    fa.first_ts = L->span.p;
-    fa.last_ts = L->span.p + R;
-    fa.cattr = L->cattr.p;
-    fa.attr_set = dset;
-    fa.n_attr = (int32_t)aset.size();
-    fa.t_lo = spec->t_lo;
-    fa.t_hi = spec->t_hi;
-    fa.mode = spec->mode;
-    fa.case_ok = ok;
     fa.kept = kept;
     fa.new_off = F->bucket_off.p;
     const unsigned gb = std::min<unsigned>(L->nb, 8u * c->num_sms);
     {
       KTime t(c, "filter");
-      k_case_ok<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(fa);
-      if ((st = check_launch(c, "k_case_ok"))) break;
       k_filter_count<<<gb, 256, 0, c->stream>>>(fa);
       if ((st = check_launch(c, "k_filter_count"))) break;
     }
@@ -1521,12 +1492,197 @@ int pm4g_filter(pm4g_log *L, const pm4g_filter_spec *spec, pm4g_log **out) {
     st = run_segment(F, nullptr, false);
   } while (0);
   if (st != PM4G_OK) {
-    if (st == PM4G_ENOMEM) set_error("pm4g_filter: out of device memory");
+    if (st == PM4G_ENOMEM) set_error("filter: out of device memory");
     release_log(F);
     return st;
   }
   *out = F;
   return PM4G_OK;
+}
+
+int pm4g_filter(pm4g_log *L, const pm4g_filter_spec *spec, pm4g_log **out) {
+  pm4g::ApiRange nvtx_range("pm4g_filter");
+  if (!L || !spec || !out) {
+    set_error("pm4g_filter: NULL argument");
+    return PM4G_EINVAL;
+  }
+  *out = nullptr;
+  if (spec->mode < PM4G_TW_NONE || spec->mode > PM4G_TW_CASES_INTERSECTING || spec->n_attr < 0 ||
+      (spec->n_attr > 0 && !spec->attr_set)) {
+    set_error("pm4g_filter: bad mode or attribute set");
+    return PM4G_EINVAL;
+  }
+  if (spec->n_attr > 0 && !L->has_attr) {
+    set_error("pm4g_filter: the log was loaded without a case attribute");
+    return PM4G_EINVAL;
+  }
+  Ctx *c = L->ctx;
+  PM4G_CK(cudaSetDevice(c->device));
+  if (L->n == 0 || L->nb == 0) return extract_sublog(L, FilterArgs{}, out);
+  PM4G_TRY(ensure_span(L));
+  const uint64_t R = L->R;
+  Scratch S(c);
+  std::vector<int32_t> aset(spec->attr_set, spec->attr_set + spec->n_attr);
+  std::sort(aset.begin(), aset.end());
+  aset.erase(std::unique(aset.begin(), aset.end()), aset.end());
+  int32_t *dset = S.get<int32_t>(aset.size());
+  uint8_t *ok = S.get<uint8_t>(R);
+  if (!ok || (!aset.empty() && !dset)) {
+    set_error("pm4g_filter: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  if (!aset.empty())
+    PM4G_CK(cudaMemcpyAsync(dset, aset.data(), aset.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  FilterArgs fa{};
+  fa.n_slots = R;
+  fa.first_ts = L->span.p;
+  fa.last_ts = L->span.p + R;
+  fa.cattr = L->cattr.p;
+  fa.attr_set = dset;
+  fa.n_attr = (int32_t)aset.size();
+  fa.t_lo = spec->t_lo;
+  fa.t_hi = spec->t_hi;
+  fa.mode = spec->mode;
+  fa.case_ok = ok;
+  {
+    KTime t(c, "filter");
+    k_case_ok<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(fa);
+    PM4G_TRY(check_launch(c, "k_case_ok"));
+  }
+  return extract_sublog(L, fa, out);
+}
+
+// Bitmap of the activity codes of a host set (NULL when the set is empty);
+// PM4G_EINVAL for a code outside [0, A).
+static int activity_bits(Ctx *c, Scratch &S, const int32_t *set, int32_t n, int32_t A, const char *what,
+                         uint32_t **out) {
+  *out = nullptr;
+  if (n == 0) return PM4G_OK;
+  std::vector<uint32_t> bits(((size_t)A + 31) / 32, 0u);
+  for (int32_t k = 0; k < n; ++k) {
+    if (set[k] < 0 || set[k] >= A) {
+      set_error("pm4g_filter_cases: %s holds activity %d outside [0, %d)", what, set[k], A);
+      return PM4G_EINVAL;
+    }
+    bits[(uint32_t)set[k] >> 5] |= 1u << (set[k] & 31);
+  }
+  uint32_t *d = S.get<uint32_t>(bits.size());
+  if (!d) return PM4G_ENOMEM;
+  PM4G_CK(cudaMemcpyAsync(d, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  *out = d;
+  return PM4G_OK;
+}
+
+int pm4g_filter_cases(pm4g_log *L, const pm4g_case_filter *spec, pm4g_log **out) {
+  pm4g::ApiRange nvtx_range("pm4g_filter_cases");
+  if (!L || !spec || !out) {
+    set_error("pm4g_filter_cases: NULL argument");
+    return PM4G_EINVAL;
+  }
+  *out = nullptr;
+  if (spec->n_start < 0 || spec->n_end < 0 || spec->n_act < 0 || spec->n_variant < 0 ||
+      (spec->n_start > 0 && !spec->start_set) || (spec->n_end > 0 && !spec->end_set) ||
+      (spec->n_act > 0 && !spec->act_set) || (spec->n_variant > 0 && !spec->variant_set)) {
+    set_error("pm4g_filter_cases: negative set size or NULL set");
+    return PM4G_EINVAL;
+  }
+  Ctx *c = L->ctx;
+  PM4G_CK(cudaSetDevice(c->device));
+  Scratch S(c);
+  CaseFilterArgs ca{};
+  PM4G_TRY(activity_bits(c, S, spec->start_set, spec->n_start, L->A, "start_set", (uint32_t **)&ca.start_bits));
+  PM4G_TRY(activity_bits(c, S, spec->end_set, spec->n_end, L->A, "end_set", (uint32_t **)&ca.end_bits));
+  PM4G_TRY(activity_bits(c, S, spec->act_set, spec->n_act, L->A, "act_set", (uint32_t **)&ca.act_bits));
+  if (L->n == 0 || L->nb == 0) return extract_sublog(L, FilterArgs{}, out);
+  PM4G_TRY(ensure_span(L));
+  PM4G_TRY(ensure_offsets(L));
+  std::vector<int32_t> vset(spec->variant_set, spec->variant_set + spec->n_variant);
+  std::sort(vset.begin(), vset.end());
+  vset.erase(std::unique(vset.begin(), vset.end()), vset.end());
+  if (!vset.empty()) {
+    PM4G_TRY(ensure_variants(L));
+    PM4G_TRY(ensure_case_variants(L));
+    int32_t *dv = S.get<int32_t>(vset.size());
+    if (!dv) return PM4G_ENOMEM;
+    PM4G_CK(cudaMemcpyAsync(dv, vset.data(), vset.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    ca.variants = dv;
+    ca.n_variants = (int32_t)vset.size();
+    ca.cvar = L->cvar.p;
+  }
+  const uint64_t R = L->R;
+  uint8_t *ok = S.get<uint8_t>(R);
+  if (!ok) return PM4G_ENOMEM;
+  ca.n_slots = R;
+  ca.len = L->len.p;
+  ca.off = L->off.p;
+  ca.act_s = L->act_s.p;
+  ca.first_ts = L->span.p;
+  ca.last_ts = L->span.p + R;
+  ca.min_events = spec->min_events;
+  ca.max_events = spec->max_events;
+  ca.min_duration = spec->min_duration;
+  ca.max_duration = spec->max_duration;
+  ca.exclude = spec->exclude;
+  ca.case_ok = ok;
+  {
+    KTime t(c, "filter");
+    k_case_filter<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(ca);
+    PM4G_TRY(check_launch(c, "k_case_filter"));
+  }
+  FilterArgs fa{};
+  fa.case_ok = ok;
+  fa.mode = PM4G_TW_NONE;
+  return extract_sublog(L, fa, out);
+}
+
+int pm4g_filter_paths(pm4g_log *L, const int32_t *src, const int32_t *dst, int32_t n_pairs, int32_t exclude,
+                      pm4g_log **out) {
+  pm4g::ApiRange nvtx_range("pm4g_filter_paths");
+  if (!L || !out || n_pairs < 0 || (n_pairs > 0 && (!src || !dst))) {
+    set_error("pm4g_filter_paths: NULL argument or negative pair count");
+    return PM4G_EINVAL;
+  }
+  *out = nullptr;
+  const uint32_t A = (uint32_t)L->A;
+  std::vector<uint64_t> keys((size_t)n_pairs);
+  for (int32_t k = 0; k < n_pairs; ++k) {
+    if (src[k] < 0 || (uint32_t)src[k] >= A || dst[k] < 0 || (uint32_t)dst[k] >= A) {
+      set_error("pm4g_filter_paths: pair %d holds an activity outside [0, %u)", k, A);
+      return PM4G_EINVAL;
+    }
+    keys[k] = (uint64_t)src[k] * A + (uint32_t)dst[k];
+  }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  Ctx *c = L->ctx;
+  PM4G_CK(cudaSetDevice(c->device));
+  if (L->n == 0 || L->nb == 0) return extract_sublog(L, FilterArgs{}, out);
+  PM4G_TRY(ensure_offsets(L));
+  const uint64_t n = L->n, R = L->R;
+  Scratch S(c);
+  int64_t *row_s = S.get<int64_t>(n);
+  uint8_t *start = S.get<uint8_t>(n), *keep = S.get<uint8_t>(n);
+  uint64_t *dkeys = S.get<uint64_t>(keys.size());
+  if (!row_s || !start || !keep || (!keys.empty() && !dkeys)) {
+    set_error("pm4g_filter_paths: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  if (!keys.empty())
+    PM4G_CK(cudaMemcpyAsync(dkeys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  // the original row of every formatted position, and where cases start
+  PM4G_TRY(run_export(L, nullptr, nullptr, nullptr, row_s));
+  PM4G_CK(cudaMemsetAsync(start, 0, n, c->stream));
+  {
+    KTime t(c, "filter");
+    k_mark_case_starts<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(L->len.p, L->off.p, R, start);
+    PM4G_TRY(check_launch(c, "k_mark_case_starts"));
+    k_path_keep<<<grid_for((int64_t)n, 256, 65535), 256, 0, c->stream>>>(n, L->act_s.p, start, row_s, dkeys,
+                                                                         (int32_t)keys.size(), A, exclude, keep);
+    PM4G_TRY(check_launch(c, "k_path_keep"));
+  }
+  FilterArgs fa{};
+  fa.row_keep = keep;
+  return extract_sublog(L, fa, out);
 }
 
 

@@ -203,6 +203,7 @@ struct FilterArgs {
   int64_t t_lo, t_hi;
   int32_t mode;
   uint8_t *case_ok;  // per slot
+  const uint8_t *row_keep;  // optional, per original row: replaces case_ok and the window
   uint32_t *kept;    // per bucket
   const uint32_t *new_off;
   uint4 *out;
@@ -211,6 +212,27 @@ __global__ void k_case_span(FilterArgs a);
 __global__ void k_case_ok(FilterArgs a);
 __global__ void k_filter_count(FilterArgs a);
 __global__ void k_filter_write(FilterArgs a);
+
+// Case filters on derived results: one thread per case slot.
+struct CaseFilterArgs {
+  uint64_t n_slots;
+  const uint32_t *len, *off;     // per slot: events, first formatted position
+  const int32_t *act_s;          // activities in formatted order
+  const int64_t *first_ts, *last_ts;
+  const int32_t *cvar;           // per slot variant id (only with variants)
+  int64_t min_events, max_events, min_duration, max_duration;  // negative: absent
+  const uint32_t *start_bits, *end_bits, *act_bits;            // activity bitmaps, NULL: absent
+  const int32_t *variants;       // sorted variant ids
+  int32_t n_variants;            // 0: absent
+  int32_t exclude;
+  uint8_t *case_ok;
+};
+__global__ void k_case_filter(CaseFilterArgs a);
+// Paths filter: first formatted position of every case, then the kept rows.
+__global__ void k_mark_case_starts(const uint32_t *len, const uint32_t *off, uint64_t n_slots, uint8_t *start);
+__global__ void k_path_keep(uint64_t n, const int32_t *act_s, const uint8_t *start, const int64_t *row_s,
+                            const uint64_t *keys, int32_t n_keys, uint32_t n_act, int32_t exclude,
+                            uint8_t *row_keep);
 
 // Summaries (summaries.cu)
 __global__ void k_dfg_flags(const unsigned long long *cnt, int64_t cells, uint32_t *flags);

@@ -568,106 +568,4 @@ __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long 
     p[i] = v;
 }
 
-// ---------------------------------------------------------------------------
-// Drill-down filter (Section 3, timestamp.py / attributes.py).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_case_span(FilterArgs a) {
-  extern __shared__ unsigned long long s_span[];
-  const int ncl = 1 << a.clb;
-  unsigned long long *mn = s_span, *mx = s_span + ncl;
-  for (uint32_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-    for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
-      mn[c] = ~0ull;
-      mx[c] = 0ull;
-    }
-    __syncthreads();
-    const uint32_t lo = a.bucket_off[b], hi = a.bucket_off[b + 1];
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const uint4 r = a.rec[i];
-      const uint32_t c = (r.x >> a.act_bits) & ((1u << a.clb) - 1);
-      const unsigned long long k = ts_key(rec_ts(r));
-      atomicMin(&mn[c], k);
-      atomicMax(&mx[c], k);
-    }
-    __syncthreads();
-    const uint64_t slot0 = (uint64_t)b << a.clb;
-    for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
-      const uint64_t slot = slot0 + (uint64_t)c;
-      if (slot < a.n_slots) {
-        a.first_ts[slot] = (int64_t)(mn[c] ^ 0x8000000000000000ULL);
-        a.last_ts[slot] = (int64_t)(mx[c] ^ 0x8000000000000000ULL);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void k_case_ok(FilterArgs a) {
-  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_slots;
-       s += (uint64_t)gridDim.x * blockDim.x) {
-    bool ok = true;
-    if (a.n_attr > 0) {
-      const int32_t v = a.cattr[s];
-      int lo = 0, hi = a.n_attr;  // first index with attr_set[i] >= v
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a.attr_set[mid] < v) lo = mid + 1;
-        else hi = mid;
-      }
-      ok = lo < a.n_attr && a.attr_set[lo] == v;
-    }
-    const int64_t f = a.first_ts[s], l = a.last_ts[s];
-    if (ok && a.mode == PM4G_TW_CASES_CONTAINED) ok = f >= a.t_lo && l <= a.t_hi;
-    if (ok && a.mode == PM4G_TW_CASES_INTERSECTING) ok = f <= a.t_hi && l >= a.t_lo;
-    a.case_ok[s] = ok ? 1 : 0;
-  }
-}
-
-__device__ __forceinline__ bool filter_keep(const FilterArgs &a, uint32_t b, uint4 r) {
-  const uint64_t slot = ((uint64_t)b << a.clb) + ((r.x >> a.act_bits) & ((1u << a.clb) - 1));
-  if (!a.case_ok[slot]) return false;
-  if (a.mode == PM4G_TW_EVENTS) {
-    const int64_t t = rec_ts(r);
-    return t >= a.t_lo && t <= a.t_hi;
-  }
-  return true;
-}
-
-__global__ void __launch_bounds__(256) k_filter_count(FilterArgs a) {
-  for (uint32_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-    const uint32_t lo = a.bucket_off[b], hi = a.bucket_off[b + 1];
-    uint32_t k = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) k += filter_keep(a, b, a.rec[i]) ? 1u : 0u;
-    k = __reduce_add_sync(kFull, k);
-    __shared__ uint32_t s_k;
-    if (threadIdx.x == 0) s_k = 0;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) atomicAdd(&s_k, k);
-    __syncthreads();
-    if (threadIdx.x == 0) a.kept[b] = s_k;
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(256) k_filter_write(FilterArgs a) {
-  __shared__ uint32_t s_warp[32];
-  for (uint32_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-    const uint32_t lo = a.bucket_off[b], hi = a.bucket_off[b + 1];
-    uint32_t out = a.new_off[b];
-    for (uint32_t t0 = lo; t0 < hi; t0 += blockDim.x) {
-      const uint32_t i = t0 + threadIdx.x;
-      uint4 r = make_uint4(0, 0, 0, 0);
-      bool keep = false;
-      if (i < hi) {
-        r = a.rec[i];
-        keep = filter_keep(a, b, r);
-      }
-      uint32_t tot;
-      const uint32_t pre = block_exclusive_scan<256>(keep ? 1u : 0u, s_warp, tot);
-      if (keep) a.out[out + pre] = r;
-      out += tot;
-    }
-  }
-}
-
 }  // namespace pm4g

@@ -51,6 +51,12 @@ class _FilterSpec(ctypes.Structure):
     _fields_ = [("attr_set", _P), ("n_attr", _i32), ("t_lo", _i64), ("t_hi", _i64), ("mode", _i32)]
 
 
+class _CaseFilter(ctypes.Structure):
+    _fields_ = [("min_events", _i64), ("max_events", _i64), ("min_duration", _i64), ("max_duration", _i64),
+                ("start_set", _P), ("n_start", _i32), ("end_set", _P), ("n_end", _i32), ("act_set", _P),
+                ("n_act", _i32), ("variant_set", _P), ("n_variant", _i32), ("exclude", _i32)]
+
+
 class _BatchSpec(ctypes.Structure):
     _fields_ = [("n_sub", _i32), ("attr_off", _P), ("attr_vals", _P), ("t_lo", _P), ("t_hi", _P),
                 ("mode", _P), ("var_top_k", _i64)]
@@ -89,6 +95,8 @@ lib.pm4g_start_end.argtypes = [_P, _P, _P, _P]
 lib.pm4g_variants.argtypes = [_P, _i64, _u32, ctypes.POINTER(_Variants)]
 lib.pm4g_variants_free.argtypes = [ctypes.POINTER(_Variants)]
 lib.pm4g_filter.argtypes = [_P, ctypes.POINTER(_FilterSpec), ctypes.POINTER(_P)]
+lib.pm4g_filter_cases.argtypes = [_P, ctypes.POINTER(_CaseFilter), ctypes.POINTER(_P)]
+lib.pm4g_filter_paths.argtypes = [_P, _P, _P, _i32, _i32, ctypes.POINTER(_P)]
 lib.pm4g_batch_dfg.argtypes = [_P, ctypes.POINTER(_BatchSpec), ctypes.POINTER(_BatchDfg)]
 lib.pm4g_batch_dfg_free.argtypes = [ctypes.POINTER(_BatchDfg)]
 lib.pm4g_batch_dfg_into.argtypes = [_P, ctypes.POINTER(_BatchSpec), ctypes.POINTER(_BatchDfg), _i64]
@@ -305,6 +313,35 @@ def pm4g_filter(log: int, attr_set=None, t_lo: int = -(2**63), t_hi: int = 2**63
     spec = _FilterSpec(aset.ctypes.data if aset.size else None, int(aset.size), int(t_lo), int(t_hi), int(mode))
     h = _P()
     _check(lib.pm4g_filter(log, ctypes.byref(spec), ctypes.byref(h)), "pm4g_filter")
+    return h.value
+
+
+def pm4g_filter_paths(log: int, pairs, exclude: bool = False) -> int:
+    """A new log of the events whose (previous activity in the case, activity)
+    is one of `pairs` ((src, dst) activity codes), or with exclude the other
+    events."""
+    pr = np.asarray(pairs if len(pairs) else np.empty((0, 2)), dtype=np.int32).reshape(-1, 2)
+    src, dst = np.ascontiguousarray(pr[:, 0]), np.ascontiguousarray(pr[:, 1])
+    h = _P()
+    _check(lib.pm4g_filter_paths(log, src.ctypes.data if src.size else None, dst.ctypes.data if dst.size else None,
+                                 int(src.size), int(bool(exclude)), ctypes.byref(h)), "pm4g_filter_paths")
+    return h.value
+
+
+def pm4g_filter_cases(log: int, min_events: int = -1, max_events: int = -1, min_duration: int = -1,
+                      max_duration: int = -1, start_set=(), end_set=(), act_set=(), variant_set=(),
+                      exclude: bool = False) -> int:
+    """A new log of the cases that meet every given criterion (bounds
+    inclusive, negative = absent; empty set = absent; variant ids are the ranks
+    of pm4g_variants), or with exclude the other cases."""
+    sets = [np.ascontiguousarray(np.asarray(x, dtype=np.int32).ravel()) for x in (start_set, end_set, act_set,
+                                                                                  variant_set)]
+    ptr = [x.ctypes.data if x.size else None for x in sets]
+    spec = _CaseFilter(int(min_events), int(max_events), int(min_duration), int(max_duration), ptr[0],
+                       int(sets[0].size), ptr[1], int(sets[1].size), ptr[2], int(sets[2].size), ptr[3],
+                       int(sets[3].size), int(bool(exclude)))
+    h = _P()
+    _check(lib.pm4g_filter_cases(log, ctypes.byref(spec), ctypes.byref(h)), "pm4g_filter_cases")
     return h.value
 
 
