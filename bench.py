@@ -12,6 +12,7 @@ Under torchrun every rank processes its own copy of the workload (replicas;
 weak scaling); value = events of all ranks / max rank time.
 
     python bench.py --mode drilldown [--views 4096] [--plain-views 4096]
+    python bench.py --mode filters
 
 Drill-down: a resident drilldown_log (100M events, A = 2000, case attributes)
 and 4096 drill-down views (attribute set + time window, EVENTS mode). One step
@@ -19,6 +20,14 @@ and 4096 drill-down views (attribute set + time window, EVENTS mode). One step
 start/end per view, results on the host); value = sub-log events / step time.
 The same views through plain calls (pm4g_filter + pm4g_perf_dfg +
 pm4g_start_end + pm4g_log_free per view) are timed once beside it.
+
+Filters on derived results: the resident very_large_log and a fixed mix of six
+filters (the 20 most frequent paths; cases of at least the median size; cases
+whose throughput time lies between its quartiles; cases ending in one of the
+three most frequent end activities; cases containing one of the five rarest
+activities; cases of the ten most frequent variants). One step = each filter,
+then pm4g_perf_dfg of its sub-log and pm4g_log_free; value = input events of
+the six filters / step time.
 """
 
 from __future__ import annotations
@@ -93,7 +102,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cases", type=int, default=1_000_000)
-    p.add_argument("--mode", default="single", choices=["single", "drilldown", "serve"])
+    p.add_argument("--mode", default="single", choices=["single", "drilldown", "serve", "filters"])
     p.add_argument("--rates", default="100,300,1000,3000,10000", help="serve: Poisson request rates (req/s)")
     p.add_argument("--seconds", type=float, default=3.0, help="serve: seconds of arrivals per rate")
     p.add_argument("--views", type=int, default=4096)
@@ -511,8 +520,200 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+FILTERS_METRIC = "input events/s for filter + performance DFG of the sub-log (six-filter mix)"
+
+
+def filter_mix(oracle_summary, L):
+    """The benchmark's six filters, from the log's own summaries: (name, kind,
+    arguments) with kind 'paths' or 'cases'."""
+    R = oracle_summary
+    order = np.argsort(-R["count"].astype(np.int64), kind="stable")[:20]
+    pairs = [(int(R["src"][i]), int(R["dst"][i])) for i in order]
+    lens, dur = R["case_len"], R["duration"]
+    return [
+        ("paths_top20", "paths", {"pairs": pairs}),
+        ("size_ge_median", "cases", {"min_events": int(np.median(lens))}),
+        ("duration_iqr", "cases", {"min_duration": int(np.percentile(dur, 25)),
+                                   "max_duration": int(np.percentile(dur, 75))}),
+        ("end_top3", "cases", {"end_set": [int(a) for a in np.argsort(-R["end"].astype(np.int64))[:3]]}),
+        ("contains_rare5", "cases", {"act_set": [int(a) for a in np.argsort(R["freq"].astype(np.int64))[:5]]}),
+        ("variant_top10", "cases", {"variant_set": list(range(10))}),
+    ]
+
+
+def run_filters(args):
+    """Filters on derived results over the resident single log."""
+    if args.impl == "reference":
+        return run_reference_filters(args)
+    import torch
+    from paper_2204_04898_b300 import pm4g
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    spec = workload_spec(args)
+    t_gen = time.perf_counter()
+    L = synth.generate(spec, pinned=True)
+    t_gen = time.perf_counter() - t_gen
+    N, A = L.n_events, L.n_activities
+    dev = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns)]
+    stream = torch.cuda.Stream()
+    ctx = pm4g.pm4g_ctx_create(local, stream=stream.cuda_stream)
+    log = pm4g.pm4g_load_log(ctx, *dev, n_activities=A)
+    # the filters' arguments from the log's own summaries (through the engine)
+    p = pm4g.pm4g_perf_dfg(log)
+    st, en, fr = pm4g.pm4g_start_end(log, A)
+    e = pm4g.pm4g_log_export(log)
+    starts = np.flatnonzero(np.r_[True, e["case_id"][1:] != e["case_id"][:-1]])
+    ends = np.r_[starts[1:], e["case_id"].size] - 1
+    summ = {"count": p.count, "src": p.src, "dst": p.dst, "end": en, "freq": fr,
+            "case_len": ends - starts + 1,
+            "duration": (e["ts_ns"][ends].astype(np.uint64) - e["ts_ns"][starts].astype(np.uint64)).astype(np.int64)}
+    summ_cases = summ["case_len"].size
+    del e
+    mix = filter_mix(summ, L)
+
+    def run_one(kind, kw):
+        f = pm4g.pm4g_filter_paths(log, **kw) if kind == "paths" else pm4g.pm4g_filter_cases(log, **kw)
+        try:
+            d = pm4g.pm4g_perf_dfg(f)
+            return pm4g.pm4g_log_info(f)[0], d
+        finally:
+            pm4g.pm4g_log_free(f)
+
+    kept = {}
+    for name, kind, kw in mix:
+        kept[name] = run_one(kind, kw)[0]
+    for _ in range(args.warmup):
+        for name, kind, kw in mix:
+            run_one(kind, kw)
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 1)
+    pm4g.pm4g_ctx_timing_reset(ctx)
+    launches0 = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
+    per = {name: 0.0 for name, _, _ in mix}
+    d2h = 0
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            for name, kind, kw in mix:
+                t = time.perf_counter()
+                _, d = run_one(kind, kw)
+                per[name] += time.perf_counter() - t
+                d2h += sum(x.nbytes for x in (d.src, d.dst, d.count, d.sum_lo, d.sum_hi, d.min, d.max, d.mean))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    kt = {k: pm4g.pm4g_ctx_timing(ctx, k) for k in ("filter", "segment", "partition", "export", "scan", "dfg",
+                                                   "variants", "radix_sort", "bucket_hist", "stats")}
+    launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0] - launches0
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
+    if dist is not None:
+        t_ = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        ms = float(t_[0])
+    value = len(mix) * N * world * 1e3 / ms
+    kt = {k: v for k, v in kt.items() if v[0] > 0}
+    dom = max(kt, key=lambda k: kt[k][1])
+    peak, peak_kind = peaks()
+    # byte model of a filter: read every event once (16 B) and write the kept
+    # ones (16 B each); charged to the filter kernels of the step
+    alg = sum(16.0 * N + 16.0 * kept[name] for name, _, _ in mix)
+    filt_ms = kt.get("filter", (0, 0.0))[1] / args.steps
+    achieved = alg / (filt_ms * 1e-3) / 1e9 if filt_ms > 0 else 0.0
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = reference_filters_sample(args, spec)
+    pm4g.pm4g_log_free(log)
+    pm4g.pm4g_ctx_destroy(ctx)
+    if rank != 0:
+        return
+    line = {
+        "metric": FILTERS_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "filters_mix", "log": spec.name, "n_events": N, "n_cases": int(summ_cases),
+                   "n_activities": A, "filters": [name for name, _, _ in mix],
+                   "kept_events": kept, "ms_per_filter": {k: round(1e3 * v / args.steps, 3) for k, v in per.items()},
+                   "l2": "resident log larger than L2; no flush", "parallelism": f"replicas x{world}",
+                   "generate_s": round(t_gen, 1)},
+        "roofline": {"bound": "hbm", "kernel": "filter", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "alg_bytes_per_step": alg, "filter_kernels_ms_per_step": filt_ms},
+        "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kt.items(), key=lambda x: -x[1][1])},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        # each filter's result (the sub-log's performance DFG) is read on the host
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h / args.steps)},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def reference_filters_sample(args, spec):
+    """The oracle's six filters on a bounded sample of the same log law."""
+    import oracle
+    small = spec.scaled(max(2000, min(spec.n_cases, args.cpu_sample_cases // 4)))
+    S = synth.generate(small)
+    R = oracle.summarize(S.case_id, S.activity, S.ts_ns, S.n_activities)
+    rows = R.sorted_rows
+    off = np.r_[0, np.cumsum(R.case_len)]
+    summ = {"count": R.count, "src": R.src, "dst": R.dst, "end": R.end, "freq": R.freq, "case_len": R.case_len,
+            "duration": (S.ts_ns[rows[off[1:] - 1]].astype(np.uint64) - S.ts_ns[rows[off[:-1]]].astype(np.uint64)).astype(np.int64)}
+    mix = filter_mix(summ, S)
+    t = time.perf_counter()
+    for _, kind, kw in mix:
+        if kind == "paths":
+            k = oracle.filter_paths(S.case_id, S.activity, S.ts_ns, S.n_activities, kw["pairs"])
+        else:
+            k = oracle.filter_cases(S.case_id, S.activity, S.ts_ns, S.n_activities, **kw)
+        sub = S.take(k)
+        oracle.summarize(sub.case_id, sub.activity, sub.ts_ns, S.n_activities)
+    dt = time.perf_counter() - t
+    return {"value": len(mix) * S.n_events / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the six filters (each followed by its sub-log's summary) on a {small.name} law log with "
+                      f"{small.n_cases} cases ({S.n_events} events), one run, {dt:.1f} s on 1 of "
+                      f"{os.cpu_count()} host cores"}
+
+
+def run_reference_filters(args):
+    rank, world, _ = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    spec = workload_spec(args)
+    vals = []
+    cpu = None
+    for i in range(args.warmup + args.steps):
+        cpu = reference_filters_sample(args, spec)
+        if i >= args.warmup:
+            vals.append(cpu["value"])
+    value = statistics.median(vals)
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": FILTERS_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "filters_mix", "log": spec.name}, "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def main():
     args = parse()
+    if args.mode == "filters":
+        return run_filters(args)
     if args.mode == "serve":
         return run_serve(args)
     if args.mode == "drilldown":
