@@ -1544,6 +1544,7 @@ int pm4g_filter(pm4g_log *L, const pm4g_filter_spec *spec, pm4g_log **out) {
   fa.t_hi = spec->t_hi;
   fa.mode = spec->mode;
   fa.case_ok = ok;
+  fa.len = L->len.p;
   {
     KTime t(c, "filter");
     k_case_ok<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(fa);
@@ -1632,6 +1633,7 @@ int pm4g_filter_cases(pm4g_log *L, const pm4g_case_filter *spec, pm4g_log **out)
   FilterArgs fa{};
   fa.case_ok = ok;
   fa.mode = PM4G_TW_NONE;
+  fa.len = L->len.p;
   return extract_sublog(L, fa, out);
 }
 

@@ -77,11 +77,20 @@ __device__ __forceinline__ bool filter_keep(const FilterArgs &a, uint32_t b, uin
   return true;
 }
 
+// Kept events per bucket: a predicate on whole cases (no row flags, no event
+// window) sums the lengths of the bucket's kept case slots; otherwise every
+// record is tested.
 __global__ void __launch_bounds__(256) k_filter_count(FilterArgs a) {
+  const bool by_case = a.len && !a.row_keep && a.mode != PM4G_TW_EVENTS;
   for (uint32_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-    const uint32_t lo = a.bucket_off[b], hi = a.bucket_off[b + 1];
     uint32_t k = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) k += filter_keep(a, b, a.rec[i]) ? 1u : 0u;
+    if (by_case) {
+      const uint64_t s0 = (uint64_t)b << a.clb, s1 = min((uint64_t)a.n_slots, s0 + ((uint64_t)1 << a.clb));
+      for (uint64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) k += a.case_ok[s] ? a.len[s] : 0u;
+    } else {
+      const uint32_t lo = a.bucket_off[b], hi = a.bucket_off[b + 1];
+      for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) k += filter_keep(a, b, a.rec[i]) ? 1u : 0u;
+    }
     k = __reduce_add_sync(kFull, k);
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) s_k = 0;
@@ -98,6 +107,12 @@ __global__ void __launch_bounds__(256) k_filter_write(FilterArgs a) {
   for (uint32_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
     const uint32_t lo = a.bucket_off[b], hi = a.bucket_off[b + 1];
     uint32_t out = a.new_off[b];
+    const uint32_t kept = a.new_off[b + 1] - out;
+    if (kept == 0) continue;  // nothing of this bucket is kept
+    if (kept == hi - lo) {    // all of it: a straight copy
+      for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) a.out[out + (i - lo)] = a.rec[i];
+      continue;
+    }
     for (uint32_t t0 = lo; t0 < hi; t0 += blockDim.x) {
       const uint32_t i = t0 + threadIdx.x;
       uint4 r = make_uint4(0, 0, 0, 0);

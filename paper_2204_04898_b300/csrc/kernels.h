@@ -204,6 +204,7 @@ struct FilterArgs {
   int32_t mode;
   uint8_t *case_ok;  // per slot
   const uint8_t *row_keep;  // optional, per original row: replaces case_ok and the window
+  const uint32_t *len;      // optional, per slot: whole-case predicates count kept events from it
   uint32_t *kept;    // per bucket
   const uint32_t *new_off;
   uint4 *out;
