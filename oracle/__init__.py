@@ -7,7 +7,8 @@ and the two share no code.
 ``pm4g_oracle.cpp`` is a plain single-threaded C++17 statement of the
 definitions in Section 3 of the paper (ordering by case, timestamp and row;
 directly-follows pairs; performance aggregates; start/end activities; variants;
-timestamp and attribute filters; paths and case filters). This module compiles it with g++ and exposes
+timestamp and attribute filters; paths and case filters; the eventually-follows
+graph and temporal profile). This module compiles it with g++ and exposes
 it through ctypes with numpy arrays.
 """
 
@@ -67,6 +68,12 @@ def _bind(lib):
     lib.oracle_filter.argtypes = [_P, _P, _P, _P, i64, i32, _P, i32, i64, i64, i32, _P]
     lib.oracle_filter_paths.restype = i64
     lib.oracle_filter_paths.argtypes = [_P, _P, _P, i64, i32, _P, _P, i32, i32, _P]
+    lib.oracle_efg.restype = _P
+    lib.oracle_efg.argtypes = [_P, _P, _P, i64, i32, _P]
+    lib.oracle_efg_pairs.restype = None
+    lib.oracle_efg_pairs.argtypes = [_P] * 11
+    lib.oracle_free_efg.restype = None
+    lib.oracle_free_efg.argtypes = [_P]
     lib.oracle_filter_cases.restype = i64
     lib.oracle_filter_cases.argtypes = [_P, _P, _P, i64, i32, i64, i64, i64, i64, _P, i32, _P, i32, _P, i32, _P, i32,
                                         i32, _P]
@@ -237,6 +244,48 @@ def filter_cases(case_id, activity, ts_ns, n_activities: int, min_events: int = 
     if m < 0:
         raise OracleError(int(m))
     return out[:m].copy()
+
+
+@dataclass
+class Efg:
+    """Eventually-follows graph and temporal profile, pairs ascending by (a, b)."""
+
+    src: np.ndarray      # int32[P]
+    dst: np.ndarray      # int32[P]
+    count: np.ndarray    # uint64[P]
+    sum_lo: np.ndarray   # uint64[P]
+    sum_hi: np.ndarray   # uint64[P]
+    sq0: np.ndarray      # uint64[P]: sum of squares, low word
+    sq1: np.ndarray      # uint64[P]
+    sq2: np.ndarray      # uint64[P]: high word
+    mean: np.ndarray     # float64[P]
+    stdev: np.ndarray    # float64[P]
+
+    def sums(self) -> list[int]:
+        return [int(lo) | (int(hi) << 64) for lo, hi in zip(self.sum_lo, self.sum_hi)]
+
+    def squares(self) -> list[int]:
+        return [int(a) | (int(b) << 64) | (int(c) << 128) for a, b, c in zip(self.sq0, self.sq1, self.sq2)]
+
+
+def efg(case_id, activity, ts_ns, n_activities: int, lib=None) -> Efg:
+    """Eventually-follows graph and temporal profile of a log."""
+    lib = lib or load()
+    case_id, activity, ts_ns = _c(case_id, np.int32), _c(activity, np.int32), _c(ts_ns, np.int64)
+    n = int(case_id.shape[0])
+    P = ctypes.c_int64()
+    h = lib.oracle_efg(_ptr(case_id), _ptr(activity), _ptr(ts_ns), n, int(n_activities), ctypes.byref(P))
+    if not h:
+        raise OracleError(EINVAL)
+    try:
+        m = int(P.value)
+        i32 = [np.empty(max(m, 1), np.int32) for _ in range(2)]
+        u64 = [np.empty(max(m, 1), np.uint64) for _ in range(6)]
+        f64 = [np.empty(max(m, 1), np.float64) for _ in range(2)]
+        lib.oracle_efg_pairs(h, *[_ptr(x) for x in i32 + u64 + f64])
+        return Efg(*[x[:m].copy() for x in i32 + u64 + f64])
+    finally:
+        lib.oracle_free_efg(h)
 
 
 def mutant_library(replace_from: str, replace_to: str, count: int = 1) -> str:

@@ -45,10 +45,21 @@
 //    set; at least one event whose activity is in the activity set; variant id
 //    (the rank above) in the variant set. With exclude, exactly the other cases
 //    are kept. Either way the result is the kept rows, ascending.
+//  * Eventually-follows graph and temporal profile (Section 3, efg.py): a pair
+//    of events (i, j) of one case eventually follows when i comes before j in
+//    the case's order (i < j as positions; a pair needs two distinct events).
+//    Per activity pair (a, b) with at least one such pair: the count, the exact
+//    sum of ts_j - ts_i (128-bit) and the exact sum of their squares (192-bit);
+//    mean = (double)sum / (double)count as for the DFG; the standard deviation
+//    is the population one, sqrt(var) with var = rn(count * sumsq - sum^2) /
+//    (double)count / (double)count, where rn rounds the exact non-negative
+//    integer to the nearest double (ties to even) and every other step is one
+//    IEEE operation.
 //
 // Status codes: 0 ok, -1 invalid argument, -2 activity code outside [0, A).
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -373,5 +384,139 @@ int64_t oracle_filter_cases(const int32_t *case_id, const int32_t *act, const in
     if (keep[r]) rows_out[m++] = r;
   return m;
 }
+
+// Unsigned integers of four 64-bit limbs (little end first), for the exact
+// variance numerator of the temporal profile.
+struct U256 {
+  uint64_t w[4] = {0, 0, 0, 0};
+};
+
+U256 mul_u64_by(const uint64_t *x, int nx, uint64_t m) {  // x (nx limbs) times m
+  U256 r;
+  u128 carry = 0;
+  for (int k = 0; k < 4; ++k) {
+    const u128 p = (k < nx ? (u128)x[k] * m : 0) + carry;
+    r.w[k] = (uint64_t)p;
+    carry = p >> 64;
+  }
+  return r;
+}
+
+U256 square_u128(u128 v) {  // v * v, exactly
+  const uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+  const uint64_t x[2] = {lo, hi};
+  U256 a = mul_u64_by(x, 2, lo), b = mul_u64_by(x, 2, hi);
+  U256 r;  // a + (b << 64)
+  u128 carry = 0;
+  for (int k = 0; k < 4; ++k) {
+    const u128 t = (u128)a.w[k] + (k >= 1 ? b.w[k - 1] : 0) + carry;
+    r.w[k] = (uint64_t)t;
+    carry = t >> 64;
+  }
+  return r;
+}
+
+U256 sub_u256(const U256 &a, const U256 &b) {  // a - b, a >= b
+  U256 r;
+  uint64_t borrow = 0;
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t d = a.w[k] - b.w[k] - borrow;
+    borrow = (a.w[k] < b.w[k] || (a.w[k] == b.w[k] && borrow)) ? 1 : 0;
+    r.w[k] = d;
+  }
+  return r;
+}
+
+// The nearest double to x, ties to even (the top 53 significant bits, then
+// the round bit and the sticky bits below it).
+double u256_to_double(const U256 &x) {
+  int top = -1;
+  for (int k = 3; k >= 0 && top < 0; --k)
+    for (int b = 63; b >= 0; --b)
+      if ((x.w[k] >> b) & 1) {
+        top = 64 * k + b;
+        break;
+      }
+  if (top < 0) return 0.0;
+  auto bit = [&](int i) -> uint64_t { return i < 0 ? 0 : (x.w[i / 64] >> (i % 64)) & 1; };
+  if (top < 53) {
+    double v = 0;
+    for (int i = top; i >= 0; --i) v = v * 2 + (double)bit(i);
+    return v;
+  }
+  uint64_t mant = 0;
+  for (int i = top; i > top - 53; --i) mant = (mant << 1) | bit(i);
+  const int rpos = top - 53;
+  const uint64_t round = bit(rpos);
+  bool sticky = false;
+  for (int i = rpos - 1; i >= 0 && !sticky; --i) sticky = bit(i) != 0;
+  if (round && (sticky || (mant & 1))) ++mant;  // may carry into bit 53: still exact below
+  return std::ldexp((double)mant, rpos + 1);
+}
+
+struct EfAgg {
+  uint64_t count = 0;
+  u128 sum = 0;
+  U256 sq;  // sum of squared durations (at most 192 bits)
+};
+
+// Eventually-follows graph and temporal profile (Section 3, efg.py). Returns a
+// handle (released with oracle_free_efg) and the number of activity pairs in
+// *n_pairs, or NULL on a bad argument or activity code.
+void *oracle_efg(const int32_t *case_id, const int32_t *act, const int64_t *ts, int64_t n, int32_t n_activities,
+                 int64_t *n_pairs) {
+  if (validate(case_id, act, ts, n, n_activities) != 0 || !n_pairs) return nullptr;
+  std::vector<int64_t> s = sort_rows(case_id, ts, n);
+  auto *M = new std::map<std::pair<int32_t, int32_t>, EfAgg>();
+  int64_t b = 0;
+  while (b < n) {
+    int64_t e = b + 1;
+    while (e < n && case_id[s[e]] == case_id[s[b]]) ++e;
+    for (int64_t i = b; i < e; ++i)
+      for (int64_t j = i + 1; j < e; ++j) {
+        const uint64_t d = (uint64_t)ts[s[j]] - (uint64_t)ts[s[i]];
+        EfAgg &g = (*M)[std::make_pair(act[s[i]], act[s[j]])];
+        g.count += 1;
+        g.sum += (u128)d;
+        const u128 d2 = (u128)d * d;
+        u128 carry = 0;
+        const uint64_t add[4] = {(uint64_t)d2, (uint64_t)(d2 >> 64), 0, 0};
+        for (int k = 0; k < 4; ++k) {
+          const u128 t = (u128)g.sq.w[k] + add[k] + carry;
+          g.sq.w[k] = (uint64_t)t;
+          carry = t >> 64;
+        }
+      }
+    b = e;
+  }
+  *n_pairs = (int64_t)M->size();
+  return M;
+}
+
+// The pairs ascending by (a, b): counts, sums (low, high words), sums of
+// squares (three words, low first), means and standard deviations.
+void oracle_efg_pairs(void *h, int32_t *src, int32_t *dst, uint64_t *count, uint64_t *sum_lo, uint64_t *sum_hi,
+                      uint64_t *sq0, uint64_t *sq1, uint64_t *sq2, double *mean, double *stdev) {
+  const auto *M = static_cast<std::map<std::pair<int32_t, int32_t>, EfAgg> *>(h);
+  size_t k = 0;
+  for (const auto &kv : *M) {
+    const EfAgg &g = kv.second;
+    src[k] = kv.first.first;
+    dst[k] = kv.first.second;
+    count[k] = g.count;
+    sum_lo[k] = (uint64_t)g.sum;
+    sum_hi[k] = (uint64_t)(g.sum >> 64);
+    sq0[k] = g.sq.w[0];
+    sq1[k] = g.sq.w[1];
+    sq2[k] = g.sq.w[2];
+    mean[k] = (double)g.sum / (double)g.count;
+    const U256 num = sub_u256(mul_u64_by(g.sq.w, 3, g.count), square_u128(g.sum));
+    const double var = u256_to_double(num) / (double)g.count / (double)g.count;
+    stdev[k] = std::sqrt(var);
+    ++k;
+  }
+}
+
+void oracle_free_efg(void *h) { delete static_cast<std::map<std::pair<int32_t, int32_t>, EfAgg> *>(h); }
 
 }  // extern "C"

@@ -163,3 +163,21 @@ def filter_cases(case, act, ts, min_events=-1, max_events=-1, min_duration=-1, m
         if ok != bool(exclude):
             keep.extend(m)
     return sorted(keep)
+
+
+def efg(case, act, ts):
+    """Eventually-follows pairs from the definitions, with Python integers:
+    {(a, b): (count, sum of durations, sum of squared durations)} over pairs of
+    distinct events i, j of one case with i preceding j."""
+    n = len(case)
+    out = {}
+    for i in range(n):
+        for j in range(n):
+            if i == j or case[i] != case[j] or not _before(ts, i, j):
+                continue
+            d = ts[j] - ts[i]
+            c = out.setdefault((act[i], act[j]), [0, 0, 0])
+            c[0] += 1
+            c[1] += d
+            c[2] += d * d
+    return {k: tuple(v) for k, v in sorted(out.items())}

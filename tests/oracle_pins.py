@@ -381,6 +381,88 @@ def check_golden_filters(lib, name):
         assert got.tolist() == chk["rows"], (chk, got)
 
 
+def _ulps(x, y):
+    """Distance between two doubles in units of the larger one's last place."""
+    import math
+    if x == y:
+        return 0.0
+    return abs(x - y) / math.ulp(max(abs(x), abs(y)))
+
+
+def check_efg_bruteforce(lib, n_logs=150, seed=17):
+    """Eventually-follows pairs against their definition on random tiny logs:
+    exact counts, sums and sums of squares; the mean within one unit in the last
+    place of the exact quotient, the standard deviation within four of the
+    correctly rounded population deviation."""
+    import statistics
+    from fractions import Fraction
+    rng = np.random.default_rng(seed)
+    for it in range(n_logs):
+        n = int(rng.integers(0, 12))
+        case = rng.integers(0, 3, n).tolist()
+        act = rng.integers(0, 3, n).tolist()
+        big = it % 3 == 0  # durations near 2^62: squares need the third word
+        ts = (rng.integers(0, 2**62, n) if big else rng.integers(0, 7, n)).tolist()
+        E = oracle.efg(case, act, ts, 3, lib=lib)
+        want = bf.efg(case, act, ts)
+        got = {(int(a), int(b)): (int(c), s, q) for a, b, c, s, q in
+               zip(E.src, E.dst, E.count, E.sums(), E.squares())}
+        assert got == want, (case, act, ts, got, want)
+        for k, (key, (c, sm, sq)) in enumerate(want.items()):
+            assert _ulps(float(E.mean[k]), float(Fraction(sm, c))) <= 1.0, (key, E.mean[k], sm, c)
+            durs = [ts[j] - ts[i] for i in range(n) for j in range(n)
+                    if i != j and case[i] == case[j] and (ts[i], i) < (ts[j], j) and (act[i], act[j]) == key]
+            ref = statistics.pstdev(durs) if len(durs) > 1 else 0.0
+            assert _ulps(float(E.stdev[k]), ref) <= 4.0 or abs(E.stdev[k] - ref) <= 1e-300, (key, E.stdev[k], ref)
+
+
+def check_efg_invariants(lib, log, seed=19):
+    """Identities of the eventually-follows graph on a workload-shaped log."""
+    rng = np.random.default_rng(seed)
+    A = log.n_activities
+    E = oracle.efg(log.case_id, log.activity, log.ts_ns, A, lib=lib)
+    R = oracle.summarize(log.case_id, log.activity, log.ts_ns, A, lib=lib)
+    L = R.case_len.astype(np.int64)
+    assert int(E.count.astype(np.int64).sum()) == int(np.sum(L * (L - 1) // 2))
+    ef = {(int(a), int(b)): int(c) for a, b, c in zip(E.src, E.dst, E.count)}
+    for a, b, c in zip(R.src, R.dst, R.count):  # every directly-follows pair eventually follows
+        assert ef[(int(a), int(b))] >= int(c)
+    assert np.all(E.stdev[E.count == 1] == 0.0) and np.all(E.mean >= 0)
+    # shifting one case's timestamps changes nothing; shuffling rows neither
+    shift = rng.integers(-10**9, 10**9, int(log.case_id.max()) + 1)
+    E2 = oracle.efg(log.case_id, log.activity, log.ts_ns + shift[log.case_id], A, lib=lib)
+    for f in ("src", "dst", "count", "sum_lo", "sum_hi", "sq0", "sq1", "sq2", "mean", "stdev"):
+        assert np.array_equal(getattr(E, f), getattr(E2, f)), f
+    pairs = np.stack([log.case_id.astype(np.int64), log.ts_ns], axis=1)
+    if np.unique(pairs, axis=0).shape[0] == log.n_events:  # no tied timestamps in a case: rows do not matter
+        p = rng.permutation(log.n_events)
+        E3 = oracle.efg(log.case_id[p], log.activity[p], log.ts_ns[p], A, lib=lib)
+        for f in ("src", "dst", "count", "sum_lo", "sq0", "sq1", "stdev"):
+            assert np.array_equal(getattr(E, f), getattr(E3, f)), f"shuffle: {f}"
+
+
+def check_golden_efg(lib, name):
+    from fractions import Fraction
+    import math
+    g = load_golden(name)
+    base = load_golden(g["log"])
+    lg = base["log"]
+    E = oracle.efg(lg["case"], lg["activity"], lg["ts"], base["n_activities"], lib=lib)
+    assert [(int(a), int(b)) for a, b in zip(E.src, E.dst)] == [(p["src"], p["dst"]) for p in g["pairs"]]
+    for k, p in enumerate(g["pairs"]):
+        assert int(E.count[k]) == p["count"] and E.sums()[k] == p["sum"] and E.squares()[k] == p["sumsq"], p
+        if isinstance(p["mean"], str):
+            num, den = (int(x) for x in p["mean"].split("/"))
+            assert _ulps(float(E.mean[k]), float(Fraction(num, den))) <= 1.0, p
+        else:
+            assert float(E.mean[k]) == p["mean"], p
+        var = Fraction(*p["var"])
+        if p["stdev"] is not None:
+            assert float(E.stdev[k]) == p["stdev"], p
+        else:
+            assert _ulps(float(E.stdev[k]), math.sqrt(float(var))) <= 2.0, p
+
+
 def load_golden(name):
     with open(os.path.join(GOLDEN, name)) as f:
         return json.load(f)
@@ -422,12 +504,16 @@ def run_all(lib, quick=True):
     check_big_durations(lib)
     check_filters_bruteforce(lib, n_logs=60 if quick else 300)
     check_derived_filters_bruteforce(lib, n_logs=60 if quick else 300)
+    check_efg_bruteforce(lib, n_logs=60 if quick else 300)
     for name in sorted(os.listdir(GOLDEN)):
         if name.endswith(".json"):
-            (check_golden_filters if name.startswith("filters_") else check_golden)(lib, name)
+            check = check_golden_filters if name.startswith("filters_") else (
+                check_golden_efg if name.startswith("efg_") else check_golden)
+            check(lib, name)
     for log in small_logs():
         R = check_invariants(lib, log)
         check_closed_form_sums(lib, log, R)
         check_replication(lib, log, k=2)
         check_filters(lib, log)
         check_derived_filters(lib, log)
+    check_efg_invariants(lib, small_logs()[0])

@@ -5,8 +5,10 @@ wrong duration sign, a 64-bit sum, a swapped min/max, wrong end activity,
 reversed variant orders, unsigned case ordering, a filter boundary, the case
 attribute read at the wrong event, a path across cases or reversed, an open
 size bound, a throughput time from the wrong event, the end set read at the
-first event, an activity test that skips the last event. The pristine oracle
-passes every pin."""
+first event, an activity test that skips the last event, eventually-follows
+pairs reversed or including an event with itself, a dropped carry in the sums
+of squares, a sample instead of a population variance, a truncated mean. The
+pristine oracle passes every pin."""
 
 import pytest
 
@@ -45,6 +47,14 @@ MUTANTS = {
                                    "const uint64_t dur = (uint64_t)ts[s[e - 1]] - (uint64_t)ts[s[b + (e - b > 1)]];"),
     "end_set_reads_first": ("if (n_end > 0 && !in(end_set, n_end, act[s[e - 1]])) ok = false;",
                             "if (n_end > 0 && !in(end_set, n_end, act[s[b]])) ok = false;"),
+    "ef_reversed": ("EfAgg &g = (*M)[std::make_pair(act[s[i]], act[s[j]])];",
+                    "EfAgg &g = (*M)[std::make_pair(act[s[j]], act[s[i]])];"),
+    "ef_self_pairs": ("for (int64_t j = i + 1; j < e; ++j) {", "for (int64_t j = i; j < e; ++j) {"),
+    "ef_square_carry_dropped": ("          carry = t >> 64;\n        }\n      }", "          carry = 0;\n        }\n      }"),
+    "ef_sample_variance": ("/ (double)g.count / (double)g.count;",
+                           "/ (double)g.count / (double)(g.count > 1 ? g.count - 1 : 1);"),
+    "ef_mean_truncated": ("mean[k] = (double)g.sum / (double)g.count;\n    const U256",
+                          "mean[k] = (double)(uint64_t)(g.sum / g.count);\n    const U256"),
     "contains_skips_last": ("for (int64_t i = b; i < e; ++i) any = any || in(act_set, n_act, act[s[i]]);",
                             "for (int64_t i = b; i + 1 < e; ++i) any = any || in(act_set, n_act, act[s[i]]);"),
 }

@@ -71,6 +71,17 @@ def test_derived_filters(oracle_lib, logs):
         pins.check_derived_filters(oracle_lib, log)
 
 
+def test_efg(oracle_lib, logs):
+    """Eventually-follows graph and temporal profile: the hand-derived
+    fixture, the definition on random tiny logs (exact integer moments, means
+    and deviations within a few units in the last place of exact references),
+    identities on workload-shaped logs."""
+    pins.check_golden_efg(oracle_lib, "efg_fine_process.json")
+    pins.check_efg_bruteforce(oracle_lib, n_logs=400)
+    for log in logs[:2]:
+        pins.check_efg_invariants(oracle_lib, log)
+
+
 def test_filter_then_summarize_keeps_tie_order(oracle_lib):
     # the sub-log keeps original rows, so ties inside a case resolve as before
     case = [1, 1, 1, 2, 2]
