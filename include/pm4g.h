@@ -240,6 +240,26 @@ typedef struct {
 } pm4g_case_filter;
 int pm4g_filter_cases(pm4g_log *log, const pm4g_case_filter *spec, pm4g_log **out);
 
+/* Eventually-follows graph and temporal profile (Section 3, efg.py). A pair
+ * of events (i, j) of one case eventually follows when i comes before j in the
+ * case's (timestamp, row) order. For every activity pair (src, dst) with at
+ * least one such pair, ascending by (src, dst): count; the exact sum of
+ * ts_j - ts_i as sum_lo/sum_hi; the exact sum of their squares as sq0 (low
+ * word), sq1, sq2; mean = the sum rounded to double over the count (as for
+ * the DFG); stdev = the population standard deviation sqrt(v / n / n) with v
+ * the exact integer n * S2 - S1^2 rounded to the nearest double (ties to even)
+ * and n = (double)count, each step one IEEE operation. Library-allocated
+ * arrays, released with pm4g_efg_free. Errors: PM4G_EINVAL (NULL), PM4G_ENOMEM,
+ * PM4G_ECUDA. */
+typedef struct {
+  int64_t n_pairs;
+  int32_t *src, *dst;
+  uint64_t *count, *sum_lo, *sum_hi, *sq0, *sq1, *sq2;
+  double *mean, *stdev;
+} pm4g_efg_t;
+int pm4g_efg(pm4g_log *log, pm4g_efg_t *out);
+int pm4g_efg_free(pm4g_efg_t *res);
+
 /* Batched drill-down (Section 1, drill-down; Section 3, filters then the
  * frequency and performance DFG): for each of n_sub sub-logs, the results that
  * pm4g_filter(log, spec_i) followed by pm4g_perf_dfg and pm4g_start_end on the

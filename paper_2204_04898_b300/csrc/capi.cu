@@ -428,7 +428,7 @@ static int choose_clb(Ctx *c, int64_t n, uint64_t R, int32_t A, int act_bits) {
 const char *pm4g_last_error(void) { return pm4g::g_err; }
 
 const char *pm4g_kernel_names(void) {
-  return "stats,bucket_hist,bucket_scatter,partition,segment,fallback,scan,radix_sort,filter,variants,dfg,export,batch";
+  return "stats,bucket_hist,bucket_scatter,partition,segment,fallback,scan,radix_sort,filter,variants,dfg,export,batch,efg";
 }
 
 int pm4g_ctx_create(pm4g_ctx **out, int device, void *cuda_stream, const pm4g_allocator *alloc) {

@@ -57,6 +57,11 @@ class _CaseFilter(ctypes.Structure):
                 ("n_act", _i32), ("variant_set", _P), ("n_variant", _i32), ("exclude", _i32)]
 
 
+class _Efg(ctypes.Structure):
+    _fields_ = [("n_pairs", _i64)] + [(k, _P) for k in ("src", "dst", "count", "sum_lo", "sum_hi", "sq0", "sq1",
+                                                          "sq2", "mean", "stdev")]
+
+
 class _BatchSpec(ctypes.Structure):
     _fields_ = [("n_sub", _i32), ("attr_off", _P), ("attr_vals", _P), ("t_lo", _P), ("t_hi", _P),
                 ("mode", _P), ("var_top_k", _i64)]
@@ -96,6 +101,8 @@ lib.pm4g_variants.argtypes = [_P, _i64, _u32, ctypes.POINTER(_Variants)]
 lib.pm4g_variants_free.argtypes = [ctypes.POINTER(_Variants)]
 lib.pm4g_filter.argtypes = [_P, ctypes.POINTER(_FilterSpec), ctypes.POINTER(_P)]
 lib.pm4g_filter_cases.argtypes = [_P, ctypes.POINTER(_CaseFilter), ctypes.POINTER(_P)]
+lib.pm4g_efg.argtypes = [_P, ctypes.POINTER(_Efg)]
+lib.pm4g_efg_free.argtypes = [ctypes.POINTER(_Efg)]
 lib.pm4g_filter_paths.argtypes = [_P, _P, _P, _i32, _i32, ctypes.POINTER(_P)]
 lib.pm4g_batch_dfg.argtypes = [_P, ctypes.POINTER(_BatchSpec), ctypes.POINTER(_BatchDfg)]
 lib.pm4g_batch_dfg_free.argtypes = [ctypes.POINTER(_BatchDfg)]
@@ -343,6 +350,36 @@ def pm4g_filter_cases(log: int, min_events: int = -1, max_events: int = -1, min_
     h = _P()
     _check(lib.pm4g_filter_cases(log, ctypes.byref(spec), ctypes.byref(h)), "pm4g_filter_cases")
     return h.value
+
+
+@dataclass
+class Efg:
+    """Eventually-follows graph and temporal profile, pairs ascending by
+    (src, dst): counts, exact sums (sum_lo/sum_hi), exact sums of squares
+    (sq0 low word .. sq2), means and population standard deviations."""
+    src: np.ndarray
+    dst: np.ndarray
+    count: np.ndarray
+    sum_lo: np.ndarray
+    sum_hi: np.ndarray
+    sq0: np.ndarray
+    sq1: np.ndarray
+    sq2: np.ndarray
+    mean: np.ndarray
+    stdev: np.ndarray
+
+
+def pm4g_efg(log: int) -> Efg:
+    r = _Efg()
+    _check(lib.pm4g_efg(log, ctypes.byref(r)), "pm4g_efg")
+    try:
+        P = int(r.n_pairs)
+        u = np.uint64
+        return Efg(_np(r.src, P, np.int32), _np(r.dst, P, np.int32), _np(r.count, P, u), _np(r.sum_lo, P, u),
+                   _np(r.sum_hi, P, u), _np(r.sq0, P, u), _np(r.sq1, P, u), _np(r.sq2, P, u),
+                   _np(r.mean, P, np.float64), _np(r.stdev, P, np.float64))
+    finally:
+        lib.pm4g_efg_free(ctypes.byref(r))
 
 
 @dataclass

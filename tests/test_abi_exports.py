@@ -27,7 +27,8 @@ def lib_path():
 def test_header_declares_the_boundary():
     names = declared()
     for must in ("pm4g_load_log", "pm4g_dfg", "pm4g_perf_dfg", "pm4g_start_end", "pm4g_variants",
-                 "pm4g_filter", "pm4g_filter_paths", "pm4g_filter_cases", "pm4g_log_free", "pm4g_last_error"):
+                 "pm4g_filter", "pm4g_filter_paths", "pm4g_filter_cases", "pm4g_efg", "pm4g_log_free",
+                 "pm4g_last_error"):
         assert must in names
 
 
