@@ -13,6 +13,7 @@ weak scaling); value = events of all ranks / max rank time.
 
     python bench.py --mode drilldown [--views 4096] [--plain-views 4096]
     python bench.py --mode filters
+    python bench.py --mode efg
 
 Drill-down: a resident drilldown_log (100M events, A = 2000, case attributes)
 and 4096 drill-down views (attribute set + time window, EVENTS mode). One step
@@ -28,6 +29,11 @@ three most frequent end activities; cases containing one of the five rarest
 activities; cases of the ten most frequent variants). One step = each filter,
 then pm4g_perf_dfg of its sub-log and pm4g_log_free; value = input events of
 the six filters / step time.
+
+Eventually-follows graph / temporal profile: the resident very_large_log; one
+step = pm4g_efg (every ordered pair of events of a case, exact count, sum and
+sum of squares per activity pair, means and deviations, results on the host);
+value = pairs / step time (and events / step time beside it).
 """
 
 from __future__ import annotations
@@ -102,7 +108,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cases", type=int, default=1_000_000)
-    p.add_argument("--mode", default="single", choices=["single", "drilldown", "serve", "filters"])
+    p.add_argument("--mode", default="single", choices=["single", "drilldown", "serve", "filters", "efg"])
     p.add_argument("--rates", default="100,300,1000,3000,10000", help="serve: Poisson request rates (req/s)")
     p.add_argument("--seconds", type=float, default=3.0, help="serve: seconds of arrivals per rate")
     p.add_argument("--views", type=int, default=4096)
@@ -710,8 +716,130 @@ def run_reference_filters(args):
         dist.barrier()
 
 
+EFG_METRIC = "eventually-follows pairs/s for the EFG + temporal profile (exact moments)"
+
+
+def efg_sample(args, spec):
+    """The oracle's eventually-follows graph on a bounded sample of the law."""
+    import oracle
+    small = spec.scaled(max(500, min(spec.n_cases, args.cpu_sample_cases // 50)))
+    S = synth.generate(small)
+    t = time.perf_counter()
+    E = oracle.efg(S.case_id, S.activity, S.ts_ns, S.n_activities)
+    dt = time.perf_counter() - t
+    pairs = int(E.count.astype(np.int64).sum())
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{small.name} law with {small.n_cases} cases ({S.n_events} events, {pairs} pairs), one run, "
+                      f"{dt:.1f} s on 1 of {os.cpu_count()} host cores"}
+
+
+def run_efg(args):
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            if rank != 0:
+                dist.barrier()
+                return
+        spec = workload_spec(args)
+        vals = []
+        cpu = None
+        for i in range(args.warmup + args.steps):
+            cpu = efg_sample(args, spec)
+            if i >= args.warmup:
+                vals.append(cpu["value"])
+        cpu["value"] = statistics.median(vals)
+        print(json.dumps({"impl": "reference", "metric": EFG_METRIC, "value": cpu["value"], "unit": "pairs/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                          "data": "synthetic", "config": {"workload": "efg", "log": spec.name}, "cpu_baseline": cpu,
+                          "e2e": {"value": cpu["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        return
+    import torch
+    from paper_2204_04898_b300 import pm4g
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    spec = workload_spec(args)
+    t_gen = time.perf_counter()
+    L = synth.generate(spec, pinned=True)
+    t_gen = time.perf_counter() - t_gen
+    N, A = L.n_events, L.n_activities
+    dev = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns)]
+    stream = torch.cuda.Stream()
+    ctx = pm4g.pm4g_ctx_create(local, stream=stream.cuda_stream)
+    log = pm4g.pm4g_load_log(ctx, *dev, n_activities=A)
+    E = pm4g.pm4g_efg(log)  # also forms the timestamps in case order, once
+    pairs = int(E.count.astype(np.int64).sum())
+    n_cells = int(E.count.size)
+    d2h = sum(x.nbytes for x in (E.src, E.dst, E.count, E.sum_lo, E.sum_hi, E.sq0, E.sq1, E.sq2, E.mean, E.stdev))
+    for _ in range(args.warmup):
+        pm4g.pm4g_efg(log)
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 1)
+    pm4g.pm4g_ctx_timing_reset(ctx)
+    launches0 = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            pm4g.pm4g_efg(log)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    n_k, efg_ms = pm4g.pm4g_ctx_timing(ctx, "efg")
+    scan_ms = pm4g.pm4g_ctx_timing(ctx, "scan")[1]
+    launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0] - launches0
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
+    if dist is not None:
+        t_ = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        ms = float(t_[0])
+    cpu = efg_sample(args, spec) if rank == 0 and not args.no_cpu_baseline else None
+    pm4g.pm4g_log_free(log)
+    pm4g.pm4g_ctx_destroy(ctx)
+    if rank != 0:
+        return
+    value = pairs * world * 1e3 / ms
+    peak, peak_kind = peaks()
+    # byte model: every pair reads its two events' activity and timestamp
+    # (24 B) and updates one cell (six 8-byte words, read and written)
+    alg = 24.0 * pairs + 96.0 * pairs
+    kern_ms = efg_ms / args.steps
+    line = {
+        "metric": EFG_METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "efg", "log": spec.name, "n_events": N, "n_activities": A, "pairs": pairs,
+                   "activity_pairs": n_cells, "events_per_s": N * world * 1e3 / ms,
+                   "l2": "resident log larger than L2; the A x A table (48 B a cell) stays in L2",
+                   "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
+        "roofline": {"bound": "l2_atomics", "kernel": "efg", "achieved": alg / (kern_ms * 1e-3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / (kern_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                     "peak_kind": peak_kind, "alg_bytes_per_step": alg, "efg_kernels_ms_per_step": kern_ms,
+                     "note": "pair updates are 64-bit atomics on an L2-resident table; the HBM peak is context"},
+        "kernels_ms_per_step": {"efg": round(kern_ms, 4), "scan": round(scan_ms / args.steps, 4)},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "efg":
+        return run_efg(args)
     if args.mode == "filters":
         return run_filters(args)
     if args.mode == "serve":

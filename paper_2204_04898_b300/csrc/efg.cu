@@ -11,8 +11,12 @@
 // The pass reads the formatted log (activities and timestamps in case order):
 // one warp per case holds up to 32 of its events in registers and, for every
 // event i, the lanes j > i add their pair to a dense A x A table of exact
-// sums with 64-bit atomics (carries propagate to the next word at once). A
-// flag/scan/compaction lists the pairs with their mean and deviation.
+// sums with 64-bit atomics (carries propagate to the next word at once). The
+// frequent activity pairs would serialise those atomics at one L2 slice each,
+// so the blocks share K copies of the table (block b uses copy b mod K, as
+// many copies as fit a share of L2), folded exactly into the first one
+// afterwards. A flag/scan/compaction lists the pairs with their mean and
+// deviation.
 
 #include <algorithm>
 #include <cstdlib>
@@ -51,8 +55,11 @@ __device__ __forceinline__ void ef_add(const EfTable &t, uint32_t key, uint64_t 
 // later events; the earlier event is broadcast).
 __global__ void __launch_bounds__(256) k_efg_pairs(const uint32_t *len, const uint32_t *off, uint64_t n_slots,
                                                    const int32_t *act_s, const int64_t *ts_s, uint32_t A,
-                                                   EfTable t, unsigned long long *work) {
+                                                   EfTable t0, uint64_t copy_stride, uint32_t n_copies,
+                                                   unsigned long long *work) {
   const int lane = threadIdx.x & 31;
+  const uint64_t sh = (uint64_t)(blockIdx.x % n_copies) * copy_stride;  // this block's copy of the table
+  const EfTable t{t0.cnt + sh, t0.s_lo + sh, t0.s_hi + sh, t0.q0 + sh, t0.q1 + sh, t0.q2 + sh};
   for (;;) {
     unsigned long long s0 = 0;
     if (lane == 0) s0 = atomicAdd(work, 32ull);  // 32 slots per claim
@@ -82,6 +89,34 @@ __global__ void __launch_bounds__(256) k_efg_pairs(const uint32_t *len, const ui
         }
       }
     }
+  }
+}
+
+// Adds copies 1..K-1 of the table into copy 0, exactly (carries between the
+// words of each sum).
+__global__ void k_efg_fold(EfTable t, uint64_t cells, uint64_t copy_stride, uint32_t n_copies) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cells; k += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t c = t.cnt[k], slo = t.s_lo[k], shi = t.s_hi[k], q0 = t.q0[k], q1 = t.q1[k], q2 = t.q2[k];
+    for (uint32_t r = 1; r < n_copies; ++r) {
+      const uint64_t o = k + (uint64_t)r * copy_stride;
+      c += t.cnt[o];
+      const uint64_t a = t.s_lo[o];
+      slo += a;
+      shi += t.s_hi[o] + (slo < a ? 1u : 0u);
+      const uint64_t b0 = t.q0[o], b1 = t.q1[o];
+      q0 += b0;
+      const uint64_t c0 = q0 < b0 ? 1u : 0u;
+      const uint64_t s1 = q1 + b1;
+      const uint64_t c1 = s1 < q1 ? 1u : 0u;
+      q1 = s1 + c0;
+      q2 += t.q2[o] + c1 + (q1 < s1 ? 1u : 0u);
+    }
+    t.cnt[k] = c;
+    t.s_lo[k] = slo;
+    t.s_hi[k] = shi;
+    t.q0[k] = q0;
+    t.q1[k] = q1;
+    t.q2[k] = q2;
   }
 }
 
@@ -232,8 +267,11 @@ int pm4g_efg(pm4g_log *L, pm4g_efg_t *out) {
     PM4G_TRY(alloc_buf(c, L->ts_s, (size_t)L->n));
     PM4G_TRY(run_export(L, nullptr, nullptr, L->ts_s.p, nullptr));
   }
+  // copies of the table: as many as fit 64 MB (a share of L2), at most 8
+  const uint64_t table_bytes = 48 * cells;
+  const uint32_t K = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(8, (64ull << 20) / std::max<uint64_t>(table_bytes, 1)));
   Scratch S(c);
-  unsigned long long *tab = S.get<unsigned long long>(6 * cells);
+  unsigned long long *tab = S.get<unsigned long long>(6 * cells * K);
   unsigned long long *work = S.get<unsigned long long>(1);
   uint32_t *flags = S.get<uint32_t>(cells), *pos = S.get<uint32_t>(cells + 1);
   if (!tab || !work || !flags || !pos) {
@@ -241,13 +279,20 @@ int pm4g_efg(pm4g_log *L, pm4g_efg_t *out) {
     return PM4G_ENOMEM;
   }
   cudaStream_t s = c->stream;
-  PM4G_CK(cudaMemsetAsync(tab, 0, 6 * cells * 8, s));
+  PM4G_CK(cudaMemsetAsync(tab, 0, 6 * cells * K * 8, s));
   PM4G_CK(cudaMemsetAsync(work, 0, 8, s));
-  EfTable t{tab, tab + cells, tab + 2 * cells, tab + 3 * cells, tab + 4 * cells, tab + 5 * cells};
+  // layout: word w of copy r of cell k at tab[(w * K + r) * cells + k]
+  const uint64_t cs = cells;  // stride between copies of one word
+  EfTable t{tab, tab + cells * K, tab + 2 * cells * K, tab + 3 * cells * K, tab + 4 * cells * K, tab + 5 * cells * K};
   {
     KTime kt(c, "efg");
-    k_efg_pairs<<<8 * c->num_sms, 256, 0, s>>>(L->len.p, L->off.p, L->R, L->act_s.p, L->ts_s.p, A, t, work);
+    k_efg_pairs<<<8 * c->num_sms, 256, 0, s>>>(L->len.p, L->off.p, L->R, L->act_s.p, L->ts_s.p, A, t, cs, K,
+                                               work);
     PM4G_TRY(check_launch(c, "k_efg_pairs"));
+    if (K > 1) {
+      k_efg_fold<<<grid_for((int64_t)cells, 256, 65535), 256, 0, s>>>(t, cells, cs, K);
+      PM4G_TRY(check_launch(c, "k_efg_fold"));
+    }
     k_efg_flags<<<grid_for((int64_t)cells, 256, 65535), 256, 0, s>>>(t.cnt, cells, flags);
     PM4G_TRY(check_launch(c, "k_efg_flags"));
   }
