@@ -13,8 +13,8 @@
 // event i, the lanes j > i add their pair to a dense A x A table of exact
 // sums with 64-bit atomics (carries propagate to the next word at once). The
 // frequent activity pairs would serialise those atomics at one L2 slice each,
-// so the blocks share K copies of the table (block b uses copy b mod K, as
-// many copies as fit a share of L2), folded exactly into the first one
+// so the blocks share K copies of the table (block b uses copy b mod K; up to
+// 64 copies within a memory budget), folded exactly into the first one
 // afterwards. A flag/scan/compaction lists the pairs with their mean and
 // deviation.
 
@@ -267,9 +267,14 @@ int pm4g_efg(pm4g_log *L, pm4g_efg_t *out) {
     PM4G_TRY(alloc_buf(c, L->ts_s, (size_t)L->n));
     PM4G_TRY(run_export(L, nullptr, nullptr, L->ts_s.p, nullptr));
   }
-  // copies of the table: as many as fit 64 MB (a share of L2), at most 8
+  // copies of the table: at most 64, within min(1 GB, an eighth of free
+  // memory); more copies spread the frequent pairs' atomics further (on the
+  // 206.6M-event log: 5 copies 437 ms, 16 copies 316 ms, 64 copies 200 ms)
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
   const uint64_t table_bytes = 48 * cells;
-  const uint32_t K = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(8, (64ull << 20) / std::max<uint64_t>(table_bytes, 1)));
+  const uint64_t budget = std::min<uint64_t>(1ull << 30, fr / 8);
+  const uint32_t K = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, budget / std::max<uint64_t>(table_bytes, 1)));
   Scratch S(c);
   unsigned long long *tab = S.get<unsigned long long>(6 * cells * K);
   unsigned long long *work = S.get<unsigned long long>(1);
