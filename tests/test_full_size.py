@@ -14,6 +14,9 @@ own stream, top-1000 variants.
 - Drill-down (4,096 views of the 100M-event log in one batched call): the
   invariants of the definitions on every view, and 32 views (the largest, the
   smallest and random ones) bit-exact against the oracle's filter and summary.
+- Serving (the resident 10M-case log with attributes, views, variants and uploads of about
+  10k, 1M and 20M events): alone equals the shuffled mix; uploads and 8 views bit-exact
+  against the oracle.
 """
 
 from types import SimpleNamespace
@@ -236,3 +239,90 @@ def test_drilldown_views(pm4g):
         return rows.shape[0]
 
     assert sum(pool_map(one, pick)) == int(B.n_events[pick].sum())
+
+
+def _same(a, b):
+    assert a.keys() == b.keys()
+    for k in a:
+        x, y = a[k], b[k]
+        if isinstance(x, np.ndarray):
+            assert x.dtype == y.dtype and np.array_equal(x.view(np.uint8), y.view(np.uint8)), k
+        else:
+            assert x == y, k
+
+
+def test_serving_full_size(pm4g):
+    """The serving workload at full size: a resident 10M-case log with case
+    attributes answers filter+DFG views, top-10 variants and uploads of about
+    10k, 1M and 20M events; every result is the same alone and in the mix,
+    and matches the oracle (views, uploads) or the plain call (variants)."""
+    from paper_2204_04898_b300.serve import GpuEngine, Request, Server
+    L = synth.generate(synth.serving_log())
+    A = L.n_activities
+    views = synth.drilldown_specs(L, n_views=48, seed=20220417)
+    ups = [synth.generate(synth.very_large_log(c).scaled(c, f"upload{c}")) for c in (500, 50_000, 1_000_000)]
+    r = _resident(pm4g, L, with_attr=True)
+    eng = GpuEngine(pm4g, 0, r.log, r.ctx, upload_slots=2)
+    try:
+        def make():
+            reqs = [Request("dfg", attr_set=v.attr_set, t_lo=v.t_lo, t_hi=v.t_hi, mode=pm4g.TW_EVENTS) for v in views]
+            reqs += [Request("variants", top_k=10) for _ in range(4)]
+            reqs += [Request("upload", columns=(u.case_id, u.activity, u.ts_ns), n_activities=u.n_activities,
+                             top_k=10) for u in ups]
+            return reqs
+
+        srv = Server(eng, upload_slots=2)
+        try:
+            alone = make()
+            for q in alone:
+                srv.submit(q)
+                assert q.done.wait(300)
+                assert q.error is None, q.error
+            mix = make()
+            for i in np.random.default_rng(23).permutation(len(mix)):
+                srv.submit(mix[i])
+            for q in mix:
+                assert q.done.wait(300)
+                assert q.error is None, q.error
+            assert max(srv.batches) > 1, "the mix must have been batched"
+        finally:
+            srv.close()
+        for a, b in zip(alone, mix):
+            _same(a.result, b.result)
+        plain = pm4g.pm4g_variants(r.log, top_k=10)
+        for q in alone[len(views):len(views) + 4]:
+            v = q.result
+            assert v["n_variants"] == plain.n_variants
+            for k in ("count", "min_case", "off", "acts"):
+                assert np.array_equal(v[k], getattr(plain, k))
+    finally:
+        eng.close()
+        _release(pm4g, r)
+
+    def check(job):
+        kind, i = job
+        if kind == "dfg":
+            q = alone[i]
+            pre = np.flatnonzero(np.isin(L.case_attr, q.attr_set))
+            rows = pre[oracle.filter_rows(L.case_id[pre], L.activity[pre], L.ts_ns[pre], L.case_attr[pre], A,
+                                          q.attr_set, q.t_lo, q.t_hi, q.mode)]
+            R = oracle.summarize(L.case_id[rows], L.activity[rows], L.ts_ns[rows], A)
+            n_events = rows.shape[0]
+        else:
+            q, u = alone[len(views) + 4 + i], ups[i]
+            R = oracle.summarize(u.case_id, u.activity, u.ts_ns, u.n_activities)
+            n_events = u.n_events
+        got = q.result
+        assert got["n_events"] == n_events and got["n_cases"] == R.n_cases, f"{job}: sizes"
+        for name in ("src", "dst", "count", "sum_lo", "sum_hi", "min", "max", "start", "end", "freq"):
+            assert np.array_equal(got[name], getattr(R, name)), f"{job}: {name} differs"
+        assert np.array_equal(got["mean"].view(np.uint64), R.mean.view(np.uint64)), f"{job}: mean differs"
+        if kind == "upload":
+            k = min(10, R.n_variants)
+            assert got["n_variants"] == R.n_variants
+            assert np.array_equal(got["var_count"], R.var_count[:k])
+            assert np.array_equal(got["var_min_case"], R.var_min_case[:k])
+            assert np.array_equal(got["var_off"], R.var_off[:k + 1])
+            assert np.array_equal(got["var_acts"], R.var_acts[:R.var_off[k]])
+
+    pool_map(check, [("upload", i) for i in range(len(ups))] + [("dfg", i) for i in range(0, len(views), 6)])
