@@ -73,31 +73,47 @@ struct BatchArgs {
 };
 
 __host__ __device__ inline size_t bt_smem_bytes(uint32_t n_act) {
-  return (size_t)kBtSlots * 24 + (size_t)n_act * 8 + 64;
+  return (size_t)kBtSlots * 24 + (size_t)n_act * 8 + 64 + (size_t)kBtWarps * 64 * 4;
 }
 
-// Kept run [j0, j1) of one case of L events at formatted position o.
+// First index of the non-decreasing t[0, L) whose value is >= v (strict: > v).
+template <bool kStrict>
+__device__ __forceinline__ uint32_t ts_bound(const int64_t *__restrict__ t, uint32_t L, int64_t v) {
+  uint32_t lo = 0, n = L;
+  while (n > 0) {
+    const uint32_t h = n >> 1;
+    const int64_t x = t[lo + h];
+    if (kStrict ? x <= v : x < v) {
+      lo += h + 1;
+      n -= h + 1;
+    } else {
+      n = h;
+    }
+  }
+  return lo;
+}
+
+// Kept run [j0, j1) of one case of L events at formatted position o, found by
+// one lane. Timestamps are non-decreasing along a case, so EVENTS keeps the
+// events from the first at or after t_lo up to the last at or before t_hi;
+// cases wholly inside or outside the window (most of them) take two loads.
 __device__ __forceinline__ void kept_run(const BatchArgs &a, uint32_t o, uint32_t L, int mode, int64_t t_lo,
                                          int64_t t_hi, uint32_t &j0, uint32_t &j1) {
   j0 = 0;
   j1 = L;
   if (mode == PM4G_TW_NONE || L == 0) return;
+  const int64_t first = a.ts_s[o], last = a.ts_s[o + L - 1];
   if (mode == PM4G_TW_EVENTS) {
-    // timestamps are non-decreasing along the case: count those below t_lo
-    // and those at most t_hi
-    const int lane = (int)lane_id();
-    uint32_t below = 0, upto = 0;
-    for (uint32_t base = 0; base < L; base += 32) {
-      const uint32_t j = base + (uint32_t)lane;
-      const int64_t t = j < L ? a.ts_s[o + j] : 0;
-      below += __popc(__ballot_sync(kFull, j < L && t < t_lo));
-      upto += __popc(__ballot_sync(kFull, j < L && t <= t_hi));
+    if (first >= t_lo && last <= t_hi) return;
+    if (last < t_lo || first > t_hi) {
+      j1 = 0;
+      return;
     }
-    j0 = below;
-    j1 = max(upto, below);
+    j0 = first >= t_lo ? 0u : ts_bound<false>(a.ts_s + o, L, t_lo);
+    j1 = last <= t_hi ? L : ts_bound<true>(a.ts_s + o, L, t_hi);
+    j1 = max(j1, j0);
     return;
   }
-  const int64_t first = a.ts_s[o], last = a.ts_s[o + L - 1];
   const bool keep = mode == PM4G_TW_CASES_CONTAINED ? (first >= t_lo && last <= t_hi)
                                                     : (first <= t_hi && last >= t_lo);
   if (!keep) j1 = 0;
@@ -115,6 +131,8 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
   uint32_t *en = st + a.n_act;
   uint32_t *misc = en + a.n_act;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // per warp: sequence hash words (low, high) of its 32 cases
+  uint32_t *wl = misc + 16 + warp * 64, *wh = wl + 32;
   const uint32_t A = a.n_act;
   for (;;) {
     if (tid == 0) misc[0] = atomicAdd(a.work, 1u);
@@ -143,75 +161,96 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
                   (uint32_t)__clz((uint32_t)kBtSlots) + 1u, 1, st, en, nullptr, nullptr, g,
                   a.start + (uint64_t)sub * A, a.end + (uint64_t)sub * A};
     sink.probes = 16;
-    uint64_t ev = 0, cs = 0;
+    uint64_t ev = 0, cs = 0;  // this lane's kept events and cases
     for (uint32_t r = item.y; r < item.z; ++r) {
       const uint2 rg = a.ranges[r];
-      // Each warp takes cases k, k + kBtWarps, ... of the range; while one
-      // case is processed, the extent of the case two ahead is loaded.
-      uint32_t k = rg.x + (uint32_t)warp;
-      uint32_t o = 0, L = 0, on = 0, Ln = 0, o2 = 0, L2 = 0;  // extents of cases k, k + kBtWarps, k + 2 kBtWarps
-      if (k < rg.y) {
-        o = a.aoff[k];
-        L = a.alen[k];
-      }
-      if (k + kBtWarps < rg.y) {
-        on = a.aoff[k + kBtWarps];
-        Ln = a.alen[k + kBtWarps];
-      }
-      for (; k < rg.y; k += kBtWarps, o = on, L = Ln, on = o2, Ln = L2) {
-        o2 = 0;
-        L2 = 0;
-        if (k + 2 * kBtWarps < rg.y) {
-          o2 = a.aoff[k + 2 * kBtWarps];
-          L2 = a.alen[k + 2 * kBtWarps];
+      // A warp takes 32 consecutive cases of the range, one per lane: each
+      // lane finds its case's kept run, then the warp walks the runs' events
+      // 32 at a time across case boundaries (lane-dense), each lane locating
+      // its event's case by a binary search over the runs' prefix.
+      for (uint32_t k0 = rg.x + 32u * (uint32_t)warp; k0 < rg.y; k0 += 32u * kBtWarps) {
+        const uint32_t k = k0 + (uint32_t)lane;
+        const bool have = k < rg.y;
+        uint32_t o = 0, L = 0, j0 = 0, j1 = 0;
+        if (have) {
+          o = a.aoff[k];
+          L = a.alen[k];
+          kept_run(a, o, L, mode, t_lo, t_hi, j0, j1);
         }
-        const uint32_t rec = a.rlen ? a.rbase[r] + (k - rg.x) : 0u;
-        uint32_t j0, j1;
-        kept_run(a, o, L, mode, t_lo, t_hi, j0, j1);
-        if (j1 <= j0) {
-          if (a.rlen && lane == 0) a.rlen[rec] = 0;
-          continue;
+        const uint32_t n = j1 - j0, pos0 = o + j0;
+        uint32_t incl = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t v = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += v;
         }
-        ev += j1 - j0;
-        cs += 1;
-        uint32_t hl = 0, hh = 0;  // sequence hash of the kept run (as the segment pass forms it)
-        for (uint32_t base = j0; base < j1; base += 32) {
-          const uint32_t j = base + (uint32_t)lane;
-          const bool valid = j < j1;
-          const bool first = valid && j == j0, last = valid && j + 1 == j1;
+        const uint32_t excl = incl - n, T = __shfl_sync(kFull, incl, 31);
+        if (a.rlen) {
+          wl[lane] = 0;
+          wh[lane] = 0;
+          __syncwarp();
+        }
+        for (uint32_t b = 0; b < T; b += 32) {
+          const uint32_t x = b + (uint32_t)lane;
+          const bool valid = x < T;
+          // the case of x: the last lane whose prefix is at most x (it has a
+          // non-empty run containing x)
+          uint32_t c = 0;
+#pragma unroll
+          for (uint32_t d = 16; d >= 1; d >>= 1) {
+            const uint32_t e = __shfl_sync(kFull, excl, (int)(c + d));
+            if (e <= x) c += d;
+          }
+          const uint32_t ce = __shfl_sync(kFull, excl, (int)c);
+          const uint32_t cn = __shfl_sync(kFull, n, (int)c);
+          const uint32_t cp = __shfl_sync(kFull, pos0, (int)c);
+          const uint32_t i = x - ce, p = cp + i;
+          const bool first = valid && i == 0, last = valid && i + 1 == cn;
           const bool has_edge = valid && !last;
           uint32_t act = 0, e = 0;
           int64_t ts = 0;
           if (valid) {
-            ts = a.ts_s[o + j];
-            if (a.rlen || first || last) act = (uint32_t)a.act_s[o + j];
-            if (has_edge) e = a.eidx_s[o + j];
+            ts = a.ts_s[p];
+            if (a.rlen || first || last) act = (uint32_t)a.act_s[p];
+            if (has_edge) e = a.eidx_s[p];
           }
           if (first) sink.start(act);
           if (last) sink.end(act);
           int64_t nts = __shfl_down_sync(kFull, ts, 1);
-          if (lane == 31 && has_edge) nts = a.ts_s[o + j + 1];
+          if (lane == 31 && has_edge) nts = a.ts_s[p + 1];
           aggregate_edges(sink, has_edge, e, (uint64_t)nts - (uint64_t)ts);
           if (a.rlen && valid) {
-            const uint64_t t = event_hash(act, j - j0, 0);
-            hl += (uint32_t)t;
-            hh += (uint32_t)(t >> 32);
+            // the sequence hash of the kept run, as the segment pass forms it
+            const uint64_t t = event_hash(act, i, 0);
+            atomicAdd(&wl[c], (uint32_t)t);
+            atomicAdd(&wh[c], (uint32_t)(t >> 32));
           }
         }
+        ev += n;
+        cs += n ? 1u : 0u;
         if (a.rlen) {
-          hl = __reduce_add_sync(kFull, hl);
-          hh = __reduce_add_sync(kFull, hh);
-          if (lane == 0) {
-            a.rq[rec] = sub;
-            a.rslot[rec] = a.aslots[k];
-            a.rpos[rec] = o + j0;
-            a.rlen[rec] = j1 - j0;
-            a.rhash[rec] = ((uint64_t)hh << 32) | hl;
+          __syncwarp();
+          if (have) {
+            const uint32_t rec = a.rbase[r] + (k - rg.x);
+            if (n == 0) {
+              a.rlen[rec] = 0;
+            } else {
+              a.rq[rec] = sub;
+              a.rslot[rec] = a.aslots[k];
+              a.rpos[rec] = pos0;
+              a.rlen[rec] = n;
+              a.rhash[rec] = ((uint64_t)wh[lane] << 32) | wl[lane];
+            }
           }
+          __syncwarp();
         }
       }
     }
-    // lane 0 of every warp holds the warp's case and event counts
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+      ev += __shfl_down_sync(kFull, ev, d);
+      cs += __shfl_down_sync(kFull, cs, d);
+    }
     if (lane == 0 && cs) {
       atomicAdd(&a.n_ev[sub], (unsigned long long)ev);
       atomicAdd(&a.n_cs[sub], (unsigned long long)cs);
