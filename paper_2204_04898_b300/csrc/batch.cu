@@ -46,6 +46,7 @@ namespace {
 constexpr int kBtThreads = 1024;
 constexpr int kBtWarps = kBtThreads / 32;
 constexpr int kBtSlots = 8192;  // shared edge table (hashed)
+constexpr int kBtChunk = 16;    // cases a warp takes at once (a power of two, at most 32)
 
 struct BatchArgs {
   const uint32_t *aslots;  // present slots in (attribute, slot) order
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
   uint32_t *en = st + a.n_act;
   uint32_t *misc = en + a.n_act;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // per warp: sequence hash words (low, high) of its 32 cases
+  // per warp: sequence hash words (low, high) of its chunk's cases
   uint32_t *wl = misc + 16 + warp * 64, *wh = wl + 32;
   const uint32_t A = a.n_act;
   for (;;) {
@@ -162,15 +163,21 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
                   a.start + (uint64_t)sub * A, a.end + (uint64_t)sub * A};
     sink.probes = 16;
     uint64_t ev = 0, cs = 0;  // this lane's kept events and cases
+    uint32_t q = 0;  // chunks in the item's earlier ranges
     for (uint32_t r = item.y; r < item.z; ++r) {
       const uint2 rg = a.ranges[r];
-      // A warp takes 32 consecutive cases of the range, one per lane: each
-      // lane finds its case's kept run, then the warp walks the runs' events
-      // 32 at a time across case boundaries (lane-dense), each lane locating
-      // its event's case by a binary search over the runs' prefix.
-      for (uint32_t k0 = rg.x + 32u * (uint32_t)warp; k0 < rg.y; k0 += 32u * kBtWarps) {
-        const uint32_t k = k0 + (uint32_t)lane;
-        const bool have = k < rg.y;
+      // The item's ranges are cut into chunks of kBtChunk consecutive cases,
+      // dealt to the warps round-robin across ranges. A warp takes a chunk
+      // one case per lane: each lane finds its case's kept run, then the warp
+      // walks the runs' events 32 at a time across case boundaries
+      // (lane-dense), each lane locating its event's case by a binary search
+      // over the runs' prefix.
+      const uint32_t nch = (rg.y - rg.x + kBtChunk - 1) / kBtChunk;
+      uint32_t jc = ((uint32_t)warp + kBtWarps - q % kBtWarps) % kBtWarps;
+      q += nch;
+      for (; jc < nch; jc += kBtWarps) {
+        const uint32_t k = rg.x + jc * kBtChunk + (uint32_t)lane;
+        const bool have = lane < kBtChunk && k < rg.y;
         uint32_t o = 0, L = 0, j0 = 0, j1 = 0;
         if (have) {
           o = a.aoff[k];
@@ -178,13 +185,13 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
           kept_run(a, o, L, mode, t_lo, t_hi, j0, j1);
         }
         const uint32_t n = j1 - j0, pos0 = o + j0;
-        uint32_t incl = n;
+        uint32_t incl = n;  // inclusive prefix over lanes [0, kBtChunk)
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
+        for (int d = 1; d < kBtChunk; d <<= 1) {
           const uint32_t v = __shfl_up_sync(kFull, incl, d);
           if (lane >= d) incl += v;
         }
-        const uint32_t excl = incl - n, T = __shfl_sync(kFull, incl, 31);
+        const uint32_t excl = incl - n, T = __shfl_sync(kFull, incl, kBtChunk - 1);
         if (a.rlen) {
           wl[lane] = 0;
           wh[lane] = 0;
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
           // non-empty run containing x)
           uint32_t c = 0;
 #pragma unroll
-          for (uint32_t d = 16; d >= 1; d >>= 1) {
+          for (uint32_t d = kBtChunk / 2; d >= 1; d >>= 1) {
             const uint32_t e = __shfl_sync(kFull, excl, (int)(c + d));
             if (e <= x) c += d;
           }
