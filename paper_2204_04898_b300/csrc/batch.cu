@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
   uint32_t *wl = misc + 16 + warp * 64, *wh = wl + 32;
   const uint32_t A = a.n_act;
   for (;;) {
-    if (tid == 0) misc[0] = atomicAdd(a.work, 1u);
+    if (tid == 0) {
+      misc[0] = atomicAdd(a.work, 1u);
+      misc[1] = 0;  // next chunk of the item
+    }
     for (int i = tid; i < kBtSlots; i += kBtThreads) {
       tkey[i] = kEmptyKey;
       tcnt[i] = 0;
@@ -163,19 +166,32 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
                   a.start + (uint64_t)sub * A, a.end + (uint64_t)sub * A};
     sink.probes = 16;
     uint64_t ev = 0, cs = 0;  // this lane's kept events and cases
-    uint32_t q = 0;  // chunks in the item's earlier ranges
-    for (uint32_t r = item.y; r < item.z; ++r) {
-      const uint2 rg = a.ranges[r];
-      // The item's ranges are cut into chunks of kBtChunk consecutive cases,
-      // dealt to the warps round-robin across ranges. A warp takes a chunk
-      // one case per lane: each lane finds its case's kept run, then the warp
-      // walks the runs' events 32 at a time across case boundaries
-      // (lane-dense), each lane locating its event's case by a binary search
-      // over the runs' prefix.
-      const uint32_t nch = (rg.y - rg.x + kBtChunk - 1) / kBtChunk;
-      uint32_t jc = ((uint32_t)warp + kBtWarps - q % kBtWarps) % kBtWarps;
-      q += nch;
-      for (; jc < nch; jc += kBtWarps) {
+    // The item's ranges are cut into chunks of kBtChunk consecutive cases,
+    // numbered across the ranges; warps take chunks from a shared counter.
+    // A warp takes a chunk one case per lane: each lane finds its case's kept
+    // run, then the warp walks the runs' events 32 at a time across case
+    // boundaries (lane-dense), each lane locating its event's case by a
+    // binary search over the runs' prefix.
+    uint32_t r = item.y, qb = 0, nch = 0;  // the warp's range; it holds chunks [qb, qb + nch)
+    uint2 rg = make_uint2(0, 0);
+    if (r < item.z) {
+      rg = a.ranges[r];
+      nch = (rg.y - rg.x + kBtChunk - 1) / kBtChunk;
+    }
+    for (;;) {
+      uint32_t q = 0;
+      if (lane == 0) q = atomicAdd(&misc[1], 1u);
+      q = __shfl_sync(kFull, q, 0);
+      while (r < item.z && q >= qb + nch) {
+        qb += nch;
+        if (++r < item.z) {
+          rg = a.ranges[r];
+          nch = (rg.y - rg.x + kBtChunk - 1) / kBtChunk;
+        }
+      }
+      if (r >= item.z) break;
+      {
+        const uint32_t jc = q - qb;
         const uint32_t k = rg.x + jc * kBtChunk + (uint32_t)lane;
         const bool have = lane < kBtChunk && k < rg.y;
         uint32_t o = 0, L = 0, j0 = 0, j1 = 0;
