@@ -146,8 +146,34 @@ char *pinned(Ctx *c, size_t bytes) {
   return (char *)c->pin;
 }
 
+namespace {
+constexpr size_t kSmallBytes = 256;
+__global__ void k_small_copy(const unsigned char *__restrict__ src, unsigned char *dst, uint32_t n) {
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+}  // namespace
+
 int d2h(Ctx *c, void *dst, const void *src, size_t bytes) {
   if (!bytes) return PM4G_OK;
+  if (bytes <= kSmallBytes) {
+    if (!c->small) {
+      if (cudaHostAlloc(&c->small, kSmallBytes, cudaHostAllocMapped) != cudaSuccess ||
+          cudaHostGetDevicePointer(&c->small_dev, c->small, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->small) cudaFreeHost(c->small);
+        c->small = nullptr;
+        c->small_dev = nullptr;
+      }
+    }
+    if (c->small) {
+      k_small_copy<<<1, 64, 0, c->stream>>>((const unsigned char *)src, (unsigned char *)c->small_dev,
+                                            (uint32_t)bytes);
+      PM4G_TRY(check_launch(c, "k_small_copy"));
+      PM4G_CK(cudaStreamSynchronize(c->stream));
+      memcpy(dst, c->small, bytes);
+      return PM4G_OK;
+    }
+  }
   D2HBatch b(c, bytes);
   b.add(dst, src, bytes);
   return b.finish();
@@ -494,6 +520,7 @@ int pm4g_ctx_destroy(pm4g_ctx *c) {
   cache_flush(c);
   cudaStreamSynchronize(c->stream);
   if (c->pin) cudaFreeHost(c->pin);
+  if (c->small) cudaFreeHost(c->small);
   if (c->copy_stream) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamDestroy(c->copy_stream);

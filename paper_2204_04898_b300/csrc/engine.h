@@ -67,6 +67,11 @@ struct Ctx {
   // event that orders it after the context stream (created when first used)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_ready = nullptr;
+  // page-locked, device-mapped bytes for small results (counts, totals): a
+  // kernel writes them over the bus, so reading one does not queue behind
+  // bulk result copies on the copy engines (allocated when first used)
+  void *small = nullptr;
+  void *small_dev = nullptr;
   // device blocks freed by this context, kept for reuse in stream order
   // (rounded size -> blocks); every kernel of the context runs on its stream
   std::multimap<size_t, void *> cache;
@@ -198,7 +203,8 @@ struct D2HBatch {
   }
 };
 
-// One device-to-host copy, synchronised.
+// One device-to-host copy, synchronised (up to 256 bytes through the mapped
+// bytes of the context).
 int d2h(Ctx *c, void *dst, const void *src, size_t bytes);
 
 }  // namespace pm4g
