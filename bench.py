@@ -144,21 +144,24 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, warm=None):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.warm = warm  # untimed steps run after the sampler starts, so the idle wait does not reach the timed steps
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(prefix="pm4g_clocks_", suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         time.sleep(0.3)
+        if self.warm is not None:
+            self.warm()
         return self
 
     def __exit__(self, *exc):
@@ -331,7 +334,12 @@ def run_drilldown(args):
     if dist is not None:
         dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    def rewarm():
+        for _ in range(3):
+            pm4g.pm4g_batch_dfg(log, out=buf, var_top_k=vk, spec=bspec)
+        pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
+
+    with ClockSampler(local, rewarm) as clk:
         torch.cuda.synchronize()
         t = time.perf_counter()
         ev0.record(stream)
@@ -604,7 +612,12 @@ def run_filters(args):
     if dist is not None:
         dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    def rewarm():
+        for name, kind, kw in mix:
+            run_one(kind, kw)
+        pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
+
+    with ClockSampler(local, rewarm) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -789,7 +802,11 @@ def run_efg(args):
     if dist is not None:
         dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    def rewarm():
+        pm4g.pm4g_efg(log)
+        pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
+
+    with ClockSampler(local, rewarm) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -902,7 +919,12 @@ def main():
     torch.cuda.synchronize()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    def rewarm():
+        for _ in range(3):
+            step(dev)
+        pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
+
+    with ClockSampler(local, rewarm) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):

@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <type_traits>
 #include <vector>
 
@@ -46,6 +47,7 @@ namespace {
 constexpr int kBtThreads = 1024;
 constexpr int kBtWarps = kBtThreads / 32;
 constexpr int kBtSlots = 8192;  // shared edge table (hashed)
+constexpr int kBtStages = 4;   // groups a pipelined batch is cut into
 constexpr int kBtChunk = 16;    // cases a warp takes at once (a power of two, at most 32)
 
 struct BatchArgs {
@@ -782,6 +784,11 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
   const size_t per_sub = (size_t)E * 40 + (size_t)A * 24 + 64 + (size_t)E * 8;
   const size_t rec_bytes = want_var ? 128 : 0;  // records, their sort and the variant table, per case
   const size_t budget = std::max<size_t>(std::min<size_t>(fr / 3, (size_t)32 << 30), per_sub);
+  // Into caller-owned arrays (which never move), a batch of many sub-logs
+  // runs as a pipeline of about kBtStages groups: a group's result copies
+  // (copy stream) overlap the next group's kernels (context stream).
+  const bool pipelined = caller && Q >= 64;
+  const int32_t group_cap = pipelined ? (Q + kBtStages - 1) / kBtStages : Q;
   std::vector<std::pair<int32_t, int32_t>> groups;
   {
     int32_t g0 = 0;
@@ -791,7 +798,7 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       uint64_t ci = 0;
       for (const uint2 &rg : sub_ranges[i]) ci += rg.y - rg.x;
       const size_t m = per_sub + (size_t)ci * rec_bytes;
-      if (i > g0 && (mem + m > budget || (want_var && recs + ci > (1ull << 31)))) {
+      if (i > g0 && (mem + m > budget || (want_var && recs + ci > (1ull << 31)) || i - g0 >= group_cap)) {
         groups.emplace_back(g0, i - g0);
         g0 = i;
         mem = 0;
@@ -804,6 +811,49 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
   }
   const uint64_t W = std::max<uint64_t>(1 << 15, total_ev / ((uint64_t)c->num_sms * 4) + 1);
   bool overflow = false;
+  // A group whose results are still being copied out: its scratch (the
+  // copies' sources), the host vectors the copies land in, and the events
+  // after its last work on each stream. Destroying it waits for both.
+  struct Pending {
+    std::unique_ptr<Scratch> S;
+    std::vector<int64_t> goff;
+    std::vector<unsigned long long> gcnt;
+    std::vector<uint32_t> gvq, grow0;
+    int32_t q0 = 0, Qg = 0;
+    size_t base = 0, vbase = 0;
+    cudaEvent_t ev_s = nullptr, ev_cs = nullptr;
+    ~Pending() {
+      if (ev_s) cudaEventSynchronize(ev_s);
+      if (ev_cs) cudaEventSynchronize(ev_cs);
+      if (ev_s) cudaEventDestroy(ev_s);
+      if (ev_cs) cudaEventDestroy(ev_cs);
+    }
+  };
+  // Waits for a group's copies and fills the per-sub-log host results.
+  auto finish = [&](Pending &p) -> int {
+    cudaError_t ce = cudaEventSynchronize(p.ev_s);
+    const cudaError_t ce2 = cudaEventSynchronize(p.ev_cs);
+    if (ce == cudaSuccess) ce = ce2;
+    if (ce != cudaSuccess) {
+      set_error("pm4g_batch_dfg: result copy failed: %s", cudaGetErrorString(ce));
+      return PM4G_ECUDA;
+    }
+    for (int32_t q = 0; q < p.Qg; ++q) {
+      out->n_events[p.q0 + q] = (int64_t)p.gcnt[q];
+      out->n_cases[p.q0 + q] = (int64_t)p.gcnt[p.Qg + q];
+      out->edge_off[p.q0 + q] = (int64_t)p.base + p.goff[q];
+    }
+    out->edge_off[p.q0 + p.Qg] = (int64_t)p.base + p.goff[p.Qg];
+    if (want_var) {
+      for (int32_t q = 0; q < p.Qg; ++q) {
+        out->n_variants[p.q0 + q] = p.gvq[q];
+        out->var_off[p.q0 + q] = (int64_t)p.vbase + p.grow0[q];
+      }
+      out->var_off[p.q0 + p.Qg] = (int64_t)p.vbase + p.grow0[p.Qg];
+    }
+    return PM4G_OK;
+  };
+  std::unique_ptr<Pending> prev;
   for (const auto &grp : groups) {
     if (st != PM4G_OK) break;
     const int32_t q0 = grp.first, Qg = grp.second;
@@ -840,7 +890,8 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     }
     std::stable_sort(P.items.begin(), P.items.end(), [](const uint4 &x, const uint4 &y) { return x.w > y.w; });
     const uint64_t cellsg = (uint64_t)Qg * E;
-    Scratch S(c);
+    auto Sp = std::make_unique<Scratch>(c);
+    Scratch &S = *Sp;
     unsigned long long *acc = S.get<unsigned long long>(5 * cellsg);
     unsigned long long *se = S.get<unsigned long long>(3 * (size_t)Qg * A);  // start, end, freq
     unsigned long long *cnts = S.get<unsigned long long>(2 * (size_t)Qg);
@@ -1012,8 +1063,11 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     // group's scratch (their sources) goes back to the block cache
     struct CopyWait {
       cudaStream_t cs;
-      ~CopyWait() { cudaStreamSynchronize(cs); }
-    } copy_wait{cs};
+      bool armed;
+      ~CopyWait() {
+        if (armed) cudaStreamSynchronize(cs);
+      }
+    } copy_wait{cs, true};
     // variants of the group's sub-logs
     uint32_t rows_g = 0, acts_g = 0;
     uint32_t *vq = nullptr, *row0 = nullptr, *o_seq = nullptr;
@@ -1153,11 +1207,9 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
         if ((st = check_launch(c, "k_bv_acts")) != PM4G_OK) break;
       }
     }
-    auto cp = [&](void *dst, const void *src, size_t bytes) {
-      if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
-    };
-    cp(goff.data(), doff, ((size_t)Qg + 1) * 8);
-    cp(gcnt.data(), cnts, 2 * (size_t)Qg * 8);
+    // The group's remaining results go out on the copy stream too, after the
+    // variant kernels: the context stream carries no copy that the next
+    // group's kernels would queue behind.
     std::vector<uint32_t> gvq, grow0;
     bool vfits = false;
     const size_t vbase = Vt, abase = At;
@@ -1170,46 +1222,66 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
       if (!vfits) overflow = true;
       gvq.resize(Qg);
       grow0.resize((size_t)Qg + 1);
-      cp(gvq.data(), vq, (size_t)Qg * 4);
-      cp(grow0.data(), row0, ((size_t)Qg + 1) * 4);
-      if (vfits) {
-        if (rows_g + 1 > 0) {
-          k_bv_seq64<<<grid_for((int64_t)rows_g + 1, 256, 65535), 256, 0, s>>>(o_seq, rows_g + 1, (int64_t)abase,
-                                                                              o_seq64);
-          if (ce == cudaSuccess) ce = cudaGetLastError();
-        }
-        cp(out->var_seq_off + vbase, o_seq64, ((size_t)rows_g + 1) * 8);
-        cp(out->var_count + vbase, o_count, (size_t)rows_g * 8);
-        cp(out->var_min_case + vbase, o_min, (size_t)rows_g * 4);
-        cp(out->var_acts + abase, o_acts, (size_t)acts_g * 4);
+      if (vfits && rows_g + 1 > 0) {
+        k_bv_seq64<<<grid_for((int64_t)rows_g + 1, 256, 65535), 256, 0, s>>>(o_seq, rows_g + 1, (int64_t)abase,
+                                                                            o_seq64);
+        if (ce == cudaSuccess) ce = cudaGetLastError();
       }
     }
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    {  // the copy stream too, whatever happened (its sources are this group's scratch)
-      const cudaError_t ce2 = cudaStreamSynchronize(cs);
-      if (ce == cudaSuccess) ce = ce2;
+    if (ce == cudaSuccess) ce = cudaEventRecord(c->copy_ready, s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, c->copy_ready, 0);
+    cpc(goff.data(), doff, ((size_t)Qg + 1) * 8);
+    cpc(gcnt.data(), cnts, 2 * (size_t)Qg * 8);
+    if (want_var) {
+      cpc(gvq.data(), vq, (size_t)Qg * 4);
+      cpc(grow0.data(), row0, ((size_t)Qg + 1) * 4);
+      if (vfits) {
+        cpc(out->var_seq_off + vbase, o_seq64, ((size_t)rows_g + 1) * 8);
+        cpc(out->var_count + vbase, o_count, (size_t)rows_g * 8);
+        cpc(out->var_min_case + vbase, o_min, (size_t)rows_g * 4);
+        cpc(out->var_acts + abase, o_acts, (size_t)acts_g * 4);
+      }
     }
+    auto pend = std::make_unique<Pending>();
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pend->ev_s, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pend->ev_cs, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventRecord(pend->ev_s, s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(pend->ev_cs, cs);
     if (ce != cudaSuccess) {
       set_error("pm4g_batch_dfg: result copy failed: %s", cudaGetErrorString(ce));
       st = PM4G_ECUDA;
       break;
     }
+    pend->S = std::move(Sp);
+    pend->goff = std::move(goff);
+    pend->gcnt = std::move(gcnt);
+    pend->gvq = std::move(gvq);
+    pend->grow0 = std::move(grow0);
+    pend->q0 = q0;
+    pend->Qg = Qg;
+    pend->base = base;
+    pend->vbase = vbase;
+    copy_wait.armed = false;  // the pending group now waits for its copies
     Et = base + Eg;
-    for (int32_t q = 0; q < Qg; ++q) {
-      out->n_events[q0 + q] = (int64_t)gcnt[q];
-      out->n_cases[q0 + q] = (int64_t)gcnt[Qg + q];
-      out->edge_off[q0 + q] = (int64_t)base + goff[q];
-    }
-    out->edge_off[q0 + Qg] = (int64_t)base + goff[Qg];
     if (want_var) {
-      for (int32_t q = 0; q < Qg; ++q) {
-        out->n_variants[q0 + q] = gvq[q];
-        out->var_off[q0 + q] = (int64_t)vbase + grow0[q];
-      }
-      out->var_off[q0 + Qg] = (int64_t)vbase + grow0[Qg];
       Vt = vbase + rows_g;
       At = abase + acts_g;
     }
+    if (prev) {
+      st = finish(*prev);
+      prev.reset();
+      if (st != PM4G_OK) break;
+    }
+    prev = std::move(pend);
+    if (!pipelined) {
+      st = finish(*prev);
+      prev.reset();
+      if (st != PM4G_OK) break;
+    }
+  }
+  if (prev) {
+    if (st == PM4G_OK) st = finish(*prev);
+    prev.reset();
   }
   if (st == PM4G_OK && !caller && (!room(Et) || !room_var(Vt, At))) st = PM4G_ENOMEM;  // arrays exist even when empty
   if (st != PM4G_OK) return fail_out(st);

@@ -101,7 +101,27 @@ void dfree(Ctx *c, void *p, size_t bytes) {
   }
 }
 
+// Adds the durations of the finished timing pairs at the front of the pending
+// list to the totals and returns their events to the pool (no wait).
+static void settle_finished(Ctx *c) {
+  size_t k = 0;
+  for (; k < c->pending.size(); ++k) {
+    const TimingRec &p = c->pending[k];
+    if (cudaEventQuery(p.b) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    auto &t = c->totals[p.name];
+    t.first += 1;
+    t.second += ms;
+    c->free_events.push_back(p.a);
+    c->free_events.push_back(p.b);
+  }
+  cudaGetLastError();  // a query of an unfinished event is not an error
+  c->pending.erase(c->pending.begin(), c->pending.begin() + k);
+}
+
 static cudaEvent_t get_event(Ctx *c) {
+  if (c->free_events.empty()) settle_finished(c);
   if (!c->free_events.empty()) {
     cudaEvent_t e = c->free_events.back();
     c->free_events.pop_back();
