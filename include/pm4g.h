@@ -59,7 +59,10 @@ extern "C" {
 #define PM4G_TW_CASES_INTERSECTING 3
 
 /* Context options (pm4g_ctx_set_option) */
-#define PM4G_OPT_TIMING 1            /* 1 = time every kernel launch with CUDA events */
+#define PM4G_OPT_TIMING 1            /* 1 = time every kernel launch with CUDA events;
+                                        2 = time only the dominant kernels (segment,
+                                        partition, batch_dfg, efg, filter), whose
+                                        events then cost the host little; 0 = off */
 #define PM4G_OPT_TEST_HASH_BITS 2    /* test only: keep this many bits (1..63) of the
                                         variant key, forcing the collision path; 0 = off */
 #define PM4G_OPT_TEST_BUCKET_CAP 3   /* test only: events a bucket may hold in shared

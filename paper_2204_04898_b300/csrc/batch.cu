@@ -978,8 +978,7 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
         st = PM4G_ECUDA;
         break;
       }
-      KTime t(c, "batch");
-      c->launches++;
+      KTime t(c, "batch_dfg");
       k_batch_dfg<<<std::min<unsigned>(a.n_items, (unsigned)c->num_sms), kBtThreads, smem, s>>>(a);
       if ((st = check_launch(c, "k_batch_dfg")) != PM4G_OK) break;
     }

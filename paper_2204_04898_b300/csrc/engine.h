@@ -51,7 +51,7 @@ struct Ctx {
   int num_sms = 148;
   int smem_optin = 227 * 1024;
   // options
-  bool timing = false;
+  int timing = 0;  // PM4G_OPT_TIMING: 0 off, 1 every launch, 2 the dominant kernels
   int test_hash_bits = 0;
   int test_bucket_cap = 0;
   // timing
