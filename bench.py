@@ -606,7 +606,7 @@ def run_filters(args):
     for _ in range(args.warmup):
         for name, kind, kw in mix:
             run_one(kind, kw)
-    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 1)
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 2)  # the filter and segment kernels
     pm4g.pm4g_ctx_timing_reset(ctx)
     launches0 = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
     per = {name: 0.0 for name, _, _ in mix}
