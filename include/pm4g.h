@@ -68,6 +68,13 @@ extern "C" {
 #define PM4G_OPT_TEST_BUCKET_CAP 3   /* test only: events a bucket may hold in shared
                                         memory (>= 32); smaller values force the
                                         global-memory path; 0 = default */
+/* Launch choices of pm4g_batch_dfg (0 = default; results never depend on them;
+ * an autotuner picks them by timing, see paper_2204_04898_b300/autotune.py): */
+#define PM4G_OPT_BATCH_CHUNK 4       /* cases a warp takes at once: 8, 16 (default) or 32 */
+#define PM4G_OPT_BATCH_STAGES 5      /* groups a batch of >= 64 views into caller-owned
+                                        arrays is pipelined in: 1..16 (default 4) */
+#define PM4G_OPT_BATCH_ITEMS_PER_SM 6 /* work items per SM a batch's events are cut
+                                        into: 1..32 (default 4) */
 
 typedef struct pm4g_ctx pm4g_ctx;
 typedef struct pm4g_log pm4g_log;

@@ -47,8 +47,12 @@ namespace {
 constexpr int kBtThreads = 1024;
 constexpr int kBtWarps = kBtThreads / 32;
 constexpr int kBtSlots = 8192;  // shared edge table (hashed)
-constexpr int kBtStages = 4;   // groups a pipelined batch is cut into
-constexpr int kBtChunk = 16;    // cases a warp takes at once (a power of two, at most 32)
+// Defaults of the tunable launch choices (PM4G_OPT_BATCH_*): groups a
+// pipelined batch is cut into, cases a warp takes at once, work items per SM.
+constexpr int kBtStages = 4;
+constexpr int kBtChunk = 16;
+constexpr int kBtItemsPerSm = 4;
+static_assert(kBtChunk == 8 || kBtChunk == 16 || kBtChunk == 32, "the launch switch covers 8, 16 and 32");
 
 struct BatchArgs {
   const uint32_t *aslots;  // present slots in (attribute, slot) order
@@ -122,6 +126,7 @@ __device__ __forceinline__ void kept_run(const BatchArgs &a, uint32_t o, uint32_
   if (!keep) j1 = 0;
 }
 
+template <int kChunk>  // cases a warp takes at once: a power of two, at most 32
 __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *tl = reinterpret_cast<uint32_t *>(smem);
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
                   a.start + (uint64_t)sub * A, a.end + (uint64_t)sub * A};
     sink.probes = 16;
     uint64_t ev = 0, cs = 0;  // this lane's kept events and cases
-    // The item's ranges are cut into chunks of kBtChunk consecutive cases,
+    // The item's ranges are cut into chunks of kChunk consecutive cases,
     // numbered across the ranges; warps take chunks from a shared counter.
     // A warp takes a chunk one case per lane: each lane finds its case's kept
     // run, then the warp walks the runs' events 32 at a time across case
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
     uint2 rg = make_uint2(0, 0);
     if (r < item.z) {
       rg = a.ranges[r];
-      nch = (rg.y - rg.x + kBtChunk - 1) / kBtChunk;
+      nch = (rg.y - rg.x + kChunk - 1) / kChunk;
     }
     for (;;) {
       uint32_t q = 0;
@@ -188,14 +193,14 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
         qb += nch;
         if (++r < item.z) {
           rg = a.ranges[r];
-          nch = (rg.y - rg.x + kBtChunk - 1) / kBtChunk;
+          nch = (rg.y - rg.x + kChunk - 1) / kChunk;
         }
       }
       if (r >= item.z) break;
       {
         const uint32_t jc = q - qb;
-        const uint32_t k = rg.x + jc * kBtChunk + (uint32_t)lane;
-        const bool have = lane < kBtChunk && k < rg.y;
+        const uint32_t k = rg.x + jc * kChunk + (uint32_t)lane;
+        const bool have = lane < kChunk && k < rg.y;
         uint32_t o = 0, L = 0, j0 = 0, j1 = 0;
         if (have) {
           o = a.aoff[k];
@@ -203,13 +208,13 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
           kept_run(a, o, L, mode, t_lo, t_hi, j0, j1);
         }
         const uint32_t n = j1 - j0, pos0 = o + j0;
-        uint32_t incl = n;  // inclusive prefix over lanes [0, kBtChunk)
+        uint32_t incl = n;  // inclusive prefix over lanes [0, kChunk)
 #pragma unroll
-        for (int d = 1; d < kBtChunk; d <<= 1) {
+        for (int d = 1; d < kChunk; d <<= 1) {
           const uint32_t v = __shfl_up_sync(kFull, incl, d);
           if (lane >= d) incl += v;
         }
-        const uint32_t excl = incl - n, T = __shfl_sync(kFull, incl, kBtChunk - 1);
+        const uint32_t excl = incl - n, T = __shfl_sync(kFull, incl, kChunk - 1);
         if (a.rlen) {
           wl[lane] = 0;
           wh[lane] = 0;
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
           // non-empty run containing x)
           uint32_t c = 0;
 #pragma unroll
-          for (uint32_t d = kBtChunk / 2; d >= 1; d >>= 1) {
+          for (uint32_t d = kChunk / 2; d >= 1; d >>= 1) {
             const uint32_t e = __shfl_sync(kFull, excl, (int)(c + d));
             if (e <= x) c += d;
           }
@@ -787,8 +792,9 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
   // Into caller-owned arrays (which never move), a batch of many sub-logs
   // runs as a pipeline of about kBtStages groups: a group's result copies
   // (copy stream) overlap the next group's kernels (context stream).
-  const bool pipelined = caller && Q >= 64;
-  const int32_t group_cap = pipelined ? (Q + kBtStages - 1) / kBtStages : Q;
+  const int stages = c->batch_stages ? c->batch_stages : kBtStages;
+  const bool pipelined = caller && Q >= 64 && stages > 1;
+  const int32_t group_cap = pipelined ? (Q + stages - 1) / stages : Q;
   std::vector<std::pair<int32_t, int32_t>> groups;
   {
     int32_t g0 = 0;
@@ -809,7 +815,8 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     }
     groups.emplace_back(g0, Q - g0);
   }
-  const uint64_t W = std::max<uint64_t>(1 << 15, total_ev / ((uint64_t)c->num_sms * 4) + 1);
+  const uint64_t per_sm = (uint64_t)(c->batch_items_per_sm ? c->batch_items_per_sm : kBtItemsPerSm);
+  const uint64_t W = std::max<uint64_t>(1 << 15, total_ev / ((uint64_t)c->num_sms * per_sm) + 1);
   bool overflow = false;
   // A group whose results are still being copied out: its scratch (the
   // copies' sources), the host vectors the copies land in, and the events
@@ -973,13 +980,15 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     unsigned long long *freq = se + 2 * (size_t)Qg * A;
     if (!P.items.empty()) {
       const size_t smem = bt_smem_bytes(A);
-      if (cudaFuncSetAttribute(k_batch_dfg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max()) != cudaSuccess) {
+      const int chunk = c->batch_chunk ? c->batch_chunk : kBtChunk;
+      void (*kern)(BatchArgs) = chunk == 8 ? k_batch_dfg<8> : chunk == 32 ? k_batch_dfg<32> : k_batch_dfg<16>;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max()) != cudaSuccess) {
         set_error("pm4g_batch_dfg: shared memory attribute: %s", cudaGetErrorString(cudaGetLastError()));
         st = PM4G_ECUDA;
         break;
       }
       KTime t(c, "batch_dfg");
-      k_batch_dfg<<<std::min<unsigned>(a.n_items, (unsigned)c->num_sms), kBtThreads, smem, s>>>(a);
+      kern<<<std::min<unsigned>(a.n_items, (unsigned)c->num_sms), kBtThreads, smem, s>>>(a);
       if ((st = check_launch(c, "k_batch_dfg")) != PM4G_OK) break;
     }
     // compaction of the group's edges, sub-log by sub-log in edge order

@@ -575,6 +575,18 @@ int pm4g_ctx_set_option(pm4g_ctx *c, int option, int64_t value) {
       if (value < 0 || value > 63) break;
       c->test_hash_bits = (int)value;
       return PM4G_OK;
+    case PM4G_OPT_BATCH_CHUNK:
+      if (value != 0 && value != 8 && value != 16 && value != 32) break;
+      c->batch_chunk = (int)value;
+      return PM4G_OK;
+    case PM4G_OPT_BATCH_STAGES:
+      if (value < 0 || value > 16) break;
+      c->batch_stages = (int)value;
+      return PM4G_OK;
+    case PM4G_OPT_BATCH_ITEMS_PER_SM:
+      if (value < 0 || value > 32) break;
+      c->batch_items_per_sm = (int)value;
+      return PM4G_OK;
     case PM4G_OPT_TEST_BUCKET_CAP:
       if (value != 0 && (value < 32 || value > 65535)) break;
       c->test_bucket_cap = (int)value;

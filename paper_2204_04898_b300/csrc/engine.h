@@ -54,6 +54,10 @@ struct Ctx {
   int timing = 0;  // PM4G_OPT_TIMING: 0 off, 1 every launch, 2 the dominant kernels
   int test_hash_bits = 0;
   int test_bucket_cap = 0;
+  // launch choices of the batched drill-down (PM4G_OPT_BATCH_*; 0 = default)
+  int batch_chunk = 0;
+  int batch_stages = 0;
+  int batch_items_per_sm = 0;
   // timing
   std::vector<TimingRec> pending;
   std::vector<cudaEvent_t> free_events;

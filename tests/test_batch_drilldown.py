@@ -294,3 +294,58 @@ def test_batch_variants_into_buffers(pm4g, ctx):
         _check_batch(B2, L, specs, top_k=-1)
     finally:
         pm4g.pm4g_log_free(log)
+
+
+def _same_batch(A, B):
+    for k in ("n_events", "n_cases", "edge_off", "src", "dst", "count", "sum_lo", "sum_hi", "min", "max", "start",
+              "end", "freq", "n_variants", "var_off", "var_count", "var_min_case", "var_seq_off", "var_acts"):
+        x, y = getattr(A, k), getattr(B, k)
+        assert np.array_equal(np.asarray(x), np.asarray(y)), k
+    assert np.array_equal(A.mean.view(np.uint64), B.mean.view(np.uint64))
+
+
+def test_launch_choices_do_not_change_results(pm4g, ctx):
+    """Every launch choice of the batch (cases per warp chunk, items per SM,
+    pipeline groups into caller-owned buffers) gives the same results, bit
+    for bit; the default choice is checked against the oracle."""
+    L = synth.generate(synth.drilldown_log(8000))
+    log = _load(pm4g, ctx, L)
+    try:
+        specs = _random_specs(L, np.random.default_rng(17), 80)
+        spec = pm4g.BatchSpec([s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs],
+                              [s[3] for s in specs])
+        ref = pm4g.pm4g_batch_dfg(log, spec=spec, var_top_k=5)
+        _check_batch(ref, L, specs, top_k=5)
+        for chunk, items, stages in ((8, 2, 1), (32, 8, 2), (16, 1, 3), (8, 32, 16), (32, 4, 4)):
+            for knob, v in ((pm4g.OPT_BATCH_CHUNK, chunk), (pm4g.OPT_BATCH_ITEMS_PER_SM, items),
+                            (pm4g.OPT_BATCH_STAGES, stages)):
+                pm4g.pm4g_ctx_set_option(ctx, knob, v)
+            _same_batch(pm4g.pm4g_batch_dfg(log, spec=spec, var_top_k=5), ref)
+            buf = pm4g.BatchBuffers(len(specs), L.n_activities, 0)  # caller-owned: the pipelined path
+            _same_batch(pm4g.pm4g_batch_dfg(log, spec=spec, out=buf, var_top_k=5), ref)
+        for knob in (pm4g.OPT_BATCH_CHUNK, pm4g.OPT_BATCH_ITEMS_PER_SM, pm4g.OPT_BATCH_STAGES):
+            with pytest.raises(pm4g.Pm4gError):
+                pm4g.pm4g_ctx_set_option(ctx, knob, 7 if knob == pm4g.OPT_BATCH_CHUNK else 99)
+            pm4g.pm4g_ctx_set_option(ctx, knob, 0)
+    finally:
+        pm4g.pm4g_log_free(log)
+
+
+def test_autotuner_applies_a_choice_that_keeps_results(pm4g, ctx, tmp_path):
+    from paper_2204_04898_b300 import autotune
+    L = synth.generate(synth.drilldown_log(8000))
+    log = _load(pm4g, ctx, L)
+    try:
+        specs = _random_specs(L, np.random.default_rng(19), 70)
+        spec = pm4g.BatchSpec([s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs],
+                              [s[3] for s in specs])
+        ref = pm4g.pm4g_batch_dfg(log, spec=spec, var_top_k=3)
+        buf = pm4g.BatchBuffers(len(specs), L.n_activities, 0)
+        tuner = autotune.Tuner(cache_path=str(tmp_path / "tune.json"))
+        choice = tuner.tune_batch(ctx, log, spec, var_top_k=3, out=buf, reps=1)
+        assert all(choice[k] in autotune.SPACE[k] for k in autotune.SPACE)
+        _same_batch(pm4g.pm4g_batch_dfg(log, spec=spec, out=buf, var_top_k=3), ref)
+        assert autotune.Tuner(cache_path=str(tmp_path / "tune.json")).cache  # persisted
+        autotune.Tuner.apply(ctx, {})
+    finally:
+        pm4g.pm4g_log_free(log)
