@@ -441,6 +441,47 @@ def run_drilldown(args):
 SERVE_METRIC = "served events/s (filter+DFG views and uploads) under a Poisson request mix; p50/p99 request ms"
 
 
+def small_log_latency(pm4g, device: int, n_cases: int = 500, reps: int = 50) -> dict:
+    """Latency of the DFG, performance DFG and start/end counts of a small log
+    (workload-3 law, about 10k events, host columns) through the regular calls,
+    the allocation-free call, and the allocation-free call captured once in a
+    CUDA graph and replayed (median ms over `reps` calls, results on the device
+    for the last two, copied to the host for the first)."""
+    import torch
+    L = synth.generate(synth.very_large_log(n_cases).scaled(n_cases, "small_upload"), pinned=True)
+    A = L.n_activities
+    ctx = pm4g.pm4g_ctx_create(device)
+    dev = [torch.from_numpy(x).cuda(device) for x in (L.case_id, L.activity, L.ts_ns)]
+    g = pm4g.NoallocGraph(A, device)
+
+    def regular():
+        log = pm4g.pm4g_load_log(ctx, L.case_id, L.activity, L.ts_ns, n_activities=A)
+        try:
+            pm4g.pm4g_perf_dfg(log)
+            pm4g.pm4g_start_end(log, A)
+        finally:
+            pm4g.pm4g_log_free(log)
+
+    def noalloc():
+        pm4g.pm4g_dfg_noalloc(*dev, n_activities=A)
+        torch.cuda.synchronize(device)
+
+    def graph():
+        g.run(L.case_id, L.activity, L.ts_ns)
+
+    out = {"events": int(L.n_events), "n_activities": A}
+    for name, fn in (("regular_ms", regular), ("noalloc_ms", noalloc), ("graph_replay_ms", graph)):
+        fn()
+        ts = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            fn()
+            ts.append(1e3 * (time.perf_counter() - t))
+        out[name] = round(float(np.median(ts)), 3)
+    pm4g.pm4g_ctx_destroy(ctx)
+    return out
+
+
 def run_serve(args):
     """Serving: a resident serving_log, Poisson arrivals of 70 % filter+DFG,
     20 % variants top-10, 10 % uploads of LogUniform(10k, 50M)-event logs of
@@ -534,6 +575,7 @@ def run_serve(args):
                    "load_ms": round(load_ms, 1), "generate_s": round(t_gen, 1),
                    "l2": "resident log larger than L2; no flush"},
         "rates": per_rate,
+        "small_log": small_log_latency(pm4g, local),
         "p50_ms": top["all"].get("p50_ms"), "p99_ms": top["all"].get("p99_ms"),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

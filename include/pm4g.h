@@ -371,6 +371,24 @@ int pm4g_dfg_noalloc(const int32_t *case_id, const int32_t *activity, const int6
                      uint64_t *sum_lo, uint64_t *sum_hi, uint64_t *min, uint64_t *max,
                      uint64_t *start, uint64_t *end);
 
+/* The capturable form of pm4g_dfg_noalloc: no host synchronisation, no
+ * allocation and launch shapes that do not depend on the log, so a CUDA graph
+ * captured around one call replays for any log of up to 262,144 events copied
+ * into the same input arrays. The event count is read from device memory
+ * (*n_events_dev); everything is enqueued on cuda_stream and the call returns
+ * at once. Input errors come back in *status_dev (device memory, written last):
+ * bit 0 an activity outside [0, n_activities), bit 1 a case of more than 512
+ * events, bit 2 case ids spanning more than 262,144 values, bit 3 an event
+ * count outside [0, 262,144]; with bit 0, 2 or 3 set the outputs hold only
+ * their initial values (zero; minima all ones). Host-side argument errors
+ * return EINVAL at once. The scratch array and the limits are those of
+ * pm4g_dfg_noalloc, and so is the rule on overlapping calls; make one call
+ * (of either form) on the device before a stream capture begins. */
+int pm4g_dfg_noalloc_async(const int32_t *case_id, const int32_t *activity, const int64_t *ts_ns,
+                           const int64_t *n_events_dev, int32_t n_activities, void *cuda_stream, uint64_t *count,
+                           uint64_t *sum_lo, uint64_t *sum_hi, uint64_t *min, uint64_t *max, uint64_t *start,
+                           uint64_t *end, uint32_t *status_dev);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *pm4g_last_error(void);
 

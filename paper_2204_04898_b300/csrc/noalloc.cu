@@ -44,6 +44,7 @@ struct NaArgs {
   const int32_t *activity;
   const int64_t *ts;
   int64_t n;
+  const int64_t *n_dev;  // the capturable form: the event count in device memory (else NULL)
   uint32_t n_act;
   unsigned char *scratch;
   unsigned long long *count, *sum_lo, *sum_hi, *mn, *mx, *start, *end;
@@ -51,6 +52,36 @@ struct NaArgs {
 
 __device__ __forceinline__ int32_t *na_minmax(const NaArgs &a) { return (int32_t *)(a.scratch + kMiscOff); }
 __device__ __forceinline__ uint32_t *na_status(const NaArgs &a) { return (uint32_t *)(a.scratch + kMiscOff + 8); }
+
+// Status bits of a call
+constexpr uint32_t kNaBadActivity = 1, kNaLongCase = 2, kNaWideSpan = 4, kNaBadCount = 8;
+
+// The events of the call: the host's count, or in the capturable form the
+// device's (0 when it is out of range; the status then says so).
+__device__ __forceinline__ int64_t na_n(const NaArgs &a) {
+  if (!a.n_dev) return a.n;
+  const int64_t n = *a.n_dev;
+  return (n < 0 || n > kNoAllocMaxEvents) ? 0 : n;
+}
+
+// In the capturable form the host does not read the case-id range: every
+// kernel after the range check takes it from the scratch array, and does no
+// work once the status holds an input error (so no index leaves its array).
+constexpr uint32_t kNaFromDevice = 0xFFFFFFFFu;
+__device__ __forceinline__ bool na_span(const NaArgs &a, uint32_t R_in, int32_t min_in, uint32_t &R,
+                                        int32_t &min_case) {
+  if (R_in != kNaFromDevice) {
+    R = R_in;
+    min_case = min_in;
+    return true;
+  }
+  if (*(volatile uint32_t *)na_status(a) & (kNaBadActivity | kNaWideSpan | kNaBadCount)) return false;
+  const int32_t mn = na_minmax(a)[0], mx = na_minmax(a)[1];
+  if (na_n(a) == 0 || mx < mn) return false;
+  R = (uint32_t)((int64_t)mx - (int64_t)mn + 1);
+  min_case = mn;
+  return true;
+}
 
 __global__ void k_na_init(NaArgs a) {
   const int64_t cells = (int64_t)a.n_act * a.n_act;
@@ -68,7 +99,7 @@ __global__ void k_na_init(NaArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     na_minmax(a)[0] = INT_MAX;
     na_minmax(a)[1] = INT_MIN;
-    *na_status(a) = 0;
+    *na_status(a) = (a.n_dev && (*a.n_dev < 0 || *a.n_dev > kNoAllocMaxEvents)) ? kNaBadCount : 0u;
   }
 }
 
@@ -76,7 +107,8 @@ __global__ void k_na_init(NaArgs a) {
 __global__ void k_na_minmax(NaArgs a) {
   int mn = INT_MAX, mx = INT_MIN;
   bool bad = false;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t n = na_n(a);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     mn = min(mn, a.case_id[i]);
     mx = max(mx, a.case_id[i]);
     bad |= (uint32_t)a.activity[i] >= a.n_act;
@@ -94,20 +126,37 @@ __global__ void k_na_minmax(NaArgs a) {
   }
 }
 
-__global__ void k_na_zero(NaArgs a, uint32_t R) {
+// The range check's verdict in the capturable form (one thread; the kernels
+// after it read the status it leaves).
+__global__ void k_na_span_check(NaArgs a) {
+  const int32_t mn = na_minmax(a)[0], mx = na_minmax(a)[1];
+  if (na_n(a) > 0 && mx >= mn && (int64_t)mx - (int64_t)mn + 1 > kNoAllocMaxSlots) atomicOr(na_status(a), kNaWideSpan);
+}
+
+__global__ void k_na_zero(NaArgs a, uint32_t R_in) {
+  uint32_t R;
+  int32_t min_case;
+  if (!na_span(a, R_in, 0, R, min_case)) return;
   uint32_t *cnt = (uint32_t *)(a.scratch + kCntOff);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x) cnt[i] = 0;
 }
 
-__global__ void k_na_count(NaArgs a, int32_t min_case) {
+__global__ void k_na_count(NaArgs a, uint32_t R_in, int32_t min_in) {
+  uint32_t R;
+  int32_t min_case;
+  if (!na_span(a, R_in, min_in, R, min_case)) return;
   uint32_t *cnt = (uint32_t *)(a.scratch + kCntOff);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+  const int64_t n = na_n(a);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     atomicAdd(&cnt[(uint32_t)a.case_id[i] - (uint32_t)min_case], 1u);
 }
 
 // Exclusive scan of the case counts into the placement cursors (one CTA).
-__global__ void __launch_bounds__(1024) k_na_scan(NaArgs a, uint32_t R) {
+__global__ void __launch_bounds__(1024) k_na_scan(NaArgs a, uint32_t R_in) {
   __shared__ uint32_t s_warp[32];
+  uint32_t R;
+  int32_t min_case;
+  if (!na_span(a, R_in, 0, R, min_case)) return;
   const uint32_t *cnt = (const uint32_t *)(a.scratch + kCntOff);
   uint32_t *cur = (uint32_t *)(a.scratch + kCurOff);
   uint32_t carry = 0;
@@ -121,10 +170,14 @@ __global__ void __launch_bounds__(1024) k_na_scan(NaArgs a, uint32_t R) {
   }
 }
 
-__global__ void k_na_place(NaArgs a, int32_t min_case) {
+__global__ void k_na_place(NaArgs a, uint32_t R_in, int32_t min_in) {
+  uint32_t R;
+  int32_t min_case;
+  if (!na_span(a, R_in, min_in, R, min_case)) return;
   uint4 *rec = (uint4 *)(a.scratch + kRecOff);
   uint32_t *cur = (uint32_t *)(a.scratch + kCurOff);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t n = na_n(a);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t pos = atomicAdd(&cur[(uint32_t)a.case_id[i] - (uint32_t)min_case], 1u);
     const uint64_t t = (uint64_t)a.ts[i];
     rec[pos] = make_uint4((uint32_t)a.activity[i], (uint32_t)i, (uint32_t)t, (uint32_t)(t >> 32));
@@ -177,7 +230,10 @@ __device__ __forceinline__ void na_case(const NaArgs &a, const uint4 *rec, uint3
   }
 }
 
-__global__ void k_na_cases(NaArgs a, uint32_t R) {
+__global__ void k_na_cases(NaArgs a, uint32_t R_in) {
+  uint32_t R;
+  int32_t min_case;
+  if (!na_span(a, R_in, 0, R, min_case)) return;
   const uint4 *rec = (const uint4 *)(a.scratch + kRecOff);
   const uint32_t *cnt = (const uint32_t *)(a.scratch + kCntOff);
   const uint32_t *cur = (const uint32_t *)(a.scratch + kCurOff);  // now the end of every case
@@ -192,9 +248,11 @@ __global__ void k_na_cases(NaArgs a, uint32_t R) {
     else if (L <= 128) na_case<4>(a, rec, s0, L);
     else if (L <= 256) na_case<8>(a, rec, s0, L);
     else if (L <= (uint32_t)kNoAllocMaxCase) na_case<16>(a, rec, s0, L);
-    else if (lane_id() == 0) atomicOr(na_status(a), 2u);
+    else if (lane_id() == 0) atomicOr(na_status(a), kNaLongCase);
   }
 }
+
+__global__ void k_na_status_out(NaArgs a, uint32_t *status_out) { *status_out = *na_status(a); }
 
 std::mutex g_na_mu;
 void *g_na_addr[256] = {};
@@ -258,7 +316,7 @@ int pm4g_dfg_noalloc(const int32_t *case_id, const int32_t *activity, const int6
   const int st = na_scratch(device, &scratch);
   if (st != PM4G_OK) return st;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  NaArgs a{case_id, activity, ts_ns, n_events, (uint32_t)n_activities, scratch,
+  NaArgs a{case_id, activity, ts_ns, n_events, nullptr, (uint32_t)n_activities, scratch,
            (unsigned long long *)count, (unsigned long long *)sum_lo, (unsigned long long *)sum_hi,
            (unsigned long long *)min, (unsigned long long *)max, (unsigned long long *)start,
            (unsigned long long *)end};
@@ -287,9 +345,9 @@ int pm4g_dfg_noalloc(const int32_t *case_id, const int32_t *activity, const int6
   }
   const uint32_t r = (uint32_t)R;
   k_na_zero<<<(r + 255) / 256, 256, 0, s>>>(a, r);
-  k_na_count<<<g, 256, 0, s>>>(a, h[0]);
+  k_na_count<<<g, 256, 0, s>>>(a, r, h[0]);
   k_na_scan<<<1, 1024, 0, s>>>(a, r);
-  k_na_place<<<g, 256, 0, s>>>(a, h[0]);
+  k_na_place<<<g, 256, 0, s>>>(a, r, h[0]);
   k_na_cases<<<(unsigned)std::min<int64_t>((R * 32 + 255) / 256, 4096), 256, 0, s>>>(a, r);
   NA_CK(cudaGetLastError());
   uint32_t status = 0;
@@ -299,5 +357,46 @@ int pm4g_dfg_noalloc(const int32_t *case_id, const int32_t *activity, const int6
     set_error("pm4g_dfg_noalloc: a case has more than %d events", kNoAllocMaxCase);
     return PM4G_EINVAL;
   }
+  return PM4G_OK;
+}
+
+int pm4g_dfg_noalloc_async(const int32_t *case_id, const int32_t *activity, const int64_t *ts_ns,
+                           const int64_t *n_events_dev, int32_t n_activities, void *cuda_stream, uint64_t *count,
+                           uint64_t *sum_lo, uint64_t *sum_hi, uint64_t *min, uint64_t *max, uint64_t *start,
+                           uint64_t *end, uint32_t *status_dev) {
+  pm4g::ApiRange nvtx_range("pm4g_dfg_noalloc_async");
+  if (n_activities < 1 || n_activities > 2048) {
+    set_error("pm4g_dfg_noalloc_async: n_activities %d outside [1, 2048]", n_activities);
+    return PM4G_EINVAL;
+  }
+  if (!case_id || !activity || !ts_ns || !n_events_dev || !count || !sum_lo || !sum_hi || !min || !max || !start ||
+      !end || !status_dev) {
+    set_error("pm4g_dfg_noalloc_async: NULL pointer");
+    return PM4G_EINVAL;
+  }
+  int device = 0;
+  NA_CK(cudaGetDevice(&device));
+  unsigned char *scratch = nullptr;
+  const int st = na_scratch(device, &scratch);
+  if (st != PM4G_OK) return st;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  NaArgs a{case_id, activity, ts_ns, 0, n_events_dev, (uint32_t)n_activities, scratch,
+           (unsigned long long *)count, (unsigned long long *)sum_lo, (unsigned long long *)sum_hi,
+           (unsigned long long *)min, (unsigned long long *)max, (unsigned long long *)start,
+           (unsigned long long *)end};
+  // Fixed launch shapes, sized for the largest call: the same launches serve
+  // every event count, so a captured graph replays for any log that fits.
+  const int64_t cells = (int64_t)n_activities * n_activities;
+  const unsigned g = (unsigned)(kNoAllocMaxEvents / 256);
+  k_na_init<<<(unsigned)std::min<int64_t>((cells + 255) / 256 + 1, 4096), 256, 0, s>>>(a);
+  k_na_minmax<<<g, 256, 0, s>>>(a);
+  k_na_span_check<<<1, 1, 0, s>>>(a);
+  k_na_zero<<<(unsigned)(kNoAllocMaxSlots / 256), 256, 0, s>>>(a, kNaFromDevice);
+  k_na_count<<<g, 256, 0, s>>>(a, kNaFromDevice, 0);
+  k_na_scan<<<1, 1024, 0, s>>>(a, kNaFromDevice);
+  k_na_place<<<g, 256, 0, s>>>(a, kNaFromDevice, 0);
+  k_na_cases<<<4096, 256, 0, s>>>(a, kNaFromDevice);
+  k_na_status_out<<<1, 1, 0, s>>>(a, status_dev);
+  NA_CK(cudaGetLastError());
   return PM4G_OK;
 }

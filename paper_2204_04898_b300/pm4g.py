@@ -111,6 +111,7 @@ lib.pm4g_batch_dfg_into.argtypes = [_P, ctypes.POINTER(_BatchSpec), ctypes.POINT
 lib.pm4g_last_error.restype = ctypes.c_char_p
 lib.pm4g_last_error.argtypes = []
 lib.pm4g_dfg_noalloc.argtypes = [_P, _P, _P, _i64, _i32, _P] + [_P] * 7
+lib.pm4g_dfg_noalloc_async.argtypes = [_P, _P, _P, _P, _i32, _P] + [_P] * 8
 
 
 class Pm4gError(RuntimeError):
@@ -583,3 +584,69 @@ def pm4g_dfg_noalloc(case_id, activity, ts_ns, n_activities: int, stream: int | 
                                                               "end"))),
            "pm4g_dfg_noalloc")
     return out
+
+
+NOALLOC_MAX_EVENTS = 1 << 18
+
+
+def pm4g_dfg_noalloc_async(case_id, activity, ts_ns, n_events_dev, n_activities: int, out: dict, status,
+                           stream: int | None = None) -> None:
+    """The capturable allocation-free DFG: enqueues the summary of the first
+    *n_events_dev events of the CUDA tensors case_id/activity/ts_ns on
+    `stream` into the caller's CUDA int64 tensors out[count, sum_lo, sum_hi,
+    min, max, start, end] and the int32 CUDA tensor `status`; returns at once
+    (no synchronisation, so it can be captured in a CUDA graph)."""
+    _check(lib.pm4g_dfg_noalloc_async(case_id.data_ptr(), activity.data_ptr(), ts_ns.data_ptr(),
+                                      n_events_dev.data_ptr(), int(n_activities), stream,
+                                      *(out[k].data_ptr() for k in ("count", "sum_lo", "sum_hi", "min", "max",
+                                                                    "start", "end")),
+                                      status.data_ptr()), "pm4g_dfg_noalloc_async")
+
+
+class NoallocGraph:
+    """pm4g_dfg_noalloc_async captured once in a CUDA graph over static device
+    buffers of NOALLOC_MAX_EVENTS events: run(case_id, activity, ts_ns) copies a
+    log (host arrays or CUDA tensors, at most that many events) into the
+    buffers, replays the graph and returns the dense outputs (count, sum_lo,
+    sum_hi, min, max over n_activities^2 cells; start, end) as CUDA int64
+    tensors owned by this object (valid until the next run) and the status
+    word (see pm4g_dfg_noalloc_async). One replay is the whole summary: its
+    launches go to the GPU as one graph."""
+
+    def __init__(self, n_activities: int, device: int = 0):
+        import torch
+        self.A = A = int(n_activities)
+        dev = torch.device("cuda", device)
+        m = NOALLOC_MAX_EVENTS
+        self.case_id = torch.zeros(m, dtype=torch.int32, device=dev)
+        self.activity = torch.zeros(m, dtype=torch.int32, device=dev)
+        self.ts_ns = torch.zeros(m, dtype=torch.int64, device=dev)
+        self.n = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.out = {k: torch.empty(A * A, dtype=torch.int64, device=dev) for k in ("count", "sum_lo", "sum_hi", "min",
+                                                                                   "max")}
+        self.out["start"] = torch.empty(A, dtype=torch.int64, device=dev)
+        self.out["end"] = torch.empty(A, dtype=torch.int64, device=dev)
+        self.stream = torch.cuda.Stream(device=dev)
+        def call(stream):
+            pm4g_dfg_noalloc_async(self.case_id, self.activity, self.ts_ns, self.n, A, self.out, self.status, stream)
+
+        with torch.cuda.stream(self.stream):
+            call(self.stream.cuda_stream)  # the first call (outside capture) looks up the scratch array
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            call(self.stream.cuda_stream)
+
+    def run(self, case_id, activity, ts_ns) -> tuple[dict, int]:
+        import torch
+        n = len(case_id)
+        if n > NOALLOC_MAX_EVENTS or len(activity) != n or len(ts_ns) != n:
+            raise ValueError("a log of at most NOALLOC_MAX_EVENTS events, columns of equal length")
+        with torch.cuda.stream(self.stream):
+            for dst, src in ((self.case_id, case_id), (self.activity, activity), (self.ts_ns, ts_ns)):
+                dst[:n].copy_(torch.as_tensor(src), non_blocking=True)
+            self.n.fill_(n)
+            self.graph.replay()
+        self.stream.synchronize()
+        return self.out, int(self.status.item())
