@@ -415,11 +415,11 @@ __global__ void k_bv_flags(const uint32_t *__restrict__ rlen, uint32_t n, uint32
 // sub-log's cases in ascending case order
 __global__ void k_bv_keys(const uint32_t *__restrict__ rlen, const uint32_t *__restrict__ rq,
                           const uint32_t *__restrict__ rslot, const uint32_t *__restrict__ pos, uint32_t n,
-                          uint64_t *keys, uint32_t *idx) {
+                          int sbits, uint64_t *keys, uint32_t *idx) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (!rlen[i]) continue;
     const uint32_t p = pos[i];
-    keys[p] = ((uint64_t)rq[i] << 32) | rslot[i];
+    keys[p] = ((uint64_t)rq[i] << sbits) | rslot[i];  // (view, slot), slot < 2^sbits
     idx[p] = i;
   }
 }
@@ -1114,14 +1114,15 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
         break;
       }
       const unsigned gK = grid_for((int64_t)NK, 256, 65535);
+      const int sbits = std::max(1, bits_for(L->R - 1));  // bits of a case slot
       if (NK) {
         {
           KTime t(c, "variants");
-          k_bv_keys<<<gR, 256, 0, s>>>(rlen, rq, rslot, kp, NR, k64, idx);
+          k_bv_keys<<<gR, 256, 0, s>>>(rlen, rq, rslot, kp, NR, sbits, k64, idx);
           if ((st = check_launch(c, "k_bv_keys")) != PM4G_OK) break;
         }
         const int qb = bits_for((uint64_t)std::max(Qg - 1, 0));
-        if ((st = radix_sort_u64(c, k64, idx, k64b, idxb, NK, 0, 32 + qb)) != PM4G_OK) break;
+        if ((st = radix_sort_u64(c, k64, idx, k64b, idxb, NK, 0, sbits + qb)) != PM4G_OK) break;
         KTime t(c, "variants");
         k_bv_gather<<<gK, 256, 0, s>>>(idx, NK, rq, rslot, rpos, rlen, rhash, sq, sslot, spos, slen, shash);
         if ((st = check_launch(c, "k_bv_gather")) != PM4G_OK) break;
