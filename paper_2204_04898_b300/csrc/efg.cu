@@ -14,7 +14,7 @@
 // sums with 64-bit atomics (carries propagate to the next word at once). The
 // frequent activity pairs would serialise those atomics at one L2 slice each,
 // so the blocks share K copies of the table (block b uses copy b mod K; up to
-// 64 copies within a memory budget), folded exactly into the first one
+// one per block within a memory budget), folded exactly into the first one
 // afterwards. A flag/scan/compaction lists the pairs with their mean and
 // deviation.
 
@@ -267,14 +267,18 @@ int pm4g_efg(pm4g_log *L, pm4g_efg_t *out) {
     PM4G_TRY(alloc_buf(c, L->ts_s, (size_t)L->n));
     PM4G_TRY(run_export(L, nullptr, nullptr, L->ts_s.p, nullptr));
   }
-  // copies of the table: at most 64, within min(1 GB, an eighth of free
-  // memory); more copies spread the frequent pairs' atomics further (on the
-  // 206.6M-event log: 5 copies 437 ms, 16 copies 316 ms, 64 copies 200 ms)
+  // copies of the table: at most one per block of the pair kernel, within
+  // min(8 GB, an eighth of free memory); more copies spread the frequent
+  // pairs' atomics further (on the 206.6M-event log, 12 MB a copy: 5 copies
+  // 437 ms, 16 copies 316 ms, 64 copies 200 ms, 256 copies 154 ms, 699
+  // copies 142 ms)
+  const unsigned blocks = 8u * (unsigned)c->num_sms;
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
   const uint64_t table_bytes = 48 * cells;
-  const uint64_t budget = std::min<uint64_t>(1ull << 30, fr / 8);
-  const uint32_t K = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, budget / std::max<uint64_t>(table_bytes, 1)));
+  const uint64_t budget = std::min<uint64_t>(8ull << 30, fr / 8);
+  const uint32_t K = (uint32_t)std::max<uint64_t>(
+      1, std::min<uint64_t>(blocks, budget / std::max<uint64_t>(table_bytes, 1)));
   Scratch S(c);
   unsigned long long *tab = S.get<unsigned long long>(6 * cells * K);
   unsigned long long *work = S.get<unsigned long long>(1);
@@ -291,7 +295,7 @@ int pm4g_efg(pm4g_log *L, pm4g_efg_t *out) {
   EfTable t{tab, tab + cells * K, tab + 2 * cells * K, tab + 3 * cells * K, tab + 4 * cells * K, tab + 5 * cells * K};
   {
     KTime kt(c, "efg");
-    k_efg_pairs<<<8 * c->num_sms, 256, 0, s>>>(L->len.p, L->off.p, L->R, L->act_s.p, L->ts_s.p, A, t, cs, K,
+    k_efg_pairs<<<blocks, 256, 0, s>>>(L->len.p, L->off.p, L->R, L->act_s.p, L->ts_s.p, A, t, cs, K,
                                                work);
     PM4G_TRY(check_launch(c, "k_efg_pairs"));
     if (K > 1) {
