@@ -277,8 +277,11 @@ int pm4g_efg(pm4g_log *L, pm4g_efg_t *out) {
   cudaMemGetInfo(&fr, &tot);
   const uint64_t table_bytes = 48 * cells;
   const uint64_t budget = std::min<uint64_t>(8ull << 30, fr / 8);
+  // (and one copy per 2^17 events, so a small log does not clear and fold
+  // gigabytes of copies)
+  const uint64_t by_work = std::max<uint64_t>(1, (uint64_t)L->n >> 17);
   const uint32_t K = (uint32_t)std::max<uint64_t>(
-      1, std::min<uint64_t>(blocks, budget / std::max<uint64_t>(table_bytes, 1)));
+      1, std::min<uint64_t>(std::min<uint64_t>(blocks, by_work), budget / std::max<uint64_t>(table_bytes, 1)));
   Scratch S(c);
   unsigned long long *tab = S.get<unsigned long long>(6 * cells * K);
   unsigned long long *work = S.get<unsigned long long>(1);
