@@ -1733,7 +1733,8 @@ int pm4g_filter_paths(pm4g_log *L, const int32_t *src, const int32_t *dst, int32
   const uint64_t n = L->n, R = L->R;
   Scratch S(c);
   int64_t *row_s = S.get<int64_t>(n);
-  uint8_t *start = S.get<uint8_t>(n), *keep = S.get<uint8_t>(n);
+  uint8_t *start = S.get<uint8_t>(n);
+  uint32_t *keep = S.get<uint32_t>((n + 31) / 32);
   uint64_t *dkeys = S.get<uint64_t>(keys.size());
   if (!row_s || !start || !keep || (!keys.empty() && !dkeys)) {
     set_error("pm4g_filter_paths: out of device memory");
@@ -1744,6 +1745,7 @@ int pm4g_filter_paths(pm4g_log *L, const int32_t *src, const int32_t *dst, int32
   // the original row of every formatted position, and where cases start
   PM4G_TRY(run_export(L, nullptr, nullptr, nullptr, row_s));
   PM4G_CK(cudaMemsetAsync(start, 0, n, c->stream));
+  PM4G_CK(cudaMemsetAsync(keep, 0, (n + 31) / 32 * 4, c->stream));
   {
     KTime t(c, "filter");
     k_mark_case_starts<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(L->len.p, L->off.p, R, start);

@@ -67,7 +67,7 @@ __global__ void k_case_ok(FilterArgs a) {
 }
 
 __device__ __forceinline__ bool filter_keep(const FilterArgs &a, uint32_t b, uint4 r) {
-  if (a.row_keep) return a.row_keep[r.y] != 0;
+  if (a.row_keep) return (a.row_keep[r.y >> 5] >> (r.y & 31)) & 1u;
   const uint64_t slot = ((uint64_t)b << a.clb) + ((r.x >> a.act_bits) & ((1u << a.clb) - 1));
   if (!a.case_ok[slot]) return false;
   if (a.mode == PM4G_TW_EVENTS) {
@@ -181,7 +181,7 @@ __global__ void k_mark_case_starts(const uint32_t *len, const uint32_t *off, uin
 // event at p - 1 as its previous one; its pair key is prev * A + act.
 __global__ void k_path_keep(uint64_t n, const int32_t *act_s, const uint8_t *start, const int64_t *row_s,
                             const uint64_t *keys, int32_t n_keys, uint32_t n_act, int32_t exclude,
-                            uint8_t *row_keep) {
+                            uint32_t *row_keep) {
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
     bool m = false;
     if (!start[p]) {
@@ -194,7 +194,12 @@ __global__ void k_path_keep(uint64_t n, const int32_t *act_s, const uint8_t *sta
       }
       m = lo < n_keys && keys[lo] == key;
     }
-    row_keep[row_s[p]] = m != (exclude != 0) ? 1 : 0;
+    // one bit per original row (the array, 1/8 of a byte per row, stays in
+    // L2 for the random accesses); bits start clear and kept rows set theirs
+    if (m != (exclude != 0)) {
+      const uint64_t row = (uint64_t)row_s[p];
+      atomicOr(&row_keep[row >> 5], 1u << (row & 31));
+    }
   }
 }
 

@@ -203,7 +203,7 @@ struct FilterArgs {
   int64_t t_lo, t_hi;
   int32_t mode;
   uint8_t *case_ok;  // per slot
-  const uint8_t *row_keep;  // optional, per original row: replaces case_ok and the window
+  const uint32_t *row_keep;  // optional, one bit per original row: replaces case_ok and the window
   const uint32_t *len;      // optional, per slot: whole-case predicates count kept events from it
   uint32_t *kept;    // per bucket
   const uint32_t *new_off;
@@ -233,7 +233,7 @@ __global__ void k_case_filter(CaseFilterArgs a);
 __global__ void k_mark_case_starts(const uint32_t *len, const uint32_t *off, uint64_t n_slots, uint8_t *start);
 __global__ void k_path_keep(uint64_t n, const int32_t *act_s, const uint8_t *start, const int64_t *row_s,
                             const uint64_t *keys, int32_t n_keys, uint32_t n_act, int32_t exclude,
-                            uint8_t *row_keep);
+                            uint32_t *row_keep);
 
 // Summaries (summaries.cu)
 __global__ void k_dfg_flags(const unsigned long long *cnt, int64_t cells, uint32_t *flags);
