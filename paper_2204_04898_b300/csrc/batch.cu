@@ -788,12 +788,14 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
   cudaMemGetInfo(&fr, &tot);
   const size_t per_sub = (size_t)E * 40 + (size_t)A * 24 + 64 + (size_t)E * 8;
   const size_t rec_bytes = want_var ? 128 : 0;  // records, their sort and the variant table, per case
-  const size_t budget = std::max<size_t>(std::min<size_t>(fr / 3, (size_t)32 << 30), per_sub);
   // Into caller-owned arrays (which never move), a batch of many sub-logs
   // runs as a pipeline of about kBtStages groups: a group's result copies
-  // (copy stream) overlap the next group's kernels (context stream).
+  // (copy stream) overlap the next group's kernels (context stream). Two
+  // groups' scratch is then alive at once, so each gets half the budget.
   const int stages = c->batch_stages ? c->batch_stages : kBtStages;
   const bool pipelined = caller && Q >= 64 && stages > 1;
+  const size_t budget =
+      std::max<size_t>(std::min<size_t>(fr / (pipelined ? 6 : 3), (size_t)(pipelined ? 16 : 32) << 30), per_sub);
   const int32_t group_cap = pipelined ? (Q + stages - 1) / stages : Q;
   std::vector<std::pair<int32_t, int32_t>> groups;
   {
