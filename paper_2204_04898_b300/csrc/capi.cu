@@ -235,6 +235,7 @@ static void release_log(pm4g_log *L) {
   free_buf(c, L->rep_pos);
   free_buf(c, L->status);
   free_buf(c, L->ts_s);
+  free_buf(c, L->row_s);
   free_buf(c, L->aslots);
   free_buf(c, L->apre);
   free_buf(c, L->aoff);
@@ -1731,19 +1732,29 @@ int pm4g_filter_paths(pm4g_log *L, const int32_t *src, const int32_t *dst, int32
   if (L->n == 0 || L->nb == 0) return extract_sublog(L, FilterArgs{}, out);
   PM4G_TRY(ensure_offsets(L));
   const uint64_t n = L->n, R = L->R;
+  // the original row of every formatted position, kept on the log for later
+  // path filters (the export pass that forms it costs about as much as a
+  // filter's other kernels)
+  if (!L->row_s.p) {
+    PM4G_TRY(alloc_buf(c, L->row_s, (size_t)n));
+    const int st = run_export(L, nullptr, nullptr, nullptr, L->row_s.p);
+    if (st != PM4G_OK) {
+      free_buf(c, L->row_s);
+      return st;
+    }
+  }
+  const int64_t *row_s = L->row_s.p;
   Scratch S(c);
-  int64_t *row_s = S.get<int64_t>(n);
   uint8_t *start = S.get<uint8_t>(n);
   uint32_t *keep = S.get<uint32_t>((n + 31) / 32);
   uint64_t *dkeys = S.get<uint64_t>(keys.size());
-  if (!row_s || !start || !keep || (!keys.empty() && !dkeys)) {
+  if (!start || !keep || (!keys.empty() && !dkeys)) {
     set_error("pm4g_filter_paths: out of device memory");
     return PM4G_ENOMEM;
   }
   if (!keys.empty())
     PM4G_CK(cudaMemcpyAsync(dkeys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  // the original row of every formatted position, and where cases start
-  PM4G_TRY(run_export(L, nullptr, nullptr, nullptr, row_s));
+  // where cases start
   PM4G_CK(cudaMemsetAsync(start, 0, n, c->stream));
   PM4G_CK(cudaMemsetAsync(keep, 0, (n + 31) / 32 * 4, c->stream));
   {

@@ -290,6 +290,7 @@ struct pm4g_log {
   // drill-down index (batched drill-down; built on first use)
   bool dd_ready = false;
   pm4g::DBuf<int64_t> ts_s;       // timestamps in (case, timestamp, row) order
+  pm4g::DBuf<int64_t> row_s;      // original rows in that order (paths filter; built on first use)
   pm4g::DBuf<uint32_t> aslots;    // present case slots ordered by (attribute, slot)
   pm4g::DBuf<uint32_t> apre;      // events before each entry of aslots (C + 1)
   pm4g::DBuf<uint32_t> aoff, alen; // first formatted position and length of each entry of aslots
