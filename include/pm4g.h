@@ -223,7 +223,10 @@ int pm4g_filter(pm4g_log *log, const pm4g_filter_spec *spec, pm4g_log **out);
  *
  * pm4g_filter_paths keeps the events that have a previous event in their case
  * and whose pair (previous activity, activity) is one of the n_pairs pairs
- * (src[k], dst[k]); with exclude != 0, exactly the other events.
+ * (src[k], dst[k]); with exclude != 0, exactly the other events. The first
+ * paths filter of a log forms the original row of every formatted position
+ * and keeps it on the log (8 bytes per event) for later paths filters, until
+ * the log is freed: the log's device footprint grows by that much.
  *
  * pm4g_filter_cases keeps the cases for which every given criterion holds (a
  * negative bound or an empty set is absent): number of events in [min_events,
@@ -354,7 +357,14 @@ int pm4g_batch_dfg_into(pm4g_log *log, const pm4g_batch_spec *spec, pm4g_batch_d
  *   case_id, activity, ts_ns: device columns of n_events entries
  *     (0 <= n_events <= 262144; max case id - min case id < 262144; no case
  *     longer than 512 events; activity in [0, n_activities), n_activities <=
- *     2048). Larger inputs are rejected with PM4G_EINVAL.
+ *     2048).
+ *   Errors: an event count or alphabet outside these limits, a NULL pointer,
+ *     or case ids spanning more values return PM4G_EINVAL before any output
+ *     is written (beyond the cleared initial values); an activity outside
+ *     [0, n_activities) returns PM4G_ERANGE with the outputs cleared only.
+ *     A case of more than 512 events returns PM4G_EINVAL after the other
+ *     cases' pairs have been added: the outputs are then partly written and
+ *     undefined, and must be discarded.
  *   count, sum_lo, sum_hi, min, max: device arrays of n_activities^2 cells,
  *     cell src * n_activities + dst, written by the call (cells without a
  *     pair: count 0, min UINT64_MAX, max 0). start, end: device arrays of

@@ -502,8 +502,24 @@ int ensure_drilldown(pm4g_log *L) {
   Ctx *c = L->ctx;
   const uint32_t C = (uint32_t)L->C;
   PM4G_TRY(ensure_offsets(L));
-  PM4G_TRY(alloc_buf(c, L->ts_s, (size_t)L->n));
-  PM4G_TRY(run_export(L, nullptr, nullptr, L->ts_s.p, nullptr));
+  // timestamps in formatted order: shared with the eventually-follows graph,
+  // which may have formed them already; dropped again if forming them fails
+  if (!L->ts_s.p) {
+    PM4G_TRY(alloc_buf(c, L->ts_s, (size_t)L->n));
+    const int st = run_export(L, nullptr, nullptr, L->ts_s.p, nullptr);
+    if (st != PM4G_OK) {
+      free_buf(c, L->ts_s);
+      return st;
+    }
+  }
+  // what an earlier attempt that failed part way left behind
+  free_buf(c, L->aslots);
+  free_buf(c, L->apre);
+  free_buf(c, L->emap);
+  free_buf(c, L->e_pair);
+  free_buf(c, L->aoff);
+  free_buf(c, L->alen);
+  free_buf(c, L->eidx_s);
   // present cases in (attribute, slot) order
   PM4G_TRY(alloc_buf(c, L->aslots, C));
   PM4G_TRY(alloc_buf(c, L->apre, (size_t)C + 1));

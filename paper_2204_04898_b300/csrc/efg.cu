@@ -265,7 +265,11 @@ int pm4g_efg(pm4g_log *L, pm4g_efg_t *out) {
   PM4G_TRY(ensure_offsets(L));
   if (!L->ts_s.p) {  // timestamps in formatted order (shared with the drill-down index)
     PM4G_TRY(alloc_buf(c, L->ts_s, (size_t)L->n));
-    PM4G_TRY(run_export(L, nullptr, nullptr, L->ts_s.p, nullptr));
+    const int st = run_export(L, nullptr, nullptr, L->ts_s.p, nullptr);
+    if (st != PM4G_OK) {  // an unfilled array must not look formed to the next call
+      free_buf(c, L->ts_s);
+      return st;
+    }
   }
   // copies of the table: at most one per block of the pair kernel, within
   // min(8 GB, an eighth of free memory); more copies spread the frequent

@@ -643,6 +643,9 @@ class NoallocGraph:
         n = len(case_id)
         if n > NOALLOC_MAX_EVENTS or len(activity) != n or len(ts_ns) != n:
             raise ValueError("a log of at most NOALLOC_MAX_EVENTS events, columns of equal length")
+        if any(isinstance(x, torch.Tensor) and x.is_cuda for x in (case_id, activity, ts_ns)):
+            # device inputs may still be being written on the caller's stream
+            self.stream.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(self.stream):
             for dst, src in ((self.case_id, case_id), (self.activity, activity), (self.ts_ns, ts_ns)):
                 dst[:n].copy_(torch.as_tensor(src), non_blocking=True)
