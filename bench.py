@@ -113,6 +113,11 @@ def parse():
     p.add_argument("--seconds", type=float, default=3.0, help="serve: seconds of arrivals per rate")
     p.add_argument("--views", type=int, default=4096)
     p.add_argument("--plain-views", type=int, default=4096, help="views timed through plain calls")
+    p.add_argument("--no-drilldown", action="store_true", help="single mode: leave out the drill-down object")
+    p.add_argument("--no-serving", action="store_true", help="single mode: leave out the serving object")
+    p.add_argument("--dd-steps", type=int, default=10, help="single mode: timed drill-down batches")
+    p.add_argument("--serve-rates", default="300,1000,3000", help="single mode: serving rates (req/s)")
+    p.add_argument("--serve-seconds", type=float, default=10.0, help="single mode: seconds of arrivals per rate")
     return p.parse_args()
 
 
@@ -289,15 +294,14 @@ def run_reference_drilldown(args):
         dist.barrier()
 
 
-def run_drilldown(args):
+def drilldown_core(args, local: int, steps: int, warmup: int, plain_views: int, tune: bool = True,
+                   cpu_baseline: bool = True) -> dict:
+    """Batched drill-down on one GPU: the resident drilldown_log, its 4,096
+    views, `steps` timed pm4g_batch_dfg calls (CUDA events on the context
+    stream; inputs resident, results into reused page-locked buffers), then
+    the first `plain_views` views through plain calls."""
     import torch
     from paper_2204_04898_b300 import pm4g
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     spec = drilldown_workload(args)
     t_gen = time.perf_counter()
     L = synth.generate(spec, pinned=True)
@@ -316,6 +320,7 @@ def run_drilldown(args):
     log = pm4g.pm4g_load_log(ctx, *dev[:3], case_attr=dev[3], n_activities=A)
     torch.cuda.synchronize()
     load_ms = 1e3 * (time.perf_counter() - t)
+    del dev
     buf = pm4g.BatchBuffers(len(views), A, 0)  # page-locked result buffers, reused every step
     bspec = pm4g.BatchSpec(sets, lo, hi, modes)  # the views as flat arrays, built once
     t = time.perf_counter()
@@ -327,49 +332,45 @@ def run_drilldown(args):
     out_vars = int(B.var_off[-1])
     # launch choices (cases per warp chunk, items per SM, pipeline groups) by
     # the autotuner, timed on this batch before the timed region
-    from paper_2204_04898_b300 import autotune
-    t = time.perf_counter()
-    tuned = autotune.Tuner().tune_batch(ctx, log, bspec, var_top_k=vk, out=buf, reps=2,
-                                        device=torch.cuda.get_device_name(local))
-    tune_s = time.perf_counter() - t
-    for _ in range(max(0, args.warmup - 1)):
+    tuned, tune_s = None, 0.0
+    if tune:
+        from paper_2204_04898_b300 import autotune
+        t = time.perf_counter()
+        tuned = autotune.Tuner().tune_batch(ctx, log, bspec, var_top_k=vk, out=buf, reps=2,
+                                            device=torch.cuda.get_device_name(local))
+        tune_s = time.perf_counter() - t
+    for _ in range(max(0, warmup - 1)):
         pm4g.pm4g_batch_dfg(log, out=buf, var_top_k=vk, spec=bspec)
     # CUDA events around the batch kernel's launches only (level 2), so the
     # events add no host work to the other launches of the step
     pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 2)
     pm4g.pm4g_ctx_timing_reset(ctx)
-    launches0 = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
     torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = [0]
+
     def rewarm():
         for _ in range(3):
             pm4g.pm4g_batch_dfg(log, out=buf, var_top_k=vk, spec=bspec)
         pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
+        launches0[0] = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
 
     with ClockSampler(local, rewarm) as clk:
         torch.cuda.synchronize()
         t = time.perf_counter()
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             pm4g.pm4g_batch_dfg(log, out=buf, var_top_k=vk, spec=bspec)
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t
-    dev_ms = ev0.elapsed_time(ev1) / args.steps
-    wall_ms = 1e3 * wall / args.steps
+    dev_ms = ev0.elapsed_time(ev1) / steps
+    wall_ms = 1e3 * wall / steps
     n_b, batch_ms = pm4g.pm4g_ctx_timing(ctx, "batch_dfg")
-    launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0] - launches0
+    launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0] - launches0[0]
     pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
-    ms = dev_ms
-    if dist is not None:
-        t_ = torch.tensor([ms, wall_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
-        ms, wall_ms = float(t_[0]), float(t_[1])
-    value = sub_events * world * 1e3 / ms
-    # plain calls over the first plain-views views
-    P = min(args.plain_views, len(views))
+    # plain calls over the first plain_views views
+    P = min(plain_views, len(views))
     plain = None
     if P > 0:
         torch.cuda.synchronize()
@@ -386,10 +387,11 @@ def run_drilldown(args):
                 pm4g.pm4g_log_free(f)
         torch.cuda.synchronize()
         pt = time.perf_counter() - t
-        plain = {"value": pev / pt, "unit": UNIT, "views": P, "ms_per_view": 1e3 * pt / P,
+        plain = {"value": pev / pt, "unit": UNIT, "views": P, "sub_log_events": pev, "ms_per_view": 1e3 * pt / P,
+                 "timing": "host wall clock over the plain calls, results on the host",
                  "calls": "pm4g_filter + pm4g_perf_dfg + pm4g_start_end + pm4g_variants + pm4g_log_free per view"}
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if cpu_baseline:
         import oracle
         small = spec.scaled(max(2000, min(spec.n_cases, args.cpu_sample_cases // 4)))
         S = synth.generate(small)
@@ -404,36 +406,75 @@ def run_drilldown(args):
     spec_bytes = sum(x.size for x in sets) * 4 + len(views) * (8 + 8 + 8 + 4)
     pm4g.pm4g_log_free(log)
     pm4g.pm4g_ctx_destroy(ctx)
-    if rank != 0:
-        return
+    del buf, B
     peak, peak_kind = peaks()
-    # activity + timestamp of every sub-log event; a step's views run as a few
+    # the method's bytes: activity + timestamp of every sub-log event, read
+    # once from the resident formatted log; a step's views run as a few
     # launches (pipelined groups), so per launch is the step's bytes / launches
-    per_launch = 12.0 * sub_events * args.steps / max(1, n_b)
+    per_launch = 12.0 * sub_events * steps / max(1, n_b)
     kernel_ms = batch_ms / max(1, n_b)
     achieved = per_launch / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else 0.0
-    line = {
-        "metric": DD_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "drilldown_views", "log": spec.name, "n_events": L.n_events,
-                   "n_cases": spec.n_cases, "n_activities": A, "n_views": len(views), "mode": "EVENTS",
-                   "sub_log_events": sub_events, "out_edges": out_edges, "var_top_k": vk,
-                   "out_variants": out_vars, "batch_dfg_launches_per_step": n_b / max(1, args.steps),
-                   "autotuned": tuned, "autotune_s": round(tune_s, 2),
-                   "l2": "resident log %.1f GB of activity+timestamp, larger than L2; no flush" % (12 * L.n_events / 1e9),
-                   "load_ms": round(load_ms, 1), "first_call_ms_with_index": round(first_ms, 1),
-                   "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
-        "wall_ms_per_step": wall_ms,
-        "plain": plain,
+    value = sub_events * 1e3 / dev_ms
+    return {
+        "value": value, "ms_per_step": dev_ms, "wall_ms_per_step": wall_ms, "steps": steps, "warmup": warmup,
+        "spec": spec, "n_events": L.n_events, "n_activities": A, "n_views": len(views),
+        "sub_log_events": sub_events, "out_edges": out_edges, "out_variants": out_vars, "var_top_k": vk,
+        "launches_per_step": n_b / max(1, steps), "tuned": tuned, "tune_s": tune_s, "load_ms": load_ms,
+        "first_ms": first_ms, "t_gen": t_gen, "plain": plain,
+        "ratio_vs_plain": (value / plain["value"]) if plain else None,
         "roofline": {"bound": "hbm", "kernel": "batch_dfg", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": per_launch, "launch_ms": kernel_ms},
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
-        "e2e": {"value": sub_events * world * 1e3 / wall_ms, "unit": UNIT, "h2d_bytes_per_step": int(spec_bytes),
+                     "alg_bytes_per_launch": per_launch, "launch_ms": kernel_ms,
+                     "note": "12 B (activity + timestamp) per sub-log event; overlapping views re-read the "
+                             "resident log mostly from L2"},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "e2e": {"value": sub_events * 1e3 / wall_ms, "unit": UNIT, "h2d_bytes_per_step": int(spec_bytes),
                 "d2h_bytes_per_step": int(res_bytes)},
         "cpu_baseline": cpu,
+    }
+
+
+def run_drilldown(args):
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+    r = drilldown_core(args, local, args.steps, args.warmup, args.plain_views,
+                       cpu_baseline=rank == 0 and not args.no_cpu_baseline)
+    ms, wall_ms = r["ms_per_step"], r["wall_ms_per_step"]
+    if dist is not None:
+        t_ = torch.tensor([ms, wall_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        ms, wall_ms = float(t_[0]), float(t_[1])
+    if rank != 0:
+        return
+    spec = r["spec"]
+    line = {
+        "metric": DD_METRIC, "value": r["sub_log_events"] * world * 1e3 / ms, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "drilldown_views", "log": spec.name, "n_events": r["n_events"],
+                   "n_cases": spec.n_cases, "n_activities": r["n_activities"], "n_views": r["n_views"],
+                   "mode": "EVENTS", "sub_log_events": r["sub_log_events"], "out_edges": r["out_edges"],
+                   "var_top_k": r["var_top_k"], "out_variants": r["out_variants"],
+                   "batch_dfg_launches_per_step": r["launches_per_step"],
+                   "autotuned": r["tuned"], "autotune_s": round(r["tune_s"], 2),
+                   "l2": "resident log %.1f GB of activity+timestamp, larger than L2; no flush"
+                         % (12 * r["n_events"] / 1e9),
+                   "load_ms": round(r["load_ms"], 1), "first_call_ms_with_index": round(r["first_ms"], 1),
+                   "parallelism": f"replicas x{world}", "generate_s": round(r["t_gen"], 1)},
+        "wall_ms_per_step": wall_ms,
+        "plain": r["plain"],
+        "ratio_vs_plain": r["ratio_vs_plain"],
+        "roofline": r["roofline"],
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
+        "e2e": {**r["e2e"], "value": r["sub_log_events"] * world * 1e3 / wall_ms},
+        "cpu_baseline": r["cpu_baseline"],
     }
     print(json.dumps(line), flush=True)
 
@@ -482,15 +523,14 @@ def small_log_latency(pm4g, device: int, n_cases: int = 500, reps: int = 50) -> 
     return out
 
 
-def run_serve(args):
-    """Serving: a resident serving_log, Poisson arrivals of 70 % filter+DFG,
-    20 % variants top-10, 10 % uploads of LogUniform(10k, 50M)-event logs of
-    the workload-3 law, at each rate; latency from arrival to result on host."""
+def serve_core(args, local: int, rates: list, seconds: float, small_log: bool = True) -> dict:
+    """Serving on one GPU: a resident serving_log and, at each rate, Poisson
+    arrivals for `seconds` of 70 % filter+DFG, 20 % variants top-10, 10 %
+    uploads of LogUniform(10k, 50M)-event logs of the workload-3 law; latency
+    from arrival to result on the host."""
     import torch
     from paper_2204_04898_b300 import pm4g
     from paper_2204_04898_b300.serve import GpuEngine, Request, Server, latency_summary
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
     spec = synth.serving_log(args.cases) if args.cases else synth.serving_log()
     t_gen = time.perf_counter()
     L = synth.generate(spec, pinned=True)
@@ -519,9 +559,9 @@ def run_serve(args):
     srv = Server(eng, upload_slots=2)
     per_rate = []
     with ClockSampler(local) as clk:
-        for rate in [float(x) for x in args.rates.split(",") if x]:
-            n = max(1, int(rng.poisson(rate * args.seconds)))
-            arrivals = np.sort(rng.uniform(0, args.seconds, n))
+        for rate in rates:
+            n = max(1, int(rng.poisson(rate * seconds)))
+            arrivals = np.sort(rng.uniform(0, seconds, n))
             kinds = rng.choice(3, n, p=[0.7, 0.2, 0.1])
             reqs = []
             for kd in kinds:
@@ -564,21 +604,34 @@ def run_serve(args):
     eng.close()
     pm4g.pm4g_log_free(log)
     pm4g.pm4g_ctx_destroy(ctx)
+    return {"spec": spec, "n_events": L.n_events, "n_activities": A, "per_rate": per_rate,
+            "upload_events": [int(u.n_events) for u in pool], "seconds_per_rate": seconds, "load_ms": load_ms,
+            "t_gen": t_gen, "gpu_launches": int(launches), "clocks": clk.summary(),
+            "small_log": small_log_latency(pm4g, local) if small_log else None}
+
+
+def run_serve(args):
+    import torch
+    _, _, local = dist_info()
+    torch.cuda.set_device(local)
+    r = serve_core(args, local, [float(x) for x in args.rates.split(",") if x], args.seconds)
+    per_rate = r["per_rate"]
+    spec = r["spec"]
     top = per_rate[-1]
     line = {
         "metric": SERVE_METRIC, "value": top["events_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(per_rate),
         "warmup": 1, "ms_per_step": 1e3 * top["wall_s"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "serving_mix", "log": spec.name, "n_events": L.n_events, "n_cases": spec.n_cases,
-                   "n_activities": A, "mix": "70% filter+DFG (EVENTS), 20% variants top-10, 10% upload",
-                   "upload_events": [int(u.n_events) for u in pool], "seconds_per_rate": args.seconds,
-                   "load_ms": round(load_ms, 1), "generate_s": round(t_gen, 1),
+        "config": {"workload": "serving_mix", "log": spec.name, "n_events": r["n_events"], "n_cases": spec.n_cases,
+                   "n_activities": r["n_activities"], "mix": "70% filter+DFG (EVENTS), 20% variants top-10, 10% upload",
+                   "upload_events": r["upload_events"], "seconds_per_rate": r["seconds_per_rate"],
+                   "load_ms": round(r["load_ms"], 1), "generate_s": round(r["t_gen"], 1),
                    "l2": "resident log larger than L2; no flush"},
         "rates": per_rate,
-        "small_log": small_log_latency(pm4g, local),
+        "small_log": r["small_log"],
         "p50_ms": top["all"].get("p50_ms"), "p99_ms": top["all"].get("p99_ms"),
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
         # every latency above is end to end (arrival to result on the host)
         "e2e": {"value": top["events_per_s"], "unit": UNIT, "h2d_bytes_per_step": int(top["upload_h2d_bytes"]),
                 "d2h_bytes_per_step": int(top["d2h_bytes"])},
@@ -694,9 +747,10 @@ def run_filters(args):
     kt = {k: v for k, v in kt.items() if v[0] > 0}
     dom = max(kt, key=lambda k: kt[k][1])
     peak, peak_kind = peaks()
-    # byte model of a filter: read every event once (16 B) and write the kept
-    # ones (16 B each); charged to the filter kernels of the step
-    alg = sum(16.0 * N + 16.0 * kept[name] for name, _, _ in mix)
+    # the method's bytes of a filter: read every event's activity and
+    # timestamp once (12 B) and write the kept ones (12 B each); the sub-log's
+    # own formatting (its segment pass) is not charged to the filter kernels
+    alg = sum(12.0 * N + 12.0 * kept[name] for name, _, _ in mix)
     filt_ms = kt.get("filter", (0, 0.0))[1] / args.steps
     achieved = alg / (filt_ms * 1e-3) / 1e9 if filt_ms > 0 else 0.0
     cpu = None
@@ -882,9 +936,12 @@ def run_efg(args):
         return
     value = pairs * world * 1e3 / ms
     peak, peak_kind = peaks()
-    # byte model: every pair reads its two events' activity and timestamp
-    # (24 B) and updates one cell (six 8-byte words, read and written)
-    alg = 24.0 * pairs + 96.0 * pairs
+    # the method's bytes: the resident formatted log's activity and timestamp
+    # (12 B/event), read once; every pair then lives in registers and is added
+    # to an L2-resident A x A table by 64-bit atomics (implementation traffic,
+    # reported beside it and never held against the HBM peak)
+    alg = 12.0 * N
+    atomic_bytes = 96.0 * pairs
     kern_ms = efg_ms / args.steps
     line = {
         "metric": EFG_METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -894,10 +951,13 @@ def run_efg(args):
                    "activity_pairs": n_cells, "events_per_s": N * world * 1e3 / ms,
                    "l2": "resident log larger than L2; the A x A table (48 B a cell) stays in L2",
                    "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
-        "roofline": {"bound": "l2_atomics", "kernel": "efg", "achieved": alg / (kern_ms * 1e-3) / 1e9, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "efg", "achieved": alg / (kern_ms * 1e-3) / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": alg / (kern_ms * 1e-3) / 1e9 / peak, "traffic": None,
                      "peak_kind": peak_kind, "alg_bytes_per_step": alg, "efg_kernels_ms_per_step": kern_ms,
-                     "note": "pair updates are 64-bit atomics on an L2-resident table; the HBM peak is context"},
+                     "l2_atomic_bytes_per_step": atomic_bytes,
+                     "note": "algorithmic bytes: 12 B/event of the formatted log read once; the pair updates "
+                             "(64-bit atomics, 96 B a pair, on an L2-resident table) are implementation "
+                             "traffic and have no fraction"},
         "kernels_ms_per_step": {"efg": round(kern_ms, 4), "scan": round(scan_ms / args.steps, 4)},
         "gpu_launches": int(launches), "clocks": clk.summary(),
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)},
@@ -1048,6 +1108,42 @@ def main():
                          f"{dt:.1f} s on 1 of {os.cpu_count()} host cores"}
 
     pm4g.pm4g_ctx_destroy(ctx)
+    del dev, L
+    torch.cuda.empty_cache()
+    # The batched and served forms (drill-down views and the serving mix) on
+    # one GPU, after the single-log pass: at N = 1 only (replicas add nothing)
+    drill = serving = None
+    if world == 1 and not args.no_drilldown:
+        r = drilldown_core(args, local, max(1, args.dd_steps), max(3, args.warmup), args.plain_views, tune=True,
+                           cpu_baseline=False)
+        drill = {"metric": DD_METRIC, "workload": "drilldown_views", "log": r["spec"].name,
+                 "n_events": r["n_events"], "n_activities": r["n_activities"], "n_views": r["n_views"],
+                 "sub_log_events": r["sub_log_events"], "var_top_k": r["var_top_k"],
+                 "batched": {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                             "steps": r["steps"], "warmup": r["warmup"],
+                             "timing": "CUDA events on the context stream around each pm4g_batch_dfg call",
+                             "launches_per_step": r["launches_per_step"], "autotuned": r["tuned"]},
+                 "plain": r["plain"], "ratio_vs_plain": r["ratio_vs_plain"],
+                 "e2e": r["e2e"], "roofline": r["roofline"], "gpu_launches": r["gpu_launches"],
+                 "first_call_ms_with_index": round(r["first_ms"], 1), "clocks": r["clocks"]}
+        torch.cuda.empty_cache()
+    if world == 1 and not args.no_serving:
+        r = serve_core(args, local, [float(x) for x in args.serve_rates.split(",") if x], args.serve_seconds,
+                       small_log=False)
+        serving = {"metric": SERVE_METRIC, "workload": "serving_mix", "log": r["spec"].name,
+                   "n_events": r["n_events"], "seconds_per_rate": r["seconds_per_rate"],
+                   "mix": "70% filter+DFG (EVENTS), 20% variants top-10, 10% upload",
+                   "upload_events": r["upload_events"],
+                   "rates": [{"rate": e["rate"], "requests": e["requests"], "completed": e["completed"],
+                              "errors": e["errors"], "events_per_s": e["events_per_s"],
+                              "p50_ms": e["all"].get("p50_ms"), "p99_ms": e["all"].get("p99_ms"),
+                              "dfg_p50_ms": e["dfg"].get("p50_ms"), "dfg_p99_ms": e["dfg"].get("p99_ms"),
+                              "variants_p99_ms": e["variants"].get("p99_ms"),
+                              "upload_p99_ms": e["upload"].get("p99_ms"), "dfg_batches": e["dfg_batches"]}
+                             for e in r["per_rate"]],
+                   "latency": "arrival to result on the host", "gpu_launches": r["gpu_launches"],
+                   "clocks": r["clocks"]}
+        torch.cuda.empty_cache()
     if rank != 0:
         return
     line = {
@@ -1070,6 +1166,8 @@ def main():
         "clocks": clk.summary(),
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "drilldown": drill if world == 1 else "measured at N = 1 only",
+        "serving": serving if world == 1 else "measured at N = 1 only",
     }
     print(json.dumps(line), flush=True)
 

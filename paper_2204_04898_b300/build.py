@@ -2,6 +2,10 @@
 
 nvcc cross-compiles for sm_103a (B300) without needing a GPU:
     python -m paper_2204_04898_b300.build
+
+Each .cu file is compiled to an object in parallel (no device code crosses
+files: kernels are launched through host stubs), then the objects are linked
+with the static CUDA runtime.
 """
 
 from __future__ import annotations
@@ -10,16 +14,18 @@ import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpm4g.so")
+OBJ = os.path.join(HERE, "_build")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-shared", "-cudart", "static"]
+         "--expt-relaxed-constexpr"]
 
 
 def sources() -> list[str]:
@@ -41,13 +47,28 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     if not force and up_to_date():
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [NVCC, *ARCH_FLAGS, *FLAGS, *(extra or []), "-I", os.path.join(ROOT, "include"),
-           *sources(), "-o", tmp]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    os.makedirs(OBJ, exist_ok=True)
+    tag = os.getpid()
+
+    def compile_one(src: str) -> str:
+        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + f".{tag}.o")
+        cmd = [NVCC, *ARCH_FLAGS, *FLAGS, *(extra or []), "-I", os.path.join(ROOT, "include"), "-c", src,
+               "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.check_call(cmd)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, sources()))
+    tmp = LIB + f".{tag}.tmp"
+    try:
+        subprocess.check_call([NVCC, *ARCH_FLAGS, "-shared", "-cudart", "static", *objs, "-o", tmp])
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
       tcnt[i] = 0;
       tl[i] = 0;
       tm[i] = 0;
-      tminh[i] = 0xFFFFFFFFu;
-      tmaxh[i] = 0;
+      tminh[i] = kGuardMinInit;
+      tmaxh[i] = kGuardMaxInit;
     }
     for (uint32_t i = tid; i < A; i += kBtThreads) {
       st[i] = 0;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
     const uint64_t row = (uint64_t)sub * a.n_edges;
     const DfgTable g{a.acc.cnt + row, a.acc.lo + row, a.acc.hi + row, a.acc.mn + row, a.acc.mx + row};
     SmemSink sink{tkey, tcnt, tminh, tmaxh, tl, tm, (uint32_t)(kBtSlots - 1),
-                  (uint32_t)__clz((uint32_t)kBtSlots) + 1u, 1, st, en, nullptr, nullptr, g,
+                  (uint32_t)__clz((uint32_t)kBtSlots) + 1u, 1, st, en, g,
                   a.start + (uint64_t)sub * A, a.end + (uint64_t)sub * A};
     sink.probes = 16;
     uint64_t ev = 0, cs = 0;  // this lane's kept events and cases

@@ -220,7 +220,6 @@ static void release_log(pm4g_log *L) {
   free_buf(c, L->bucket_off);
   free_buf(c, L->act_s);
   free_buf(c, L->len);
-  free_buf(c, L->hash);
   free_buf(c, L->cattr);
   free_buf(c, L->uniq);
   free_buf(c, L->dfg);
@@ -302,8 +301,6 @@ static SegArgs seg_args(pm4g_log *L, const SegConfig &sc, uint32_t *work, uint32
   a.work = work;
   a.act_s = L->act_s.p;
   a.len = L->len.p;
-  a.hash = L->hash.p;
-  a.seed = 0;
   const size_t cells = (size_t)L->A * L->A;
   a.g.cnt = L->dfg.p;
   a.g.lo = L->dfg.p + cells;
@@ -371,11 +368,6 @@ static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) 
     PM4G_TRY(check_launch(c, "k_fb_hist"));
   }
   PM4G_TRY(scan_u32(c, ccnt, cstart, ncl));
-  if (!exp) {
-    const uint64_t s0 = (uint64_t)b << L->clb;
-    const uint64_t s1 = std::min<uint64_t>(L->R, s0 + (uint64_t)ncl);
-    PM4G_CK(cudaMemsetAsync(L->hash.p + s0, 0, (s1 - s0) * sizeof(uint64_t), c->stream));
-  }
   KTime t(c, "fallback");
   c->launches++;
   PM4G_CK(launch_fb_compute(exp, a, srec, n, b, cstart, g, c->stream));
@@ -387,13 +379,14 @@ static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) 
 // table, the endpoint counts and (at load) the per-case attribute; sets C.
 // err_in (optional): a device word to read back with the pass's own counters
 // (one synchronisation for both); its value goes to *err_out.
+// keys (optional): the first word of every bucketed record, in bucket order,
+// written by the partition; with it, time-ordered logs take the streaming pass.
 static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, const uint32_t *err_in = nullptr,
-                       uint32_t *err_out = nullptr) {
+                       uint32_t *err_out = nullptr, const uint32_t *keys = nullptr) {
   Ctx *c = L->ctx;
   const size_t cells = (size_t)L->A * L->A;
   PM4G_TRY(alloc_buf(c, L->act_s, L->n));
-  PM4G_TRY(alloc_buf(c, L->len, L->R));
-  PM4G_TRY(alloc_buf(c, L->hash, L->R));
+  if (!L->len.p) PM4G_TRY(alloc_buf(c, L->len, L->R));
   PM4G_TRY(alloc_buf(c, L->dfg, 5 * cells));
   PM4G_TRY(alloc_buf(c, L->ends, 2 * (size_t)L->A));
   PM4G_CK(cudaMemsetAsync(L->dfg.p, 0, 3 * cells * sizeof(unsigned long long), c->stream));
@@ -430,6 +423,32 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   a.n_sorted = n_cases + 1;
   a.attr_in = attr_in;
   a.cattr = write_cattr ? L->cattr.p : nullptr;
+  a.err = ctr + 2;
+  if (keys && L->status.p && c->test_bucket_cap == 0 && sc.cap >= 32) {
+    // time-ordered logs: the streaming pass (it returns at once otherwise,
+    // and the sorting pass below then does the work)
+    const int w = stream_segment_warps(L->clb, sc.a_s, (size_t)c->smem_optin);
+    const size_t cells = (size_t)L->A * L->A;
+    uint32_t *emap = w > 0 ? S.get<uint32_t>(cells) : nullptr;
+    uint32_t *key_of = w > 0 ? S.get<uint32_t>(kStSlots) : nullptr;
+    if (w > 0 && (!emap || !key_of)) {
+      set_error("segment pass: out of device memory for the edge ids");
+      return PM4G_ENOMEM;
+    }
+    if (w > 0) {
+      PM4G_CK(cudaMemsetAsync(emap, 0xFF, cells * sizeof(uint32_t), c->stream));
+      a.keys = keys;
+      a.emap = emap;
+      a.key_of = key_of;
+      a.n_ids = ctr + 3;
+      const size_t smem = st_smem_layout(1 << L->clb, sc.a_s, w).total;
+      const unsigned grid = std::min<unsigned>((L->nb + w - 1) / w, (unsigned)c->num_sms);
+      KTime t(c, "segment");
+      c->launches++;
+      PM4G_CK(launch_stream_segment(a, w, grid, smem, c->stream));
+      a.skip_ordered = 1;
+    }
+  }
   if (sc.cap >= 32) {
     const unsigned grid = std::min<unsigned>(L->nb, (unsigned)c->num_sms);
     KTime t(c, "segment");
@@ -447,6 +466,10 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   Status h{};
   PM4G_TRY(d2h(c, &h, blk, sizeof(Status)));
   if (err_out) *err_out = h.err[0];
+  if (h.ctr[2] & 1u) {
+    set_error("internal: case lengths counted by the partition disagree with the bucketed records");
+    return PM4G_ECUDA;
+  }
   const uint32_t n_ovf = h.ctr[1];
   if (n_ovf) {
     std::vector<uint32_t> list(n_ovf);
@@ -795,6 +818,9 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         fail(PM4G_ECUDA);
         break;
       }
+      // the first word of every record in bucket order, written by the
+      // partition's final level (the streaming pass counts cases from it)
+      uint32_t *keys = nullptr;
       FormatArgs fa{};
       fa.case_id = keycol;
       fa.activity = dact;
@@ -868,6 +894,8 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         pa.bucket_off = L->bucket_off.p;
         pa.nb = L->nb;
         pa.err_flags = err;
+        keys = S.get<uint32_t>(n);
+        pa.keys_out = keys;
         uint4 *tmp = nullptr;
         if (two_level) {
           {
@@ -947,7 +975,7 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
       }
       if (st) break;
       uint32_t errv = 0;
-      if (fail(run_segment(L, dattr, L->has_attr, err, &errv))) break;
+      if (fail(run_segment(L, dattr, L->has_attr, err, &errv, keys))) break;
       if (errv & 1u) {
         set_error("pm4g_load_log: activity code outside [0, %d)", A);
         fail(PM4G_ERANGE);
@@ -1290,10 +1318,22 @@ static int ensure_variants(pm4g_log *L) {
     return PM4G_OK;
   }
   Scratch S(c);
+  // every case's sequence hash, from the formatted activities
+  uint64_t *hash = S.get<uint64_t>(R);
+  if (!hash) {
+    set_error("variants: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  {
+    KTime t(c, "variants");
+    k_case_hash<<<grid_for((int64_t)((R + 3) / 4) * 32, 256, 8 * (unsigned)c->num_sms), 256, 0, c->stream>>>(
+        L->len.p, L->off.p, L->act_s.p, R, 0, hash);
+    PM4G_TRY(check_launch(c, "k_case_hash"));
+  }
   VarArgs a{};
   a.n_slots = R;
   a.len = L->len.p;
-  a.hash = L->hash.p;
+  a.hash = hash;
   a.off = L->off.p;
   a.act_s = L->act_s.p;
   a.bits = c->test_hash_bits;

@@ -156,6 +156,31 @@ __device__ __forceinline__ double edge_mean(uint64_t sum_hi, uint64_t sum_lo, ui
   return u128_to_double_rn(sum_hi, sum_lo) / __ull2double_rn(count);
 }
 
+// Fire-and-forget 64-bit global minimum / maximum (no value comes back, so
+// the issuing warp does not wait for the memory system).
+__device__ __forceinline__ void red_min_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_max_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Guards of the extremes a block has pushed to global memory, kept as the bit
+// patterns of non-negative floats (which order like their bits). A minimum
+// guard holds a value rounded up from one already pushed, so a duration whose
+// downward-rounded float is at or above it cannot lower the global minimum; a
+// maximum guard holds a value rounded down, so a duration whose upward-rounded
+// float is at or below it cannot raise the global maximum. Only durations
+// within a float's relative precision of the pushed extreme, or beyond it,
+// are pushed.
+__device__ __forceinline__ uint32_t guard_up(uint64_t v) { return __float_as_uint(__ull2float_ru(v)); }
+__device__ __forceinline__ uint32_t guard_down(uint64_t v) { return __float_as_uint(__ull2float_rd(v)); }
+constexpr uint32_t kGuardMinInit = 0x7F800000u;  // +infinity: nothing pushed yet
+constexpr uint32_t kGuardMaxInit = 0u;           // 0.0f: the global maxima start at 0, so 0 needs no push
+
 // ---------------------------------------------------------------------------
 // Warp helpers
 // ---------------------------------------------------------------------------
@@ -178,6 +203,35 @@ __device__ __forceinline__ uint32_t run_head(uint32_t key, uint32_t &run_len) {
   const uint32_t next = above ? (uint32_t)(__ffs(above) - 1) : 32u;
   run_len = next - lane;
   return head;
+}
+
+// Mask of the run of consecutive lanes holding this lane's key (the runs of
+// run_head): every lane of a run computes the same mask, so the mask can be
+// passed to a redux.sync by all lanes of the warp at once.
+__device__ __forceinline__ uint32_t run_mask(uint32_t key) {
+  const uint32_t lane = lane_id();
+  const uint32_t prev = __shfl_up_sync(kFull, key, 1);
+  const uint32_t heads = __ballot_sync(kFull, lane == 0 || prev != key);
+  const uint32_t le = 0xFFFFFFFFu >> (31 - lane);  // lanes 0..lane
+  const uint32_t head = 31 - __clz(heads & le);
+  const uint32_t after = heads & ~le;              // run heads after this lane
+  const uint32_t below_next = after ? ((1u << (__ffs(after) - 1)) - 1) : 0xFFFFFFFFu;
+  return below_next & ~((1u << head) - 1);
+}
+
+// Mask of the lanes whose (valid, key) equals this lane's, where key has
+// `bits` significant bits (invalid lanes must pass the same key, e.g. 0): one
+// ballot per key bit, no shared memory. Equal inputs give equal masks, so the
+// mask can be passed to a redux.sync by all lanes of the warp at once.
+__device__ __forceinline__ uint32_t peer_mask(uint32_t key, bool valid, int bits) {
+  const uint32_t vb = __ballot_sync(kFull, valid);
+  uint32_t m = valid ? vb : ~vb;
+  for (int k = 0; k < bits; ++k) {
+    const bool bit = (key >> k) & 1u;
+    const uint32_t b = __ballot_sync(kFull, bit);
+    m &= bit ? b : ~b;
+  }
+  return m;
 }
 
 // Exact sum of 64-bit values over the lanes of `peers` (all lanes of `peers`

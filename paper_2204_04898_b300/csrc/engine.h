@@ -265,7 +265,6 @@ struct pm4g_log {
   pm4g::DBuf<uint32_t> bucket_off;
   pm4g::DBuf<int32_t> act_s;
   pm4g::DBuf<uint32_t> len;
-  pm4g::DBuf<uint64_t> hash;
   pm4g::DBuf<int32_t> cattr;
   pm4g::DBuf<int32_t> uniq;  // sorted distinct case ids when renumbered
   pm4g::DBuf<unsigned long long> dfg;  // 5 * A * A: cnt, lo, hi, min, max

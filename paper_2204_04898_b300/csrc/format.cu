@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   uint32_t *cur = pm + kPartWarps * nbins;  // next output index of every digit
   uint32_t *tst = cur + nbins;              // staged start of every digit, nbins + 1
   uint32_t *sw = tst + nbins + 1;           // block-scan scratch, 32 words
+  uint32_t *dlt = sw + 32;                  // every digit's output position minus its staged position
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // item indices fit 32 bits (at most 2^31 - 1 events)
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
           }
           rec[r] = make_uint4(((slot & kSlotLoMask) << a.act_bits) | act, i, rec[r].z, rec[r].w);
           dg[r] = slot >> shift1;
+
         } else {
           dg[r] = ((rec[r].x >> a.act_bits) >> a.clb) & fmask;
         }
@@ -468,6 +470,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
       const uint32_t pre = block_exclusive_scan<kPartThreads>(tot, sw, all);
       if ((uint32_t)tid < nbins) {
         tst[tid] = pre;
+        dlt[tid] = cur[tid] - pre;
         uint32_t run = pre;
         for (int w = 0; w < kPartWarps; ++w) {
           const uint32_t t = wh[w * nbins + tid];
@@ -481,10 +484,25 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kPartItems; ++r)
-      if (dg[r] != 0xFFFFFFFFu) stg[myh[dg[r]] + rk[r]] = rec[r];
+    for (int r = 0; r < kPartItems; ++r) {
+      if (dg[r] != 0xFFFFFFFFu) {
+        const uint32_t sp = myh[dg[r]] + rk[r];
+        stg[sp] = rec[r];
+        // one level only: the final bucketing, so the key words go out here
+        if (kLevel == 1 && a.fbits == 0 && a.keys_out) a.keys_out[dlt[dg[r]] + sp] = rec[r].x;
+      }
+    }
     fence_smem_to_async();
     __syncthreads();
+    if (kLevel == 2 && a.keys_out) {
+      // the first word of every record, in final order, from the staged tile
+      // (consecutive staged records of a digit go to consecutive positions)
+      const uint32_t cnt = tst[nbins];
+      for (uint32_t k = tid; k < cnt; k += kPartThreads) {
+        const uint32_t x = stg[k].x;
+        a.keys_out[dlt[((x >> a.act_bits) >> a.clb) & fmask] + k] = x;
+      }
+    }
     if (base + kPartTile < i1) load_tile(base + kPartTile);
     // each digit's run is one bulk copy, issued by the digit's thread; the
     // copies proceed while the next tile is loaded and ranked

@@ -52,14 +52,15 @@ struct PartArgs {
   int splits;                // level 2: units per coarse bucket
   uint4 *rec_out;
   uint32_t *err_flags;
+  uint32_t *keys_out;        // optional: the final level also writes every record's first word here
 };
 
 __host__ __device__ inline size_t part_wh_bytes(uint32_t nbins) { return ((size_t)kPartWarps * nbins * 2 + 15) / 16 * 16; }
 // staging tile, per-warp 16-bit counts, per-warp peer masks, cursors, staged
-// starts and block-scan scratch
+// starts, block-scan scratch and each digit's output-minus-staged offset
 __host__ __device__ inline size_t part_smem_bytes_hd(uint32_t nbins) {
   return (size_t)kPartTile * 16 + part_wh_bytes(nbins) + (size_t)kPartWarps * nbins * 4 +
-         (size_t)(2 * nbins + 1 + 32) * 4;
+         (size_t)(3 * nbins + 1 + 32) * 4;
 }
 inline size_t part_smem_bytes(uint32_t nbins) { return part_smem_bytes_hd(nbins); }
 cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s);
@@ -96,8 +97,6 @@ struct SegArgs {
   uint32_t *work; // bucket work counter
   int32_t *act_s;
   uint32_t *len;
-  uint64_t *hash;
-  uint64_t seed;
   const int32_t *attr_in;
   int32_t *cattr;
   DfgTable g;
@@ -113,10 +112,41 @@ struct SegArgs {
   int32_t min_case;
   const int32_t *uniq;
   const uint32_t *order_flags;  // optional: bit 1 clear = every case's records are in (timestamp, row) order
+  int skip_ordered;             // sorting pass: do nothing when the streaming pass handles the log
+  uint32_t *err;                // streaming pass: bit 0 set when case lengths disagree with the records
+  const uint32_t *keys;         // streaming pass: first word of every bucketed record (bucket order)
+  // streaming pass: edge ids (emap, A * A, ~0 = none yet), the key of every
+  // id (key_of, kStSlots) and the id counter; ids below kStSlots index the
+  // shared edge table directly
+  uint32_t *emap, *key_of, *n_ids;
 };
 
+// Streaming segment pass (stream.cu): one warp per bucket, for logs whose
+// timestamps never decrease in row order. Shared memory: an edge table of
+// kStSlots slots indexed by edge id (count, low and middle sum words, high
+// words of the pushed minimum and maximum), the endpoint counts, then per
+// warp the case state of its bucket (last timestamp, first position, events
+// seen, last activity: 20 bytes per case slot).
+constexpr int kStMaxThreads = 768;
+constexpr int kStSlots = 4096;
+struct StSmem {
+  size_t tcnt, st, warp0, per_warp, total;
+};
+__host__ __device__ inline StSmem st_smem_layout(int ncl, int a_s, int n_warps) {
+  StSmem L;
+  L.tcnt = 0;
+  L.st = (size_t)kStSlots * 20;
+  L.warp0 = (L.st + (size_t)a_s * 8 + 15) / 16 * 16;
+  L.per_warp = ((size_t)ncl * 20 + 15) / 16 * 16;
+  L.total = L.warp0 + (size_t)n_warps * L.per_warp;
+  return L;
+}
+// warps per block whose layout fits smem_optin (0: none)
+int stream_segment_warps(int clb, int a_s, size_t smem_optin);
+cudaError_t launch_stream_segment(const SegArgs &a, int n_warps, unsigned grid, size_t smem, cudaStream_t s);
+
 struct SegSmem {
-  size_t rec, tlo, chash, hw, rng, flg, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;
+  size_t rec, tlo, hw, rng, flg, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;
 };
 
 constexpr int kSegThreads = 1024;
@@ -137,8 +167,6 @@ __host__ __device__ inline SegSmem seg_smem_layout(int cap, int ncl, int a_s, in
   o += (size_t)cap * 16;
   L.tlo = o;
   o += (size_t)tbl_slots * 8;
-  L.chash = o;
-  o += (size_t)ncl * 8;
   L.hw = o;
   const size_t hw_bytes = (size_t)kSegWarps * ((ncl + 1) & ~1) * 2, idx_bytes = (size_t)cap * 2;
   o += seg_align(hw_bytes > idx_bytes ? hw_bytes : idx_bytes, 16);

@@ -19,9 +19,10 @@
 //     sorts only those, one warp per case (warp bitonic sort in registers of
 //     up to 128 events; longer cases merge sorted 128-event chunks by rank);
 //  4. walks the ordered positions 32 at a time per warp: writes the activity
-//     sequence, counts start/end activities, forms the directly-follows pair
-//     (a_i, a_{i+1}) with duration ts_{i+1} - ts_i and aggregates it, and sums
-//     each case's sequence-hash terms with a segmented warp scan.
+//     sequence, counts start/end activities, and forms the directly-follows
+//     pair (a_i, a_{i+1}) with duration ts_{i+1} - ts_i and aggregates it.
+// (The variant step forms each case's sequence hash from the activity
+// sequence written here.)
 // Pair aggregation uses full-warp operations only: twice, the lanes holding
 // the same edge as the first pending lane are reduced together (count, exact
 // sum, min, max) and one lane updates the table; the remaining lanes update it
@@ -30,9 +31,9 @@
 // addressing on src*A+dst; misses go to global atomics) and is flushed once
 // per CTA. Sums are exact: 32-bit low and middle words with every carry out of
 // bit 63 added to the global high word. Minimum and maximum are pushed to
-// global memory with fire-and-forget atomics only when they can improve: the
-// table keeps the high 32 bits of the extremes this CTA already pushed, and a
-// value whose high word is beyond them cannot win.
+// global memory with fire-and-forget reductions only when they can improve:
+// the table keeps float guards of the extremes this CTA already pushed,
+// rounded outward, and a value the guard shows cannot win is not pushed.
 //
 // Buckets holding a case longer than kMaxCaseSmem go to the global-memory path
 // at the end of this file (device radix sort, then the same per-position code).
@@ -50,16 +51,11 @@ struct GlobalSink {
   uint64_t slot_base;
   __device__ __forceinline__ void edge_group(uint32_t key, uint32_t cnt, u128 sum, uint64_t mn, uint64_t mx) {
     global_edge_group(a->g, key, cnt, (uint64_t)sum, (uint64_t)(sum >> 64));
-    atomicMin(&a->g.mn[key], (unsigned long long)mn);
-    atomicMax(&a->g.mx[key], (unsigned long long)mx);
+    red_min_u64(&a->g.mn[key], mn);
+    red_max_u64(&a->g.mx[key], mx);
   }
   __device__ __forceinline__ void start(uint32_t act) { atomicAdd(&a->g_start[act], 1ull); }
   __device__ __forceinline__ void end(uint32_t act) { atomicAdd(&a->g_end[act], 1ull); }
-  __device__ __forceinline__ void hash_add(uint32_t c, uint64_t v) {
-    uint32_t *h = reinterpret_cast<uint32_t *>(&a->hash[slot_base + c]);  // little endian: low word first
-    atomicAdd(&h[0], (uint32_t)v);
-    atomicAdd(&h[1], (uint32_t)(v >> 32));
-  }
 };
 
 // One warp handles 32 consecutive ordered positions p = base + lane of a
@@ -111,8 +107,6 @@ __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, 
   }
   const int64_t nts = (int64_t)(((uint64_t)nw << 32) | nz);
   aggregate_edges(sink, has_edge, act * a.n_act + (nx & act_mask), (uint64_t)nts - (uint64_t)ts);
-  // sequence hash: each event adds its term to its case's sum
-  if (valid) sink.hash_add(c, event_hash(act, (uint32_t)p - cs, a.seed));
 }
 
 template <int E>
@@ -191,7 +185,6 @@ struct SegShared {
   uint4 *rec;
   uint16_t *idx;
   uint32_t *ccnt, *cstart;
-  uint32_t *hl, *hh;
   uint8_t *flg;  // per case: events out of (timestamp, row) order
 };
 
@@ -224,8 +217,6 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   }
   for (int j = tid; j < kSegWarps * hws; j += kSegThreads) hw[j] = 0;
   for (int c = tid; c < ncl; c += kSegThreads) {
-    S.hl[c] = 0;
-    S.hh[c] = 0;
     S.flg[c] = 0;
   }
   __syncthreads();
@@ -327,7 +318,6 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
       if (slot < a.n_slots) {
         const uint32_t Lc = S.ccnt[c];
         a.len[slot] = Lc;
-        a.hash[slot] = Lc ? (((uint64_t)S.hh[c] << 32) | S.hl[c]) : 0ull;
         if (a.cattr) {
           const uint32_t q = S.cstart[c];
           a.cattr[slot] = (Lc && a.attr_in) ? a.attr_in[S.rec[S.flg[c] ? S.idx[q] : q].y] : 0;
@@ -347,6 +337,8 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
 template <bool kExport>
 __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // time-ordered logs go through the streaming pass when it is launched too
+  if (a.skip_ordered && a.order_flags && !(*(volatile uint32_t *)a.order_flags & 2u)) return;
   const int ncl = 1 << a.clb;
   const int a_s = a.ep_smem ? (int)a.n_act : 0;
   const SegSmem L = seg_smem_layout(a.cap, ncl, a_s, a.tbl_slots, a.tbl_mode);
@@ -355,8 +347,6 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   S.idx = reinterpret_cast<uint16_t *>(smem + L.hw);  // shares the per-warp counts' area (dead by the sort)
   S.ccnt = reinterpret_cast<uint32_t *>(smem + L.ccnt);
   S.cstart = reinterpret_cast<uint32_t *>(smem + L.cstart);
-  S.hl = reinterpret_cast<uint32_t *>(smem + L.chash);
-  S.hh = S.hl + ncl;
   S.flg = smem + L.flg;
   uint32_t *tl = reinterpret_cast<uint32_t *>(smem + L.tlo);
   uint32_t *tm = tl + a.tbl_slots;
@@ -379,8 +369,8 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
       tcnt[i] = 0;
       tl[i] = 0;
       tm[i] = 0;
-      tminh[i] = 0xFFFFFFFFu;
-      tmaxh[i] = 0;
+      tminh[i] = kGuardMinInit;
+      tmaxh[i] = kGuardMaxInit;
       if (a.tbl_mode) tkey[i] = kEmptyKey;
     }
     for (int i = tid; i < a_s; i += kSegThreads) {
@@ -390,7 +380,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   }
   SmemSink sink{tkey, tcnt, tminh, tmaxh, tl, tm, (uint32_t)(a.tbl_slots - 1),
                 (uint32_t)__clz((uint32_t)a.tbl_slots) + 1u, a.tbl_mode,
-                a_s ? st : nullptr, a_s ? en : nullptr, S.hl, S.hh, a.g, a.g_start, a.g_end};
+                a_s ? st : nullptr, a_s ? en : nullptr, a.g, a.g_start, a.g_end};
   uint32_t n_sorted = 0;
   // Buckets are claimed one ahead (misc[0] and misc[1] alternate between the
   // current and the next claim): while a bucket is processed, lane 0 of the

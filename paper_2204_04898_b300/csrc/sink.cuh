@@ -14,7 +14,7 @@ constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 __device__ __forceinline__ void global_sum(const DfgTable &g, uint32_t key, uint64_t lo, uint64_t hi) {
   const unsigned long long old = atomicAdd(&g.lo[key], (unsigned long long)lo);
   const unsigned long long h2 = hi + (old + lo < old ? 1ull : 0ull);
-  if (h2) atomicAdd(&g.hi[key], h2);
+  if (h2) red_add_u64(&g.hi[key], h2);
 }
 
 __device__ __forceinline__ void global_edge_group(const DfgTable &g, uint32_t key, uint32_t cnt, uint64_t lo,
@@ -24,13 +24,12 @@ __device__ __forceinline__ void global_edge_group(const DfgTable &g, uint32_t ke
 }
 
 struct SmemSink {
-  uint32_t *tkey, *tcnt, *tminh, *tmaxh;
+  uint32_t *tkey, *tcnt, *tminh, *tmaxh;  // tminh/tmaxh: float guards (device_common.cuh)
   uint32_t *tl, *tm;  // low and middle 32-bit words of the slot's sum
   uint32_t mask;
   uint32_t shift;  // 32 - log2(slots), for the multiplicative slot hash
   int mode;
   uint32_t *st, *en;
-  uint32_t *hl, *hh;  // per-case sequence hash, low and high words
   DfgTable g;         // global accumulators (misses and carries)
   unsigned long long *g_start, *g_end;
   int probes = 64;    // hashed mode: slots tried before a pair goes to g
@@ -67,20 +66,21 @@ struct SmemSink {
         const uint32_t old_m = atomicAdd(&tm[s], (uint32_t)madd);
         if (old_m + (uint32_t)madd < old_m) top += 1;
       }
-      if (top) atomicAdd(&g.hi[key], (unsigned long long)top);
-      const uint32_t mnh = (uint32_t)(mn >> 32), mxh = (uint32_t)(mx >> 32);
-      if (mnh <= *(volatile uint32_t *)&tminh[s]) {
-        atomicMin(&tminh[s], mnh);
-        atomicMin(&g.mn[key], (unsigned long long)mn);
+      if (top) red_add_u64(&g.hi[key], top);
+      // extremes pushed (fire-and-forget) only when the float guards of what
+      // this block already pushed allow them to improve
+      if (__float_as_uint(__ull2float_rd(mn)) < *(volatile uint32_t *)&tminh[s]) {
+        atomicMin(&tminh[s], guard_up(mn));
+        red_min_u64(&g.mn[key], mn);
       }
-      if (mxh >= *(volatile uint32_t *)&tmaxh[s]) {
-        atomicMax(&tmaxh[s], mxh);
-        atomicMax(&g.mx[key], (unsigned long long)mx);
+      if (__float_as_uint(__ull2float_ru(mx)) > *(volatile uint32_t *)&tmaxh[s]) {
+        atomicMax(&tmaxh[s], guard_down(mx));
+        red_max_u64(&g.mx[key], mx);
       }
     } else {
       global_edge_group(g, key, cnt, lo64, top);
-      atomicMin(&g.mn[key], (unsigned long long)mn);
-      atomicMax(&g.mx[key], (unsigned long long)mx);
+      red_min_u64(&g.mn[key], mn);
+      red_max_u64(&g.mx[key], mx);
     }
   }
   __device__ __forceinline__ void start(uint32_t act) {
@@ -90,12 +90,6 @@ struct SmemSink {
   __device__ __forceinline__ void end(uint32_t act) {
     if (en) atomicAdd(&en[act], 1u);
     else atomicAdd(&g_end[act], 1ull);
-  }
-  // The case hash is two independent 32-bit wrap-around sums (low and high
-  // words of the event terms), so each term is two fire-and-forget adds.
-  __device__ __forceinline__ void hash_add(uint32_t c, uint64_t v) {
-    atomicAdd(&hl[c], (uint32_t)v);
-    atomicAdd(&hh[c], (uint32_t)(v >> 32));
   }
 };
 

@@ -78,6 +78,38 @@ __device__ __forceinline__ bool var_item(const VarArgs &a, const uint32_t *list,
   return a.len[s] != 0;
 }
 
+// Sequence hash of every case slot from the formatted activity sequence:
+// the wrap-around sums, over the case's events, of the low and high words of
+// event_hash(activity, position, seed). Eight lanes share a case and read
+// eight consecutive activities per step; a warp takes four cases at a time.
+__global__ void k_case_hash(const uint32_t *__restrict__ len, const uint32_t *__restrict__ off,
+                            const int32_t *__restrict__ act_s, uint64_t n_slots, uint64_t seed,
+                            uint64_t *__restrict__ hash) {
+  const uint32_t lane = threadIdx.x & 31, g8 = lane >> 3, l8 = lane & 7;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t base = warp * 4; base < n_slots; base += n_warps * 4) {
+    const uint64_t s = base + g8;
+    uint32_t L = 0, o = 0;
+    if (s < n_slots) {
+      L = len[s];
+      o = off[s];
+    }
+    uint32_t hl = 0, hh = 0;
+    for (uint32_t k = l8; k < L; k += 8) {
+      const uint64_t t = event_hash((uint32_t)act_s[o + k], k, seed);
+      hl += (uint32_t)t;
+      hh += (uint32_t)(t >> 32);
+    }
+#pragma unroll
+    for (int x = 1; x < 8; x <<= 1) {
+      hl += __shfl_xor_sync(kFull, hl, x);
+      hh += __shfl_xor_sync(kFull, hh, x);
+    }
+    if (s < n_slots && l8 == 0) hash[s] = L ? (((uint64_t)hh << 32) | hl) : 0ull;
+  }
+}
+
 __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t round) {
   const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -85,7 +117,7 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
     if (!var_item(a, list, n_list, i, s)) continue;
     const uint32_t L = a.len[s];
     uint64_t h;
-    if (round == 0) {
+    if (round == 0 && a.hash) {
       h = a.hash[s];
     } else {
       h = 0;

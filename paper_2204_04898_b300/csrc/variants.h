@@ -18,7 +18,7 @@ struct __align__(16) VarSlot {
 struct VarArgs {
   uint64_t n_slots;
   const uint32_t *len;     // per case slot, 0 = no case
-  const uint64_t *hash;    // per case slot, sequence hash (seed 0)
+  const uint64_t *hash;    // per case slot, sequence hash (seed 0); NULL: formed from act_s in round 0
   const uint32_t *off;     // per case slot, first position in the ordered log
   const int32_t *act_s;    // activity of every event in (case, ts, row) order
   int bits;                // key truncation (tests only), 0 = full key
@@ -37,6 +37,8 @@ struct VarArgs {
 struct Ctx;
 int group_variants(Ctx *c, VarArgs a, uint64_t n_items);
 
+__global__ void k_case_hash(const uint32_t *len, const uint32_t *off, const int32_t *act_s, uint64_t n_slots,
+                            uint64_t seed, uint64_t *hash);
 __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t round);
 __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out, uint32_t *n_bad);
 __global__ void k_var_final(VarArgs a, const uint32_t *list, uint32_t n_list);

@@ -349,3 +349,45 @@ def test_autotuner_applies_a_choice_that_keeps_results(pm4g, ctx, tmp_path):
         autotune.Tuner.apply(ctx, {})
     finally:
         pm4g.pm4g_log_free(log)
+
+
+def test_efg_then_drilldown_shares_timestamps_without_leaking(pm4g):
+    """The eventually-follows graph and the drill-down index both use the
+    log's timestamps in formatted order. Running pm4g_efg first and then a
+    batched drill-down on the same log must give the oracle's results and
+    leave no device buffer behind once the log is freed, however often the
+    pair is repeated (a counting allocator sees every block)."""
+    import torch
+    live = {}
+
+    def alloc(nbytes, stream):
+        t = torch.empty(max(1, nbytes), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def free(ptr, nbytes, stream):
+        live.pop(ptr, None)
+
+    ctx = pm4g.pm4g_ctx_create(0, allocator=(alloc, free))
+    try:
+        L = synth.generate(synth.drilldown_log(3000))
+        specs = _random_specs(L, np.random.default_rng(21), 10)
+        W = oracle.efg(L.case_id, L.activity, L.ts_ns, L.n_activities)
+        held = []
+        for rep in range(4):
+            log = _load(pm4g, ctx, L)
+            try:
+                G = pm4g.pm4g_efg(log)
+                for f in ("src", "dst", "count", "sum_lo", "sum_hi"):
+                    assert np.array_equal(getattr(G, f), getattr(W, f)), f
+                B = _run(pm4g, log, specs, top_k=3)
+                if rep == 0:
+                    _check_batch(B, L, specs, top_k=3)
+            finally:
+                pm4g.pm4g_log_free(log)
+            torch.cuda.synchronize()
+            held.append(sum(t.numel() for t in live.values()))
+        assert held[0] == 0, f"{held[0]} bytes still held after the log was freed"
+        assert held == [held[0]] * len(held), f"device bytes held after each repeat: {held}"
+    finally:
+        pm4g.pm4g_ctx_destroy(ctx)
