@@ -1283,8 +1283,14 @@ int pm4g::group_variants(Ctx *c, VarArgs a, uint64_t n_items) {
     PM4G_CK(cudaMemsetAsync(n_bad, 0, 4, c->stream));
     const unsigned g = grid_for((int64_t)items, 256, 65535);
     KTime t(c, "variants");
-    k_var_insert<<<g, 256, 0, c->stream>>>(a, list, n_list, round);
-    PM4G_TRY(check_launch(c, "k_var_insert"));
+    if (round == 0 && !a.hash && !list) {
+      k_var_hash_insert<<<grid_for((int64_t)((R + 31) / 32) * 32, kHiThreads, 16 * (unsigned)c->num_sms), kHiThreads,
+                          0, c->stream>>>(a);
+      PM4G_TRY(check_launch(c, "k_var_hash_insert"));
+    } else {
+      k_var_insert<<<g, 256, 0, c->stream>>>(a, list, n_list, round);
+      PM4G_TRY(check_launch(c, "k_var_insert"));
+    }
     k_var_verify<<<g, 256, 0, c->stream>>>(a, list, n_list, out_list, n_bad);
     PM4G_TRY(check_launch(c, "k_var_verify"));
     k_var_final<<<g, 256, 0, c->stream>>>(a, list, n_list);
@@ -1318,22 +1324,10 @@ static int ensure_variants(pm4g_log *L) {
     return PM4G_OK;
   }
   Scratch S(c);
-  // every case's sequence hash, from the formatted activities
-  uint64_t *hash = S.get<uint64_t>(R);
-  if (!hash) {
-    set_error("variants: out of device memory");
-    return PM4G_ENOMEM;
-  }
-  {
-    KTime t(c, "variants");
-    k_case_hash<<<grid_for((int64_t)((R + 3) / 4) * 32, 256, 8 * (unsigned)c->num_sms), 256, 0, c->stream>>>(
-        L->len.p, L->off.p, L->act_s.p, R, 0, hash);
-    PM4G_TRY(check_launch(c, "k_case_hash"));
-  }
   VarArgs a{};
   a.n_slots = R;
   a.len = L->len.p;
-  a.hash = hash;
+  a.hash = nullptr;  // formed from the formatted activities in the first round
   a.off = L->off.p;
   a.act_s = L->act_s.p;
   a.bits = c->test_hash_bits;

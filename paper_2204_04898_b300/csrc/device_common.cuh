@@ -79,12 +79,14 @@ __device__ __forceinline__ int64_t rec_ts(uint4 r) {
 __device__ __forceinline__ uint64_t ts_key(int64_t ts) { return (uint64_t)ts ^ 0x8000000000000000ULL; }
 
 // ---------------------------------------------------------------------------
-// Hashing. fmix64 is the 64-bit finalizer of MurmurHash3 (Austin Appleby,
-// public domain). A case's variant hash sums, over its events, the term fmix64
-// of (activity, position in case, seed): its low words and its high words
-// each in a 32-bit wrap-around sum. It is order-sensitive through the
-// position, and any thread can add any event's term. It only accelerates
-// grouping; equality of sequences is always verified.
+// Hashing. fmix64 and fmix32 are the finalizers of MurmurHash3 (Austin
+// Appleby, public domain). A case's variant hash sums, over its events, a
+// 64-bit term of (activity, position in case, seed): its low words and its
+// high words each in a 32-bit wrap-around sum. The two words of a term are
+// two independent 32-bit mixes, so a term costs two fmix32 rather than a
+// 64-bit multiply chain. The sum is order-sensitive through the position, and
+// any thread can add any event's term. It only accelerates grouping; equality
+// of sequences is always verified.
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   k ^= k >> 33;
@@ -94,16 +96,6 @@ __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   k ^= k >> 33;
   return k;
 }
-__host__ __device__ __forceinline__ uint64_t event_hash(uint32_t act, uint32_t pos, uint64_t seed) {
-  return fmix64((((uint64_t)act << 32) | pos) + seed * 0x9E3779B97F4A7C15ULL + 0x632BE59BD9B4E019ULL);
-}
-// Grouping key of a case from its sequence hash and length; never 0 (0 marks
-// an empty table slot). bits < 64 truncates it (tests force collisions).
-__host__ __device__ __forceinline__ uint64_t variant_key(uint64_t h, uint32_t len, int bits) {
-  uint64_t k = fmix64(h ^ fmix64((uint64_t)len * 0xD6E8FEB86659FD93ULL + 1));
-  if (bits > 0 && bits < 64) k &= ((1ULL << bits) - 1);
-  return k == 0 ? 1 : k;
-}
 __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   h ^= h >> 16;
   h *= 0x85ebca6bu;
@@ -111,6 +103,19 @@ __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   h *= 0xc2b2ae35u;
   h ^= h >> 16;
   return h;
+}
+__host__ __device__ __forceinline__ uint64_t event_hash(uint32_t act, uint32_t pos, uint64_t seed) {
+  const uint32_t s0 = (uint32_t)seed * 0x9E3779B9u, s1 = (uint32_t)(seed >> 32) ^ 0x7F4A7C15u;
+  const uint32_t lo = fmix32(act * 0x9E3779B1u + pos * 0x85EBCA77u + s0 + 0x632BE59Bu);
+  const uint32_t hi = fmix32((act ^ 0x5BD1E995u) * 0xC2B2AE3Du + pos * 0x27D4EB2Fu + (s0 ^ s1) + 0x165667B1u);
+  return ((uint64_t)hi << 32) | lo;
+}
+// Grouping key of a case from its sequence hash and length; never 0 (0 marks
+// an empty table slot). bits < 64 truncates it (tests force collisions).
+__host__ __device__ __forceinline__ uint64_t variant_key(uint64_t h, uint32_t len, int bits) {
+  uint64_t k = fmix64(h ^ fmix64((uint64_t)len * 0xD6E8FEB86659FD93ULL + 1));
+  if (bits > 0 && bits < 64) k &= ((1ULL << bits) - 1);
+  return k == 0 ? 1 : k;
 }
 
 // ---------------------------------------------------------------------------

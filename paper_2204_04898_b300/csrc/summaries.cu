@@ -78,35 +78,77 @@ __device__ __forceinline__ bool var_item(const VarArgs &a, const uint32_t *list,
   return a.len[s] != 0;
 }
 
-// Sequence hash of every case slot from the formatted activity sequence:
-// the wrap-around sums, over the case's events, of the low and high words of
-// event_hash(activity, position, seed). Eight lanes share a case and read
-// eight consecutive activities per step; a warp takes four cases at a time.
-__global__ void k_case_hash(const uint32_t *__restrict__ len, const uint32_t *__restrict__ off,
-                            const int32_t *__restrict__ act_s, uint64_t n_slots, uint64_t seed,
-                            uint64_t *__restrict__ hash) {
-  const uint32_t lane = threadIdx.x & 31, g8 = lane >> 3, l8 = lane & 7;
+// Inserts item s (a case slot, or a list entry) with sequence hash h into the
+// grouping table: finds or claims the slot of its key, counts it and keeps the
+// smallest member.
+__device__ __forceinline__ void var_insert_one(const VarArgs &a, uint32_t s, uint32_t L, uint64_t h,
+                                               uint32_t round) {
+  if (a.cls) h ^= fmix64(((uint64_t)a.cls[s] << 1) | 1u);  // keys of different classes differ
+  const unsigned long long key = variant_key(h, L, a.bits);
+  uint32_t g = (uint32_t)fmix64(key ^ round) & a.tmask;
+  for (uint32_t it = 0; it <= a.tmask; ++it) {
+    const unsigned long long k = *(volatile unsigned long long *)&a.tab[g].key;
+    if (k == key) break;
+    if (k == 0) {
+      const unsigned long long old = atomicCAS(&a.tab[g].key, 0ull, key);
+      if (old == 0 || old == key) break;
+    }
+    g = (g + 1) & a.tmask;
+  }
+  a.grp[s] = g;
+  atomicAdd(&a.tab[g].cnt, 1u);
+  atomicMax(&a.tab[g].nmin, ~s);
+}
+
+// First grouping round over all case slots, with the sequence hash (seed 0)
+// formed on the way from the formatted activities. A warp takes 32
+// consecutive case slots, whose events are contiguous in the formatted order,
+// and walks them 32 events at a time, lane-dense: each lane finds its event's
+// case by a shuffle binary search over the slots' length prefix, the terms of
+// a case's lanes (consecutive) are summed with redux.sync over the run, and
+// the run's first lane adds them to the case's per-warp accumulator. Each
+// lane then inserts its own slot.
+__global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
+  __shared__ uint32_t s_acc[kHiThreads / 32][64];  // per warp: low words, then high words, of 32 cases
+  const uint32_t lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  uint32_t *acc = s_acc[wb];
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t base = warp * 4; base < n_slots; base += n_warps * 4) {
-    const uint64_t s = base + g8;
-    uint32_t L = 0, o = 0;
-    if (s < n_slots) {
-      L = len[s];
-      o = off[s];
-    }
-    uint32_t hl = 0, hh = 0;
-    for (uint32_t k = l8; k < L; k += 8) {
-      const uint64_t t = event_hash((uint32_t)act_s[o + k], k, seed);
-      hl += (uint32_t)t;
-      hh += (uint32_t)(t >> 32);
-    }
+  for (uint64_t s0 = warp * 32; s0 < a.n_slots; s0 += n_warps * 32) {
+    const uint64_t s = s0 + lane;
+    const uint32_t L = s < a.n_slots ? a.len[s] : 0u;
+    uint32_t incl = L;  // events of this warp's slots up to and including this lane's
 #pragma unroll
-    for (int x = 1; x < 8; x <<= 1) {
-      hl += __shfl_xor_sync(kFull, hl, x);
-      hh += __shfl_xor_sync(kFull, hh, x);
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if ((int)lane >= o) incl += y;
     }
-    if (s < n_slots && l8 == 0) hash[s] = L ? (((uint64_t)hh << 32) | hl) : 0ull;
+    const uint32_t excl = incl - L;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t off0 = a.off[s0];  // first formatted position of the slots
+    acc[lane] = 0;
+    acc[32 + lane] = 0;
+    __syncwarp();
+    for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+      const uint32_t p = p0 + lane;
+      const bool valid = p < total;
+      // the case of position p: the number of slots whose events end at or before p
+      uint32_t c = 0;
+#pragma unroll
+      for (uint32_t step = 16; step >= 1; step >>= 1)
+        if (__shfl_sync(kFull, incl, c + step - 1) <= p) c += step;
+      const uint32_t k = p - __shfl_sync(kFull, excl, c & 31);
+      const uint64_t t = valid ? event_hash((uint32_t)a.act_s[off0 + p], k, 0) : 0ull;
+      const uint32_t rm = run_mask(valid ? c : 32u);
+      const uint32_t sl = __reduce_add_sync(rm, (uint32_t)t), sh = __reduce_add_sync(rm, (uint32_t)(t >> 32));
+      if (valid && lane == (uint32_t)(__ffs(rm) - 1)) {  // the run's first lane; each case has one run per step
+        acc[c] += sl;
+        acc[32 + c] += sh;
+      }
+      __syncwarp();
+    }
+    if (L) var_insert_one(a, (uint32_t)s, L, ((uint64_t)acc[32 + lane] << 32) | acc[lane], 0);
+    __syncwarp();
   }
 }
 
@@ -130,21 +172,7 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
       }
       h = ((uint64_t)hh << 32) | hl;
     }
-    if (a.cls) h ^= fmix64(((uint64_t)a.cls[s] << 1) | 1u);  // keys of different classes differ
-    const unsigned long long key = variant_key(h, L, a.bits);
-    uint32_t g = (uint32_t)fmix64(key ^ round) & a.tmask;
-    for (uint32_t it = 0; it <= a.tmask; ++it) {
-      const unsigned long long k = *(volatile unsigned long long *)&a.tab[g].key;
-      if (k == key) break;
-      if (k == 0) {
-        const unsigned long long old = atomicCAS(&a.tab[g].key, 0ull, key);
-        if (old == 0 || old == key) break;
-      }
-      g = (g + 1) & a.tmask;
-    }
-    a.grp[s] = g;
-    atomicAdd(&a.tab[g].cnt, 1u);
-    atomicMax(&a.tab[g].nmin, ~s);
+    var_insert_one(a, s, L, h, round);
   }
 }
 

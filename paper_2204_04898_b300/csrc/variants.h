@@ -37,8 +37,9 @@ struct VarArgs {
 struct Ctx;
 int group_variants(Ctx *c, VarArgs a, uint64_t n_items);
 
-__global__ void k_case_hash(const uint32_t *len, const uint32_t *off, const int32_t *act_s, uint64_t n_slots,
-                            uint64_t seed, uint64_t *hash);
+// First round over all slots with the hash formed from act_s (a.hash NULL).
+constexpr int kHiThreads = 256;
+__global__ void k_var_hash_insert(VarArgs a);
 __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t round);
 __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out, uint32_t *n_bad);
 __global__ void k_var_final(VarArgs a, const uint32_t *list, uint32_t n_list);
