@@ -65,11 +65,13 @@ ALG_BYTES = {
     "partition": (28.0, 0.0),  # (per event, per case), over the kernel's launches in one step
     "bucket_scatter": (28.0, 0.0),
     "segment": (12.0, 0.0),
+    "segment_sort": (12.0, 0.0),
     "variants": (0.0, 4.0),
 }
 # Source file of each timed kernel: a DRAM-traffic figure recorded under
 # profiles/ is used only while this file is unchanged since the capture.
-KERNEL_SOURCE = {"segment": "segment.cu", "partition": "format.cu", "bucket_scatter": "format.cu",
+KERNEL_SOURCE = {"segment": "stream.cu", "segment_sort": "segment.cu", "partition": "format.cu",
+                 "bucket_scatter": "format.cu",
                  "variants": "summaries.cu"}
 
 
@@ -735,7 +737,8 @@ def run_filters(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
-    kt = {k: pm4g.pm4g_ctx_timing(ctx, k) for k in ("filter", "segment", "partition", "export", "scan", "dfg",
+    kt = {k: pm4g.pm4g_ctx_timing(ctx, k) for k in ("filter", "segment", "segment_sort", "partition", "export",
+                                                   "scan", "dfg",
                                                    "variants", "radix_sort", "bucket_hist", "stats")}
     launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0] - launches0
     pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
@@ -1050,7 +1053,7 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     ms_max = max_over_ranks(ms)
     value = N * world * 1e3 / ms_max
-    live = {name: pm4g.pm4g_ctx_timing(ctx, name) for name in ("segment", "partition")}
+    live = {name: pm4g.pm4g_ctx_timing(ctx, name) for name in ("segment", "segment_sort", "partition")}
     launches = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
 
     # the breakdown of every kernel (CUDA events around each launch), same

@@ -135,7 +135,7 @@ static cudaEvent_t get_event(Ctx *c) {
 // The kernels PM4G_OPT_TIMING = 2 times: each is one launch carrying most of
 // its call's device time.
 static bool dominant_kernel(const char *nm) {
-  static const char *const names[] = {"segment", "partition", "batch_dfg", "efg", "filter"};
+  static const char *const names[] = {"segment", "segment_sort", "partition", "batch_dfg", "efg", "filter"};
   for (const char *x : names)
     if (strcmp(nm, x) == 0) return true;
   return false;
@@ -451,7 +451,7 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   }
   if (sc.cap >= 32) {
     const unsigned grid = std::min<unsigned>(L->nb, (unsigned)c->num_sms);
-    KTime t(c, "segment");
+    KTime t(c, "segment_sort");
     c->launches++;
     PM4G_CK(launch_segment(false, a, grid, sc.smem, c->stream));
   } else {
@@ -507,8 +507,8 @@ static int choose_clb(Ctx *c, int64_t n, uint64_t R, int32_t A, int act_bits) {
 const char *pm4g_last_error(void) { return pm4g::g_err; }
 
 const char *pm4g_kernel_names(void) {
-  return "stats,bucket_hist,bucket_scatter,partition,segment,fallback,scan,radix_sort,filter,variants,dfg,export,batch,"
-         "batch_dfg,efg";
+  return "stats,bucket_hist,bucket_scatter,partition,segment,segment_sort,fallback,scan,radix_sort,filter,variants,dfg,"
+         "export,batch,batch_dfg,efg";
 }
 
 int pm4g_ctx_create(pm4g_ctx **out, int device, void *cuda_stream, const pm4g_allocator *alloc) {
