@@ -21,7 +21,13 @@
  *    inputs are read only until pm4g_load_log returns.
  *  - Log handles and result arrays are owned by the library. Result arrays are
  *    host memory (malloc) released by the matching *_free call.
- *  - Limits: 0 <= n_events <= 2^31 - 1; 1 <= n_activities <= 2048.
+ *  - Limits: 0 <= n_events <= 2^31 - 1; 1 <= n_activities <= 65536. Up to
+ *    4096 activities the directly-follows pairs are aggregated into a table
+ *    dense over the A x A pairs; above that, into an open-addressing table
+ *    of twice as many slots as the log can have distinct pairs (Section 3:
+ *    the DFG of large alphabets goes to a hashed global table). Results are
+ *    the same either way. pm4g_efg needs its dense A x A table (48 bytes a
+ *    cell) to fit the device, and pm4g_dfg_noalloc keeps its own limits.
  *
  * Outputs are exact: counts and duration sums/min/max are integers (durations
  * are unsigned 64-bit nanosecond differences, sums 128-bit); the mean duration
@@ -70,6 +76,8 @@ extern "C" {
                                         global-memory path; 0 = default */
 /* Launch choices of pm4g_batch_dfg (0 = default; results never depend on them;
  * an autotuner picks them by timing, see paper_2204_04898_b300/autotune.py): */
+#define PM4G_OPT_TEST_EDGE_HASH 7     /* test only: 1 = the hashed global edge table (the one used
+                                        above 4096 activities) for every log loaded afterwards */
 #define PM4G_OPT_BATCH_CHUNK 4       /* cases a warp takes at once: 8, 16 (default) or 32 */
 #define PM4G_OPT_BATCH_STAGES 5      /* groups a batch of >= 64 views into caller-owned
                                         arrays is pipelined in: 1..16 (default 4) */

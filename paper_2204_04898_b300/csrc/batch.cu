@@ -62,6 +62,7 @@ struct BatchArgs {
   const int64_t *ts_s;
   const uint32_t *eidx_s;  // edge index of each event's pair with the next event of its case
   uint32_t n_act;
+  uint32_t a_s;  // endpoint counters kept in shared memory (n_act, or 0 for large alphabets: global adds)
   uint32_t n_edges;
   const uint4 *items;   // {sub, first range, end range, 0}
   uint32_t n_items;
@@ -136,8 +137,8 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
   uint32_t *tminh = tcnt + kBtSlots;
   uint32_t *tmaxh = tminh + kBtSlots;
   uint32_t *st = tmaxh + kBtSlots;
-  uint32_t *en = st + a.n_act;
-  uint32_t *misc = en + a.n_act;
+  uint32_t *en = st + a.a_s;
+  uint32_t *misc = en + a.a_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // per warp: sequence hash words (low, high) of its chunk's cases
   uint32_t *wl = misc + 16 + warp * 64, *wh = wl + 32;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
       tminh[i] = kGuardMinInit;
       tmaxh[i] = kGuardMaxInit;
     }
-    for (uint32_t i = tid; i < A; i += kBtThreads) {
+    for (uint32_t i = tid; i < a.a_s; i += kBtThreads) {
       st[i] = 0;
       en[i] = 0;
     }
@@ -169,7 +170,8 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
     const uint64_t row = (uint64_t)sub * a.n_edges;
     const DfgTable g{a.acc.cnt + row, a.acc.lo + row, a.acc.hi + row, a.acc.mn + row, a.acc.mx + row};
     SmemSink sink{tkey, tcnt, tminh, tmaxh, tl, tm, (uint32_t)(kBtSlots - 1),
-                  (uint32_t)__clz((uint32_t)kBtSlots) + 1u, 1, st, en, g,
+                  (uint32_t)__clz((uint32_t)kBtSlots) + 1u, 1, a.a_s ? st : nullptr,
+                  a.a_s ? en : nullptr, g,
                   a.start + (uint64_t)sub * A, a.end + (uint64_t)sub * A};
     sink.probes = 16;
     uint64_t ev = 0, cs = 0;  // this lane's kept events and cases
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_batch_dfg(BatchArgs a) {
       const uint32_t c = tcnt[s];
       if (c) global_edge_group(g, tkey[s], c, tl[s] | ((uint64_t)tm[s] << 32), 0);
     }
-    for (uint32_t i = tid; i < A; i += kBtThreads) {
+    for (uint32_t i = tid; i < a.a_s; i += kBtThreads) {
       if (st[i]) atomicAdd(&sink.g_start[i], (unsigned long long)st[i]);
       if (en[i]) atomicAdd(&sink.g_end[i], (unsigned long long)en[i]);
     }
@@ -351,9 +353,36 @@ __global__ void k_dd_case_cols(const uint32_t *__restrict__ aslots, const uint32
 }
 // One warp per case: the edge index of every event's pair with the next
 // event of its case (~0 for the case's last event).
+// Edge e of a hashed table's ascending keys: its key and its (src, dst).
+__global__ void k_dd_pairs_of_keys(const uint32_t *__restrict__ keys, uint32_t E, uint32_t A, uint32_t *ekey,
+                                   int32_t *pair) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const uint32_t k = keys[e];
+    ekey[e] = k;
+    pair[e] = (int32_t)(k / A);
+    pair[E + e] = (int32_t)(k % A);
+  }
+}
+// With no dense map (large alphabets), the edge index is found by binary
+// search over the log's edge keys (src * A + dst), ascending.
+__device__ __forceinline__ uint32_t edge_of(const uint32_t *__restrict__ emap, const uint32_t *__restrict__ ekey,
+                                            uint32_t E, uint32_t key) {
+  if (emap) return emap[key];
+  uint32_t lo = 0, n = E;
+  while (n > 0) {
+    const uint32_t h = n >> 1;
+    if (ekey[lo + h] < key) {
+      lo += h + 1;
+      n -= h + 1;
+    } else {
+      n = h;
+    }
+  }
+  return lo < E && ekey[lo] == key ? lo : 0xFFFFFFFFu;
+}
 __global__ void k_dd_eidx(const uint32_t *__restrict__ aoff, const uint32_t *__restrict__ alen, uint32_t C,
-                          const int32_t *__restrict__ act_s, const uint32_t *__restrict__ emap, uint32_t A,
-                          uint32_t *eidx) {
+                          const int32_t *__restrict__ act_s, const uint32_t *__restrict__ emap,
+                          const uint32_t *__restrict__ ekey, uint32_t E, uint32_t A, uint32_t *eidx) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -364,7 +393,7 @@ __global__ void k_dd_eidx(const uint32_t *__restrict__ aoff, const uint32_t *__r
       const uint32_t act = j < L ? (uint32_t)act_s[o + j] : 0u;
       uint32_t nact = __shfl_down_sync(kFull, act, 1);
       if (lane == 31 && j + 1 < L) nact = (uint32_t)act_s[o + j + 1];
-      if (j + 1 < L) eidx[o + j] = emap[act * A + nact];
+      if (j + 1 < L) eidx[o + j] = edge_of(emap, ekey, E, act * A + nact);
       else if (j + 1 == L) eidx[o + j] = 0xFFFFFFFFu;
     }
   }
@@ -516,6 +545,7 @@ int ensure_drilldown(pm4g_log *L) {
   free_buf(c, L->aslots);
   free_buf(c, L->apre);
   free_buf(c, L->emap);
+  free_buf(c, L->ekey);
   free_buf(c, L->e_pair);
   free_buf(c, L->aoff);
   free_buf(c, L->alen);
@@ -566,9 +596,9 @@ int ensure_drilldown(pm4g_log *L) {
     PM4G_TRY(hb.finish());
   }
   // edge index of every directly-follows pair of the resident log
-  {
+  if (!L->ghash) {
     Scratch S(c);
-    const int64_t cells = (int64_t)L->A * L->A;
+    const int64_t cells = (int64_t)L->gcells;
     uint32_t *flags = S.get<uint32_t>(cells), *pos = S.get<uint32_t>(cells + 1);
     if (!flags || !pos) return PM4G_ENOMEM;
     k_dfg_flags<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(L->dfg.p, cells, flags);
@@ -582,6 +612,19 @@ int ensure_drilldown(pm4g_log *L) {
     k_dd_emap<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(flags, pos, cells, (uint32_t)L->A, L->emap.p,
                                                                  L->e_pair.p, E);
     PM4G_TRY(check_launch(c, "k_dd_emap"));
+  } else {
+    // large alphabets: the edges' keys, ascending, searched per pair
+    Scratch S(c);
+    uint32_t *keys = nullptr, *slots = nullptr, E = 0;
+    PM4G_TRY(hashed_edges(L, S, keys, slots, E));
+    L->n_edges = E;
+    PM4G_TRY(alloc_buf(c, L->ekey, (size_t)E));
+    PM4G_TRY(alloc_buf(c, L->e_pair, 2 * (size_t)E));
+    if (E) {
+      k_dd_pairs_of_keys<<<grid_for(E, 256, 4096), 256, 0, c->stream>>>(keys, E, (uint32_t)L->A, L->ekey.p,
+                                                                         L->e_pair.p);
+      PM4G_TRY(check_launch(c, "k_dd_pairs_of_keys"));
+    }
   }
   // per-entry case columns in attribute order, and the edge index of every pair
   PM4G_TRY(alloc_buf(c, L->aoff, C));
@@ -591,9 +634,8 @@ int ensure_drilldown(pm4g_log *L) {
     k_dd_case_cols<<<grid_for((int64_t)C, 256, 65535), 256, 0, c->stream>>>(L->aslots.p, L->off.p, L->len.p, C,
                                                                             L->aoff.p, L->alen.p);
     PM4G_TRY(check_launch(c, "k_dd_case_cols"));
-    k_dd_eidx<<<grid_for((int64_t)C * 32, 256, 65535), 256, 0, c->stream>>>(L->aoff.p, L->alen.p, C, L->act_s.p,
-                                                                            L->emap.p, (uint32_t)L->A,
-                                                                            L->eidx_s.p);
+    k_dd_eidx<<<grid_for((int64_t)C * 32, 256, 65535), 256, 0, c->stream>>>(
+        L->aoff.p, L->alen.p, C, L->act_s.p, L->emap.p, L->ekey.p, L->n_edges, (uint32_t)L->A, L->eidx_s.p);
     PM4G_TRY(check_launch(c, "k_dd_eidx"));
   }
   L->dd_ready = true;
@@ -976,6 +1018,7 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     a.ts_s = L->ts_s.p;
     a.eidx_s = L->eidx_s.p;
     a.n_act = A;
+    a.a_s = A <= 2048 ? A : 0;
     a.n_edges = E;
     a.items = ditems;
     a.n_items = (uint32_t)P.items.size();
@@ -997,7 +1040,7 @@ static int batch_dfg(pm4g_log *L, const pm4g_batch_spec *spec, pm4g_batch_dfg_t 
     a.rhash = rhash;
     unsigned long long *freq = se + 2 * (size_t)Qg * A;
     if (!P.items.empty()) {
-      const size_t smem = bt_smem_bytes(A);
+      const size_t smem = bt_smem_bytes(A <= 2048 ? A : 0);
       const int chunk = c->batch_chunk ? c->batch_chunk : kBtChunk;
       void (*kern)(BatchArgs) = chunk == 8 ? k_batch_dfg<8> : chunk == 32 ? k_batch_dfg<32> : k_batch_dfg<16>;
       if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max()) != cudaSuccess) {

@@ -223,6 +223,8 @@ static void release_log(pm4g_log *L) {
   free_buf(c, L->cattr);
   free_buf(c, L->uniq);
   free_buf(c, L->dfg);
+  free_buf(c, L->gkey);
+  free_buf(c, L->ekey);
   free_buf(c, L->ends);
   free_buf(c, L->span);
   free_buf(c, L->off);
@@ -301,12 +303,14 @@ static SegArgs seg_args(pm4g_log *L, const SegConfig &sc, uint32_t *work, uint32
   a.work = work;
   a.act_s = L->act_s.p;
   a.len = L->len.p;
-  const size_t cells = (size_t)L->A * L->A;
+  const size_t cells = L->gcells;
   a.g.cnt = L->dfg.p;
   a.g.lo = L->dfg.p + cells;
   a.g.hi = L->dfg.p + 2 * cells;
   a.g.mn = L->dfg.p + 3 * cells;
   a.g.mx = L->dfg.p + 4 * cells;
+  a.g.key = L->ghash ? L->gkey.p : nullptr;
+  a.g.mask = L->ghash ? cells - 1 : 0;
   a.g_start = L->ends.p;
   a.g_end = L->ends.p + L->A;
   a.order_flags = L->status.p;  // NULL for a filtered log: its cases are checked
@@ -384,7 +388,20 @@ static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) 
 static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, const uint32_t *err_in = nullptr,
                        uint32_t *err_out = nullptr, const uint32_t *keys = nullptr) {
   Ctx *c = L->ctx;
-  const size_t cells = (size_t)L->A * L->A;
+  // The global edge table: dense over the A * A pairs up to A = 4096 (at most
+  // 670 MB); beyond that, or when a test asks for it, open addressing with
+  // twice as many slots as the log can have distinct pairs (a power of two).
+  L->ghash = L->A > kDenseMaxActivities || c->test_edge_hash;
+  size_t cells = (size_t)L->A * L->A;
+  if (L->ghash) {
+    const uint64_t pairs = std::min<uint64_t>((uint64_t)L->A * (uint64_t)L->A, (uint64_t)std::max<int64_t>(L->n, 1));
+    uint64_t T = 4096;
+    while (T < 2 * pairs) T <<= 1;
+    cells = T;
+    PM4G_TRY(alloc_buf(c, L->gkey, cells));
+    PM4G_CK(cudaMemsetAsync(L->gkey.p, 0, cells * sizeof(unsigned long long), c->stream));
+  }
+  L->gcells = cells;
   PM4G_TRY(alloc_buf(c, L->act_s, L->n));
   if (!L->len.p) PM4G_TRY(alloc_buf(c, L->len, L->R));
   PM4G_TRY(alloc_buf(c, L->dfg, 5 * cells));
@@ -424,7 +441,8 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   a.attr_in = attr_in;
   a.cattr = write_cattr ? L->cattr.p : nullptr;
   a.err = ctr + 2;
-  if (keys && L->status.p && c->test_bucket_cap == 0 && sc.cap >= 32) {
+  a.g.err = ctr + 2;
+  if (keys && L->status.p && c->test_bucket_cap == 0 && sc.cap >= 32 && !L->ghash && L->A <= 2048) {
     // time-ordered logs: the streaming pass (it returns at once otherwise,
     // and the sorting pass below then does the work)
     const int w = stream_segment_warps(L->clb, sc.a_s, (size_t)c->smem_optin);
@@ -468,6 +486,10 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   if (err_out) *err_out = h.err[0];
   if (h.ctr[2] & 1u) {
     set_error("internal: case lengths counted by the partition disagree with the bucketed records");
+    return PM4G_ECUDA;
+  }
+  if (h.ctr[2] & 2u) {
+    set_error("internal: the hashed edge table is full");
     return PM4G_ECUDA;
   }
   const uint32_t n_ovf = h.ctr[1];
@@ -615,6 +637,10 @@ int pm4g_ctx_set_option(pm4g_ctx *c, int option, int64_t value) {
       if (value != 0 && (value < 32 || value > 65535)) break;
       c->test_bucket_cap = (int)value;
       return PM4G_OK;
+    case PM4G_OPT_TEST_EDGE_HASH:
+      if (value < 0 || value > 1) break;
+      c->test_edge_hash = (int)value;
+      return PM4G_OK;
     default:
       break;
   }
@@ -672,8 +698,8 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
     set_error("pm4g_load_log: n_events %lld outside [0, 2^31-1]", (long long)n);
     return PM4G_EINVAL;
   }
-  if (A < 1 || A > 2048) {
-    set_error("pm4g_load_log: n_activities %d outside [1, 2048]", A);
+  if (A < 1 || A > kMaxActivities) {
+    set_error("pm4g_load_log: n_activities %d outside [1, %d]", A, kMaxActivities);
     return PM4G_EINVAL;
   }
   if (flags != PM4G_HOST_PTRS && flags != PM4G_DEVICE_PTRS) {
@@ -1092,34 +1118,93 @@ int pm4g::ensure_offsets(pm4g_log *L) {
 // ---------------------------------------------------------------------------
 // DFG / endpoints
 // ---------------------------------------------------------------------------
-static int ensure_edges(pm4g_log *L) {
-  if (L->edges_ready) return PM4G_OK;
+int pm4g::hashed_edges(pm4g_log *L, Scratch &S, uint32_t *&keys, uint32_t *&slots, uint32_t &E) {
   Ctx *c = L->ctx;
-  const int64_t cells = (int64_t)L->A * L->A;
-  const uint32_t A = (uint32_t)L->A;
-  Scratch S(c);
-  uint32_t *flags = S.get<uint32_t>(cells), *pos = S.get<uint32_t>(cells + 1);
-  unsigned long long *freq = S.get<unsigned long long>(A);
-  if (!flags || !pos || !freq) {
+  const uint64_t T = L->gcells;
+  uint32_t *flags = S.get<uint32_t>(T), *pos = S.get<uint32_t>(T + 1);
+  if (!flags || !pos) {
     set_error("dfg: out of device memory");
     return PM4G_ENOMEM;
   }
-  const unsigned long long *g = L->dfg.p;
+  const unsigned gT = grid_for((int64_t)T, 256, 65535);
   {
     KTime t(c, "dfg");
-    k_dfg_flags<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(g, cells, flags);
-    PM4G_TRY(check_launch(c, "k_dfg_flags"));
+    k_gkey_flags<<<gT, 256, 0, c->stream>>>(L->gkey.p, T, flags);
+    PM4G_TRY(check_launch(c, "k_gkey_flags"));
   }
-  PM4G_TRY(scan_u32(c, flags, pos, cells));
-  uint32_t E = 0;
-  PM4G_TRY(d2h(c, &E, pos + cells, 4));
-  int32_t *src = S.get<int32_t>(E), *dst = S.get<int32_t>(E);
-  unsigned long long *o[5];
-  for (auto &p : o) p = S.get<unsigned long long>(E);
-  double *mean = S.get<double>(E);
-  if (!src || !dst || !o[0] || !o[1] || !o[2] || !o[3] || !o[4] || !mean) return PM4G_ENOMEM;
-  DfgTable t{L->dfg.p, L->dfg.p + cells, L->dfg.p + 2 * cells, L->dfg.p + 3 * cells, L->dfg.p + 4 * cells};
+  PM4G_TRY(scan_u32(c, flags, pos, (int64_t)T));
+  E = 0;
+  PM4G_TRY(d2h(c, &E, pos + T, 4));
+  keys = S.get<uint32_t>(E);
+  slots = S.get<uint32_t>(E);
+  uint32_t *k2 = S.get<uint32_t>(E), *v2 = S.get<uint32_t>(E);
+  if (!keys || !slots || !k2 || !v2) {
+    set_error("dfg: out of device memory");
+    return PM4G_ENOMEM;
+  }
   {
+    KTime t(c, "dfg");
+    k_gkey_compact<<<gT, 256, 0, c->stream>>>(L->gkey.p, T, flags, pos, keys, slots);
+    PM4G_TRY(check_launch(c, "k_gkey_compact"));
+  }
+  const int kb = std::max(1, bits_for((uint64_t)L->A * (uint64_t)L->A - 1));
+  if (E > 1) PM4G_TRY(radix_sort_u32(c, keys, slots, k2, v2, E, 0, kb));
+  return PM4G_OK;
+}
+
+static int ensure_edges(pm4g_log *L) {
+  if (L->edges_ready) return PM4G_OK;
+  Ctx *c = L->ctx;
+  const int64_t cells = (int64_t)L->gcells;
+  const uint32_t A = (uint32_t)L->A;
+  Scratch S(c);
+  unsigned long long *freq = S.get<unsigned long long>(A);
+  if (!freq) {
+    set_error("dfg: out of device memory");
+    return PM4G_ENOMEM;
+  }
+  DfgTable t{L->dfg.p, L->dfg.p + cells, L->dfg.p + 2 * cells, L->dfg.p + 3 * cells, L->dfg.p + 4 * cells};
+  uint32_t E = 0;
+  int32_t *src = nullptr, *dst = nullptr;
+  unsigned long long *o[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *mean = nullptr;
+  auto alloc_out = [&]() {
+    src = S.get<int32_t>(E);
+    dst = S.get<int32_t>(E);
+    for (auto &p : o) p = S.get<unsigned long long>(E);
+    mean = S.get<double>(E);
+    return src && dst && o[0] && o[1] && o[2] && o[3] && o[4] && mean;
+  };
+  if (L->ghash) {
+    // the occupied slots in (src, dst) order; frequencies from the edges
+    uint32_t *keys = nullptr, *slots = nullptr;
+    PM4G_TRY(hashed_edges(L, S, keys, slots, E));
+    if (!alloc_out()) return PM4G_ENOMEM;
+    KTime tk(c, "dfg");
+    PM4G_CK(cudaMemsetAsync(freq, 0, (size_t)A * sizeof(unsigned long long), c->stream));
+    if (E) {
+      k_dfg_gather<<<grid_for(E, 256, 4096), 256, 0, c->stream>>>(t, keys, slots, E, A, src, dst, o[0], o[1], o[2],
+                                                                   o[3], o[4], mean);
+      PM4G_TRY(check_launch(c, "k_dfg_gather"));
+      k_freq_edges<<<grid_for(E, 256, 4096), 256, 0, c->stream>>>(src, o[0], E, freq);
+      PM4G_TRY(check_launch(c, "k_freq_edges"));
+    }
+    k_freq_end<<<grid_for(A, 256, 4096), 256, 0, c->stream>>>(L->ends.p + A, A, freq);
+    PM4G_TRY(check_launch(c, "k_freq_end"));
+  } else {
+    uint32_t *flags = S.get<uint32_t>(cells), *pos = S.get<uint32_t>(cells + 1);
+    if (!flags || !pos) {
+      set_error("dfg: out of device memory");
+      return PM4G_ENOMEM;
+    }
+    {
+      KTime tk(c, "dfg");
+      k_dfg_flags<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(L->dfg.p, cells, flags);
+      PM4G_TRY(check_launch(c, "k_dfg_flags"));
+    }
+    PM4G_TRY(scan_u32(c, flags, pos, cells));
+    PM4G_TRY(d2h(c, &E, pos + cells, 4));
+    if (!alloc_out()) return PM4G_ENOMEM;
     KTime tk(c, "dfg");
     k_dfg_compact<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(t, cells, A, flags, pos, src, dst, o[0], o[1],
                                                                      o[2], o[3], o[4], mean);

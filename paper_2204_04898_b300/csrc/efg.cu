@@ -281,6 +281,12 @@ int pm4g_efg(pm4g_log *L, pm4g_efg_t *out) {
   cudaMemGetInfo(&fr, &tot);
   const uint64_t table_bytes = 48 * cells;
   const uint64_t budget = std::min<uint64_t>(8ull << 30, fr / 8);
+  // the dense A x A table must fit at least once (large alphabets)
+  if (table_bytes > std::max<uint64_t>(budget, fr / 2)) {
+    set_error("pm4g_efg: the %d x %d activity-pair table (%llu bytes) does not fit the device", (int)A, (int)A,
+              (unsigned long long)table_bytes);
+    return PM4G_ENOMEM;
+  }
   // (and one copy per 2^17 events, so a small log does not clear and fold
   // gigabytes of copies)
   const uint64_t by_work = std::max<uint64_t>(1, (uint64_t)L->n >> 17);

@@ -18,6 +18,11 @@
 
 namespace pm4g {
 
+// Activity alphabets: codes fit 16 bits of a bucketed record; the global edge
+// table is dense over the A * A pairs up to kDenseMaxActivities.
+constexpr int32_t kMaxActivities = 65536;
+constexpr int32_t kDenseMaxActivities = 4096;
+
 void set_error(const char *fmt, ...);
 
 #define PM4G_CK(call)                                                                  \
@@ -54,6 +59,7 @@ struct Ctx {
   int timing = 0;  // PM4G_OPT_TIMING: 0 off, 1 every launch, 2 the dominant kernels
   int test_hash_bits = 0;
   int test_bucket_cap = 0;
+  int test_edge_hash = 0;  // 1: the hashed global edge table at any alphabet size
   // launch choices of the batched drill-down (PM4G_OPT_BATCH_*; 0 = default)
   int batch_chunk = 0;
   int batch_stages = 0;
@@ -218,6 +224,9 @@ namespace pm4g {
 // (any may be NULL), and the per-slot case offsets L->off.
 int run_export(pm4g_log *L, int32_t *ec, int32_t *ea, int64_t *et, int64_t *er);
 int ensure_offsets(pm4g_log *L);
+// The edges of a hashed global table: their keys (src * A + dst), ascending,
+// and slot indices, in arrays of the scope S.
+int hashed_edges(pm4g_log *L, Scratch &S, uint32_t *&keys, uint32_t *&slots, uint32_t &E);
 
 
 // ---- primitives (prims.cu) ----
@@ -267,7 +276,13 @@ struct pm4g_log {
   pm4g::DBuf<uint32_t> len;
   pm4g::DBuf<int32_t> cattr;
   pm4g::DBuf<int32_t> uniq;  // sorted distinct case ids when renumbered
-  pm4g::DBuf<unsigned long long> dfg;  // 5 * A * A: cnt, lo, hi, min, max
+  // global edge table: 5 arrays of gcells cells (cnt, lo, hi, min, max),
+  // dense over the A * A pairs, or (ghash) open addressing whose keys
+  // (key + 1, 0 = empty) are in gkey
+  pm4g::DBuf<unsigned long long> dfg;
+  uint64_t gcells = 0;
+  bool ghash = false;
+  pm4g::DBuf<unsigned long long> gkey;
   pm4g::DBuf<unsigned long long> ends; // 2 * A: start, end
   // one device word: bit 0 an activity outside [0, A) was seen; bit 1 the
   // bucketed records of a case may not be in (timestamp, row) order (clear
@@ -299,6 +314,7 @@ struct pm4g_log {
   std::vector<uint32_t> attr_ev;  // events before that entry
   pm4g::DBuf<uint32_t> emap;      // A * A: edge index of a directly-follows pair, or ~0
   pm4g::DBuf<int32_t> e_pair;     // 2 * E: src and dst of every edge, (src, dst) order
+  pm4g::DBuf<uint32_t> ekey;      // E: src * A + dst of every edge, ascending (hashed table only)
   uint32_t n_edges = 0;
 };
 

@@ -77,9 +77,15 @@ __global__ void k_case_heads(const uint32_t *keys, int64_t n, uint32_t *head);
 __global__ void k_case_dense(const uint32_t *keys, const uint32_t *rows, const uint32_t *head,
                              const uint32_t *head_excl, int64_t n, int32_t *dense, int32_t *uniq);
 
-// Global DFG table: dense over A*A cells.
+// Global DFG table: dense over the A*A cells (key = src*A + dst indexes it),
+// or, when key is set, open addressing over mask + 1 slots whose key array
+// holds key + 1 (0 marks an empty slot); err (hashed only) gets bit 0 if a
+// pair finds the table full.
 struct DfgTable {
   unsigned long long *cnt, *lo, *hi, *mn, *mx;
+  unsigned long long *key = nullptr;
+  uint64_t mask = 0;
+  uint32_t *err = nullptr;
 };
 
 struct SegArgs {
@@ -271,5 +277,13 @@ __global__ void k_dfg_compact(DfgTable g, int64_t cells, uint32_t n_act, const u
                               unsigned long long *mx, double *mean);
 __global__ void k_freq(const unsigned long long *cnt, const unsigned long long *end, uint32_t n_act,
                        unsigned long long *freq);
+__global__ void k_gkey_flags(const unsigned long long *gkey, uint64_t T, uint32_t *flags);
+__global__ void k_gkey_compact(const unsigned long long *gkey, uint64_t T, const uint32_t *flags, const uint32_t *pos,
+                               uint32_t *keys, uint32_t *slots);
+__global__ void k_dfg_gather(DfgTable g, const uint32_t *keys, const uint32_t *slots, uint32_t E, uint32_t n_act,
+                             int32_t *src, int32_t *dst, unsigned long long *cnt, unsigned long long *lo,
+                             unsigned long long *hi, unsigned long long *mn, unsigned long long *mx, double *mean);
+__global__ void k_freq_edges(const int32_t *src, const unsigned long long *cnt, uint32_t E, unsigned long long *freq);
+__global__ void k_freq_end(const unsigned long long *end, uint32_t n_act, unsigned long long *freq);
 
 }  // namespace pm4g

@@ -50,9 +50,7 @@ struct GlobalSink {
   const SegArgs *a;
   uint64_t slot_base;
   __device__ __forceinline__ void edge_group(uint32_t key, uint32_t cnt, u128 sum, uint64_t mn, uint64_t mx) {
-    global_edge_group(a->g, key, cnt, (uint64_t)sum, (uint64_t)(sum >> 64));
-    red_min_u64(&a->g.mn[key], mn);
-    red_max_u64(&a->g.mx[key], mx);
+    global_edge_add(a->g, key, cnt, (uint64_t)sum, (uint64_t)(sum >> 64), mn, mx);
   }
   __device__ __forceinline__ void start(uint32_t act) { atomicAdd(&a->g_start[act], 1ull); }
   __device__ __forceinline__ void end(uint32_t act) { atomicAdd(&a->g_end[act], 1ull); }

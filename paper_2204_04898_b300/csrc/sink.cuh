@@ -11,16 +11,52 @@ namespace pm4g {
 
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 
-__device__ __forceinline__ void global_sum(const DfgTable &g, uint32_t key, uint64_t lo, uint64_t hi) {
-  const unsigned long long old = atomicAdd(&g.lo[key], (unsigned long long)lo);
-  const unsigned long long h2 = hi + (old + lo < old ? 1ull : 0ull);
-  if (h2) red_add_u64(&g.hi[key], h2);
+// Index of a pair's cell in the global table: the key itself when the table
+// is dense; otherwise the slot holding key + 1, claimed by compare-and-swap
+// when the pair is new (~0 if the table is full, which the host's sizing
+// rules out and the error word reports).
+__device__ __forceinline__ uint64_t g_index(const DfgTable &g, uint32_t key) {
+  if (!g.key) return key;
+  const unsigned long long k1 = (unsigned long long)key + 1ull;
+  uint64_t h = fmix64(k1) & g.mask;
+  for (uint64_t it = 0; it <= g.mask; ++it) {
+    const unsigned long long k = *(volatile unsigned long long *)&g.key[h];
+    if (k == k1) return h;
+    if (k == 0) {
+      const unsigned long long old = atomicCAS(&g.key[h], 0ull, k1);
+      if (old == 0 || old == k1) return h;
+    }
+    h = (h + 1) & g.mask;
+  }
+  atomicOr(g.err, 1u);
+  return ~0ull;
 }
 
+__device__ __forceinline__ void global_sum_at(const DfgTable &g, uint64_t i, uint64_t lo, uint64_t hi) {
+  const unsigned long long old = atomicAdd(&g.lo[i], (unsigned long long)lo);
+  const unsigned long long h2 = hi + (old + lo < old ? 1ull : 0ull);
+  if (h2) red_add_u64(&g.hi[i], h2);
+}
+
+// Adds cnt pairs with exact sum (hi:lo) and extremes mn, mx to the pair's cell.
+__device__ __forceinline__ void global_edge_add(const DfgTable &g, uint32_t key, uint32_t cnt, uint64_t lo,
+                                                uint64_t hi, uint64_t mn, uint64_t mx) {
+  const uint64_t i = g_index(g, key);
+  if (i == ~0ull) return;
+  red_add_u64(&g.cnt[i], cnt);
+  global_sum_at(g, i, lo, hi);
+  red_min_u64(&g.mn[i], mn);
+  red_max_u64(&g.mx[i], mx);
+}
+
+// The same without extremes (a shared table's flush: its extremes were pushed
+// as they came).
 __device__ __forceinline__ void global_edge_group(const DfgTable &g, uint32_t key, uint32_t cnt, uint64_t lo,
                                                   uint64_t hi) {
-  atomicAdd(&g.cnt[key], (unsigned long long)cnt);
-  global_sum(g, key, lo, hi);
+  const uint64_t i = g_index(g, key);
+  if (i == ~0ull) return;
+  red_add_u64(&g.cnt[i], cnt);
+  global_sum_at(g, i, lo, hi);
 }
 
 struct SmemSink {
@@ -36,6 +72,7 @@ struct SmemSink {
 
   __device__ __forceinline__ int find(uint32_t key) {
     if (mode == 0) return (int)key;
+    if (key == kEmptyKey) return -1;  // the pair (65535, 65535) of a 65,536-activity log: global table
     uint32_t h = (key * 0x9E3779B1u) >> shift;
     for (int it = 0; it < probes; ++it) {
       const uint32_t k = *(volatile uint32_t *)&tkey[h];
@@ -66,21 +103,22 @@ struct SmemSink {
         const uint32_t old_m = atomicAdd(&tm[s], (uint32_t)madd);
         if (old_m + (uint32_t)madd < old_m) top += 1;
       }
-      if (top) red_add_u64(&g.hi[key], top);
       // extremes pushed (fire-and-forget) only when the float guards of what
       // this block already pushed allow them to improve
-      if (__float_as_uint(__ull2float_rd(mn)) < *(volatile uint32_t *)&tminh[s]) {
-        atomicMin(&tminh[s], guard_up(mn));
-        red_min_u64(&g.mn[key], mn);
-      }
-      if (__float_as_uint(__ull2float_ru(mx)) > *(volatile uint32_t *)&tmaxh[s]) {
-        atomicMax(&tmaxh[s], guard_down(mx));
-        red_max_u64(&g.mx[key], mx);
+      const bool pmn = __float_as_uint(__ull2float_rd(mn)) < *(volatile uint32_t *)&tminh[s];
+      const bool pmx = __float_as_uint(__ull2float_ru(mx)) > *(volatile uint32_t *)&tmaxh[s];
+      if (top || pmn || pmx) {
+        const uint64_t i = g_index(g, key);
+        if (i != ~0ull) {
+          if (top) red_add_u64(&g.hi[i], top);
+          if (pmn) red_min_u64(&g.mn[i], mn);
+          if (pmx) red_max_u64(&g.mx[i], mx);
+        }
+        if (pmn) atomicMin(&tminh[s], guard_up(mn));
+        if (pmx) atomicMax(&tmaxh[s], guard_down(mx));
       }
     } else {
-      global_edge_group(g, key, cnt, lo64, top);
-      red_min_u64(&g.mn[key], mn);
-      red_max_u64(&g.mx[key], mx);
+      global_edge_add(g, key, cnt, lo64, top, mn, mx);
     }
   }
   __device__ __forceinline__ void start(uint32_t act) {

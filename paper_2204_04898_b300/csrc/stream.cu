@@ -101,19 +101,20 @@ struct EdgeTable {
       const uint32_t hm = h + (ol + l < ol ? 1u : 0u);  // wraps to 0 only for h = 2^32 - 1 with a carry
       const uint32_t om = atomicAdd(&tm[e], hm);
       const uint32_t top = (om + hm < om ? 1u : 0u) + (hm < h ? 1u : 0u);
-      if (top) red_add_u64(&g.hi[key], top);
-      if (__float_as_uint(__ull2float_rd(d)) < tminh[e]) {
-        atomicMin(&tminh[e], guard_up(d));
-        red_min_u64(&g.mn[key], d);
-      }
-      if (__float_as_uint(__ull2float_ru(d)) > tmaxh[e]) {
-        atomicMax(&tmaxh[e], guard_down(d));
-        red_max_u64(&g.mx[key], d);
+      const bool pmn = __float_as_uint(__ull2float_rd(d)) < tminh[e];
+      const bool pmx = __float_as_uint(__ull2float_ru(d)) > tmaxh[e];
+      if (top || pmn || pmx) {
+        const uint64_t i = g_index(g, key);
+        if (i != ~0ull) {
+          if (top) red_add_u64(&g.hi[i], top);
+          if (pmn) red_min_u64(&g.mn[i], d);
+          if (pmx) red_max_u64(&g.mx[i], d);
+        }
+        if (pmn) atomicMin(&tminh[e], guard_up(d));
+        if (pmx) atomicMax(&tmaxh[e], guard_down(d));
       }
     } else {
-      global_edge_group(g, key, 1, d, 0);
-      red_min_u64(&g.mn[key], d);
-      red_max_u64(&g.mx[key], d);
+      global_edge_add(g, key, 1, d, 0, d, d);
     }
   }
 };

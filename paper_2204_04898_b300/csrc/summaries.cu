@@ -43,6 +43,51 @@ __global__ void k_dfg_compact(DfgTable g, int64_t cells, uint32_t n_act, const u
   }
 }
 
+// ---- hashed global table (large alphabets) ----
+__global__ void k_gkey_flags(const unsigned long long *__restrict__ gkey, uint64_t T, uint32_t *__restrict__ flags) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += (uint64_t)gridDim.x * blockDim.x)
+    flags[i] = gkey[i] ? 1u : 0u;
+}
+// The occupied slots' keys (src * A + dst) and slot indices, in slot order.
+__global__ void k_gkey_compact(const unsigned long long *__restrict__ gkey, uint64_t T,
+                               const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos,
+                               uint32_t *__restrict__ keys, uint32_t *__restrict__ slots) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (!flags[i]) continue;
+    const uint32_t p = pos[i];
+    keys[p] = (uint32_t)(gkey[i] - 1ull);
+    slots[p] = (uint32_t)i;
+  }
+}
+// Edge p (keys ascending) from its slot, with the mean as for the dense table.
+__global__ void k_dfg_gather(DfgTable g, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ slots,
+                             uint32_t E, uint32_t n_act, int32_t *src, int32_t *dst, unsigned long long *cnt,
+                             unsigned long long *lo, unsigned long long *hi, unsigned long long *mn,
+                             unsigned long long *mx, double *mean) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < E; p += gridDim.x * blockDim.x) {
+    const uint32_t k = keys[p], i = slots[p];
+    const unsigned long long c = g.cnt[i], l = g.lo[i], h = g.hi[i];
+    src[p] = (int32_t)(k / n_act);
+    dst[p] = (int32_t)(k % n_act);
+    cnt[p] = c;
+    lo[p] = l;
+    hi[p] = h;
+    mn[p] = g.mn[i];
+    mx[p] = g.mx[i];
+    mean[p] = edge_mean(h, l, c);
+  }
+}
+// Activity frequency from the listed edges: out-edges of each activity, plus
+// its end count.
+__global__ void k_freq_edges(const int32_t *__restrict__ src, const unsigned long long *__restrict__ cnt, uint32_t E,
+                             unsigned long long *freq) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < E; p += gridDim.x * blockDim.x)
+    atomicAdd(&freq[src[p]], cnt[p]);
+}
+__global__ void k_freq_end(const unsigned long long *__restrict__ end, uint32_t n_act, unsigned long long *freq) {
+  for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n_act; a += gridDim.x * blockDim.x) freq[a] += end[a];
+}
+
 // Activity frequency: every event is either followed by another event of its
 // case (one out-edge) or is its case's last event, so freq(a) = sum over b of
 // count(a, b) + end(a).

@@ -23,6 +23,8 @@ VARIANTS_CASES = 0x1
 TW_NONE, TW_EVENTS, TW_CASES_CONTAINED, TW_CASES_INTERSECTING = 0, 1, 2, 3
 OPT_TIMING, OPT_TEST_HASH_BITS, OPT_TEST_BUCKET_CAP = 1, 2, 3
 OPT_BATCH_CHUNK, OPT_BATCH_STAGES, OPT_BATCH_ITEMS_PER_SM = 4, 5, 6
+OPT_TEST_EDGE_HASH = 7
+MAX_ACTIVITIES = 65536
 
 _P = ctypes.c_void_p
 _i32, _i64, _u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32

@@ -85,8 +85,18 @@ class GpuEngine:
 
     @staticmethod
     def upload_bytes(n_events: int, n_activities: int) -> int:
-        # input columns, two record buffers, activity sequence and per-case arrays
-        return int(n_events) * 80 + int(n_activities) ** 2 * 40 + (64 << 20)
+        # input columns, two record buffers, activity sequence and per-case
+        # arrays, and the global edge table: dense (40 B a pair) up to 4096
+        # activities, else hashed (48 B a slot, twice the possible pairs)
+        n, A = int(n_events), int(n_activities)
+        if A <= 4096:
+            table = A * A * 40
+        else:
+            slots = 4096
+            while slots < 2 * max(1, min(A * A, n)):
+                slots <<= 1
+            table = slots * 48
+        return n * 80 + table + (64 << 20)
 
     def batch_dfg(self, reqs: list[Request]) -> list[dict]:
         pm4g = self.pm4g
