@@ -76,8 +76,15 @@ extern "C" {
                                         global-memory path; 0 = default */
 /* Launch choices of pm4g_batch_dfg (0 = default; results never depend on them;
  * an autotuner picks them by timing, see paper_2204_04898_b300/autotune.py): */
-#define PM4G_OPT_TEST_EDGE_HASH 7     /* test only: 1 = the hashed global edge table (the one used
-                                        above 4096 activities) for every log loaded afterwards */
+/* Launch choices of pm4g_load_log's single-log pass (results never depend on
+ * them; 0 = the library's default; set by the autotuner): */
+#define PM4G_OPT_EDGE_TABLE 7         /* global edge table: 0 = dense up to 4096 activities,
+                                        hashed above; 1 = hashed at any alphabet size */
+#define PM4G_OPT_LOAD_CLB 8           /* log2 of the case slots of a bucket, 1..8 */
+#define PM4G_OPT_LOAD_SPLITS 9        /* units each coarse bucket's second partition level is
+                                        cut into, 1..64 */
+#define PM4G_OPT_STREAM_WARPS 10      /* warps per block of the streaming segment pass, 1..24 */
+#define PM4G_OPT_STREAM_OFF 11        /* 1 = the sorting segment pass for time-ordered logs too */
 #define PM4G_OPT_BATCH_CHUNK 4       /* cases a warp takes at once: 8, 16 (default) or 32 */
 #define PM4G_OPT_BATCH_STAGES 5      /* groups a batch of >= 64 views into caller-owned
                                         arrays is pipelined in: 1..16 (default 4) */

@@ -391,7 +391,7 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   // The global edge table: dense over the A * A pairs up to A = 4096 (at most
   // 670 MB); beyond that, or when a test asks for it, open addressing with
   // twice as many slots as the log can have distinct pairs (a power of two).
-  L->ghash = L->A > kDenseMaxActivities || c->test_edge_hash;
+  L->ghash = L->A > kDenseMaxActivities || c->edge_table == 1;
   size_t cells = (size_t)L->A * L->A;
   if (L->ghash) {
     const uint64_t pairs = std::min<uint64_t>((uint64_t)L->A * (uint64_t)L->A, (uint64_t)std::max<int64_t>(L->n, 1));
@@ -442,10 +442,12 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   a.cattr = write_cattr ? L->cattr.p : nullptr;
   a.err = ctr + 2;
   a.g.err = ctr + 2;
-  if (keys && L->status.p && c->test_bucket_cap == 0 && sc.cap >= 32 && !L->ghash && L->A <= 2048) {
+  if (keys && L->status.p && c->test_bucket_cap == 0 && sc.cap >= 32 && !L->ghash && L->A <= 2048 &&
+      !c->stream_off) {
     // time-ordered logs: the streaming pass (it returns at once otherwise,
     // and the sorting pass below then does the work)
-    const int w = stream_segment_warps(L->clb, sc.a_s, (size_t)c->smem_optin);
+    int w = stream_segment_warps(L->clb, sc.a_s, (size_t)c->smem_optin);
+    if (c->stream_warps > 0) w = std::min(w, c->stream_warps);
     const size_t cells = (size_t)L->A * L->A;
     uint32_t *emap = w > 0 ? S.get<uint32_t>(cells) : nullptr;
     uint32_t *key_of = w > 0 ? S.get<uint32_t>(kStSlots) : nullptr;
@@ -509,6 +511,7 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
 // Chooses the bucket width (2^clb case slots) so that a bucket's expected
 // events stay well inside the on-chip capacity.
 static int choose_clb(Ctx *c, int64_t n, uint64_t R, int32_t A, int act_bits) {
+  if (c->load_clb > 0) return std::min(c->load_clb, 32 - act_bits);  // a launch choice (autotuner)
   const double avg = (double)n / (double)std::max<uint64_t>(R, 1);
   int best = 0;
   for (int clb = 8; clb >= 0; --clb) {  // per-warp case counts hold at most 256 slots
@@ -637,9 +640,25 @@ int pm4g_ctx_set_option(pm4g_ctx *c, int option, int64_t value) {
       if (value != 0 && (value < 32 || value > 65535)) break;
       c->test_bucket_cap = (int)value;
       return PM4G_OK;
-    case PM4G_OPT_TEST_EDGE_HASH:
+    case PM4G_OPT_EDGE_TABLE:
       if (value < 0 || value > 1) break;
-      c->test_edge_hash = (int)value;
+      c->edge_table = (int)value;
+      return PM4G_OK;
+    case PM4G_OPT_LOAD_CLB:
+      if (value < 0 || value > 8) break;
+      c->load_clb = (int)value;
+      return PM4G_OK;
+    case PM4G_OPT_LOAD_SPLITS:
+      if (value < 0 || value > 64) break;
+      c->load_splits = (int)value;
+      return PM4G_OK;
+    case PM4G_OPT_STREAM_WARPS:
+      if (value < 0 || value > kStMaxThreads / 32) break;
+      c->stream_warps = (int)value;
+      return PM4G_OK;
+    case PM4G_OPT_STREAM_OFF:
+      if (value < 0 || value > 1) break;
+      c->stream_off = (int)value;
       return PM4G_OK;
     default:
       break;
@@ -958,7 +977,8 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           // split coarse buckets at row-chunk boundaries into about four
           // waves of units, so that no short last wave idles most SMs
           pa.splits = (int)std::max<int64_t>(
-              1, std::min<int64_t>(p_ctas, (8 * (int64_t)c->num_sms + nc - 1) / (int64_t)nc));
+              1, std::min<int64_t>(p_ctas, c->load_splits > 0 ? (int64_t)c->load_splits
+                                                              : (8 * (int64_t)c->num_sms + nc - 1) / (int64_t)nc));
           {
             KTime t(c, "partition");
             c->launches++;

@@ -59,7 +59,13 @@ struct Ctx {
   int timing = 0;  // PM4G_OPT_TIMING: 0 off, 1 every launch, 2 the dominant kernels
   int test_hash_bits = 0;
   int test_bucket_cap = 0;
-  int test_edge_hash = 0;  // 1: the hashed global edge table at any alphabet size
+  // launch choices of the single-log pass (PM4G_OPT_EDGE_TABLE, _LOAD_CLB,
+  // _LOAD_SPLITS, _STREAM_WARPS, _STREAM_OFF; 0 = default)
+  int edge_table = 0;
+  int load_clb = 0;
+  int load_splits = 0;
+  int stream_warps = 0;
+  int stream_off = 0;
   // launch choices of the batched drill-down (PM4G_OPT_BATCH_*; 0 = default)
   int batch_chunk = 0;
   int batch_stages = 0;

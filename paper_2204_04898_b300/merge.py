@@ -12,6 +12,10 @@ exactly (Section 3's definitions only ever relate events of the same case):
   (count descending, smallest case id ascending); each case keeps the variant
   of its sequence.
 
+Each shard contributes its full variant table (``pm4g_variants`` with
+top_k = -1): a variant outside one shard's top-k can still rank inside the
+merged top-k, so truncated tables do not merge exactly.
+
 Shards are formed by a hash of the case id (``shard_of``). These functions are
 the exchange and merge step of a multi-GPU run; ``gather_and_merge`` performs
 the exchange over a torch.distributed process group.

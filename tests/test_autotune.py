@@ -68,3 +68,37 @@ def test_signature_groups_close_shapes():
     c = autotune.signature(100_000_000, 4_850_000, 2000, 64, 10_000_000, 1000, "B300")
     d = autotune.signature(100_000_000, 4_850_000, 2000, 4096, 664_000_000, 0, "B300")
     assert a == b and a != c and a != d
+
+
+def test_load_signature_groups_logs_of_about_the_same_shape():
+    a = autotune.load_signature(206_571_951, 10_000_000, 500, True, 1000, "B300")
+    b = autotune.load_signature(200_000_000, 9_500_000, 480, True, 10, "B300")
+    c = autotune.load_signature(206_571_951, 10_000_000, 500, False, 1000, "B300")
+    d = autotune.load_signature(20_000_000, 1_000_000, 500, True, 1000, "B300")
+    assert a == b
+    assert a != c  # row order selects the segment pass
+    assert a != d
+    assert a.startswith("load|") and a != autotune.signature(206_571_951, 10_000_000, 500, 1, 1, 1, "B300")
+
+
+def test_load_space_descent_from_the_defaults():
+    target = {"clb": 7, "splits": 4, "stream_warps": 16, "stream_off": 0, "edge_table": 0}
+
+    def cost(c):
+        return sum((autotune.LOAD_SPACE[k].index(c[k]) - autotune.LOAD_SPACE[k].index(target[k])) ** 2
+                   for k in c) + 2.0
+
+    best, t, trials = autotune.coordinate_descent(cost, autotune.LOAD_SPACE, autotune.LOAD_DEFAULTS)
+    assert best == target and t == 2.0
+    assert trials[0][0] == autotune.LOAD_DEFAULTS  # the defaults are measured first
+    assert set(best) == set(autotune.LOAD_KNOBS)
+
+
+def test_load_choices_are_cached_apart_from_batch_choices(tmp_path):
+    tuner = autotune.Tuner(cache_path=str(tmp_path / "t.json"))
+    sig = autotune.load_signature(20_000_000, 1_000_000, 50, False, 1000, "B300")
+    choice = tuner.tune(sig, lambda c: 1.0 + c["stream_off"] + c["clb"] / 100, autotune.LOAD_SPACE,
+                        autotune.LOAD_DEFAULTS)
+    assert choice["stream_off"] == 0 and choice["clb"] == 0
+    reloaded = autotune.Tuner(cache_path=str(tmp_path / "t.json"))
+    assert reloaded.tune(sig, lambda c: (_ for _ in ()).throw(AssertionError("measured again"))) == choice

@@ -3,7 +3,7 @@
 Up to 4,096 activities the engine aggregates directly-follows pairs into a
 global table dense over the A x A pairs; above that, into an open-addressing
 table keyed by src * A + dst (Section 3: the DFG of large alphabets goes to a
-hashed global table). A test option forces the hashed table at any size, so
+hashed global table). A context option forces the hashed table at any size, so
 both tables are checked on the same logs. All calls go through the C ABI.
 """
 
@@ -84,7 +84,7 @@ def test_forced_hashed_table(pm4g, law):
     L = synth.generate(synth.WORKLOADS[law]().scaled(20000, law))
     ctx = pm4g.pm4g_ctx_create(0)
     try:
-        pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TEST_EDGE_HASH, 1)
+        pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_EDGE_TABLE, 1)
         _parity(pm4g, ctx, L, L.n_activities)
     finally:
         pm4g.pm4g_ctx_destroy(ctx)
