@@ -148,15 +148,19 @@ __device__ __forceinline__ void var_insert_one(const VarArgs &a, uint32_t s, uin
 // First grouping round over all case slots, with the sequence hash (seed 0)
 // formed on the way from the formatted activities. A warp takes 32
 // consecutive case slots, whose events are contiguous in the formatted order,
-// and walks them 32 events at a time, lane-dense: each lane finds its event's
-// case by a shuffle binary search over the slots' length prefix, the terms of
-// a case's lanes (consecutive) are summed with redux.sync over the run, and
-// the run's first lane adds them to the case's per-warp accumulator. Each
-// lane then inserts its own slot.
+// and walks them 32 events at a time, lane-dense. One OR-reduction per window
+// gives the bits of the positions where a (non-empty) case starts; a lane's
+// case is then the number of starts up to its position (a popcount, counted
+// from the cases that started before the window), and the lanes of one case
+// form a run between two start bits, whose terms redux.sync sums for the
+// run's first lane to add to the case's per-warp accumulator. Each lane then
+// inserts its own slot.
 __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
-  __shared__ uint32_t s_acc[kHiThreads / 32][64];  // per warp: low words, then high words, of 32 cases
+  // per warp: low and high hash words, and first position, of up to 32 cases
+  __shared__ uint32_t s_acc[kHiThreads / 32][96];
   const uint32_t lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-  uint32_t *acc = s_acc[wb];
+  uint32_t *acc_lo = s_acc[wb], *acc_hi = acc_lo + 32, *sstart = acc_lo + 64;
+  const uint32_t le = 0xFFFFFFFFu >> (31 - lane), lt = lanemask_lt();
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t s0 = warp * 32; s0 < a.n_slots; s0 += n_warps * 32) {
@@ -171,28 +175,35 @@ __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
     const uint32_t excl = incl - L;
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     const uint32_t off0 = a.off[s0];  // first formatted position of the slots
-    acc[lane] = 0;
-    acc[32 + lane] = 0;
+    const uint32_t rank = __popc(__ballot_sync(kFull, L > 0) & lt);  // among the non-empty slots
+    if (L) {
+      acc_lo[rank] = 0;
+      acc_hi[rank] = 0;
+      sstart[rank] = excl;
+    }
     __syncwarp();
+    uint32_t before = 0;  // non-empty cases that start before the window
     for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+      const uint32_t bit = (L && excl >= p0 && excl - p0 < 32u) ? (1u << (excl - p0)) : 0u;
+      const uint32_t starts = __reduce_or_sync(kFull, bit);
+      const uint32_t M = starts | (total - p0 < 32u ? (1u << (total - p0)) : 0u);  // the end closes the last run
       const uint32_t p = p0 + lane;
       const bool valid = p < total;
-      // the case of position p: the number of slots whose events end at or before p
-      uint32_t c = 0;
-#pragma unroll
-      for (uint32_t step = 16; step >= 1; step >>= 1)
-        if (__shfl_sync(kFull, incl, c + step - 1) <= p) c += step;
-      const uint32_t k = p - __shfl_sync(kFull, excl, c & 31);
-      const uint64_t t = valid ? event_hash((uint32_t)a.act_s[off0 + p], k, 0) : 0ull;
-      const uint32_t rm = run_mask(valid ? c : 32u);
+      const uint32_t cr = valid ? before + __popc(starts & le) - 1 : 0u;  // the case's rank
+      uint64_t t = 0;
+      if (valid) t = event_hash((uint32_t)a.act_s[off0 + p], p - sstart[cr], 0);
+      const uint32_t hb = M & le, gt = M & ~le;
+      const uint32_t head = hb ? 31 - __clz(hb) : 0u;
+      const uint32_t rm = (gt ? ((1u << (__ffs(gt) - 1)) - 1) : 0xFFFFFFFFu) & ~((1u << head) - 1);
       const uint32_t sl = __reduce_add_sync(rm, (uint32_t)t), sh = __reduce_add_sync(rm, (uint32_t)(t >> 32));
-      if (valid && lane == (uint32_t)(__ffs(rm) - 1)) {  // the run's first lane; each case has one run per step
-        acc[c] += sl;
-        acc[32 + c] += sh;
+      if (valid && lane == head) {  // the run's first lane; each case has one run per window
+        acc_lo[cr] += sl;
+        acc_hi[cr] += sh;
       }
+      before += __popc(starts);
       __syncwarp();
     }
-    if (L) var_insert_one(a, (uint32_t)s, L, ((uint64_t)acc[32 + lane] << 32) | acc[lane], 0);
+    if (L) var_insert_one(a, (uint32_t)s, L, ((uint64_t)acc_hi[rank] << 32) | acc_lo[rank], 0);
     __syncwarp();
   }
 }
