@@ -53,7 +53,7 @@ LOAD_KNOBS = {
     "edge_table": _pm4g.OPT_EDGE_TABLE,
 }
 LOAD_DEFAULTS = {"clb": 0, "splits": 0, "stream_warps": 0, "stream_off": 0, "edge_table": 0}
-LOAD_SPACE = {"clb": (0, 6, 7, 8), "splits": (0, 2, 4, 8, 16), "stream_warps": (0, 12, 16, 20),
+LOAD_SPACE = {"clb": (0, 6, 7, 8), "splits": (0, 2, 4, 8, 16), "stream_warps": (0, 12, 16, 24),
               "stream_off": (0, 1), "edge_table": (0, 1)}
 
 

@@ -133,7 +133,7 @@ struct SegArgs {
 // words of the pushed minimum and maximum), the endpoint counts, then per
 // warp the case state of its bucket (last timestamp, first position, events
 // seen, last activity: 20 bytes per case slot).
-constexpr int kStMaxThreads = 768;
+constexpr int kStMaxThreads = 1024;
 constexpr int kStSlots = 4096;
 struct StSmem {
   size_t tcnt, st, warp0, per_warp, total;
