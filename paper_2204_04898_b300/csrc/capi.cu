@@ -313,7 +313,7 @@ static SegArgs seg_args(pm4g_log *L, const SegConfig &sc, uint32_t *work, uint32
   a.g.mask = L->ghash ? cells - 1 : 0;
   a.g_start = L->ends.p;
   a.g_end = L->ends.p + L->A;
-  a.order_flags = L->status.p;  // NULL for a filtered log: its cases are checked
+  a.order_flags = L->status.p;  // a filtered log carries the word of the log it comes from
   a.ovf = ovf;
   a.n_ovf = n_ovf;
   a.n_cases = n_cases;
@@ -1694,12 +1694,25 @@ static int extract_sublog(pm4g_log *L, FilterArgs fa, pm4g_log **out) {
     F->n = nsub;
     if ((st = alloc_buf(c, F->rec, nsub))) break;
     fa.out = F->rec.p;
+    // A sub-log keeps each bucket's records in the order of the log it comes
+    // from, so it is time-ordered when that log is: it then takes the
+    // streaming segment pass, which counts cases from the key words.
+    uint32_t *keys = nullptr;
+    if (L->status.p) {
+      if ((st = alloc_buf(c, F->status, 1))) break;
+      if (cudaMemcpyAsync(F->status.p, L->status.p, 4, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+        st = PM4G_ECUDA;
+        break;
+      }
+      keys = S.get<uint32_t>(nsub);  // NULL (no streaming pass) if memory is short
+    }
+    fa.keys_out = keys;
     {
       KTime t(c, "filter");
       k_filter_write<<<gb, 256, 0, c->stream>>>(fa);
       if ((st = check_launch(c, "k_filter_write"))) break;
     }
-    st = run_segment(F, nullptr, false);
+    st = run_segment(F, nullptr, false, nullptr, nullptr, keys);
   } while (0);
   if (st != PM4G_OK) {
     if (st == PM4G_ENOMEM) set_error("filter: out of device memory");

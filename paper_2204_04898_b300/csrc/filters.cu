@@ -110,7 +110,11 @@ __global__ void __launch_bounds__(256) k_filter_write(FilterArgs a) {
     const uint32_t kept = a.new_off[b + 1] - out;
     if (kept == 0) continue;  // nothing of this bucket is kept
     if (kept == hi - lo) {    // all of it: a straight copy
-      for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) a.out[out + (i - lo)] = a.rec[i];
+      for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint4 r = a.rec[i];
+        a.out[out + (i - lo)] = r;
+        if (a.keys_out) a.keys_out[out + (i - lo)] = r.x;
+      }
       continue;
     }
     for (uint32_t t0 = lo; t0 < hi; t0 += blockDim.x) {
@@ -123,7 +127,10 @@ __global__ void __launch_bounds__(256) k_filter_write(FilterArgs a) {
       }
       uint32_t tot;
       const uint32_t pre = block_exclusive_scan<256>(keep ? 1u : 0u, s_warp, tot);
-      if (keep) a.out[out + pre] = r;
+      if (keep) {
+        a.out[out + pre] = r;
+        if (a.keys_out) a.keys_out[out + pre] = r.x;
+      }
       out += tot;
     }
   }

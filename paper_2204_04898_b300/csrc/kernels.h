@@ -242,6 +242,7 @@ struct FilterArgs {
   uint32_t *kept;    // per bucket
   const uint32_t *new_off;
   uint4 *out;
+  uint32_t *keys_out;  // optional: the first word of every written record (the streaming pass's case counts)
 };
 __global__ void k_case_span(FilterArgs a);
 __global__ void k_case_ok(FilterArgs a);
