@@ -1077,6 +1077,7 @@ def main():
         if n_l:
             kt[name] = (n_l, t_ms)
     sorted_windows = pm4g.pm4g_ctx_timing(ctx, "sorted_windows")[0] // max(1, args.steps)
+    regrouped = pm4g.pm4g_ctx_timing(ctx, "variant_regrouped")[0] // max(1, args.steps)
     pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
     total_kt = sum(v[1] for v in kt.values()) or 1.0
     dom = max(kt, key=lambda k: kt[k][1])
@@ -1176,6 +1177,7 @@ def main():
         "kernel_share": {k: round(v[1] / total_kt, 4) for k, v in kt.items()},
         "gpu_launches": int(launches),
         "sorted_windows_per_step": int(sorted_windows),
+        "variant_regrouped_per_step": int(regrouped),
         "clocks": clk.summary(),
         "e2e": e2e,
         "cpu_baseline": cpu,

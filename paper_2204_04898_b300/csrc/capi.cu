@@ -1402,6 +1402,7 @@ int pm4g::group_variants(Ctx *c, VarArgs a, uint64_t n_items) {
     PM4G_TRY(check_launch(c, "k_var_final"));
     uint32_t nb = 0;
     PM4G_TRY(d2h(c, &nb, n_bad, 4));
+    c->totals["variant_regrouped"].first += nb;  // cases whose sequence differed from their group's
     if (nb == 0) break;
     if (round > 1000000) {
       set_error("variants: collision rounds did not converge");
@@ -1462,7 +1463,8 @@ static int ensure_variants(pm4g_log *L) {
     PM4G_TRY(check_launch(c, "k_rep_compact"));
   }
   PM4G_TRY(radix_sort_u32(c, keys, L->order.p, k2, v2, V, 0, cbits));
-  PM4G_CK(cudaStreamSynchronize(c->stream));
+  // (no synchronisation: the callers' work follows on the same stream, and
+  // their own result copies report any failure)
   L->var_ready = true;
   return PM4G_OK;
 }
@@ -1487,9 +1489,7 @@ static int ensure_case_variants(pm4g_log *L) {
   k_rank_scatter<<<grid_for(V, 256, 65535), 256, 0, c->stream>>>(L->order.p, V, rank_of);
   PM4G_TRY(check_launch(c, "k_rank_scatter"));
   k_case_variant<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(a, L->rep_pos.p, rank_of, L->cvar.p);
-  PM4G_TRY(check_launch(c, "k_case_variant"));
-  PM4G_CK(cudaStreamSynchronize(c->stream));
-  return PM4G_OK;
+  return check_launch(c, "k_case_variant");
 }
 
 int pm4g_variants(pm4g_log *L, int64_t top_k, uint32_t flags, pm4g_variants_t *out) {
