@@ -85,6 +85,11 @@ extern "C" {
                                         cut into, 1..64 */
 #define PM4G_OPT_STREAM_WARPS 10      /* warps per block of the streaming segment pass, 1..24 */
 #define PM4G_OPT_STREAM_OFF 11        /* 1 = the sorting segment pass for time-ordered logs too */
+#define PM4G_OPT_PART1_ITEMS 12       /* records a thread stages per tile in the first partition
+                                        level: 8 (default; 4,096-record tiles, 2 blocks an SM)
+                                        or 4 (2,048-record tiles, 3 blocks an SM) */
+#define PM4G_OPT_PART2_ITEMS 13       /* the same for the second partition level: 4 (default)
+                                        or 8 */
 #define PM4G_OPT_BATCH_CHUNK 4       /* cases a warp takes at once: 8, 16 (default) or 32 */
 #define PM4G_OPT_BATCH_STAGES 5      /* groups a batch of >= 64 views into caller-owned
                                         arrays is pipelined in: 1..16 (default 4) */

@@ -660,6 +660,11 @@ int pm4g_ctx_set_option(pm4g_ctx *c, int option, int64_t value) {
       if (value < 0 || value > 1) break;
       c->stream_off = (int)value;
       return PM4G_OK;
+    case PM4G_OPT_PART1_ITEMS:
+    case PM4G_OPT_PART2_ITEMS:
+      if (value != 0 && value != 4 && value != 8) break;
+      (option == PM4G_OPT_PART1_ITEMS ? c->part1_items : c->part2_items) = (int)value;
+      return PM4G_OK;
     default:
       break;
   }
@@ -843,8 +848,10 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         break;
       }
       L->nb = (uint32_t)nb64;
-      // bucket histogram, offsets and partition. Row chunks: two per SM.
-      const int64_t n_chunks = 2 * (int64_t)c->num_sms;
+      // bucket histogram, offsets and partition. Row chunks: one per
+      // resident first-level partition block (two per SM at 4,096-record
+      // tiles, three at 2,048-record ones).
+      const int64_t n_chunks = (c->part1_items == 4 ? 3 : 2) * (int64_t)c->num_sms;
       int64_t chunk = (n + n_chunks - 1) / n_chunks;
       chunk = (chunk + 3) / 4 * 4;
       const int p_ctas = (int)((n + chunk - 1) / chunk);
@@ -963,7 +970,7 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           {
             KTime t(c, "partition");
             c->launches++;
-            if (const cudaError_t le = launch_partition(1, pa, (unsigned)p_ctas, c->stream)) {
+            if (const cudaError_t le = launch_partition(1, pa, (unsigned)p_ctas, c->stream, c->part1_items == 4 ? 4 : 8)) {
               set_error("launch of k_partition<1> failed: %s", cudaGetErrorString(le));
               fail(PM4G_ECUDA);
               break;
@@ -982,7 +989,7 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           {
             KTime t(c, "partition");
             c->launches++;
-            if (const cudaError_t le = launch_partition(2, pa, nc * (unsigned)pa.splits, c->stream)) {
+            if (const cudaError_t le = launch_partition(2, pa, nc * (unsigned)pa.splits, c->stream, c->part2_items == 8 ? 8 : 4)) {
               set_error("launch of k_partition<2> failed: %s", cudaGetErrorString(le));
               fail(PM4G_ECUDA);
               break;
@@ -1000,7 +1007,7 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           pa.rec_out = L->rec.p;
           KTime t(c, "partition");
           c->launches++;
-          if (const cudaError_t le = launch_partition(1, pa, (unsigned)p_ctas, c->stream)) {
+          if (const cudaError_t le = launch_partition(1, pa, (unsigned)p_ctas, c->stream, c->part1_items == 4 ? 4 : 8)) {
             set_error("launch of k_partition<1> failed: %s", cudaGetErrorString(le));
             fail(PM4G_ECUDA);
             break;

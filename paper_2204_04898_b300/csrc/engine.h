@@ -60,12 +60,15 @@ struct Ctx {
   int test_hash_bits = 0;
   int test_bucket_cap = 0;
   // launch choices of the single-log pass (PM4G_OPT_EDGE_TABLE, _LOAD_CLB,
-  // _LOAD_SPLITS, _STREAM_WARPS, _STREAM_OFF; 0 = default)
+  // _LOAD_SPLITS, _STREAM_WARPS, _STREAM_OFF, _PART1_ITEMS, _PART2_ITEMS;
+  // 0 = default)
   int edge_table = 0;
   int load_clb = 0;
   int load_splits = 0;
   int stream_warps = 0;
   int stream_off = 0;
+  int part1_items = 0;
+  int part2_items = 0;
   // launch choices of the batched drill-down (PM4G_OPT_BATCH_*; 0 = default)
   int batch_chunk = 0;
   int batch_stages = 0;

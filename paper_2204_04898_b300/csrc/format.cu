@@ -307,7 +307,7 @@ namespace pm4g {
 // ---------------------------------------------------------------------------
 // Bucket partition with coalesced writes (replaces the record-by-record
 // scatter whenever the bucket count allows it). Scattered 16-byte stores run
-// about 8x slower than streaming ones on this GPU, so a tile of kPartTile
+// about 8x slower than streaming ones on this GPU, so a tile of kItems * kPartThreads
 // events is first ordered by digit in shared memory and then written out as
 // one contiguous run per digit, by a bulk copy of the tensor memory
 // accelerator that overlaps the next tile.
@@ -321,13 +321,17 @@ namespace pm4g {
 // Both levels keep row order within every digit: items of a tile are ranked by
 // warp (warps own consecutive items), then by round, then by lane.
 // ---------------------------------------------------------------------------
-template <int kLevel>
-__global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
+// kItems records a thread per tile: 8 (4,096-record tiles, two blocks per SM)
+// or 4 (2,048-record tiles in about two thirds of the shared memory, three
+// blocks per SM for more loads in flight).
+template <int kLevel, int kItems>
+__global__ void __launch_bounds__(kPartThreads, kItems == 4 ? 3 : 2) k_partition(PartArgs a) {
+  constexpr int kTile = kPartThreads * kItems;
   extern __shared__ __align__(16) unsigned char sm[];
   const uint32_t nbins = a.nbins;
   uint4 *stg = reinterpret_cast<uint4 *>(sm);
-  uint16_t *wh = reinterpret_cast<uint16_t *>(sm + (size_t)kPartTile * 16);
-  uint32_t *pm = reinterpret_cast<uint32_t *>(sm + (size_t)kPartTile * 16 + part_wh_bytes(nbins));
+  uint16_t *wh = reinterpret_cast<uint16_t *>(sm + (size_t)kTile * 16);
+  uint32_t *pm = reinterpret_cast<uint32_t *>(sm + (size_t)kTile * 16 + part_wh_bytes(nbins));
   uint32_t *cur = pm + kPartWarps * nbins;  // next output index of every digit
   uint32_t *tst = cur + nbins;              // staged start of every digit, nbins + 1
   uint32_t *sw = tst + nbins + 1;           // block-scan scratch, 32 words
@@ -367,13 +371,13 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   // the warps go on to rank tile t + 1.
   // Level 1 holds the raw columns (case id, activity, timestamp) in rec until
   // the record is formed.
-  uint4 rec[kPartItems];
+  uint4 rec[kItems];
   int64_t t_before = 0;  // level 1, lane 0: timestamp of the row before the warp's first row
   // Loading tile t + 1 also starts moving tile t + 2 into L2, so that the
   // loads of every tile after the first find their data there.
   auto prefetch_tile = [&](uint32_t base) {
     if (base >= i1 || warp != kPartWarps - 1 || lane > 2) return;
-    const uint32_t e = min(i1, base + kPartTile);
+    const uint32_t e = min(i1, base + kTile);
     if (kLevel == 1) {
       if (lane == 0) prefetch_l2_inner(a.case_id + base, (size_t)(e - base) * 4);
       if (lane == 1) prefetch_l2_inner(a.activity + base, (size_t)(e - base) * 4);
@@ -383,11 +387,11 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     }
   };
   auto load_tile = [&](uint32_t base) {
-    prefetch_tile(base + kPartTile);
-    const uint32_t wb = base + (uint32_t)warp * (32 * kPartItems) + lane;
+    prefetch_tile(base + kTile);
+    const uint32_t wb = base + (uint32_t)warp * (32 * kItems) + lane;
     if (kLevel == 1 && lane == 0 && wb > 0 && wb < i1) t_before = a.ts[wb - 1];
 #pragma unroll
-    for (int r = 0; r < kPartItems; ++r) {
+    for (int r = 0; r < kItems; ++r) {
       const uint32_t i = wb + r * 32;
       if (i < i1) {
         if (kLevel == 1) {
@@ -402,12 +406,12 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   };
   if (i0 < i1) load_tile(i0);
   bool desc = false;  // level 1: a timestamp below the previous row's
-  for (uint32_t base = i0; base < i1; base += kPartTile) {
-    uint32_t dg[kPartItems];
-    const uint32_t wbase = base + (uint32_t)warp * (32 * kPartItems) + lane;
+  for (uint32_t base = i0; base < i1; base += kTile) {
+    uint32_t dg[kItems];
+    const uint32_t wbase = base + (uint32_t)warp * (32 * kItems) + lane;
     int64_t t_last = 0;  // previous round's timestamp (lane 31's is the row before this round's lane 0)
 #pragma unroll
-    for (int r = 0; r < kPartItems; ++r) {
+    for (int r = 0; r < kItems; ++r) {
       const uint32_t i = wbase + r * 32;
       if (kLevel == 1) {
         const int64_t t = (int64_t)(((uint64_t)rec[r].w << 32) | rec[r].z);
@@ -439,11 +443,11 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     // into a per-warp mask word of the digit (cheaper than a warp match when
     // most lanes differ); all of them read the digit's count, and the lowest
     // lane adds the group's size and clears the mask for the next round.
-    uint32_t rk[kPartItems];
+    uint32_t rk[kItems];
     uint32_t *pmw = pm + warp * nbins;
     const uint32_t lt = lanemask_lt(), bit = 1u << lane;
 #pragma unroll
-    for (int r = 0; r < kPartItems; ++r) {
+    for (int r = 0; r < kItems; ++r) {
       const uint32_t d = dg[r];
       const bool v = d != 0xFFFFFFFFu;
       if (v) atomicOr(&pmw[d], bit);
@@ -484,7 +488,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kPartItems; ++r) {
+    for (int r = 0; r < kItems; ++r) {
       if (dg[r] != 0xFFFFFFFFu) {
         const uint32_t sp = myh[dg[r]] + rk[r];
         stg[sp] = rec[r];
@@ -503,7 +507,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
         a.keys_out[dlt[((x >> a.act_bits) >> a.clb) & fmask] + k] = x;
       }
     }
-    if (base + kPartTile < i1) load_tile(base + kPartTile);
+    if (base + kTile < i1) load_tile(base + kTile);
     // each digit's run is one bulk copy, issued by the digit's thread; the
     // copies proceed while the next tile is loaded and ranked
     if ((uint32_t)tid < nbins) {
@@ -523,19 +527,18 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(PartArgs a) {
   }
 }
 
-cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s) {
-  const size_t smem = part_smem_bytes(a.nbins);
-  cudaError_t e;
-  if (level == 1) {
-    e = cudaFuncSetAttribute(k_partition<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
-    if (e != cudaSuccess) return e;
-    k_partition<1><<<grid, kPartThreads, smem, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(k_partition<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
-    if (e != cudaSuccess) return e;
-    k_partition<2><<<grid, kPartThreads, smem, s>>>(a);
-  }
+template <int kLevel, int kItems>
+static cudaError_t launch_part(const PartArgs &a, unsigned grid, cudaStream_t s) {
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_partition<kLevel, kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
+  if (e != cudaSuccess) return e;
+  k_partition<kLevel, kItems><<<grid, kPartThreads, part_smem_bytes(a.nbins, kItems), s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s, int items) {
+  if (level == 1) return items == 4 ? launch_part<1, 4>(a, grid, s) : launch_part<1, 8>(a, grid, s);
+  return items == 4 ? launch_part<2, 4>(a, grid, s) : launch_part<2, 8>(a, grid, s);
 }
 
 // Coarse count matrix: mat1[p][C] = sum of mat[p][b] over the final buckets b

@@ -56,14 +56,16 @@ struct PartArgs {
 };
 
 __host__ __device__ inline size_t part_wh_bytes(uint32_t nbins) { return ((size_t)kPartWarps * nbins * 2 + 15) / 16 * 16; }
-// staging tile, per-warp 16-bit counts, per-warp peer masks, cursors, staged
-// starts, block-scan scratch and each digit's output-minus-staged offset
-__host__ __device__ inline size_t part_smem_bytes_hd(uint32_t nbins) {
-  return (size_t)kPartTile * 16 + part_wh_bytes(nbins) + (size_t)kPartWarps * nbins * 4 +
+// staging tile (items records a thread), per-warp 16-bit counts, per-warp
+// peer masks, cursors, staged starts, block-scan scratch and each digit's
+// output-minus-staged offset
+__host__ __device__ inline size_t part_smem_bytes_hd(uint32_t nbins, int items) {
+  return (size_t)kPartThreads * items * 16 + part_wh_bytes(nbins) + (size_t)kPartWarps * nbins * 4 +
          (size_t)(3 * nbins + 1 + 32) * 4;
 }
-inline size_t part_smem_bytes(uint32_t nbins) { return part_smem_bytes_hd(nbins); }
-cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s);
+inline size_t part_smem_bytes(uint32_t nbins, int items) { return part_smem_bytes_hd(nbins, items); }
+// items: records a thread takes per tile, 8 or 4
+cudaError_t launch_partition(int level, const PartArgs &a, unsigned grid, cudaStream_t s, int items);
 __global__ void k_coarse_counts(const uint32_t *mat, uint32_t nb, int p_ctas, int fbits, uint32_t nc, uint32_t *mat1);
 __global__ void k_add_base(uint32_t *mat1, int p_ctas, uint32_t nc, const uint32_t *bucket_off, int fbits);
 

@@ -151,15 +151,18 @@ __device__ __forceinline__ void var_insert_one(const VarArgs &a, uint32_t s, uin
 // and walks them 32 events at a time, lane-dense. One OR-reduction per window
 // gives the bits of the positions where a (non-empty) case starts; a lane's
 // case is then the number of starts up to its position (a popcount, counted
-// from the cases that started before the window), and the lanes of one case
-// form a run between two start bits, whose terms redux.sync sums for the
-// run's first lane to add to the case's per-warp accumulator. Each lane then
-// inserts its own slot.
+// from the cases that started before the window). The terms of the walk are
+// prefix-summed (a warp scan per window plus the running total of the windows
+// before), and each case start records the prefix sum just before it: a
+// case's hash is the difference between the next case's record (or the walk's
+// total, for the last case) and its own, so the walk needs no segmented
+// reduction. Each lane then inserts its own slot.
 __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
-  // per warp: low and high hash words, and first position, of up to 32 cases
+  // per warp: low and high words of the prefix sum before each of up to 32
+  // cases, and each case's first position
   __shared__ uint32_t s_acc[kHiThreads / 32][96];
   const uint32_t lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-  uint32_t *acc_lo = s_acc[wb], *acc_hi = acc_lo + 32, *sstart = acc_lo + 64;
+  uint32_t *gs_lo = s_acc[wb], *gs_hi = gs_lo + 32, *sstart = gs_lo + 64;
   const uint32_t le = 0xFFFFFFFFu >> (31 - lane), lt = lanemask_lt();
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -175,35 +178,54 @@ __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
     const uint32_t excl = incl - L;
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     const uint32_t off0 = a.off[s0];  // first formatted position of the slots
-    const uint32_t rank = __popc(__ballot_sync(kFull, L > 0) & lt);  // among the non-empty slots
-    if (L) {
-      acc_lo[rank] = 0;
-      acc_hi[rank] = 0;
-      sstart[rank] = excl;
-    }
+    const uint32_t ne = __ballot_sync(kFull, L > 0);
+    const uint32_t rank = __popc(ne & lt), n_ne = __popc(ne);  // among the non-empty slots
+    if (L) sstart[rank] = excl;
     __syncwarp();
-    uint32_t before = 0;  // non-empty cases that start before the window
+    // the activities of the next four windows are loaded ahead
+    const int32_t *q = a.act_s + off0 + lane;
+    int32_t q0 = lane < total ? __ldcs(q) : 0, q1 = 32 + lane < total ? __ldcs(q + 32) : 0;
+    int32_t q2 = 64 + lane < total ? __ldcs(q + 64) : 0, q3 = 96 + lane < total ? __ldcs(q + 96) : 0;
+    uint32_t before = 0;       // non-empty cases that start before the window
+    uint32_t clo = 0, chi = 0;  // sums of the terms of the windows before
     for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+      const int32_t act = q0;
+      q0 = q1;
+      q1 = q2;
+      q2 = q3;
+      q3 = p0 + 128 + lane < total ? __ldcs(q + p0 + 128) : 0;
       const uint32_t bit = (L && excl >= p0 && excl - p0 < 32u) ? (1u << (excl - p0)) : 0u;
       const uint32_t starts = __reduce_or_sync(kFull, bit);
-      const uint32_t M = starts | (total - p0 < 32u ? (1u << (total - p0)) : 0u);  // the end closes the last run
       const uint32_t p = p0 + lane;
-      const bool valid = p < total;
-      const uint32_t cr = valid ? before + __popc(starts & le) - 1 : 0u;  // the case's rank
-      uint64_t t = 0;
-      if (valid) t = event_hash((uint32_t)a.act_s[off0 + p], p - sstart[cr], 0);
-      const uint32_t hb = M & le, gt = M & ~le;
-      const uint32_t head = hb ? 31 - __clz(hb) : 0u;
-      const uint32_t rm = (gt ? ((1u << (__ffs(gt) - 1)) - 1) : 0xFFFFFFFFu) & ~((1u << head) - 1);
-      const uint32_t sl = __reduce_add_sync(rm, (uint32_t)t), sh = __reduce_add_sync(rm, (uint32_t)(t >> 32));
-      if (valid && lane == head) {  // the run's first lane; each case has one run per window
-        acc_lo[cr] += sl;
-        acc_hi[cr] += sh;
+      const uint32_t cr = before + __popc(starts & le) - 1;  // the case's rank (valid lanes)
+      uint32_t tl = 0, th = 0;
+      if (p < total) {
+        const uint64_t t = event_hash((uint32_t)act, p - sstart[cr], 0);
+        tl = (uint32_t)t;
+        th = (uint32_t)(t >> 32);
       }
+      uint32_t il = tl, ih = th;  // inclusive prefix sums within the window
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yl = __shfl_up_sync(kFull, il, o), yh = __shfl_up_sync(kFull, ih, o);
+        if ((int)lane >= o) {
+          il += yl;
+          ih += yh;
+        }
+      }
+      if ((starts >> lane) & 1u) {
+        gs_lo[cr] = clo + il - tl;
+        gs_hi[cr] = chi + ih - th;
+      }
+      clo += __shfl_sync(kFull, il, 31);
+      chi += __shfl_sync(kFull, ih, 31);
       before += __popc(starts);
-      __syncwarp();
     }
-    if (L) var_insert_one(a, (uint32_t)s, L, ((uint64_t)acc_hi[rank] << 32) | acc_lo[rank], 0);
+    __syncwarp();
+    if (L) {
+      const uint32_t nl = rank + 1 < n_ne ? gs_lo[rank + 1] : clo, nh = rank + 1 < n_ne ? gs_hi[rank + 1] : chi;
+      var_insert_one(a, (uint32_t)s, L, ((uint64_t)(nh - gs_hi[rank]) << 32) | (nl - gs_lo[rank]), 0);
+    }
     __syncwarp();
   }
 }
@@ -236,19 +258,20 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
 // The comparisons are shared out within the warp: each round, four 8-lane
 // groups take the next four items that need one and read eight consecutive
 // activities of both sequences per step, so a load instruction covers four
-// contiguous 32-byte runs instead of 32 scattered words.
+// contiguous 32-byte runs instead of 32 scattered words. An item that
+// matches records its representative; one that does not leaves its group.
 __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out,
                              uint32_t *n_bad) {
   const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
   const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t w0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); w0 < total; w0 += stride) {
-    uint32_t s = 0, g = 0, L = 0, xo = 0, yo = 0;
+    uint32_t s = 0, g = 0, L = 0, xo = 0, yo = 0, rep = 0;
     const bool item = var_item(a, list, n_list, w0 + lane, s);
     bool same = true, need = false;
     if (item) {
       g = a.grp[s];
-      const uint32_t rep = ~a.tab[g].nmin;
+      rep = ~a.tab[g].nmin;
       if (rep != s) {
         L = a.len[s];
         same = a.len[rep] == L && (!a.cls || a.cls[rep] == a.cls[s]);
@@ -284,7 +307,9 @@ __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, u
     }
     if (item) {
       a.isbad[s] = same ? 0 : 1;
-      if (!same) {
+      if (same) {
+        a.rep_of[s] = rep;
+      } else {
         atomicSub(&a.tab[g].cnt, 1u);
         bad_out[atomicAdd(n_bad, 1u)] = s;
       }
@@ -292,16 +317,15 @@ __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, u
   }
 }
 
+// The group sizes, once every mismatch of the round has left its group: the
+// representatives (never mismatched) read their slot's count.
 __global__ void k_var_final(VarArgs a, const uint32_t *list, uint32_t n_list) {
   const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s;
     if (!var_item(a, list, n_list, i, s)) continue;
-    if (a.isbad[s]) continue;
-    const uint32_t g = a.grp[s];
-    const uint32_t rep = ~a.tab[g].nmin;
-    a.rep_of[s] = rep;
-    if (rep == s) a.vcount[s] = a.tab[g].cnt;
+    if (a.isbad[s] || a.rep_of[s] != s) continue;
+    a.vcount[s] = a.tab[a.grp[s]].cnt;
   }
 }
 
