@@ -100,8 +100,9 @@ typedef struct pm4g_ctx pm4g_ctx;
 typedef struct pm4g_log pm4g_log;
 
 /* Device-memory hook. alloc returns device memory of `bytes` bytes usable on
- * `stream` (a cudaStream_t), or NULL on failure; free releases it in stream
- * order. `user` is passed through. */
+ * `stream` (a cudaStream_t), aligned to at least 16 bytes, or NULL on failure
+ * (memory that is not aligned is given back and the call fails with
+ * PM4G_ENOMEM); free releases it in stream order. `user` is passed through. */
 typedef struct {
   void *(*alloc)(size_t bytes, void *stream, void *user);
   void (*free)(void *ptr, size_t bytes, void *stream, void *user);

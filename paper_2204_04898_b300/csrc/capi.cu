@@ -63,7 +63,15 @@ static void cache_flush(Ctx *c) {
 
 void *dalloc(Ctx *c, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  if (c->has_alloc) return c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+  if (c->has_alloc) {
+    void *p = c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+    if (p && ((uintptr_t)p & 15u)) {  // bulk copies and vector loads need 16-byte alignment
+      c->alloc.free(p, bytes, (void *)c->stream, c->alloc.user);
+      set_error("the context's allocator returned memory not aligned to 16 bytes");
+      return nullptr;
+    }
+    return p;
+  }
   const size_t key = cache_round(bytes);
   auto it = c->cache.find(key);
   if (it != c->cache.end()) {
@@ -1443,6 +1451,7 @@ static int ensure_variants(pm4g_log *L) {
   a.hash = nullptr;  // formed from the formatted activities in the first round
   a.off = L->off.p;
   a.act_s = L->act_s.p;
+  a.n_events = L->n;
   a.bits = c->test_hash_bits;
   a.rep_of = L->rep_of.p;
   a.vcount = L->vcount.p;

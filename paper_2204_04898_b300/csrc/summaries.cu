@@ -123,52 +123,122 @@ __device__ __forceinline__ bool var_item(const VarArgs &a, const uint32_t *list,
   return a.len[s] != 0;
 }
 
-// Inserts item s (a case slot, or a list entry) with sequence hash h into the
-// grouping table: finds or claims the slot of its key, counts it and keeps the
-// smallest member.
-__device__ __forceinline__ void var_insert_one(const VarArgs &a, uint32_t s, uint32_t L, uint64_t h,
-                                               uint32_t round) {
+// The table slot of an item's key: the first slot along the key's probe
+// sequence that holds the key's tag (the key's high word) or that this call
+// claims, writing the tag and the item in one 64-bit word. Every item of one
+// sequence follows the same probe sequence, and a slot changes only once
+// (from empty to claimed), so all of them stop at the same slot; an item of
+// another sequence whose tag happens to match stops there too and fails the
+// sequence check. *claimer: the item that claimed the slot.
+__device__ __forceinline__ uint32_t var_slot(const VarArgs &a, uint32_t s, uint32_t L, uint64_t h, uint32_t round,
+                                             uint32_t &claimer) {
   if (a.cls) h ^= fmix64(((uint64_t)a.cls[s] << 1) | 1u);  // keys of different classes differ
   const unsigned long long key = variant_key(h, L, a.bits);
+  uint32_t tag = (uint32_t)(key >> 32);
+  if (tag == 0) tag = 1;  // 0 marks an empty slot
+  const unsigned long long mine = ((unsigned long long)tag << 32) | s;
   uint32_t g = (uint32_t)fmix64(key ^ round) & a.tmask;
   for (uint32_t it = 0; it <= a.tmask; ++it) {
-    const unsigned long long k = *(volatile unsigned long long *)&a.tab[g].key;
-    if (k == key) break;
+    unsigned long long k = *(volatile unsigned long long *)&a.tab[g].tagc;
     if (k == 0) {
-      const unsigned long long old = atomicCAS(&a.tab[g].key, 0ull, key);
-      if (old == 0 || old == key) break;
+      k = atomicCAS(&a.tab[g].tagc, 0ull, mine);
+      if (k == 0) k = mine;
+    }
+    if ((uint32_t)(k >> 32) == tag) {
+      claimer = (uint32_t)k;
+      return g;
     }
     g = (g + 1) & a.tmask;
   }
+  claimer = s;  // not reached: the table has more slots than items
+  return g;
+}
+
+// Inserts item s (a case slot, or a list entry) with sequence hash h into the
+// grouping table: finds or claims the slot of its key, counts it and keeps the
+// smallest member (every member counts; the check against the group's
+// representative follows).
+__device__ __forceinline__ void var_insert_one(const VarArgs &a, uint32_t s, uint32_t L, uint64_t h,
+                                               uint32_t round) {
+  uint32_t claimer;
+  const uint32_t g = var_slot(a, s, L, h, round, claimer);
   a.grp[s] = g;
   atomicAdd(&a.tab[g].cnt, 1u);
   atomicMax(&a.tab[g].nmin, ~s);
 }
 
+// Compares, for every lane in `todo`, the L activities at act_s[xo] with those
+// at act_s[yo], clearing `same` on a difference. The comparisons are shared
+// out within the warp: each round, four 8-lane groups take the next four
+// pending lanes and read eight consecutive activities of both sequences per
+// step, so a load instruction covers four contiguous 32-byte runs instead of
+// 32 scattered words. All lanes of the warp call it.
+__device__ __forceinline__ void warp_compare(const int32_t *act_s, uint32_t todo, uint32_t L, uint32_t xo,
+                                             uint32_t yo, bool &same) {
+  const uint32_t lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
+  while (todo) {
+    const uint32_t before = todo;
+    int src = -1;  // the item of this lane's group: the grp-th lowest pending lane
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (todo && j == (int)grp) src = __ffs(todo) - 1;
+      todo &= todo - 1;
+    }
+    const int sl = src < 0 ? 0 : src;
+    const uint32_t Ls = __shfl_sync(kFull, L, sl), xs = __shfl_sync(kFull, xo, sl), ys = __shfl_sync(kFull, yo, sl);
+    bool eq = true;
+    if (src >= 0) {
+#pragma unroll 4
+      for (uint32_t k = gl; k < Ls; k += 8) eq &= act_s[xs + k] == act_s[ys + k];
+    }
+    const uint32_t ne = __ballot_sync(kFull, !eq);
+    // the pending lanes of this round were taken by groups 0..3 in lane order
+    if ((before >> lane) & 1u) {
+      const int gi = __popc(before & lanemask_lt());
+      if (gi < 4 && ((ne >> (8 * gi)) & 0xFFu) != 0) same = false;
+    }
+  }
+}
+
 // First grouping round over all case slots, with the sequence hash (seed 0)
 // formed on the way from the formatted activities. A warp takes 32
 // consecutive case slots, whose events are contiguous in the formatted order,
-// and walks them 32 events at a time, lane-dense. One OR-reduction per window
-// gives the bits of the positions where a (non-empty) case starts; a lane's
-// case is then the number of starts up to its position (a popcount, counted
-// from the cases that started before the window). The terms of the walk are
-// prefix-summed (a warp scan per window plus the running total of the windows
-// before), and each case start records the prefix sum just before it: a
-// case's hash is the difference between the next case's record (or the walk's
-// total, for the last case) and its own, so the walk needs no segmented
-// reduction. Each lane then inserts its own slot.
+// and walks them 128 events at a time, four consecutive events a lane (one
+// 16-byte load; the walk starts at the 16-byte boundary at or before the
+// slots' first event). Four OR-reductions per window give the bits of the
+// positions where a (non-empty) case starts; a lane's first event belongs to
+// the case counted by the starts before it, and its next three events to the
+// same case unless a start bit says otherwise, so only the lane's first event
+// looks up its case's first position. The terms are prefix-summed (within the
+// lane, a warp scan of the lanes' totals, and the running total of the
+// windows before), and each case start records the prefix sum just before it:
+// a case's hash is the difference between the next case's record (or the
+// walk's total, for the last case) and its own, so the walk needs no
+// segmented reduction. Each lane then inserts its own slot. (Measured slower:
+// lanes walking whole cases of their own, whose loads touch 32 lines at once;
+// checking each case against its group's claimer inside this walk, which puts
+// the check's chain of dependent random loads on the walk's warps.)
 __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
   // per warp: low and high words of the prefix sum before each of up to 32
   // cases, and each case's first position
   __shared__ uint32_t s_acc[kHiThreads / 32][96];
   const uint32_t lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   uint32_t *gs_lo = s_acc[wb], *gs_hi = gs_lo + 32, *sstart = gs_lo + 64;
-  const uint32_t le = 0xFFFFFFFFu >> (31 - lane), lt = lanemask_lt();
+  const uint32_t lt = lanemask_lt();
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t s0 = warp * 32; s0 < a.n_slots; s0 += n_warps * 32) {
+  const uint64_t stride = n_warps * 32;
+  // the next group's lengths and first position are loaded one group ahead
+  uint64_t s0 = warp * 32;
+  uint32_t L_next = s0 + lane < a.n_slots ? a.len[s0 + lane] : 0u;
+  uint32_t off_next = s0 < a.n_slots ? a.off[s0] : 0u;
+  for (; s0 < a.n_slots; s0 += stride) {
     const uint64_t s = s0 + lane;
-    const uint32_t L = s < a.n_slots ? a.len[s] : 0u;
+    const uint32_t L = L_next, off0 = off_next;  // off0: first formatted position of the slots
+    if (s0 + stride < a.n_slots) {
+      L_next = s0 + stride + lane < a.n_slots ? a.len[s0 + stride + lane] : 0u;
+      off_next = a.off[s0 + stride];
+    }
     uint32_t incl = L;  // events of this warp's slots up to and including this lane's
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -177,34 +247,79 @@ __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
     }
     const uint32_t excl = incl - L;
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    const uint32_t off0 = a.off[s0];  // first formatted position of the slots
     const uint32_t ne = __ballot_sync(kFull, L > 0);
     const uint32_t rank = __popc(ne & lt), n_ne = __popc(ne);  // among the non-empty slots
     if (L) sstart[rank] = excl;
     __syncwarp();
-    // the activities of the next four windows are loaded ahead
-    const int32_t *q = a.act_s + off0 + lane;
-    int32_t q0 = lane < total ? __ldcs(q) : 0, q1 = 32 + lane < total ? __ldcs(q + 32) : 0;
-    int32_t q2 = 64 + lane < total ? __ldcs(q + 64) : 0, q3 = 96 + lane < total ? __ldcs(q + 96) : 0;
+    // walk position w = formatted position - e0, with e0 a multiple of four
+    const uint64_t e0 = off0 & ~3u;
+    const uint32_t sh = off0 - (uint32_t)e0, tw = total + sh;
+    const uint32_t my_ws = excl + sh;  // this slot's first event, in walk positions
+    // the lane's four activities of the window at w0, loaded two windows ahead
+    auto load4 = [&](uint32_t w0) {
+      const uint32_t wl = w0 + 4 * lane;
+      int4 v = make_int4(0, 0, 0, 0);
+      if (wl < tw) {
+        const uint64_t e = e0 + wl;
+        if (e + 4 <= a.n_events) {
+          v = __ldcs(reinterpret_cast<const int4 *>(a.act_s + e));
+        } else {
+          v.x = a.act_s[e];
+          if (e + 1 < a.n_events) v.y = a.act_s[e + 1];
+          if (e + 2 < a.n_events) v.z = a.act_s[e + 2];
+        }
+      }
+      return v;
+    };
+    int4 v1 = load4(0), v2 = load4(128);
     uint32_t before = 0;       // non-empty cases that start before the window
     uint32_t clo = 0, chi = 0;  // sums of the terms of the windows before
-    for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-      const int32_t act = q0;
-      q0 = q1;
-      q1 = q2;
-      q2 = q3;
-      q3 = p0 + 128 + lane < total ? __ldcs(q + p0 + 128) : 0;
-      const uint32_t bit = (L && excl >= p0 && excl - p0 < 32u) ? (1u << (excl - p0)) : 0u;
-      const uint32_t starts = __reduce_or_sync(kFull, bit);
-      const uint32_t p = p0 + lane;
-      const uint32_t cr = before + __popc(starts & le) - 1;  // the case's rank (valid lanes)
-      uint32_t tl = 0, th = 0;
-      if (p < total) {
-        const uint64_t t = event_hash((uint32_t)act, p - sstart[cr], 0);
-        tl = (uint32_t)t;
-        th = (uint32_t)(t >> 32);
+    for (uint32_t w0 = 0; w0 < tw; w0 += 128) {
+      const uint32_t wl = w0 + 4 * lane;  // walk position of the lane's first event
+      const int4 v = v1;
+      v1 = v2;
+      v2 = load4(w0 + 256);
+      uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+      if (L && my_ws >= w0 && my_ws - w0 < 128u) {
+        const uint32_t bi = my_ws - w0, bit = 1u << (bi & 31);
+        if (bi < 32) b0 = bit;
+        else if (bi < 64) b1 = bit;
+        else if (bi < 96) b2 = bit;
+        else b3 = bit;
       }
-      uint32_t il = tl, ih = th;  // inclusive prefix sums within the window
+      const uint32_t S0 = __reduce_or_sync(kFull, b0), S1 = __reduce_or_sync(kFull, b1);
+      const uint32_t S2 = __reduce_or_sync(kFull, b2), S3 = __reduce_or_sync(kFull, b3);
+      const uint32_t wi = lane >> 3, sb = 4 * (lane & 7);
+      const uint32_t Sw = wi == 0 ? S0 : wi == 1 ? S1 : wi == 2 ? S2 : S3;
+      const uint32_t nib = (Sw >> sb) & 0xFu;  // starts among the lane's four events
+      uint32_t cr = before + (wi > 0 ? __popc(S0) : 0u) + (wi > 1 ? __popc(S1) : 0u) + (wi > 2 ? __popc(S2) : 0u) +
+                    __popc(Sw & ((1u << sb) - 1u)) - 1u;  // case of the event before the lane's first
+      const int32_t act4[4] = {v.x, v.y, v.z, v.w};
+      uint32_t tl[4], th[4], ul = 0, uh = 0, stc[4];
+      uint32_t pos = 0;
+      bool have = false;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t w = wl + j;
+        const bool valid = w >= sh && w < tw;
+        const bool st = (nib >> j) & 1u;
+        if (st) {
+          ++cr;
+          pos = 0;
+          have = true;
+        } else if (valid) {
+          pos = have ? pos + 1 : (w - sh) - sstart[cr];
+          have = true;
+        }
+        stc[j] = cr;
+        uint64_t t = 0;
+        if (valid) t = event_hash((uint32_t)act4[j], pos, 0);
+        tl[j] = ul;  // the lane's sum before this event
+        th[j] = uh;
+        ul += (uint32_t)t;
+        uh += (uint32_t)(t >> 32);
+      }
+      uint32_t il = ul, ih = uh;  // inclusive prefix sums of the lanes' totals
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t yl = __shfl_up_sync(kFull, il, o), yh = __shfl_up_sync(kFull, ih, o);
@@ -213,13 +328,16 @@ __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
           ih += yh;
         }
       }
-      if ((starts >> lane) & 1u) {
-        gs_lo[cr] = clo + il - tl;
-        gs_hi[cr] = chi + ih - th;
-      }
+      const uint32_t xl = clo + il - ul, xh = chi + ih - uh;  // sums before the lane's first event
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if ((nib >> j) & 1u) {
+          gs_lo[stc[j]] = xl + tl[j];
+          gs_hi[stc[j]] = xh + th[j];
+        }
       clo += __shfl_sync(kFull, il, 31);
       chi += __shfl_sync(kFull, ih, 31);
-      before += __popc(starts);
+      before += __popc(S0) + __popc(S1) + __popc(S2) + __popc(S3);
     }
     __syncwarp();
     if (L) {
@@ -254,24 +372,20 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
   }
 }
 
-// Each item is compared with its group's representative, event by event.
-// The comparisons are shared out within the warp: each round, four 8-lane
-// groups take the next four items that need one and read eight consecutive
-// activities of both sequences per step, so a load instruction covers four
-// contiguous 32-byte runs instead of 32 scattered words. An item that
-// matches records its representative; one that does not leaves its group.
+// Each item is compared with its group's representative, the smallest
+// member, event by event (warp_compare). One that differs leaves its group.
 __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out,
                              uint32_t *n_bad) {
   const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
-  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint32_t lane = threadIdx.x & 31;
   for (uint64_t w0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); w0 < total; w0 += stride) {
-    uint32_t s = 0, g = 0, L = 0, xo = 0, yo = 0, rep = 0;
+    uint32_t s = 0, g = 0, L = 0, xo = 0, yo = 0;
     const bool item = var_item(a, list, n_list, w0 + lane, s);
     bool same = true, need = false;
     if (item) {
       g = a.grp[s];
-      rep = ~a.tab[g].nmin;
+      const uint32_t rep = ~a.tab[g].nmin;
       if (rep != s) {
         L = a.len[s];
         same = a.len[rep] == L && (!a.cls || a.cls[rep] == a.cls[s]);
@@ -282,34 +396,10 @@ __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, u
         }
       }
     }
-    uint32_t todo = __ballot_sync(kFull, need);
-    while (todo) {
-      const uint32_t before = todo;
-      int src = -1;  // the item of this lane's group: the grp-th lowest pending lane
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (todo && j == grp) src = __ffs(todo) - 1;
-        todo &= todo - 1;
-      }
-      const int sl = src < 0 ? 0 : src;
-      const uint32_t Ls = __shfl_sync(kFull, L, sl), xs = __shfl_sync(kFull, xo, sl), ys = __shfl_sync(kFull, yo, sl);
-      bool eq = true;
-      if (src >= 0) {
-#pragma unroll 4
-        for (uint32_t k = gl; k < Ls; k += 8) eq &= a.act_s[xs + k] == a.act_s[ys + k];
-      }
-      const uint32_t ne = __ballot_sync(kFull, !eq);
-      // the pending lanes of this round were taken by groups 0..3 in lane order
-      if ((before >> lane) & 1u) {
-        const int gi = __popc(before & lanemask_lt());
-        if (gi < 4) same = ((ne >> (8 * gi)) & 0xFFu) == 0;
-      }
-    }
+    warp_compare(a.act_s, __ballot_sync(kFull, need), L, xo, yo, same);
     if (item) {
       a.isbad[s] = same ? 0 : 1;
-      if (same) {
-        a.rep_of[s] = rep;
-      } else {
+      if (!same) {
         atomicSub(&a.tab[g].cnt, 1u);
         bad_out[atomicAdd(n_bad, 1u)] = s;
       }
@@ -317,15 +407,18 @@ __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, u
   }
 }
 
-// The group sizes, once every mismatch of the round has left its group: the
-// representatives (never mismatched) read their slot's count.
+// Every item that stayed in its group records the group's representative
+// (its smallest member), and each representative its group's size.
 __global__ void k_var_final(VarArgs a, const uint32_t *list, uint32_t n_list) {
   const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s;
     if (!var_item(a, list, n_list, i, s)) continue;
-    if (a.isbad[s] || a.rep_of[s] != s) continue;
-    a.vcount[s] = a.tab[a.grp[s]].cnt;
+    if (a.isbad[s]) continue;
+    const uint32_t g = a.grp[s];
+    const uint32_t rep = ~a.tab[g].nmin;
+    a.rep_of[s] = rep;
+    if (rep == s) a.vcount[s] = a.tab[g].cnt;
   }
 }
 

@@ -6,11 +6,12 @@
 
 namespace pm4g {
 
-// One slot of the grouping table (16 bytes, one sector): the group key, its
-// member count and the bitwise complement of its smallest slot (so that an
-// all-zero slot is empty and atomicMax keeps the smallest slot).
+// One slot of the grouping table (16 bytes, one sector): the key's tag (its
+// high word, never 0) and the item that claimed the slot in one word, the
+// member count, and the bitwise complement of the smallest member (so that
+// an all-zero slot is empty and atomicMax keeps the smallest member).
 struct __align__(16) VarSlot {
-  unsigned long long key;
+  unsigned long long tagc;  // tag << 32 | claiming item
   uint32_t cnt;
   uint32_t nmin;
 };
@@ -20,7 +21,8 @@ struct VarArgs {
   const uint32_t *len;     // per case slot, 0 = no case
   const uint64_t *hash;    // per case slot, sequence hash (seed 0); NULL: formed from act_s in round 0
   const uint32_t *off;     // per case slot, first position in the ordered log
-  const int32_t *act_s;    // activity of every event in (case, ts, row) order
+  const int32_t *act_s;    // activity of every event in (case, ts, row) order (16-byte aligned)
+  uint64_t n_events;       // length of act_s
   int bits;                // key truncation (tests only), 0 = full key
   VarSlot *tab;
   uint32_t tmask;
