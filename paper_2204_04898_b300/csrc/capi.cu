@@ -463,8 +463,11 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
       set_error("segment pass: out of device memory for the edge ids");
       return PM4G_ENOMEM;
     }
+    if (w > 0 && !L->off.p) PM4G_TRY(alloc_buf(c, L->off, L->R + 1));
     if (w > 0) {
       PM4G_CK(cudaMemsetAsync(emap, 0xFF, cells * sizeof(uint32_t), c->stream));
+      a.off_out = L->off.p;
+      a.ran = blk->err + 1;
       a.keys = keys;
       a.emap = emap;
       a.key_of = key_of;
@@ -511,6 +514,7 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
     PM4G_TRY(d2h(c, h.nc, n_cases, sizeof(h.nc)));  // the global path adds its cases
   }
   L->C = (int64_t)h.nc[0];
+  L->off_ready = h.err[1] != 0;  // the streaming pass wrote the case offsets
   auto &sw = c->totals["sorted_windows"];
   sw.first += (int64_t)h.nc[1];
   return PM4G_OK;
@@ -1145,9 +1149,11 @@ int pm4g_log_export(pm4g_log *L, int32_t *case_out, int32_t *act_out, int64_t *t
 
 // Case offsets: exclusive prefix of the per-slot lengths (R + 1 entries).
 int pm4g::ensure_offsets(pm4g_log *L) {
-  if (L->off.p) return PM4G_OK;
-  PM4G_TRY(alloc_buf(L->ctx, L->off, L->R + 1));
-  return scan_u32(L->ctx, L->len.p, L->off.p, (int64_t)L->R);
+  if (L->off_ready) return PM4G_OK;
+  if (!L->off.p) PM4G_TRY(alloc_buf(L->ctx, L->off, L->R + 1));
+  PM4G_TRY(scan_u32(L->ctx, L->len.p, L->off.p, (int64_t)L->R));
+  L->off_ready = true;
+  return PM4G_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1455,14 +1461,14 @@ static int ensure_variants(pm4g_log *L) {
   a.bits = c->test_hash_bits;
   a.rep_of = L->rep_of.p;
   a.vcount = L->vcount.p;
+  uint32_t *flags = S.get<uint32_t>(R);  // representative flags, set by the grouping rounds
+  if (!flags) return PM4G_ENOMEM;
+  a.rep_flag = flags;
   PM4G_TRY(group_variants(c, a, (uint64_t)L->C));
   // rank representatives by (count desc, smallest case asc)
   PM4G_TRY(alloc_buf(c, L->rep_pos, R + 1));
-  uint32_t *flags = S.get<uint32_t>(R), *pos = L->rep_pos.p;
-  if (!flags) return PM4G_ENOMEM;
+  uint32_t *pos = L->rep_pos.p;
   const unsigned gR = grid_for((int64_t)R, 256, 65535);
-  k_rep_flags<<<gR, 256, 0, c->stream>>>(a, flags);
-  PM4G_TRY(check_launch(c, "k_rep_flags"));
   PM4G_TRY(scan_u32(c, flags, pos, (int64_t)R));
   uint32_t V = 0;
   PM4G_TRY(d2h(c, &V, pos + R, 4));

@@ -308,6 +308,7 @@ struct pm4g_log {
   bool var_ready = false;
   uint32_t V = 0;
   pm4g::DBuf<uint32_t> off, rep_slots, order, vcount, rep_of;
+  bool off_ready = false;  // off holds the case offsets (else ensure_offsets forms them)
   pm4g::DBuf<uint32_t> rep_pos;  // exclusive prefix of the representative flags (the case variants' input)
   pm4g::DBuf<int32_t> cvar;      // variant rank of every case slot, formed when first asked for
   // drill-down index (batched drill-down; built on first use)

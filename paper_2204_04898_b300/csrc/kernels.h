@@ -127,6 +127,10 @@ struct SegArgs {
   // id (key_of, kStSlots) and the id counter; ids below kStSlots index the
   // shared edge table directly
   uint32_t *emap, *key_of, *n_ids;
+  // streaming pass, optional: every case slot's first formatted position
+  // (n_slots + 1 entries, the last = the event count), and a word set to 1
+  // when the pass ran (the log was time-ordered)
+  uint32_t *off_out, *ran;
 };
 
 // Streaming segment pass (stream.cu): one warp per bucket, for logs whose

@@ -9,7 +9,8 @@
 // reordering at all: one warp takes a bucket and
 //  1. counts its cases from the first word of every record, which the
 //     partition's final level also wrote to a compact array (4 bytes per
-//     event), and forms every case's first formatted position;
+//     event), and forms every case's first formatted position (written out
+//     as the log's case offsets);
 //  2. streams the records once, 32 at a time, linking every event to the
 //     previous event of its case:
 //     - the lanes holding events of one case are found with one ballot per
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(kClb >= 8 ? 768 : 1024, 1) k_stream_segment(Se
   extern __shared__ __align__(16) unsigned char smem[];
   // only time-ordered logs: the sorting segment pass handles the others
   if (!a.order_flags || (*(volatile uint32_t *)a.order_flags & 2u)) return;
+  if (a.ran && blockIdx.x == 0 && threadIdx.x == 0) *a.ran = 1u;
   constexpr int ncl = 1 << kClb;
   constexpr int per = (ncl + 31) >> 5;  // case slots per lane in the per-bucket loops
   const int a_s = a.ep_smem ? (int)a.n_act : 0;
@@ -221,12 +223,16 @@ __global__ void __launch_bounds__(kClb >= 8 ? 768 : 1024, 1) k_stream_segment(Se
         const int c = lane * per + k;
         if (c < ncl) {
           const uint64_t slot = slot_base + (uint64_t)c;
-          if (slot < a.n_slots) a.len[slot] = cnt[k];
+          if (slot < a.n_slots) {
+            a.len[slot] = cnt[k];
+            if (a.off_out) a.off_out[slot] = run;
+          }
           S.first[c] = run;
           S.seen[c] = 0;
           run += cnt[k];
         }
       }
+      if (a.off_out && lane == 0 && b == a.nb - 1) a.off_out[a.n_slots] = lo + n;  // the event count
     }
     __syncwarp();
     // 2. the records, 32 at a time

@@ -408,17 +408,26 @@ __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, u
 }
 
 // Every item that stayed in its group records the group's representative
-// (its smallest member), and each representative its group's size.
+// (its smallest member), and each representative its group's size. With
+// a.rep_flag, every slot of the round also gets its representative flag (a
+// slot that left its group gets 0 here and its flag in a later round).
 __global__ void k_var_final(VarArgs a, const uint32_t *list, uint32_t n_list) {
   const uint64_t total = list ? (uint64_t)n_list : a.n_slots;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s;
-    if (!var_item(a, list, n_list, i, s)) continue;
-    if (a.isbad[s]) continue;
+    if (!var_item(a, list, n_list, i, s)) {
+      if (a.rep_flag && !list) a.rep_flag[i] = 0;  // no case in the slot
+      continue;
+    }
+    if (a.isbad[s]) {
+      if (a.rep_flag) a.rep_flag[s] = 0;
+      continue;
+    }
     const uint32_t g = a.grp[s];
     const uint32_t rep = ~a.tab[g].nmin;
     a.rep_of[s] = rep;
     if (rep == s) a.vcount[s] = a.tab[g].cnt;
+    if (a.rep_flag) a.rep_flag[s] = rep == s ? 1u : 0u;
   }
 }
 

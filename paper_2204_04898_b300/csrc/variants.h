@@ -31,6 +31,7 @@ struct VarArgs {
   uint32_t *vcount;
   uint8_t *isbad;
   const uint32_t *cls;     // optional class of each slot (batched sub-logs): a variant never spans two classes
+  uint32_t *rep_flag;      // optional: 1 at every representative, 0 at every other slot (k_var_final)
 };
 
 // Groups the items of `a` (slots with len > 0, or the whole list) by exact
