@@ -188,21 +188,46 @@ constexpr size_t kSmallBytes = 256;
 __global__ void k_small_copy(const unsigned char *__restrict__ src, unsigned char *dst, uint32_t n) {
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
+struct WordSrcs {
+  const uint32_t *p[8];
+};
+__global__ void k_words_copy(WordSrcs w, int n, uint32_t *dst) {
+  if ((int)threadIdx.x < n) dst[threadIdx.x] = *w.p[threadIdx.x];
+}
 }  // namespace
+
+bool small_buffer(Ctx *c) {
+  if (!c->small) {
+    if (cudaHostAlloc(&c->small, kSmallBytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&c->small_dev, c->small, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->small) cudaFreeHost(c->small);
+      c->small = nullptr;
+      c->small_dev = nullptr;
+    }
+  }
+  return c->small != nullptr;
+}
+
+int d2h_words(Ctx *c, uint32_t *const *dst, const uint32_t *const *src, int n) {
+  if (n < 1 || n > 8) return PM4G_EINVAL;
+  if (!small_buffer(c)) {
+    for (int i = 0; i < n; ++i) PM4G_TRY(d2h(c, dst[i], src[i], 4));
+    return PM4G_OK;
+  }
+  WordSrcs w{};
+  for (int i = 0; i < n; ++i) w.p[i] = src[i];
+  k_words_copy<<<1, 32, 0, c->stream>>>(w, n, (uint32_t *)c->small_dev);
+  PM4G_TRY(check_launch(c, "k_words_copy"));
+  PM4G_CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < n; ++i) *dst[i] = ((const uint32_t *)c->small)[i];
+  return PM4G_OK;
+}
 
 int d2h(Ctx *c, void *dst, const void *src, size_t bytes) {
   if (!bytes) return PM4G_OK;
   if (bytes <= kSmallBytes) {
-    if (!c->small) {
-      if (cudaHostAlloc(&c->small, kSmallBytes, cudaHostAllocMapped) != cudaSuccess ||
-          cudaHostGetDevicePointer(&c->small_dev, c->small, 0) != cudaSuccess) {
-        cudaGetLastError();
-        if (c->small) cudaFreeHost(c->small);
-        c->small = nullptr;
-        c->small_dev = nullptr;
-      }
-    }
-    if (c->small) {
+    if (small_buffer(c)) {
       k_small_copy<<<1, 64, 0, c->stream>>>((const unsigned char *)src, (unsigned char *)c->small_dev,
                                             (uint32_t)bytes);
       PM4G_TRY(check_launch(c, "k_small_copy"));
@@ -1380,7 +1405,7 @@ static uint64_t next_pow2(uint64_t x) {
   return p;
 }
 
-int pm4g::group_variants(Ctx *c, VarArgs a, uint64_t n_items) {
+int pm4g::group_variants(Ctx *c, VarArgs a, uint64_t n_items, uint32_t *rep_pos, uint32_t *n_reps) {
   const uint64_t R = a.n_slots;
   Scratch S(c);
   // table of about 1.5 slots per item (load at most 2/3), a power of two
@@ -1408,21 +1433,32 @@ int pm4g::group_variants(Ctx *c, VarArgs a, uint64_t n_items) {
     PM4G_CK(cudaMemsetAsync(tab, 0, Tr * sizeof(VarSlot), c->stream));
     PM4G_CK(cudaMemsetAsync(n_bad, 0, 4, c->stream));
     const unsigned g = grid_for((int64_t)items, 256, 65535);
-    KTime t(c, "variants");
-    if (round == 0 && !a.hash && !list) {
-      k_var_hash_insert<<<grid_for((int64_t)((R + 31) / 32) * 32, kHiThreads, 16 * (unsigned)c->num_sms), kHiThreads,
-                          0, c->stream>>>(a);
-      PM4G_TRY(check_launch(c, "k_var_hash_insert"));
-    } else {
-      k_var_insert<<<g, 256, 0, c->stream>>>(a, list, n_list, round);
-      PM4G_TRY(check_launch(c, "k_var_insert"));
+    {
+      KTime t(c, "variants");
+      if (round == 0 && !a.hash && !list) {
+        k_var_hash_insert<<<grid_for((int64_t)((R + 31) / 32) * 32, kHiThreads, 16 * (unsigned)c->num_sms),
+                            kHiThreads, 0, c->stream>>>(a);
+        PM4G_TRY(check_launch(c, "k_var_hash_insert"));
+      } else {
+        k_var_insert<<<g, 256, 0, c->stream>>>(a, list, n_list, round);
+        PM4G_TRY(check_launch(c, "k_var_insert"));
+      }
+      k_var_verify<<<g, 256, 0, c->stream>>>(a, list, n_list, out_list, n_bad);
+      PM4G_TRY(check_launch(c, "k_var_verify"));
+      k_var_final<<<g, 256, 0, c->stream>>>(a, list, n_list);
+      PM4G_TRY(check_launch(c, "k_var_final"));
     }
-    k_var_verify<<<g, 256, 0, c->stream>>>(a, list, n_list, out_list, n_bad);
-    PM4G_TRY(check_launch(c, "k_var_verify"));
-    k_var_final<<<g, 256, 0, c->stream>>>(a, list, n_list);
-    PM4G_TRY(check_launch(c, "k_var_final"));
     uint32_t nb = 0;
-    PM4G_TRY(d2h(c, &nb, n_bad, 4));
+    if (rep_pos) {
+      // the representatives' positions, read back with the round's count of
+      // differing cases (one wait; the scan is repeated if a round follows)
+      PM4G_TRY(scan_u32(c, a.rep_flag, rep_pos, (int64_t)R));
+      uint32_t *dst[2] = {&nb, n_reps};
+      const uint32_t *src[2] = {n_bad, rep_pos + R};
+      PM4G_TRY(d2h_words(c, dst, src, 2));
+    } else {
+      PM4G_TRY(d2h(c, &nb, n_bad, 4));
+    }
     c->totals["variant_regrouped"].first += nb;  // cases whose sequence differed from their group's
     if (nb == 0) break;
     if (round > 1000000) {
@@ -1464,14 +1500,13 @@ static int ensure_variants(pm4g_log *L) {
   uint32_t *flags = S.get<uint32_t>(R);  // representative flags, set by the grouping rounds
   if (!flags) return PM4G_ENOMEM;
   a.rep_flag = flags;
-  PM4G_TRY(group_variants(c, a, (uint64_t)L->C));
-  // rank representatives by (count desc, smallest case asc)
+  // representatives in slot order (their positions and count come with the
+  // grouping's last round), then ranked by (count desc, smallest case asc)
   PM4G_TRY(alloc_buf(c, L->rep_pos, R + 1));
   uint32_t *pos = L->rep_pos.p;
-  const unsigned gR = grid_for((int64_t)R, 256, 65535);
-  PM4G_TRY(scan_u32(c, flags, pos, (int64_t)R));
   uint32_t V = 0;
-  PM4G_TRY(d2h(c, &V, pos + R, 4));
+  PM4G_TRY(group_variants(c, a, (uint64_t)L->C, pos, &V));
+  const unsigned gR = grid_for((int64_t)R, 256, 65535);
   L->V = V;
   PM4G_TRY(alloc_buf(c, L->rep_slots, V));
   PM4G_TRY(alloc_buf(c, L->order, V));

@@ -225,6 +225,9 @@ struct D2HBatch {
 // One device-to-host copy, synchronised (up to 256 bytes through the mapped
 // bytes of the context).
 int d2h(Ctx *c, void *dst, const void *src, size_t bytes);
+// Reads n (1..8) 32-bit device words with one wait on the context stream.
+int d2h_words(Ctx *c, uint32_t *const *dst, const uint32_t *const *src, int n);
+bool small_buffer(Ctx *c);
 
 }  // namespace pm4g
 struct pm4g_log;

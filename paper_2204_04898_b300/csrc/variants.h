@@ -37,8 +37,11 @@ struct VarArgs {
 // Groups the items of `a` (slots with len > 0, or the whole list) by exact
 // sequence: fills a.rep_of (smallest slot of the item's group) and a.vcount
 // (group size, at the representative). n_items bounds the present slots.
+// With rep_pos (and a.rep_flag), also the exclusive prefix of the
+// representative flags over the n_slots slots (n_slots + 1 entries) and
+// their number (*n_reps).
 struct Ctx;
-int group_variants(Ctx *c, VarArgs a, uint64_t n_items);
+int group_variants(Ctx *c, VarArgs a, uint64_t n_items, uint32_t *rep_pos = nullptr, uint32_t *n_reps = nullptr);
 
 // First round over all slots with the hash formed from act_s (a.hash NULL).
 constexpr int kHiThreads = 256;
