@@ -70,8 +70,6 @@ __device__ __forceinline__ void prefetch_l2_inner(const void *p, size_t bytes) {
   const uintptr_t b = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
   if (e > b) prefetch_l2(reinterpret_cast<const void *>(b), (uint32_t)(e - b));
 }
-__device__ __forceinline__ uint32_t rec_case_lo(uint4 r, int act_bits) { return r.x >> act_bits; }
-__device__ __forceinline__ uint32_t rec_act(uint4 r, uint32_t act_mask) { return r.x & act_mask; }
 __device__ __forceinline__ int64_t rec_ts(uint4 r) {
   return (int64_t)(((uint64_t)r.w << 32) | (uint64_t)r.z);
 }
@@ -208,46 +206,6 @@ __device__ __forceinline__ uint32_t run_head(uint32_t key, uint32_t &run_len) {
   const uint32_t next = above ? (uint32_t)(__ffs(above) - 1) : 32u;
   run_len = next - lane;
   return head;
-}
-
-// Mask of the run of consecutive lanes holding this lane's key (the runs of
-// run_head): every lane of a run computes the same mask, so the mask can be
-// passed to a redux.sync by all lanes of the warp at once.
-__device__ __forceinline__ uint32_t run_mask(uint32_t key) {
-  const uint32_t lane = lane_id();
-  const uint32_t prev = __shfl_up_sync(kFull, key, 1);
-  const uint32_t heads = __ballot_sync(kFull, lane == 0 || prev != key);
-  const uint32_t le = 0xFFFFFFFFu >> (31 - lane);  // lanes 0..lane
-  const uint32_t head = 31 - __clz(heads & le);
-  const uint32_t after = heads & ~le;              // run heads after this lane
-  const uint32_t below_next = after ? ((1u << (__ffs(after) - 1)) - 1) : 0xFFFFFFFFu;
-  return below_next & ~((1u << head) - 1);
-}
-
-// Mask of the lanes whose (valid, key) equals this lane's, where key has
-// `bits` significant bits (invalid lanes must pass the same key, e.g. 0): one
-// ballot per key bit, no shared memory. Equal inputs give equal masks, so the
-// mask can be passed to a redux.sync by all lanes of the warp at once.
-__device__ __forceinline__ uint32_t peer_mask(uint32_t key, bool valid, int bits) {
-  const uint32_t vb = __ballot_sync(kFull, valid);
-  uint32_t m = valid ? vb : ~vb;
-  for (int k = 0; k < bits; ++k) {
-    const bool bit = (key >> k) & 1u;
-    const uint32_t b = __ballot_sync(kFull, bit);
-    m &= bit ? b : ~b;
-  }
-  return m;
-}
-
-// Exact sum of 64-bit values over the lanes of `peers` (all lanes of `peers`
-// must call with the same mask). Split into 22-bit limbs so that each
-// redux.sync sum stays below 2^32.
-__device__ __forceinline__ u128 peer_sum_u64(uint32_t peers, uint64_t v) {
-  uint32_t p0 = (uint32_t)(v & 0x3FFFFF), p1 = (uint32_t)((v >> 22) & 0x3FFFFF), p2 = (uint32_t)(v >> 44);
-  uint32_t s0 = __reduce_add_sync(peers, p0);
-  uint32_t s1 = __reduce_add_sync(peers, p1);
-  uint32_t s2 = __reduce_add_sync(peers, p2);
-  return (u128)s0 + ((u128)s1 << 22) + ((u128)s2 << 44);
 }
 
 // ---------------------------------------------------------------------------
