@@ -146,33 +146,82 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples over the timed region."""
+    """nvidia-smi clock and throttle-reason samples over the timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Every nvidia-smi sample stalls the GPU's work for a few milliseconds on
+    this driver (measured: about 2.5 ms per sample, whatever fields are
+    queried), so it samples once a second, and a timed region shorter than
+    that is started so that one sample falls in its middle: the sampler's
+    phase is read from the arrival of its second sample, and the region's
+    length is estimated from the untimed warm-up steps."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 1.0
 
-    def __init__(self, gpu_index: int, warm=None):
+    def __init__(self, gpu_index: int, warm=None, steps: int = 0, warm_steps: int = 3, pad=None):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
         self.warm = warm  # untimed steps run after the sampler starts, so the idle wait does not reach the timed steps
+        self.steps = steps  # timed steps that follow (0: no alignment)
+        self.warm_steps = warm_steps
+        self.pad = pad  # one untimed step, run instead of idling until the aligned start
+
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(prefix="pm4g_clocks_", suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms",
+                                          str(int(self.PERIOD_S * 1000))],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
+        # the second sample's arrival gives the sampler's phase (its start-up
+        # is over by then)
+        t0 = time.time()
+        t_sample = None
+        while self.proc is not None and time.time() - t0 < 10.0:
+            if self._lines() >= 2:
+                t_sample = time.time()
+                break
+            time.sleep(0.005)
         if self.warm is not None:
+            tw = time.time()
             self.warm()
+            t_warm = time.time() - tw
+            per_step = t_warm / max(1, self.warm_steps)
+            region = per_step * self.steps
+            if t_sample is not None and 0 < region < self.PERIOD_S:
+                # start so that the next sample lands in the middle of the
+                # region; the GPU keeps working until then (an idle GPU is
+                # slower for its first steps): untimed steps, then the warm-up
+                # again (it also resets the counters of the timed region)
+                now = time.time()
+                k = max(1, int((now + t_warm - t_sample + region / 2) / self.PERIOD_S) + 1)
+                start = t_sample + k * self.PERIOD_S - region / 2
+                if self.pad is not None:
+                    while time.time() + per_step + t_warm <= start - region / 4:
+                        self.pad()
+                else:
+                    now = time.time()
+                    if start - t_warm > now:
+                        time.sleep(start - t_warm - now)
+                self.warm()
+        self.t_begin = time.time()
         return self
 
     def __exit__(self, *exc):
+        self.t_end = time.time()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -181,27 +230,32 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        """Median SM clock, maximum clock and throttle reasons of the samples
+        taken in the timed region (all samples if none fell in it)."""
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
             for line in open(self.path):
                 f = [x.strip() for x in line.split(",")]
-                if len(f) < 9:
+                if len(f) < 10:
                     continue
                 try:
-                    sm.append(float(f[1]))
-                    mx.append(float(f[2]))
+                    t = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((t, float(f[2]), float(f[3]),
+                                 [nm for nm, v in zip(names, f[6:10]) if v.lower().startswith("active")]))
                 except ValueError:
                     continue
-                for nm, v in zip(names, f[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
         except Exception:
             pass
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        t0, t1 = getattr(self, "t_begin", None), getattr(self, "t_end", None)
+        inside = [r for r in rows if t0 is not None and t1 is not None and t0 <= r[0] <= t1]
+        use = inside or rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "samples_in_region": 0}
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted({nm for r in use for nm in r[3]}), "samples": len(use),
+                "samples_in_region": len(inside), "period_s": self.PERIOD_S}
 
 
 def run_reference(args):
@@ -358,7 +412,8 @@ def drilldown_core(args, local: int, steps: int, warmup: int, plain_views: int, 
         pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
         launches0[0] = pm4g.pm4g_ctx_timing(ctx, "launches")[0]
 
-    with ClockSampler(local, rewarm) as clk:
+    with ClockSampler(local, rewarm, steps=steps,
+                      pad=lambda: pm4g.pm4g_batch_dfg(log, out=buf, var_top_k=vk, spec=bspec)) as clk:
         torch.cuda.synchronize()
         t = time.perf_counter()
         ev0.record(stream)
@@ -726,7 +781,8 @@ def run_filters(args):
             run_one(kind, kw)
         pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
 
-    with ClockSampler(local, rewarm) as clk:
+    with ClockSampler(local, rewarm, steps=args.steps, warm_steps=1,
+                      pad=lambda: [run_one(kind, kw) for _, kind, kw in mix]) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -917,7 +973,7 @@ def run_efg(args):
         pm4g.pm4g_efg(log)
         pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
 
-    with ClockSampler(local, rewarm) as clk:
+    with ClockSampler(local, rewarm, steps=args.steps, warm_steps=1, pad=lambda: pm4g.pm4g_efg(log)) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -1051,7 +1107,7 @@ def main():
         pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 2)
         pm4g.pm4g_ctx_timing_reset(ctx)  # the timed steps alone are counted
 
-    with ClockSampler(local, rewarm) as clk:
+    with ClockSampler(local, rewarm, steps=args.steps, pad=lambda: step(dev)) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
