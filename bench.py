@@ -253,9 +253,12 @@ class ClockSampler:
         use = inside or rows
         if not use:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "samples_in_region": 0}
+        near = [round(r[0] - t0, 3) for r in rows if t0 is not None and t1 is not None and -2 <= r[0] - t0 <= t1 - t0 + 2]
         return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
                 "reasons": sorted({nm for r in use for nm in r[3]}), "samples": len(use),
-                "samples_in_region": len(inside), "period_s": self.PERIOD_S}
+                "samples_in_region": len(inside), "period_s": self.PERIOD_S,
+                "region_s": round(t1 - t0, 3) if t0 is not None and t1 is not None else None,
+                "sample_offsets_s": near}
 
 
 def run_reference(args):
