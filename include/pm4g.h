@@ -90,6 +90,10 @@ extern "C" {
                                         or 4 (2,048-record tiles, 3 blocks an SM) */
 #define PM4G_OPT_PART2_ITEMS 13       /* the same for the second partition level: 4 (default)
                                         or 8 */
+#define PM4G_OPT_PART_FBITS 14        /* log2 of the final buckets in a coarse bucket of the
+                                        first partition level, 1..9, when above the smallest
+                                        that keeps the coarse buckets within one pass (fewer,
+                                        larger coarse buckets); 0 = that smallest */
 #define PM4G_OPT_BATCH_CHUNK 4       /* cases a warp takes at once: 8, 16 (default) or 32 */
 #define PM4G_OPT_BATCH_STAGES 5      /* groups a batch of >= 64 views into caller-owned
                                         arrays is pipelined in: 1..16 (default 4) */

@@ -20,7 +20,9 @@ The single-log pass's choices (pm4g_load_log followed by the summaries) are:
 - the global edge table: dense over the A x A pairs or hashed (the
   histogram-versus-hash switch);
 - the records a thread stages per tile in each partition level (8, or 4 for
-  smaller tiles and one more resident block per SM).
+  smaller tiles and one more resident block per SM);
+- the coarse fan-out: final buckets per coarse bucket of the first partition
+  level (fewer, larger coarse buckets).
 
 The tuner times candidate choices on the caller's own batch or log: the wall
 time of whole calls, which return with every result on the host; the best of a few
@@ -55,11 +57,13 @@ LOAD_KNOBS = {
     "edge_table": _pm4g.OPT_EDGE_TABLE,
     "part1_items": _pm4g.OPT_PART1_ITEMS,
     "part2_items": _pm4g.OPT_PART2_ITEMS,
+    "part_fbits": _pm4g.OPT_PART_FBITS,
 }
 LOAD_DEFAULTS = {"clb": 0, "splits": 0, "stream_warps": 0, "stream_off": 0, "edge_table": 0, "part1_items": 0,
-                 "part2_items": 0}
+                 "part2_items": 0, "part_fbits": 0}
 LOAD_SPACE = {"clb": (0, 6, 7, 8), "splits": (0, 2, 4, 8, 16), "stream_warps": (0, 12, 16, 24),
-              "stream_off": (0, 1), "edge_table": (0, 1), "part1_items": (0, 4), "part2_items": (0, 4)}
+              "stream_off": (0, 1), "edge_table": (0, 1), "part1_items": (0, 4), "part2_items": (0, 8),
+              "part_fbits": (0, 8, 9)}
 
 
 def load_signature(n_events: int, n_cases: int, n_activities: int, time_ordered: bool, top_k: int,

@@ -209,6 +209,30 @@ bool small_buffer(Ctx *c) {
   return c->small != nullptr;
 }
 
+char *mapped_buf(Ctx *c, size_t bytes, char **dev) {
+  if (bytes > kMappedMax) return nullptr;
+  if (bytes > c->mapped_bytes) {
+    if (c->mapped) {
+      cudaStreamSynchronize(c->stream);  // kernels in flight may still write the old buffer
+      cudaFreeHost(c->mapped);
+      c->mapped = c->mapped_dev = nullptr;
+      c->mapped_bytes = 0;
+    }
+    size_t want = (size_t)1 << 20;
+    while (want < bytes) want <<= 1;
+    if (cudaHostAlloc(&c->mapped, want, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&c->mapped_dev, c->mapped, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->mapped) cudaFreeHost(c->mapped);
+      c->mapped = c->mapped_dev = nullptr;
+      return nullptr;
+    }
+    c->mapped_bytes = want;
+  }
+  *dev = (char *)c->mapped_dev;
+  return (char *)c->mapped;
+}
+
 int d2h_words(Ctx *c, uint32_t *const *dst, const uint32_t *const *src, int n) {
   if (n < 1 || n > 8) return PM4G_EINVAL;
   if (!small_buffer(c)) {
@@ -637,6 +661,7 @@ int pm4g_ctx_destroy(pm4g_ctx *c) {
   cudaStreamSynchronize(c->stream);
   if (c->pin) cudaFreeHost(c->pin);
   if (c->small) cudaFreeHost(c->small);
+  if (c->mapped) cudaFreeHost(c->mapped);
   if (c->copy_stream) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamDestroy(c->copy_stream);
@@ -696,6 +721,10 @@ int pm4g_ctx_set_option(pm4g_ctx *c, int option, int64_t value) {
     case PM4G_OPT_STREAM_OFF:
       if (value < 0 || value > 1) break;
       c->stream_off = (int)value;
+      return PM4G_OK;
+    case PM4G_OPT_PART_FBITS:
+      if (value < 0 || value > 9) break;
+      c->part_fbits = (int)value;
       return PM4G_OK;
     case PM4G_OPT_PART1_ITEMS:
     case PM4G_OPT_PART2_ITEMS:
@@ -948,6 +977,10 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
       // record scatter otherwise.
       int fbits = 0;
       while (fbits < 8 && ((L->nb + (1u << fbits) - 1) >> fbits) > kPartMaxBins) ++fbits;
+      // a launch choice may ask for fewer, larger coarse buckets (more final
+      // buckets in each), as long as the second level's digits fit a pass
+      if (c->part_fbits > fbits && (1u << c->part_fbits) <= kPartMaxBins && L->clb + c->part_fbits <= 16)
+        fbits = c->part_fbits;
       const uint32_t nc = (L->nb + (1u << fbits) - 1) >> fbits;
       const bool two_level = fbits > 0 && nc <= kPartMaxBins && L->clb + fbits <= 16;
       uint32_t *mat1 = mat;
@@ -1269,6 +1302,49 @@ static int ensure_edges(pm4g_log *L) {
       PM4G_TRY(check_launch(c, "k_dfg_flags"));
     }
     PM4G_TRY(scan_u32(c, flags, pos, cells));
+    // the compacted edges, frequencies and endpoint counts written straight
+    // to mapped host memory (room for every cell): one wait for the query
+    const size_t need = (size_t)cells * 56 + (size_t)A * 24 + 16;
+    char *md = nullptr;
+    char *mh = mapped_buf(c, need, &md);
+    if (mh) {
+      int32_t *msrc = (int32_t *)md, *mdst = msrc + cells;
+      unsigned long long *mo = (unsigned long long *)(mdst + cells);
+      double *mmean = (double *)(mo + 5 * cells);
+      unsigned long long *mfreq = (unsigned long long *)(mmean + cells), *mends = mfreq + A;
+      {
+        KTime tk(c, "dfg");
+        k_dfg_compact<<<grid_for(cells, 256, 4096), 256, 0, c->stream>>>(t, cells, A, flags, pos, msrc, mdst, mo,
+                                                                         mo + cells, mo + 2 * cells, mo + 3 * cells,
+                                                                         mo + 4 * cells, mmean);
+        PM4G_TRY(check_launch(c, "k_dfg_compact"));
+        k_freq<<<A, 256, 0, c->stream>>>(t.cnt, L->ends.p + A, A, mfreq);
+        PM4G_TRY(check_launch(c, "k_freq"));
+      }
+      char *hends = mh + ((char *)mends - md);
+      uint32_t *hE = (uint32_t *)(hends + (size_t)A * 16);
+      PM4G_CK(cudaMemcpyAsync(hends, L->ends.p, (size_t)A * 16, cudaMemcpyDeviceToHost, c->stream));
+      PM4G_CK(cudaMemcpyAsync(hE, pos + cells, 4, cudaMemcpyDeviceToHost, c->stream));
+      PM4G_CK(cudaStreamSynchronize(c->stream));
+      E = *hE;
+      const int32_t *hsrc = (const int32_t *)mh, *hdst = hsrc + cells;
+      const unsigned long long *ho = (const unsigned long long *)(hdst + cells);
+      const double *hmean = (const double *)(ho + 5 * cells);
+      const unsigned long long *hfreq = (const unsigned long long *)(hmean + cells), *he = hfreq + A;
+      L->e_src.assign(hsrc, hsrc + E);
+      L->e_dst.assign(hdst, hdst + E);
+      L->e_cnt.assign(ho, ho + E);
+      L->e_lo.assign(ho + cells, ho + cells + E);
+      L->e_hi.assign(ho + 2 * cells, ho + 2 * cells + E);
+      L->e_min.assign(ho + 3 * cells, ho + 3 * cells + E);
+      L->e_max.assign(ho + 4 * cells, ho + 4 * cells + E);
+      L->e_mean.assign(hmean, hmean + E);
+      L->h_start.assign(he, he + A);
+      L->h_end.assign(he + A, he + 2 * A);
+      L->h_freq.assign(hfreq, hfreq + A);
+      L->edges_ready = true;
+      return PM4G_OK;
+    }
     PM4G_TRY(d2h(c, &E, pos + cells, 4));
     if (!alloc_out()) return PM4G_ENOMEM;
     KTime tk(c, "dfg");
@@ -1587,53 +1663,98 @@ int pm4g_variants(pm4g_log *L, int64_t top_k, uint32_t flags, pm4g_variants_t *o
     PM4G_TRY(check_launch(c, "k_var_out_head"));
   }
   PM4G_TRY(scan_u32(c, ol, oo, k));
-  PM4G_TRY(d2h(c, &total, oo + k, 4));
-  int32_t *oa = S.get<int32_t>(total);
-  if (!oa) return PM4G_ENOMEM;
-  if (k > 0) {
+  // the sequences go straight to mapped host memory, with room for 64
+  // activities a variant (at least 64k in all); longer top lists take a
+  // second pass sized from the offsets
+  const uint64_t cap = std::max<uint64_t>(65536, (uint64_t)k * 64);
+  char *md = nullptr;
+  char *mh = mapped_buf(c, (size_t)cap * 4, &md);
+  if (mh && k > 0) {
     KTime t(c, "variants");
-    k_var_out_acts<<<grid_for(k, 256, 65535), 256, 0, c->stream>>>(a, L->order.p, L->rep_slots.p, k, oo, oa);
+    k_var_out_acts<<<grid_for((int64_t)k * 32, 256, 65535), 256, 0, c->stream>>>(a, L->order.p, L->rep_slots.p, k, oo,
+                                                                    (int32_t *)md, cap);
     PM4G_TRY(check_launch(c, "k_var_out_acts"));
   }
   out->count = (uint64_t *)malloc(std::max<size_t>(k, 1) * 8);
   out->min_case = (int32_t *)malloc(std::max<size_t>(k, 1) * 4);
   out->off = (int64_t *)malloc(((size_t)k + 1) * 8);
-  out->acts = (int32_t *)malloc(std::max<size_t>(total, 1) * 4);
   std::vector<uint32_t> hoff((size_t)k + 1);
-  if (!out->count || !out->min_case || !out->off || !out->acts) {
+  if (!out->count || !out->min_case || !out->off) {
     pm4g_variants_free(out);
     return PM4G_ENOMEM;
   }
   cudaStream_t s = c->stream;
   const bool want_cases = (flags & PM4G_VARIANTS_CASES) != 0;
-  D2HBatch hb(c, (size_t)k * 16 + 4 + (size_t)total * 4 + (want_cases ? (size_t)L->C * 8 : 0) + 6 * 16);
-  hb.add(out->count, oc, (size_t)k * 8);
-  hb.add(out->min_case, om, (size_t)k * 4);
-  hb.add(hoff.data(), oo, ((size_t)k + 1) * 4);
-  hb.add(out->acts, oa, (size_t)total * 4);
-  if (want_cases) {
-    PM4G_TRY(ensure_case_variants(L));
-    const uint64_t R = L->R;
-    uint32_t *pf = S.get<uint32_t>(R), *pp = S.get<uint32_t>(R + 1);
-    int32_t *cid = S.get<int32_t>(L->C), *cv = S.get<int32_t>(L->C);
-    if (!pf || !pp || !cid || !cv) return PM4G_ENOMEM;
-    const unsigned gR = grid_for((int64_t)R, 256, 65535);
-    k_present_flags<<<gR, 256, 0, s>>>(L->len.p, R, pf);
-    PM4G_TRY(check_launch(c, "k_present_flags"));
-    PM4G_TRY(scan_u32(c, pf, pp, (int64_t)R));
-    k_cases_out<<<gR, 256, 0, s>>>(L->len.p, R, pp, L->cvar.p, L->min_case, L->uniq.p, cid, cv);
-    PM4G_TRY(check_launch(c, "k_cases_out"));
-    out->n_cases = L->C;
-    out->case_ids = (int32_t *)malloc(std::max<size_t>(L->C, 1) * 4);
-    out->case_variant = (int32_t *)malloc(std::max<size_t>(L->C, 1) * 4);
-    if (!out->case_ids || !out->case_variant) {
+  {
+    D2HBatch hb(c, (size_t)k * 16 + 4 + (want_cases ? (size_t)L->C * 8 : 0) + 6 * 16);
+    hb.add(out->count, oc, (size_t)k * 8);
+    hb.add(out->min_case, om, (size_t)k * 4);
+    hb.add(hoff.data(), oo, ((size_t)k + 1) * 4);
+    if (want_cases) {
+      if (const int st = ensure_case_variants(L)) {
+        pm4g_variants_free(out);
+        return st;
+      }
+      const uint64_t R = L->R;
+      uint32_t *pf = S.get<uint32_t>(R), *pp = S.get<uint32_t>(R + 1);
+      int32_t *cid = S.get<int32_t>(L->C), *cv = S.get<int32_t>(L->C);
+      if (!pf || !pp || !cid || !cv) {
+        pm4g_variants_free(out);
+        return PM4G_ENOMEM;
+      }
+      const unsigned gR = grid_for((int64_t)R, 256, 65535);
+      k_present_flags<<<gR, 256, 0, s>>>(L->len.p, R, pf);
+      int st = check_launch(c, "k_present_flags");
+      if (!st) st = scan_u32(c, pf, pp, (int64_t)R);
+      if (!st) {
+        k_cases_out<<<gR, 256, 0, s>>>(L->len.p, R, pp, L->cvar.p, L->min_case, L->uniq.p, cid, cv);
+        st = check_launch(c, "k_cases_out");
+      }
+      if (st) {
+        pm4g_variants_free(out);
+        return st;
+      }
+      out->n_cases = L->C;
+      out->case_ids = (int32_t *)malloc(std::max<size_t>(L->C, 1) * 4);
+      out->case_variant = (int32_t *)malloc(std::max<size_t>(L->C, 1) * 4);
+      if (!out->case_ids || !out->case_variant) {
+        pm4g_variants_free(out);
+        return PM4G_ENOMEM;
+      }
+      hb.add(out->case_ids, cid, L->C * 4);
+      hb.add(out->case_variant, cv, L->C * 4);
+    }
+    const int st = hb.finish();  // waits for the mapped sequences too
+    if (st != PM4G_OK) {
+      pm4g_variants_free(out);
+      return st;
+    }
+  }
+  total = hoff[k];
+  out->acts = (int32_t *)malloc(std::max<size_t>(total, 1) * 4);
+  if (!out->acts) {
+    pm4g_variants_free(out);
+    return PM4G_ENOMEM;
+  }
+  if (mh && total <= cap) {
+    if (total) memcpy(out->acts, mh, (size_t)total * 4);
+  } else if (total > 0) {
+    int32_t *oa = S.get<int32_t>(total);
+    if (!oa) {
       pm4g_variants_free(out);
       return PM4G_ENOMEM;
     }
-    hb.add(out->case_ids, cid, L->C * 4);
-    hb.add(out->case_variant, cv, L->C * 4);
-  }
-  {
+    {
+      KTime t(c, "variants");
+      k_var_out_acts<<<grid_for((int64_t)k * 32, 256, 65535), 256, 0, c->stream>>>(a, L->order.p, L->rep_slots.p, k, oo, oa,
+                                                                      ~0ull);
+    }
+    if (const int st = check_launch(c, "k_var_out_acts")) {
+      pm4g_variants_free(out);
+      return st;
+    }
+    D2HBatch hb(c, (size_t)total * 4 + 16);
+    hb.add(out->acts, oa, (size_t)total * 4);
     const int st = hb.finish();
     if (st != PM4G_OK) {
       pm4g_variants_free(out);

@@ -69,6 +69,7 @@ struct Ctx {
   int stream_off = 0;
   int part1_items = 0;
   int part2_items = 0;
+  int part_fbits = 0;
   // launch choices of the batched drill-down (PM4G_OPT_BATCH_*; 0 = default)
   int batch_chunk = 0;
   int batch_stages = 0;
@@ -91,6 +92,12 @@ struct Ctx {
   // bulk result copies on the copy engines (allocated when first used)
   void *small = nullptr;
   void *small_dev = nullptr;
+  // page-locked, device-mapped result staging: kernels write a query's
+  // results straight to host memory, so the query needs one wait in all
+  // (grown when first needed; at most kMappedMax bytes)
+  void *mapped = nullptr;
+  void *mapped_dev = nullptr;
+  size_t mapped_bytes = 0;
   // device blocks freed by this context, kept for reuse in stream order
   // (rounded size -> blocks); every kernel of the context runs on its stream
   std::multimap<size_t, void *> cache;
@@ -227,6 +234,11 @@ struct D2HBatch {
 int d2h(Ctx *c, void *dst, const void *src, size_t bytes);
 // Reads n (1..8) 32-bit device words with one wait on the context stream.
 int d2h_words(Ctx *c, uint32_t *const *dst, const uint32_t *const *src, int n);
+// Device-mapped staging of at least `bytes` (host pointer; *dev the device
+// view), or NULL if bytes > kMappedMax or the allocation fails. Growing it
+// waits for the context stream.
+constexpr size_t kMappedMax = (size_t)64 << 20;
+char *mapped_buf(Ctx *c, size_t bytes, char **dev);
 bool small_buffer(Ctx *c);
 
 }  // namespace pm4g

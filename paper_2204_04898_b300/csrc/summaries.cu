@@ -482,14 +482,23 @@ __global__ void k_var_out_head(VarArgs a, const uint32_t *order, const uint32_t 
   }
 }
 
+// The top variants' sequences at o_acts[o_off[i]]; a sequence that would end
+// beyond `cap` entries is not written (the caller then sizes a buffer from
+// the offsets and calls again).
+// One warp a variant, its lanes copying consecutive activities (coalesced
+// writes, also when o_acts is mapped host memory).
 __global__ void k_var_out_acts(VarArgs a, const uint32_t *order, const uint32_t *rep_slots, uint32_t k_out,
-                               const uint32_t *o_off, int32_t *o_acts) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k_out; i += gridDim.x * blockDim.x) {
+                               const uint32_t *o_off, int32_t *o_acts, uint64_t cap) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = w0; i < k_out; i += nw) {
     const uint32_t rep = rep_slots[order[i]];
     const int32_t *q = a.act_s + a.off[rep];
     const uint32_t L = a.len[rep];
+    if ((uint64_t)o_off[i] + L > cap) continue;
     int32_t *o = o_acts + o_off[i];
-    for (uint32_t j = 0; j < L; ++j) o[j] = q[j];
+    for (uint32_t j = lane; j < L; j += 32) o[j] = q[j];
   }
 }
 

@@ -61,6 +61,6 @@ __global__ void k_var_out_head(VarArgs a, const uint32_t *order, const uint32_t 
                                int32_t min_case, const int32_t *uniq, unsigned long long *o_count, int32_t *o_min,
                                uint32_t *o_len);
 __global__ void k_var_out_acts(VarArgs a, const uint32_t *order, const uint32_t *rep_slots, uint32_t k_out,
-                               const uint32_t *o_off, int32_t *o_acts);
+                               const uint32_t *o_off, int32_t *o_acts, uint64_t cap);
 
 }  // namespace pm4g

@@ -24,7 +24,7 @@ TW_NONE, TW_EVENTS, TW_CASES_CONTAINED, TW_CASES_INTERSECTING = 0, 1, 2, 3
 OPT_TIMING, OPT_TEST_HASH_BITS, OPT_TEST_BUCKET_CAP = 1, 2, 3
 OPT_BATCH_CHUNK, OPT_BATCH_STAGES, OPT_BATCH_ITEMS_PER_SM = 4, 5, 6
 OPT_EDGE_TABLE, OPT_LOAD_CLB, OPT_LOAD_SPLITS, OPT_STREAM_WARPS, OPT_STREAM_OFF = 7, 8, 9, 10, 11
-OPT_PART1_ITEMS, OPT_PART2_ITEMS = 12, 13
+OPT_PART1_ITEMS, OPT_PART2_ITEMS, OPT_PART_FBITS = 12, 13, 14
 MAX_ACTIVITIES = 65536
 
 _P = ctypes.c_void_p

@@ -83,7 +83,7 @@ def test_load_signature_groups_logs_of_about_the_same_shape():
 
 def test_load_space_descent_from_the_defaults():
     target = {"clb": 7, "splits": 4, "stream_warps": 16, "stream_off": 0, "edge_table": 0, "part1_items": 4,
-              "part2_items": 0}
+              "part2_items": 0, "part_fbits": 9}
 
     def cost(c):
         return sum((autotune.LOAD_SPACE[k].index(c[k]) - autotune.LOAD_SPACE[k].index(target[k])) ** 2

@@ -1,6 +1,6 @@
 """The single-log pass's launch choices (bucket width, second-level partition
 units, streaming-pass warps, streaming pass on or off, dense or hashed global
-edge table, records a thread stages per partition tile) never change a result: every output of pm4g_load_log and the
+edge table, records a thread stages per partition tile, coarse fan-out) never change a result: every output of pm4g_load_log and the
 summaries is bit-identical across choice sets and equal to the oracle's, and
 a context the autotuner tuned keeps giving the oracle's results."""
 
@@ -21,7 +21,9 @@ CHOICES = [
     {"clb": 8, "splits": 16, "stream_warps": 20},
     {"clb": 3, "stream_off": 1, "edge_table": 1},
     {"part1_items": 4},
-    {"part1_items": 4, "part2_items": 4, "clb": 7, "splits": 4},
+    {"part1_items": 4, "part2_items": 8, "clb": 7, "splits": 4},
+    {"part_fbits": 9},
+    {"part_fbits": 8, "clb": 6, "part2_items": 8},
 ]
 
 
@@ -75,7 +77,7 @@ def test_tuned_context_keeps_the_oracle_results():
     ctx = pm4g.pm4g_ctx_create(0)
     try:
         small = {"clb": (0, 6), "splits": (0, 4), "stream_warps": (0, 12), "stream_off": (0, 1),
-                 "edge_table": (0, 1), "part1_items": (0, 4), "part2_items": (0,)}
+                 "edge_table": (0, 1), "part1_items": (0, 4), "part2_items": (0,), "part_fbits": (0, 9)}
         choice = autotune.Tuner(cache_path="").tune_load(ctx, cols, L.n_activities, top_k=10, reps=1, space=small)
         assert set(choice) == set(autotune.LOAD_KNOBS)
         assert all(choice[k] in small[k] for k in choice)
