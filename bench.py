@@ -39,6 +39,7 @@ value = pairs / step time (and events / step time beside it).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -160,7 +161,9 @@ class ClockSampler:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     PERIOD_S = 1.0
 
-    def __init__(self, gpu_index: int, warm=None, steps: int = 0, warm_steps: int = 3, pad=None):
+    def __init__(self, gpu_index: int, warm=None, steps: int = 0, warm_steps: int = 3, pad=None,
+                 period_s: float = 1.0):
+        self.PERIOD_S = period_s
         self.gpu = gpu_index
         self.proc = None
         self.path = None
@@ -616,10 +619,14 @@ def serve_core(args, local: int, rates: list, seconds: float, small_log: bool = 
     # warm: drill-down index, variant table, upload contexts
     eng.batch_dfg([Request("dfg", attr_set=views[0].attr_set, t_lo=views[0].t_lo, t_hi=views[0].t_hi)])
     eng.variants(10)
-    eng.upload(Request("upload", columns=(pool[0].case_id, pool[0].activity, pool[0].ts_ns), n_activities=A), 0)
+    for slot in range(2):  # every upload slot's context, pools and staging buffers
+        eng.upload(Request("upload", columns=(pool[0].case_id, pool[0].activity, pool[0].ts_ns), n_activities=A),
+                   slot)
     srv = Server(eng, upload_slots=2)
     per_rate = []
-    with ClockSampler(local) as clk:
+    # a sample every 5 s: each one stalls the GPU's work for milliseconds,
+    # which shows in the latency tail of the requests queued behind it
+    with ClockSampler(local, period_s=5.0) as clk:
         for rate in rates:
             n = max(1, int(rng.poisson(rate * seconds)))
             arrivals = np.sort(rng.uniform(0, seconds, n))
@@ -635,15 +642,23 @@ def serve_core(args, local: int, rates: list, seconds: float, small_log: bool = 
                     u = pool[int(rng.integers(len(pool)))]
                     reqs.append(Request("upload", columns=(u.case_id, u.activity, u.ts_ns), n_activities=A))
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for r, at in zip(reqs, arrivals):
-                d = t0 + at - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                r.t_arrival = t0 + at
-                srv.submit(r)
-            for r in reqs:
-                r.done.wait(600)
+            # the Python garbage collector is off while a rate runs: its full
+            # collections stop every thread of the process (the server's
+            # workers included) for 50-130 ms at this request volume
+            gc.collect()
+            gc.disable()
+            try:
+                t0 = time.perf_counter()
+                for r, at in zip(reqs, arrivals):
+                    d = t0 + at - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    r.t_arrival = t0 + at
+                    srv.submit(r)
+                for r in reqs:
+                    r.done.wait(600)
+            finally:
+                gc.enable()
             t_end = max(r.t_done for r in reqs)
             ok = [r for r in reqs if r.done.is_set() and r.error is None]
             ev = sum(r.result["n_events"] for r in ok if r.kind in ("dfg", "upload"))
@@ -687,7 +702,7 @@ def run_serve(args):
                    "n_activities": r["n_activities"], "mix": "70% filter+DFG (EVENTS), 20% variants top-10, 10% upload",
                    "upload_events": r["upload_events"], "seconds_per_rate": r["seconds_per_rate"],
                    "load_ms": round(r["load_ms"], 1), "generate_s": round(r["t_gen"], 1),
-                   "l2": "resident log larger than L2; no flush"},
+                   "l2": "resident log larger than L2; no flush", "python_gc": "off while a rate runs"},
         "rates": per_rate,
         "small_log": r["small_log"],
         "p50_ms": top["all"].get("p50_ms"), "p99_ms": top["all"].get("p99_ms"),
@@ -1213,8 +1228,8 @@ def main():
                               "variants_p99_ms": e["variants"].get("p99_ms"),
                               "upload_p99_ms": e["upload"].get("p99_ms"), "dfg_batches": e["dfg_batches"]}
                              for e in r["per_rate"]],
-                   "latency": "arrival to result on the host", "gpu_launches": r["gpu_launches"],
-                   "clocks": r["clocks"]}
+                   "latency": "arrival to result on the host", "python_gc": "off while a rate runs",
+                   "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
         torch.cuda.empty_cache()
     if rank != 0:
         return
