@@ -189,36 +189,47 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        # the second sample's arrival gives the sampler's phase (its start-up
-        # is over by then)
+        # the arrivals of the second and third samples give the sampler's
+        # phase and period (its start-up is over by then)
         t0 = time.time()
-        t_sample = None
-        while self.proc is not None and time.time() - t0 < 10.0:
-            if self._lines() >= 2:
-                t_sample = time.time()
+        t_sample, period, seen = None, self.PERIOD_S, {}
+        while self.proc is not None and time.time() - t0 < 10.0 + 2 * self.PERIOD_S:
+            n_lines = self._lines()
+            for m in (2, 3):
+                if n_lines >= m and m not in seen:
+                    seen[m] = time.time()
+            if 3 in seen:
+                t_sample = seen[3]
+                if 2 in seen and 0.5 * self.PERIOD_S < seen[3] - seen[2] < 1.5 * self.PERIOD_S:
+                    period = seen[3] - seen[2]
                 break
-            time.sleep(0.005)
+            time.sleep(0.002)
         if self.warm is not None:
             tw = time.time()
             self.warm()
             t_warm = time.time() - tw
             per_step = t_warm / max(1, self.warm_steps)
+            if self.pad is not None:  # one more step, timed on a warm GPU
+                tp = time.time()
+                self.pad()
+                per_step = time.time() - tp
             region = per_step * self.steps
-            if t_sample is not None and 0 < region < self.PERIOD_S:
+            w2 = per_step * self.warm_steps  # the warm-up that runs last
+            if t_sample is not None and 0 < region < period:
                 # start so that the next sample lands in the middle of the
                 # region; the GPU keeps working until then (an idle GPU is
-                # slower for its first steps): untimed steps, then the warm-up
-                # again (it also resets the counters of the timed region)
+                # slower for its first steps): untimed steps, an idle gap
+                # shorter than one step, then the warm-up again (it also
+                # resets the counters of the timed region)
                 now = time.time()
-                k = max(1, int((now + t_warm - t_sample + region / 2) / self.PERIOD_S) + 1)
-                start = t_sample + k * self.PERIOD_S - region / 2
+                k = max(1, int((now + per_step + w2 - t_sample + region / 2) / period) + 1)
+                start = t_sample + k * period - region / 2
                 if self.pad is not None:
-                    while time.time() + per_step + t_warm <= start - region / 4:
+                    while time.time() + per_step + w2 <= start:
                         self.pad()
-                else:
-                    now = time.time()
-                    if start - t_warm > now:
-                        time.sleep(start - t_warm - now)
+                gap = start - w2 - time.time()
+                if gap > 0:
+                    time.sleep(gap)
                 self.warm()
         self.t_begin = time.time()
         return self
