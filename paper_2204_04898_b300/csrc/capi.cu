@@ -1567,6 +1567,14 @@ static int ensure_variants(pm4g_log *L) {
   a.n_slots = R;
   a.len = L->len.p;
   a.hash = nullptr;  // formed from the formatted activities in the first round
+  {
+    unsigned long long *gtab = S.get<unsigned long long>((size_t)std::max<int64_t>(L->A, 1));
+    if (!gtab) return PM4G_ENOMEM;
+    KTime t(c, "variants");
+    k_var_gtab<<<grid_for(L->A, 256, 256), 256, 0, c->stream>>>(gtab, (uint32_t)L->A);
+    PM4G_TRY(check_launch(c, "k_var_gtab"));
+    a.gtab = gtab;
+  }
   a.off = L->off.p;
   a.act_s = L->act_s.p;
   a.n_events = L->n;

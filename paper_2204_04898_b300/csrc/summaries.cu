@@ -200,34 +200,64 @@ __device__ __forceinline__ void warp_compare(const int32_t *act_s, uint32_t todo
   }
 }
 
-// First grouping round over all case slots, with the sequence hash (seed 0)
-// formed on the way from the formatted activities. A warp takes 32
-// consecutive case slots, whose events are contiguous in the formatted order,
-// and walks them 128 events at a time, four consecutive events a lane (one
-// 16-byte load; the walk starts at the 16-byte boundary at or before the
-// slots' first event). Four OR-reductions per window give the bits of the
-// positions where a (non-empty) case starts; a lane's first event belongs to
-// the case counted by the starts before it, and its next three events to the
-// same case unless a start bit says otherwise, so only the lane's first event
-// looks up its case's first position. The terms are prefix-summed (within the
-// lane, a warp scan of the lanes' totals, and the running total of the
-// windows before), and each case start records the prefix sum just before it:
-// a case's hash is the difference between the next case's record (or the
-// walk's total, for the last case) and its own, so the walk needs no
-// segmented reduction. Each lane then inserts its own slot. (Measured slower:
-// lanes walking whole cases of their own, whose loads touch 32 lines at once;
-// checking each case against its group's claimer inside this walk, which puts
-// the check's chain of dependent random loads on the walk's warps.)
+// First-round sequence hash: a polynomial over the case's activities,
+// H = sum_j g(a_j) r^j mod 2^64 (j the position in the case, g a table of
+// mixed 64-bit words of the activity codes, r an odd constant). It only
+// accelerates grouping (equality is always checked on the sequences), and
+// unlike a sum of mixed (activity, position) terms it needs no position per
+// event: a walk that sums g(a) r^w over walk positions w gets a case's H as
+// (sum over the case) * r^-(its first position).
+constexpr uint64_t kVarR = 0x9E3779B97F4A7C15ull;  // odd
+__host__ __device__ constexpr uint64_t inv_odd(uint64_t r) {
+  uint64_t x = r;  // r * r = 1 mod 8; each step doubles the correct low bits
+  for (int i = 0; i < 6; ++i) x *= 2 - r * x;
+  return x;
+}
+constexpr uint64_t kVarRinv = inv_odd(kVarR);
+static_assert(kVarR * kVarRinv == 1ull, "inverse of the hash base");
+__host__ __device__ constexpr uint64_t pow_u64(uint64_t b, uint64_t e) {
+  uint64_t x = 1;
+  for (; e; e >>= 1, b *= b)
+    if (e & 1) x *= b;
+  return x;
+}
+
+__global__ void k_var_gtab(unsigned long long *g, uint32_t n_act) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_act; i += gridDim.x * blockDim.x)
+    g[i] = fmix64(((uint64_t)i << 1) ^ 0x632BE59BD9B4E019ull);
+}
+
+// First grouping round over all case slots, with the polynomial hash formed
+// on the way from the formatted activities. A warp takes 32 consecutive case
+// slots, whose events are contiguous in the formatted order, and walks them
+// 128 events at a time, four consecutive events a lane (one 16-byte load; the
+// walk starts at the 16-byte boundary at or before the slots' first event).
+// Each lane sums g(a) r^(4 lane + j) over its four events; a warp scan of the
+// lanes' sums, scaled by r^(window start), and the running total of the
+// windows before give the prefix sums of the walk. Each case's lane fetches,
+// with shuffles, the prefix sum just before its first event when the window
+// holds it; a case's sum is the difference between the next case's record
+// (or the walk's total, for the last case) and its own. Each lane then
+// normalises its case's sum by r^-(first position) and inserts its slot.
+// (Measured slower: lanes walking whole cases of their own, whose loads touch
+// 32 lines at once; checking each case against its group's claimer inside
+// this walk, which puts the check's chain of dependent random loads on the
+// walk's warps; a per-event hash of (activity, position in case), which
+// needs each event's case and position.)
 __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
-  // per warp: low and high words of the prefix sum before each of up to 32
-  // cases, and each case's first position
-  __shared__ uint32_t s_acc[kHiThreads / 32][96];
+  // per warp: the prefix sum before each of up to 32 cases
+  __shared__ unsigned long long s_pre[kHiThreads / 32][32];
   const uint32_t lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-  uint32_t *gs_lo = s_acc[wb], *gs_hi = gs_lo + 32, *sstart = gs_lo + 64;
+  unsigned long long *pre = s_pre[wb];
   const uint32_t lt = lanemask_lt();
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   const uint64_t stride = n_warps * 32;
+  constexpr uint64_t kR128 = pow_u64(kVarR, 128);
+  uint64_t rp[4];  // r^(4 lane + j)
+  rp[0] = pow_u64(kVarR, 4 * lane);
+#pragma unroll
+  for (int j = 1; j < 4; ++j) rp[j] = rp[j - 1] * kVarR;
   // the next group's lengths and first position are loaded one group ahead
   uint64_t s0 = warp * 32;
   uint32_t L_next = s0 + lane < a.n_slots ? a.len[s0 + lane] : 0u;
@@ -249,8 +279,6 @@ __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     const uint32_t ne = __ballot_sync(kFull, L > 0);
     const uint32_t rank = __popc(ne & lt), n_ne = __popc(ne);  // among the non-empty slots
-    if (L) sstart[rank] = excl;
-    __syncwarp();
     // walk position w = formatted position - e0, with e0 a multiple of four
     const uint64_t e0 = off0 & ~3u;
     const uint32_t sh = off0 - (uint32_t)e0, tw = total + sh;
@@ -272,77 +300,46 @@ __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
       return v;
     };
     int4 v1 = load4(0), v2 = load4(128);
-    uint32_t before = 0;       // non-empty cases that start before the window
-    uint32_t clo = 0, chi = 0;  // sums of the terms of the windows before
+    uint64_t rw = 1;     // r^w0
+    uint64_t done = 0;   // the walk's sum over the windows before
     for (uint32_t w0 = 0; w0 < tw; w0 += 128) {
       const uint32_t wl = w0 + 4 * lane;  // walk position of the lane's first event
       const int4 v = v1;
       v1 = v2;
       v2 = load4(w0 + 256);
-      uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-      if (L && my_ws >= w0 && my_ws - w0 < 128u) {
-        const uint32_t bi = my_ws - w0, bit = 1u << (bi & 31);
-        if (bi < 32) b0 = bit;
-        else if (bi < 64) b1 = bit;
-        else if (bi < 96) b2 = bit;
-        else b3 = bit;
-      }
-      const uint32_t S0 = __reduce_or_sync(kFull, b0), S1 = __reduce_or_sync(kFull, b1);
-      const uint32_t S2 = __reduce_or_sync(kFull, b2), S3 = __reduce_or_sync(kFull, b3);
-      const uint32_t wi = lane >> 3, sb = 4 * (lane & 7);
-      const uint32_t Sw = wi == 0 ? S0 : wi == 1 ? S1 : wi == 2 ? S2 : S3;
-      const uint32_t nib = (Sw >> sb) & 0xFu;  // starts among the lane's four events
-      uint32_t cr = before + (wi > 0 ? __popc(S0) : 0u) + (wi > 1 ? __popc(S1) : 0u) + (wi > 2 ? __popc(S2) : 0u) +
-                    __popc(Sw & ((1u << sb) - 1u)) - 1u;  // case of the event before the lane's first
       const int32_t act4[4] = {v.x, v.y, v.z, v.w};
-      uint32_t tl[4], th[4], ul = 0, uh = 0, stc[4];
-      uint32_t pos = 0;
-      bool have = false;
+      uint64_t ex[4], u = 0;  // the lane's sums before each of its events, and in all
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
+        ex[j] = u;
         const uint32_t w = wl + j;
-        const bool valid = w >= sh && w < tw;
-        const bool st = (nib >> j) & 1u;
-        if (st) {
-          ++cr;
-          pos = 0;
-          have = true;
-        } else if (valid) {
-          pos = have ? pos + 1 : (w - sh) - sstart[cr];
-          have = true;
-        }
-        stc[j] = cr;
-        uint64_t t = 0;
-        if (valid) t = event_hash((uint32_t)act4[j], pos, 0);
-        tl[j] = ul;  // the lane's sum before this event
-        th[j] = uh;
-        ul += (uint32_t)t;
-        uh += (uint32_t)(t >> 32);
+        if (w >= sh && w < tw) u += (uint64_t)__ldg(a.gtab + act4[j]) * rp[j];
       }
-      uint32_t il = ul, ih = uh;  // inclusive prefix sums of the lanes' totals
+      uint64_t inc = u;  // inclusive prefix sums of the lanes' sums
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t yl = __shfl_up_sync(kFull, il, o), yh = __shfl_up_sync(kFull, ih, o);
-        if ((int)lane >= o) {
-          il += yl;
-          ih += yh;
-        }
+        const uint64_t y = __shfl_up_sync(kFull, inc, o);
+        if ((int)lane >= o) inc += y;
       }
-      const uint32_t xl = clo + il - ul, xh = chi + ih - uh;  // sums before the lane's first event
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if ((nib >> j) & 1u) {
-          gs_lo[stc[j]] = xl + tl[j];
-          gs_hi[stc[j]] = xh + th[j];
-        }
-      clo += __shfl_sync(kFull, il, 31);
-      chi += __shfl_sync(kFull, ih, 31);
-      before += __popc(S0) + __popc(S1) + __popc(S2) + __popc(S3);
+      const uint64_t x = inc - u;
+      // a case starting in this window reads the prefix sum before its first
+      // event from the lane that holds it
+      const uint32_t bi = my_ws - w0;
+      const bool mine = L && my_ws >= w0 && bi < 128u;
+      const int src = mine ? (int)(bi >> 2) : (int)lane;
+      const uint64_t p0 = __shfl_sync(kFull, x + ex[0], src), p1 = __shfl_sync(kFull, x + ex[1], src);
+      const uint64_t p2 = __shfl_sync(kFull, x + ex[2], src), p3 = __shfl_sync(kFull, x + ex[3], src);
+      if (mine) {
+        const uint32_t sub = bi & 3u;
+        pre[rank] = done + rw * (sub == 0 ? p0 : sub == 1 ? p1 : sub == 2 ? p2 : p3);
+      }
+      done += rw * __shfl_sync(kFull, inc, 31);
+      rw *= kR128;
     }
     __syncwarp();
     if (L) {
-      const uint32_t nl = rank + 1 < n_ne ? gs_lo[rank + 1] : clo, nh = rank + 1 < n_ne ? gs_hi[rank + 1] : chi;
-      var_insert_one(a, (uint32_t)s, L, ((uint64_t)(nh - gs_hi[rank]) << 32) | (nl - gs_lo[rank]), 0);
+      const uint64_t nxt = rank + 1 < n_ne ? pre[rank + 1] : done;
+      var_insert_one(a, (uint32_t)s, L, (nxt - pre[rank]) * pow_u64(kVarRinv, my_ws), 0);
     }
     __syncwarp();
   }

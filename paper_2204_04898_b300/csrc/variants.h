@@ -32,6 +32,7 @@ struct VarArgs {
   uint8_t *isbad;
   const uint32_t *cls;     // optional class of each slot (batched sub-logs): a variant never spans two classes
   uint32_t *rep_flag;      // optional: 1 at every representative, 0 at every other slot (k_var_final)
+  const unsigned long long *gtab;  // first round without a.hash: the hash's word of every activity (k_var_gtab)
 };
 
 // Groups the items of `a` (slots with len > 0, or the whole list) by exact
@@ -45,6 +46,7 @@ int group_variants(Ctx *c, VarArgs a, uint64_t n_items, uint32_t *rep_pos = null
 
 // First round over all slots with the hash formed from act_s (a.hash NULL).
 constexpr int kHiThreads = 256;
+__global__ void k_var_gtab(unsigned long long *g, uint32_t n_act);
 __global__ void k_var_hash_insert(VarArgs a);
 __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t round);
 __global__ void k_var_verify(VarArgs a, const uint32_t *list, uint32_t n_list, uint32_t *bad_out, uint32_t *n_bad);
