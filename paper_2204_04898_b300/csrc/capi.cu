@@ -370,7 +370,6 @@ static SegArgs seg_args(pm4g_log *L, const SegConfig &sc, uint32_t *work, uint32
   a.g.mask = L->ghash ? cells - 1 : 0;
   a.g_start = L->ends.p;
   a.g_end = L->ends.p + L->A;
-  a.order_flags = L->status.p;  // a filtered log carries the word of the log it comes from
   a.ovf = ovf;
   a.n_ovf = n_ovf;
   a.n_cases = n_cases;
@@ -499,10 +498,10 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   a.cattr = write_cattr ? L->cattr.p : nullptr;
   a.err = ctr + 2;
   a.g.err = ctr + 2;
-  if (keys && L->status.p && c->test_bucket_cap == 0 && sc.cap >= 32 && !L->ghash && L->A <= 2048 &&
-      !c->stream_off) {
-    // time-ordered logs: the streaming pass (it returns at once otherwise,
-    // and the sorting pass below then does the work)
+  if (keys && c->test_bucket_cap == 0 && sc.cap >= 32 && !L->ghash && L->A <= 2048 && !c->stream_off) {
+    // the streaming pass, for logs whose cases' events come in timestamp
+    // order (it checks this itself; a log where it finds a case out of order
+    // is cleared of its partial sums and redone by the sorting pass below)
     int w = stream_segment_warps(L->clb, sc.a_s, (size_t)c->smem_optin);
     if (c->stream_warps > 0) w = std::min(w, c->stream_warps);
     const size_t cells = (size_t)L->A * L->A;
@@ -523,9 +522,13 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
       a.n_ids = ctr + 3;
       const size_t smem = st_smem_layout(1 << L->clb, sc.a_s, w).total;
       const unsigned grid = std::min<unsigned>((L->nb + w - 1) / w, (unsigned)c->num_sms);
-      KTime t(c, "segment");
+      {
+        KTime t(c, "segment");
+        c->launches++;
+        PM4G_CK(launch_stream_segment(a, w, grid, smem, c->stream));
+      }
       c->launches++;
-      PM4G_CK(launch_stream_segment(a, w, grid, smem, c->stream));
+      PM4G_CK(launch_stream_undo(a, (uint32_t)L->A, (unsigned)c->num_sms, c->stream));
       a.skip_ordered = 1;
     }
   }
@@ -563,7 +566,7 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
     PM4G_TRY(d2h(c, h.nc, n_cases, sizeof(h.nc)));  // the global path adds its cases
   }
   L->C = (int64_t)h.nc[0];
-  L->off_ready = h.err[1] != 0;  // the streaming pass wrote the case offsets
+  L->off_ready = h.err[1] != 0 && !(h.ctr[2] & kStDisorder);  // the streaming pass wrote the case offsets
   auto &sw = c->totals["sorted_windows"];
   sw.first += (int64_t)h.nc[1];
   return PM4G_OK;
@@ -1084,11 +1087,9 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
           }
         }
       } else {
-        // the record scatter may reorder a case's events: the segment pass checks them all
-        if (cudaMemsetAsync(err, 2, 1, c->stream) != cudaSuccess) {
-          fail(PM4G_ECUDA);
-          break;
-        }
+        // the record scatter may reorder a case's events: no key words are
+        // written, so the sorting pass (which checks every case's order)
+        // takes the log
         for (uint32_t b0 = 0; b0 < L->nb && st == PM4G_OK; b0 += nbs_max) {
           const uint32_t nbs = std::min(nbs_max, L->nb - b0);
           KTime t(c, "bucket_scatter");

@@ -372,7 +372,6 @@ __global__ void __launch_bounds__(kPartThreads, kItems == 4 ? 3 : 2) k_partition
   // Level 1 holds the raw columns (case id, activity, timestamp) in rec until
   // the record is formed.
   uint4 rec[kItems];
-  int64_t t_before = 0;  // level 1, lane 0: timestamp of the row before the warp's first row
   // Loading tile t + 1 also starts moving tile t + 2 into L2, so that the
   // loads of every tile after the first find their data there.
   auto prefetch_tile = [&](uint32_t base) {
@@ -389,7 +388,6 @@ __global__ void __launch_bounds__(kPartThreads, kItems == 4 ? 3 : 2) k_partition
   auto load_tile = [&](uint32_t base) {
     prefetch_tile(base + kTile);
     const uint32_t wb = base + (uint32_t)warp * (32 * kItems) + lane;
-    if (kLevel == 1 && lane == 0 && wb > 0 && wb < i1) t_before = a.ts[wb - 1];
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       const uint32_t i = wb + r * 32;
@@ -405,22 +403,12 @@ __global__ void __launch_bounds__(kPartThreads, kItems == 4 ? 3 : 2) k_partition
     }
   };
   if (i0 < i1) load_tile(i0);
-  bool desc = false;  // level 1: a timestamp below the previous row's
   for (uint32_t base = i0; base < i1; base += kTile) {
     uint32_t dg[kItems];
     const uint32_t wbase = base + (uint32_t)warp * (32 * kItems) + lane;
-    int64_t t_last = 0;  // previous round's timestamp (lane 31's is the row before this round's lane 0)
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       const uint32_t i = wbase + r * 32;
-      if (kLevel == 1) {
-        const int64_t t = (int64_t)(((uint64_t)rec[r].w << 32) | rec[r].z);
-        int64_t tp = __shfl_up_sync(kFull, t, 1);
-        const int64_t t31 = __shfl_sync(kFull, t_last, 31);
-        if (lane == 0) tp = r > 0 ? t31 : (i > 0 && i < i1 ? t_before : t);
-        if (i < i1 && i > 0 && tp > t) desc = true;
-        t_last = t;
-      }
       dg[r] = 0xFFFFFFFFu;
       if (i < i1) {
         if (kLevel == 1) {
@@ -522,8 +510,7 @@ __global__ void __launch_bounds__(kPartThreads, kItems == 4 ? 3 : 2) k_partition
   }
   if ((uint32_t)tid < nbins) bulk_wait_all();
   if (kLevel == 1) {
-    const bool any_bad = __any_sync(kFull, bad), any_desc = __any_sync(kFull, desc);
-    if (lane == 0 && (any_bad || any_desc)) atomicOr(a.err_flags, (any_bad ? 1u : 0u) | (any_desc ? 2u : 0u));
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err_flags, 1u);
   }
 }
 

@@ -119,9 +119,11 @@ struct SegArgs {
   int64_t *ex_row;
   int32_t min_case;
   const int32_t *uniq;
-  const uint32_t *order_flags;  // optional: bit 1 clear = every case's records are in (timestamp, row) order
-  int skip_ordered;             // sorting pass: do nothing when the streaming pass handles the log
-  uint32_t *err;                // streaming pass: bit 0 set when case lengths disagree with the records
+  int skip_ordered;  // sorting pass: do nothing unless the streaming pass found a case out of order
+  // streaming pass: bit 0 set when case lengths disagree with the records;
+  // kStDisorder when a case's events are not in timestamp order in its
+  // bucket (the pass then stops early; the sorting pass redoes the log)
+  uint32_t *err;
   const uint32_t *keys;         // streaming pass: first word of every bucketed record (bucket order)
   // streaming pass: edge ids (emap, A * A, ~0 = none yet), the key of every
   // id (key_of, kStSlots) and the id counter; ids below kStSlots index the
@@ -129,12 +131,13 @@ struct SegArgs {
   uint32_t *emap, *key_of, *n_ids;
   // streaming pass, optional: every case slot's first formatted position
   // (n_slots + 1 entries, the last = the event count), and a word set to 1
-  // when the pass ran (the log was time-ordered)
+  // when the pass ran (its outputs count only without kStDisorder)
   uint32_t *off_out, *ran;
 };
+constexpr uint32_t kStDisorder = 4u;
 
 // Streaming segment pass (stream.cu): one warp per bucket, for logs whose
-// timestamps never decrease in row order. Shared memory: an edge table of
+// cases' events are in timestamp order in row order (it checks this itself). Shared memory: an edge table of
 // kStSlots slots indexed by edge id (count, low and middle sum words, high
 // words of the pushed minimum and maximum), the endpoint counts, then per
 // warp the case state of its bucket (last timestamp, first position, events
@@ -156,6 +159,11 @@ __host__ __device__ inline StSmem st_smem_layout(int ncl, int a_s, int n_warps) 
 // warps per block whose layout fits smem_optin (0: none)
 int stream_segment_warps(int clb, int a_s, size_t smem_optin);
 cudaError_t launch_stream_segment(const SegArgs &a, int n_warps, unsigned grid, size_t smem, cudaStream_t s);
+// After a streaming pass that found a case out of order: clears what it added
+// to the global edge table (dense), the endpoint counts, the case counter and
+// the bucket counter, so that the sorting pass starts from zero (returns at
+// once otherwise).
+cudaError_t launch_stream_undo(const SegArgs &a, uint32_t n_act, unsigned grid, cudaStream_t s);
 
 struct SegSmem {
   size_t rec, tlo, hw, rng, flg, ccnt, cstart, st, en, tkey, tcnt, tminh, tmaxh, misc, total;

@@ -197,8 +197,7 @@ struct SegShared {
 template <bool kExport>
 __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared &S, uint16_t *hw, uint32_t *misc,
                               const uint4 *src, bool from_smem, uint32_t b, uint32_t n_r, uint32_t c_a,
-                              uint32_t c_b, int64_t out_base, uint32_t act_mask, uint32_t &n_sorted,
-                              bool presorted) {
+                              uint32_t c_b, int64_t out_base, uint32_t act_mask, uint32_t &n_sorted) {
   const int ncl = 1 << a.clb;
   const int hws = (ncl + 1) & ~1;  // per-warp row of 16-bit counts, 4-byte aligned
   const uint32_t cmask = (uint32_t)ncl - 1;
@@ -271,10 +270,9 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
   }
   __syncthreads();
   // flag the cases whose events are out of (timestamp, row) order (S.flg was
-  // cleared with the per-case sums at the start of the range); nothing to
-  // check when the loaded timestamps never decrease in row order
+  // cleared with the per-case sums at the start of the range)
   bool any = false;
-  for (uint32_t p = tid + 1; !presorted && p < n_r; p += kSegThreads) {
+  for (uint32_t p = tid + 1; p < n_r; p += kSegThreads) {
     const uint4 x = S.rec[p - 1], y = S.rec[p];
     const uint32_t cx = (x.x >> a.act_bits) & cmask, cy = (y.x >> a.act_bits) & cmask;
     if (cx == cy && !kr_less(ts_key(rec_ts(x)), x.y, ts_key(rec_ts(y)), y.y)) {
@@ -335,8 +333,9 @@ __device__ bool process_range(const SegArgs &a, SmemSink &sink, const SegShared 
 template <bool kExport>
 __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // time-ordered logs go through the streaming pass when it is launched too
-  if (a.skip_ordered && a.order_flags && !(*(volatile uint32_t *)a.order_flags & 2u)) return;
+  // with the streaming pass launched before it, only a log that pass gave up
+  // on (a case out of timestamp order) is left to this pass
+  if (a.skip_ordered && !(*(volatile uint32_t *)a.err & kStDisorder)) return;
   const int ncl = 1 << a.clb;
   const int a_s = a.ep_smem ? (int)a.n_act : 0;
   const SegSmem L = seg_smem_layout(a.cap, ncl, a_s, a.tbl_slots, a.tbl_mode);
@@ -360,7 +359,6 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t act_mask = (1u << a.act_bits) - 1;
   const uint32_t cmask = (uint32_t)ncl - 1;
-  const bool presorted = a.order_flags && !(*a.order_flags & 2u);
 
   if (!kExport) {
     for (int i = tid; i < a.tbl_slots; i += kSegThreads) {
@@ -400,7 +398,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
     bool ok = true;
     if (n <= (uint32_t)a.cap) {
       ok = process_range<kExport>(a, sink, S, hw, misc, src, false, b, n, 0, (uint32_t)ncl, (int64_t)lo, act_mask,
-                                  n_sorted, presorted);
+                                  n_sorted);
     } else {
       // too large for one pass: split the case slots into ranges that fit
       for (int c = tid; c < ncl; c += kSegThreads) S.ccnt[c] = 0;
@@ -449,7 +447,7 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_segment(SegArgs a) {
         }
         __syncthreads();
         ok = process_range<kExport>(a, sink, S, hw, misc, src, true, b, cnt, c_a, c_b, (int64_t)lo + pos_a,
-                                    act_mask, n_sorted, presorted);
+                                    act_mask, n_sorted);
       }
     }
     if (!ok) {

@@ -129,8 +129,6 @@ struct EdgeTable {
 template <int kClb>
 __global__ void __launch_bounds__(kClb >= 8 ? 896 : 1024, 1) k_stream_segment(SegArgs a, int n_warps) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // only time-ordered logs: the sorting segment pass handles the others
-  if (!a.order_flags || (*(volatile uint32_t *)a.order_flags & 2u)) return;
   if (a.ran && blockIdx.x == 0 && threadIdx.x == 0) *a.ran = 1u;
   constexpr int ncl = 1 << kClb;
   constexpr int per = (ncl + 31) >> 5;  // case slots per lane in the per-bucket loops
@@ -170,9 +168,11 @@ __global__ void __launch_bounds__(kClb >= 8 ? 896 : 1024, 1) k_stream_segment(Se
   // buckets are claimed per warp (a whole-bucket L2 prefetch per warp would
   // put more bytes in flight than L2 holds; records are instead loaded into
   // registers two chunks ahead)
+  bool disorder = false;  // this lane met an event earlier than its case's previous one
   for (;;) {
     uint32_t b = 0;
-    if (lane == 0) b = atomicAdd(a.work, 1u);
+    // a case out of order anywhere: the sorting pass redoes the log
+    if (lane == 0) b = (*(volatile uint32_t *)a.err & kStDisorder) ? a.nb : atomicAdd(a.work, 1u);
     b = __shfl_sync(kFull, b, 0);
     if (b >= a.nb) break;
     const uint32_t lo = a.bucket_off[b], n = a.bucket_off[b + 1] - lo;
@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(kClb >= 8 ? 896 : 1024, 1) k_stream_segment(Se
         }
       }
       const bool has = valid && pos > 0;
+      if (has && (int64_t)ts < (int64_t)pts) disorder = true;
       const uint32_t key = pact * a.n_act + act;
       const uint32_t e = has ? T.emap[key] : kIdNone;  // used one chunk later
       if (p_has) T.add(p_key, p_d, p_e);
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(kClb >= 8 ? 896 : 1024, 1) k_stream_segment(Se
       __syncwarp();
     }
     if (p_has) T.add(p_key, p_d, p_e);
+    if (__any_sync(kFull, disorder) && lane == 0) atomicOr(a.err, kStDisorder);
     // 3. per-case outputs; the end activity is the last event seen
 #pragma unroll
     for (int k = 0; k < per; ++k) {
@@ -331,6 +333,29 @@ __global__ void __launch_bounds__(kClb >= 8 ? 896 : 1024, 1) k_stream_segment(Se
     if (st[i]) atomicAdd(&a.g_start[i], (unsigned long long)st[i]);
     if (en[i]) atomicAdd(&a.g_end[i], (unsigned long long)en[i]);
   }
+}
+
+__global__ void k_stream_undo(const uint32_t *err, DfgTable g, uint64_t cells, unsigned long long *ends,
+                              uint32_t n_act, unsigned long long *n_cases, uint32_t *work) {
+  if (!(*err & kStDisorder)) return;
+  const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = i0; i < cells; i += st) {
+    g.cnt[i] = 0;
+    g.lo[i] = 0;
+    g.hi[i] = 0;
+    g.mn[i] = ~0ull;
+    g.mx[i] = 0;
+  }
+  for (uint64_t i = i0; i < 2 * (uint64_t)n_act; i += st) ends[i] = 0;
+  if (i0 == 0) {
+    *n_cases = 0;
+    *work = 0;  // the sorting pass claims the buckets from the same counter
+  }
+}
+
+cudaError_t launch_stream_undo(const SegArgs &a, uint32_t n_act, unsigned grid, cudaStream_t s) {
+  k_stream_undo<<<grid, 256, 0, s>>>(a.err, a.g, (uint64_t)n_act * n_act, a.g_start, n_act, a.n_cases, a.work);
+  return cudaGetLastError();
 }
 
 int stream_segment_warps(int clb, int a_s, size_t smem_optin) {

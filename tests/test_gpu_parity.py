@@ -265,9 +265,10 @@ def test_filter_chain_and_reuse(pm4g, ctx):
 
 @pytest.mark.parametrize("where", ["first", "warp", "tile", "chunk", "last", "none"])
 def test_time_sorted_input_fast_path(pm4g, ctx, where):
-    """Rows sorted by timestamp let the segment pass skip its order check; one
-    descent anywhere (at a warp, tile or row-chunk boundary of the partition,
-    or at the ends) must be seen, and the case it puts out of order sorted."""
+    """Rows sorted by timestamp take the streaming segment pass; one descent
+    that puts a case out of order anywhere (at a warp, tile or row-chunk
+    boundary of the partition, or at the ends) must be seen by that pass, whose
+    partial sums are then cleared and the log redone by the sorting pass."""
     L = synth.generate(synth.very_large_log(20000))
     n = L.n_events
     case, act, ts = L.case_id.copy(), L.activity.copy(), L.ts_ns.copy()
@@ -287,6 +288,28 @@ def test_time_sorted_input_fast_path(pm4g, ctx, where):
         d = np.nonzero(np.diff(ts) < 0)[0]
         assert d.tolist() == [pos - 1]
     check_log(pm4g, ctx, case, act, ts, L.n_activities)
+
+
+def test_case_ordered_rows_take_the_streaming_pass(pm4g, ctx):
+    """Rows grouped by case, each case's events in timestamp order, are not
+    in global timestamp order, yet every case is: the streaming pass takes the
+    log (the sorting pass sorts nothing). One event moved before its case's
+    previous one sends the log to the sorting pass, with the same results as
+    the oracle's."""
+    L = synth.generate(synth.very_large_log(20000))
+    o = np.lexsort((np.arange(L.n_events), L.ts_ns, L.case_id))
+    case, act, ts = L.case_id[o].copy(), L.activity[o].copy(), L.ts_ns[o].copy()
+    assert np.any(np.diff(ts) < 0)
+    pm4g.pm4g_ctx_timing_reset(ctx)
+    check_log(pm4g, ctx, case, act, ts, L.n_activities)
+    assert pm4g.pm4g_ctx_timing(ctx, "sorted_windows")[0] == 0
+    # the last event of a case of length >= 2, at the end of the rows, now
+    # comes before its predecessor
+    r = next(i for i in range(L.n_events - 1, 0, -1) if case[i] == case[i - 1])
+    ts[r] = ts[r - 1] - 1
+    pm4g.pm4g_ctx_timing_reset(ctx)
+    check_log(pm4g, ctx, case, act, ts, L.n_activities)
+    assert pm4g.pm4g_ctx_timing(ctx, "sorted_windows")[0] > 0
 
 
 def test_one_pass_16bit_histogram(pm4g, ctx):
