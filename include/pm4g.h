@@ -84,7 +84,8 @@ extern "C" {
 #define PM4G_OPT_LOAD_SPLITS 9        /* units each coarse bucket's second partition level is
                                         cut into, 1..64 */
 #define PM4G_OPT_STREAM_WARPS 10      /* warps per block of the streaming segment pass, 1..24 */
-#define PM4G_OPT_STREAM_OFF 11        /* 1 = the sorting segment pass for time-ordered logs too */
+#define PM4G_OPT_STREAM_OFF 11        /* 1 = the sorting segment pass for every log (also those
+                                        whose cases come in timestamp order) */
 #define PM4G_OPT_PART1_ITEMS 12       /* records a thread stages per tile in the first partition
                                         level: 8 (default; 4,096-record tiles, 2 blocks an SM)
                                         or 4 (2,048-record tiles, 3 blocks an SM) */

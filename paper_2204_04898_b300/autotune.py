@@ -16,7 +16,8 @@ The single-log pass's choices (pm4g_load_log followed by the summaries) are:
   capacity of the sorting segment pass);
 - the units each coarse bucket's second partition level is cut into;
 - the warps per block of the streaming segment pass;
-- whether time-ordered logs take the streaming pass or the sorting pass;
+- whether logs whose cases come in timestamp order take the streaming pass
+  or the sorting pass;
 - the global edge table: dense over the A x A pairs or hashed (the
   histogram-versus-hash switch);
 - the records a thread stages per tile in each partition level (8, or 4 for

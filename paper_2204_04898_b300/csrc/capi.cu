@@ -440,7 +440,9 @@ static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) 
 // err_in (optional): a device word to read back with the pass's own counters
 // (one synchronisation for both); its value goes to *err_out.
 // keys (optional): the first word of every bucketed record, in bucket order,
-// written by the partition; with it, time-ordered logs take the streaming pass.
+// written by the partition; with it, the streaming pass takes the log first
+// (it gives up on a log with a case out of timestamp order, which the sorting
+// pass then formats).
 static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, const uint32_t *err_in = nullptr,
                        uint32_t *err_out = nullptr, const uint32_t *keys = nullptr) {
   Ctx *c = L->ctx;
@@ -498,7 +500,8 @@ static int run_segment(pm4g_log *L, const int32_t *attr_in, bool write_cattr, co
   a.cattr = write_cattr ? L->cattr.p : nullptr;
   a.err = ctr + 2;
   a.g.err = ctr + 2;
-  if (keys && c->test_bucket_cap == 0 && sc.cap >= 32 && !L->ghash && L->A <= 2048 && !c->stream_off) {
+  if (keys && L->row_ordered && c->test_bucket_cap == 0 && sc.cap >= 32 && !L->ghash && L->A <= 2048 &&
+      !c->stream_off) {
     // the streaming pass, for logs whose cases' events come in timestamp
     // order (it checks this itself; a log where it finds a case out of order
     // is cleared of its partial sums and redone by the sorting pass below)
@@ -1004,6 +1007,7 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         if (fail(check_launch(c, "k_bucket_colprefix"))) break;
       }
       if (fail(scan_u32(c, total, L->bucket_off.p, L->nb))) break;
+      L->row_ordered = fbits == 0 || two_level;
       if (fbits == 0 || two_level) {
         PartArgs pa{};
         pa.case_id = keycol;
@@ -1882,16 +1886,17 @@ static int extract_sublog(pm4g_log *L, FilterArgs fa, pm4g_log **out) {
     if ((st = alloc_buf(c, F->rec, nsub))) break;
     fa.out = F->rec.p;
     // A sub-log keeps each bucket's records in the order of the log it comes
-    // from, so it is time-ordered when that log is: it then takes the
-    // streaming segment pass, which counts cases from the key words.
+    // from, so its cases are in timestamp order when that log's are: it then
+    // takes the streaming segment pass, which counts cases from the key words.
     uint32_t *keys = nullptr;
+    F->row_ordered = L->row_ordered;
     if (L->status.p) {
       if ((st = alloc_buf(c, F->status, 1))) break;
       if (cudaMemcpyAsync(F->status.p, L->status.p, 4, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
         st = PM4G_ECUDA;
         break;
       }
-      keys = S.get<uint32_t>(nsub);  // NULL (no streaming pass) if memory is short
+      if (F->row_ordered) keys = S.get<uint32_t>(nsub);  // NULL (no streaming pass) if memory is short
     }
     fa.keys_out = keys;
     {

@@ -308,10 +308,10 @@ struct pm4g_log {
   bool ghash = false;
   pm4g::DBuf<unsigned long long> gkey;
   pm4g::DBuf<unsigned long long> ends; // 2 * A: start, end
-  // one device word: bit 0 an activity outside [0, A) was seen; bit 1 the
-  // bucketed records of a case may not be in (timestamp, row) order (clear
-  // only when the loaded timestamps never decrease in row order and the
-  // records were bucketed stably)
+  // every bucket's records are in row order (the stable partition bucketed
+  // them, or a filter of such a log): only then may the streaming pass run
+  bool row_ordered = false;
+  // one device word: bit 0 an activity outside [0, A) was seen
   pm4g::DBuf<uint32_t> status;
   // caches
   bool edges_ready = false;

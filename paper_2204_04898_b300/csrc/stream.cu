@@ -1,10 +1,12 @@
-// Streaming segment pass for time-ordered logs (Section 3: the directly-
-// follows pairs, the performance DFG, start/end activities and the per-case
-// variant features of the formatted log).
+// Streaming segment pass for logs whose cases' events come in timestamp
+// order (Section 3: the directly-follows pairs, the performance DFG,
+// start/end activities and the per-case variant features of the formatted
+// log).
 //
-// When the loaded timestamps never decrease in row order, the stable bucket
-// partition delivers every case's events in (timestamp, row) order inside its
-// bucket, interleaved with the other cases of the bucket. The formatting sort
+// When every case's events have non-decreasing timestamps in row order (as
+// in a log whose rows are sorted by time, or grouped by case), the stable
+// bucket partition delivers every case's events in (timestamp, row) order
+// inside its bucket, interleaved with the other cases of the bucket. The formatting sort
 // of Section 3 then reduces to grouping by case, and the grouping needs no
 // reordering at all: one warp takes a bucket and
 //  1. counts its cases from the first word of every record, which the
