@@ -58,7 +58,7 @@ struct BatchArgs {
   const uint32_t *aslots;  // present slots in (attribute, slot) order
   const uint32_t *aoff;    // first formatted position of each entry of aslots
   const uint32_t *alen;    // events of each entry of aslots
-  const int32_t *act_s;
+  const uint16_t *act_s;
   const int64_t *ts_s;
   const uint32_t *eidx_s;  // edge index of each event's pair with the next event of its case
   uint32_t n_act;
@@ -381,7 +381,7 @@ __device__ __forceinline__ uint32_t edge_of(const uint32_t *__restrict__ emap, c
   return lo < E && ekey[lo] == key ? lo : 0xFFFFFFFFu;
 }
 __global__ void k_dd_eidx(const uint32_t *__restrict__ aoff, const uint32_t *__restrict__ alen, uint32_t C,
-                          const int32_t *__restrict__ act_s, const uint32_t *__restrict__ emap,
+                          const uint16_t *__restrict__ act_s, const uint32_t *__restrict__ emap,
                           const uint32_t *__restrict__ ekey, uint32_t E, uint32_t A, uint32_t *eidx) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -516,10 +516,10 @@ __global__ void k_bv_head(const uint32_t *__restrict__ order, const uint32_t *__
 }
 __global__ void k_bv_acts(const uint32_t *__restrict__ o_rep, const uint32_t *__restrict__ seq,
                           const uint32_t *__restrict__ spos, const uint32_t *__restrict__ slen,
-                          const int32_t *__restrict__ act_s, uint32_t rows, int32_t *o_acts) {
+                          const uint16_t *__restrict__ act_s, uint32_t rows, int32_t *o_acts) {
   for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
     const uint32_t r = o_rep[row], L = slen[r];
-    const int32_t *src = act_s + spos[r];
+    const uint16_t *src = act_s + spos[r];
     int32_t *dst = o_acts + seq[row];
     for (uint32_t k = 0; k < L; ++k) dst[k] = src[k];
   }

@@ -1148,9 +1148,23 @@ int pm4g_log_free(pm4g_log *L) {
 
 // Runs the segment pass in export mode: the formatted log in (case,
 // timestamp, row) order into the given device arrays (any may be NULL).
+namespace pm4g {
+// The formatted activities widened to the export's 32-bit codes (act_s is
+// already in formatted order).
+__global__ void k_widen_acts(const uint16_t *__restrict__ src, int64_t n, int32_t *__restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+}  // namespace pm4g
+
 int pm4g::run_export(pm4g_log *L, int32_t *ec, int32_t *ea, int64_t *et, int64_t *er) {
   Ctx *c = L->ctx;
   if (L->n == 0) return PM4G_OK;
+  if (ea) {
+    k_widen_acts<<<grid_for(L->n, 256, 65535), 256, 0, c->stream>>>(L->act_s.p, L->n, ea);
+    PM4G_TRY(check_launch(c, "k_widen_acts"));
+  }
+  if (!ec && !et && !er) return PM4G_OK;
   Scratch S(c);
   uint32_t *ctr = S.get<uint32_t>(4);
   uint32_t *ovf = S.get<uint32_t>(L->nb);
@@ -1162,7 +1176,7 @@ int pm4g::run_export(pm4g_log *L, int32_t *ec, int32_t *ea, int64_t *et, int64_t
   PM4G_CK(cudaMemsetAsync(ctr, 0, 16, c->stream));
   const SegConfig sc = seg_config(c, L->clb, L->A);
   SegArgs a = seg_args(L, sc, ctr, ovf, ctr + 1, dummy);
-  a.act_s = ea;
+  a.act_s = nullptr;  // widened from act_s above
   a.ex_case = ec;
   a.ex_ts = et;
   a.ex_row = er;

@@ -54,7 +54,7 @@ __device__ __forceinline__ void ef_add(const EfTable &t, uint32_t key, uint64_t 
 // a warp walks its case's events in chunks of 32 (lanes hold a chunk of the
 // later events; the earlier event is broadcast).
 __global__ void __launch_bounds__(256) k_efg_pairs(const uint32_t *len, const uint32_t *off, uint64_t n_slots,
-                                                   const int32_t *act_s, const int64_t *ts_s, uint32_t A,
+                                                   const uint16_t *act_s, const int64_t *ts_s, uint32_t A,
                                                    EfTable t0, uint64_t copy_stride, uint32_t n_copies,
                                                    unsigned long long *work) {
   const int lane = threadIdx.x & 31;

@@ -296,7 +296,7 @@ struct pm4g_log {
   bool has_attr = false;
   pm4g::DBuf<uint4> rec;
   pm4g::DBuf<uint32_t> bucket_off;
-  pm4g::DBuf<int32_t> act_s;
+  pm4g::DBuf<uint16_t> act_s;  // activities in formatted order (16 bits: at most 65,536 activities)
   pm4g::DBuf<uint32_t> len;
   pm4g::DBuf<int32_t> cattr;
   pm4g::DBuf<int32_t> uniq;  // sorted distinct case ids when renumbered

@@ -186,7 +186,7 @@ __global__ void k_mark_case_starts(const uint32_t *len, const uint32_t *off, uin
 
 // An event at formatted position p > 0 that does not start its case has the
 // event at p - 1 as its previous one; its pair key is prev * A + act.
-__global__ void k_path_keep(uint64_t n, const int32_t *act_s, const uint8_t *start, const int64_t *row_s,
+__global__ void k_path_keep(uint64_t n, const uint16_t *act_s, const uint8_t *start, const int64_t *row_s,
                             const uint64_t *keys, int32_t n_keys, uint32_t n_act, int32_t exclude,
                             uint32_t *row_keep) {
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {

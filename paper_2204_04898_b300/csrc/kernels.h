@@ -103,7 +103,7 @@ struct SegArgs {
   int tbl_mode;   // 0: dense shared table over A*A cells, 1: hashed shared table
   int tbl_slots;  // shared table slots (power of two in hashed mode)
   uint32_t *work; // bucket work counter
-  int32_t *act_s;
+  uint16_t *act_s;
   uint32_t *len;
   const int32_t *attr_in;
   int32_t *cattr;
@@ -267,7 +267,7 @@ __global__ void k_filter_write(FilterArgs a);
 struct CaseFilterArgs {
   uint64_t n_slots;
   const uint32_t *len, *off;     // per slot: events, first formatted position
-  const int32_t *act_s;          // activities in formatted order
+  const uint16_t *act_s;         // activities in formatted order
   const int64_t *first_ts, *last_ts;
   const int32_t *cvar;           // per slot variant id (only with variants)
   int64_t min_events, max_events, min_duration, max_duration;  // negative: absent
@@ -280,7 +280,7 @@ struct CaseFilterArgs {
 __global__ void k_case_filter(CaseFilterArgs a);
 // Paths filter: first formatted position of every case, then the kept rows.
 __global__ void k_mark_case_starts(const uint32_t *len, const uint32_t *off, uint64_t n_slots, uint8_t *start);
-__global__ void k_path_keep(uint64_t n, const int32_t *act_s, const uint8_t *start, const int64_t *row_s,
+__global__ void k_path_keep(uint64_t n, const uint16_t *act_s, const uint8_t *start, const int64_t *row_s,
                             const uint64_t *keys, int32_t n_keys, uint32_t n_act, int32_t exclude,
                             uint32_t *row_keep);
 

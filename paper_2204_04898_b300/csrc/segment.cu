@@ -80,7 +80,7 @@ __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, 
   if (kExport) {
     if (valid) {
       const uint64_t slot = slot_base + c;
-      if (a.act_s) a.act_s[out_base + p] = (int32_t)act;
+      if (a.act_s) a.act_s[out_base + p] = (uint16_t)act;
       if (a.ex_case) a.ex_case[out_base + p] = a.uniq ? a.uniq[slot] : (int32_t)((uint32_t)a.min_case + (uint32_t)slot);
       if (a.ex_ts) a.ex_ts[out_base + p] = ts;
       if (a.ex_row) a.ex_row[out_base + p] = (int64_t)r.y;
@@ -89,7 +89,7 @@ __device__ __forceinline__ void process_warp_tile(const SegArgs &a, Sink &sink, 
   }
   const bool first = valid && (uint32_t)p == cs;
   const bool last = valid && (uint32_t)p + 1 == ce;
-  if (valid) a.act_s[out_base + p] = (int32_t)act;
+  if (valid) a.act_s[out_base + p] = (uint16_t)act;
   if (first) sink.start(act);
   if (last) sink.end(act);
   // the next event of the case: the next lane's, or one fetch for lane 31

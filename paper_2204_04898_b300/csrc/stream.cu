@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kClb >= 8 ? 896 : 1024, 1) k_stream_segment(Se
       if (valid) {
         // a case's events stay inside its bucket's formatted range unless the
         // counted lengths disagree with the records (reported)
-        if (first + pos < lo + n) a.act_s[first + pos] = (int32_t)act;
+        if (first + pos < lo + n) a.act_s[first + pos] = (uint16_t)act;
         else atomicOr(a.err, 1u);
         if (pos == 0) {
           if (a_s) atomicAdd(&st[act], 1u);

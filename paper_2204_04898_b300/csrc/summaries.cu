@@ -173,7 +173,7 @@ __device__ __forceinline__ void var_insert_one(const VarArgs &a, uint32_t s, uin
 // pending lanes and read eight consecutive activities of both sequences per
 // step, so a load instruction covers four contiguous 32-byte runs instead of
 // 32 scattered words. All lanes of the warp call it.
-__device__ __forceinline__ void warp_compare(const int32_t *act_s, uint32_t todo, uint32_t L, uint32_t xo,
+__device__ __forceinline__ void warp_compare(const uint16_t *act_s, uint32_t todo, uint32_t L, uint32_t xo,
                                              uint32_t yo, bool &same) {
   const uint32_t lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
   while (todo) {
@@ -230,8 +230,9 @@ __global__ void k_var_gtab(unsigned long long *g, uint32_t n_act) {
 // First grouping round over all case slots, with the polynomial hash formed
 // on the way from the formatted activities. A warp takes 32 consecutive case
 // slots, whose events are contiguous in the formatted order, and walks them
-// 128 events at a time, four consecutive events a lane (one 16-byte load; the
-// walk starts at the 16-byte boundary at or before the slots' first event).
+// 128 events at a time, four consecutive events a lane (one 8-byte load of
+// 16-bit activities; the walk starts at the 8-byte boundary at or before the
+// slots' first event).
 // Each lane sums g(a) r^(4 lane + j) over its four events; a warp scan of the
 // lanes' sums, scaled by r^(window start), and the running total of the
 // windows before give the prefix sums of the walk. Each case's lane fetches,
@@ -283,31 +284,32 @@ __global__ void __launch_bounds__(kHiThreads) k_var_hash_insert(VarArgs a) {
     const uint64_t e0 = off0 & ~3u;
     const uint32_t sh = off0 - (uint32_t)e0, tw = total + sh;
     const uint32_t my_ws = excl + sh;  // this slot's first event, in walk positions
-    // the lane's four activities of the window at w0, loaded two windows ahead
+    // the lane's four activities of the window at w0 (16 bits each, one
+    // 8-byte load), loaded two windows ahead
     auto load4 = [&](uint32_t w0) {
       const uint32_t wl = w0 + 4 * lane;
-      int4 v = make_int4(0, 0, 0, 0);
+      uint2 v = make_uint2(0, 0);
       if (wl < tw) {
         const uint64_t e = e0 + wl;
         if (e + 4 <= a.n_events) {
-          v = __ldcs(reinterpret_cast<const int4 *>(a.act_s + e));
+          v = __ldcs(reinterpret_cast<const uint2 *>(a.act_s + e));
         } else {
           v.x = a.act_s[e];
-          if (e + 1 < a.n_events) v.y = a.act_s[e + 1];
-          if (e + 2 < a.n_events) v.z = a.act_s[e + 2];
+          if (e + 1 < a.n_events) v.x |= (uint32_t)a.act_s[e + 1] << 16;
+          if (e + 2 < a.n_events) v.y = a.act_s[e + 2];
         }
       }
       return v;
     };
-    int4 v1 = load4(0), v2 = load4(128);
+    uint2 v1 = load4(0), v2 = load4(128);
     uint64_t rw = 1;     // r^w0
     uint64_t done = 0;   // the walk's sum over the windows before
     for (uint32_t w0 = 0; w0 < tw; w0 += 128) {
       const uint32_t wl = w0 + 4 * lane;  // walk position of the lane's first event
-      const int4 v = v1;
+      const uint2 v = v1;
       v1 = v2;
       v2 = load4(w0 + 256);
-      const int32_t act4[4] = {v.x, v.y, v.z, v.w};
+      const uint32_t act4[4] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16};
       uint64_t ex[4], u = 0;  // the lane's sums before each of its events, and in all
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -356,7 +358,7 @@ __global__ void k_var_insert(VarArgs a, const uint32_t *list, uint32_t n_list, u
       h = a.hash[s];
     } else {
       h = 0;
-      const int32_t *q = a.act_s + a.off[s];
+      const uint16_t *q = a.act_s + a.off[s];
       uint32_t hl = 0, hh = 0;  // same combination as the segment pass: two 32-bit sums
       for (uint32_t k = 0; k < L; ++k) {
         const uint64_t t = event_hash((uint32_t)q[k], k, round);
@@ -491,7 +493,7 @@ __global__ void k_var_out_acts(VarArgs a, const uint32_t *order, const uint32_t 
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t i = w0; i < k_out; i += nw) {
     const uint32_t rep = rep_slots[order[i]];
-    const int32_t *q = a.act_s + a.off[rep];
+    const uint16_t *q = a.act_s + a.off[rep];
     const uint32_t L = a.len[rep];
     if ((uint64_t)o_off[i] + L > cap) continue;
     int32_t *o = o_acts + o_off[i];

@@ -21,7 +21,7 @@ struct VarArgs {
   const uint32_t *len;     // per case slot, 0 = no case
   const uint64_t *hash;    // per case slot, sequence hash (seed 0); NULL: formed from act_s in round 0
   const uint32_t *off;     // per case slot, first position in the ordered log
-  const int32_t *act_s;    // activity of every event in (case, ts, row) order (16-byte aligned)
+  const uint16_t *act_s;   // activity of every event in (case, ts, row) order (16-byte aligned)
   uint64_t n_events;       // length of act_s
   int bits;                // key truncation (tests only), 0 = full key
   VarSlot *tab;
