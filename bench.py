@@ -619,7 +619,10 @@ def serve_core(args, local: int, rates: list, seconds: float, small_log: bool = 
         pool.append(u)
     views = synth.drilldown_specs(L, n_views=2048, seed=20220417)
     t_gen = time.perf_counter() - t_gen
-    ctx = pm4g.pm4g_ctx_create(local)
+    # the queries' context runs on a high-priority stream: their blocks are
+    # scheduled ahead of the uploads' whenever both wait for an SM
+    qstream = torch.cuda.Stream(device=local, priority=-1)
+    ctx = pm4g.pm4g_ctx_create(local, stream=qstream.cuda_stream)
     cols = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns, L.case_attr)]
     t = time.perf_counter()
     log = pm4g.pm4g_load_log(ctx, *cols[:3], case_attr=cols[3], n_activities=A)
@@ -627,8 +630,10 @@ def serve_core(args, local: int, rates: list, seconds: float, small_log: bool = 
     del cols
     torch.cuda.empty_cache()
     eng = GpuEngine(pm4g, local, log, ctx, upload_slots=2)
-    # warm: drill-down index, variant table, upload contexts
-    eng.batch_dfg([Request("dfg", attr_set=views[0].attr_set, t_lo=views[0].t_lo, t_hi=views[0].t_hi)])
+    # warm: drill-down index, variant table, a large batch's result buffers,
+    # upload contexts
+    eng.batch_dfg([Request("dfg", attr_set=v.attr_set, t_lo=v.t_lo, t_hi=v.t_hi, mode=pm4g.TW_EVENTS)
+                   for v in views[:1024]])
     eng.variants(10)
     for slot in range(2):  # every upload slot's context, pools and staging buffers
         eng.upload(Request("upload", columns=(pool[0].case_id, pool[0].activity, pool[0].ts_ns), n_activities=A),

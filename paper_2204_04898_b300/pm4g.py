@@ -444,23 +444,27 @@ class BatchBuffers:
             return np.empty(max(n, 1), dtype)
 
     def ensure(self, n_sub: int, n_act: int, edges: int, var_rows: int = 0, var_acts: int = 0) -> None:
+        # every array grows to at least twice its size (page-locking new host
+        # memory takes milliseconds per megabyte, so a server that sees ever
+        # larger batches reallocates a few times only)
         if n_sub > self.n_sub or n_act > self.n_act or n_sub * n_act > max(self.n_sub, 0) * max(self.n_act, 0):
-            self.n_sub, self.n_act = max(n_sub, self.n_sub), max(n_act, self.n_act)
+            self.n_sub = max(n_sub, 2 * self.n_sub) if n_sub > self.n_sub else self.n_sub
+            self.n_act = max(n_act, self.n_act)
             q, qa = self.n_sub, self.n_sub * self.n_act
             self.n_events, self.n_cases = self._alloc(q, np.int64), self._alloc(q, np.int64)
             self.edge_off = self._alloc(q + 1, np.int64)
             self.start, self.end, self.freq = (self._alloc(qa, np.uint64) for _ in range(3))
             self.n_variants, self.var_off = self._alloc(q, np.int64), self._alloc(q + 1, np.int64)
         if var_rows > self.var_rows:
-            self.var_rows = int(var_rows * 1.25) + 1024
+            self.var_rows = max(int(var_rows * 1.25), 2 * self.var_rows) + 1024
             self.var_count = self._alloc(self.var_rows, np.uint64)
             self.var_min_case = self._alloc(self.var_rows, np.int32)
             self.var_seq_off = self._alloc(self.var_rows + 1, np.int64)
         if var_acts > self.var_acts_cap:
-            self.var_acts_cap = int(var_acts * 1.25) + 4096
+            self.var_acts_cap = max(int(var_acts * 1.25), 2 * self.var_acts_cap) + 4096
             self.var_acts = self._alloc(self.var_acts_cap, np.int32)
         if edges > self.edges:
-            self.edges = int(edges * 1.25) + 1024
+            self.edges = max(int(edges * 1.25), 2 * self.edges) + 1024
             e = self.edges
             self.src, self.dst = self._alloc(e, np.int32), self._alloc(e, np.int32)
             (self.count, self.sum_lo, self.sum_hi, self.min,
