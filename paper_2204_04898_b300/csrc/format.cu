@@ -81,8 +81,7 @@ __global__ void __launch_bounds__(1024) k_bucket_hist(FormatArgs a, uint32_t b_l
   const int64_t r0 = (int64_t)blockIdx.x * a.chunk;
   const int64_t r1 = min(a.n, r0 + a.chunk);
   const bool al = ((uintptr_t)a.case_id & 15) == 0;
-  for (int64_t i = r0 + (int64_t)threadIdx.x * 4; i < r1; i += (int64_t)blockDim.x * 4) {
-    const int4 q = load4_i32(a.case_id, i, r1, al);
+  auto count4 = [&](int4 q, int64_t i) {
     const int32_t cc[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -92,7 +91,19 @@ __global__ void __launch_bounds__(1024) k_bucket_hist(FormatArgs a, uint32_t b_l
         if (b < nbs) atomicAdd(&s_h[b], 1u);
       }
     }
+  };
+  // four 16-byte loads in flight per thread before their adds (one block per
+  // SM: a single load a thread leaves the column read latency-bound)
+  const int64_t step = (int64_t)blockDim.x * 4;
+  int64_t i = r0 + (int64_t)threadIdx.x * 4;
+  for (; i + 3 * step < r1; i += 4 * step) {
+    int4 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = load4_i32(a.case_id, i + u * step, r1, al);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) count4(q[u], i + u * step);
   }
+  for (; i < r1; i += step) count4(load4_i32(a.case_id, i, r1, al), i);
   __syncthreads();
   uint32_t *row = a.mat + (int64_t)blockIdx.x * a.nb + b_lo;
   for (uint32_t b = threadIdx.x; b < nbs; b += blockDim.x) row[b] = s_h[b];
@@ -158,8 +169,7 @@ __global__ void __launch_bounds__(1024) k_bucket_hist16(FormatArgs a) {
   const int64_t r1 = min(a.n, r0 + a.chunk);
   const bool al = ((uintptr_t)a.case_id & 15) == 0;
   bool ovf = false;
-  for (int64_t i = r0 + (int64_t)threadIdx.x * 4; i < r1; i += (int64_t)blockDim.x * 4) {
-    const int4 q = load4_i32(a.case_id, i, r1, al);
+  auto count4 = [&](int4 q, int64_t i) {
     const int32_t cc[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -172,7 +182,18 @@ __global__ void __launch_bounds__(1024) k_bucket_hist16(FormatArgs a) {
         }
       }
     }
+  };
+  // four 16-byte loads in flight per thread before their adds
+  const int64_t step = (int64_t)blockDim.x * 4;
+  int64_t i = r0 + (int64_t)threadIdx.x * 4;
+  for (; i + 3 * step < r1; i += 4 * step) {
+    int4 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = load4_i32(a.case_id, i + u * step, r1, al);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) count4(q[u], i + u * step);
   }
+  for (; i < r1; i += step) count4(load4_i32(a.case_id, i, r1, al), i);
   if (ovf) s_ovf = 1;
   __syncthreads();
   uint32_t *row = a.mat + (int64_t)blockIdx.x * a.nb;
