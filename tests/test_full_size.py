@@ -11,9 +11,12 @@ own stream, top-1000 variants.
   bit-exact against the oracle run on 64 groups of cases (tests/case_groups.py
   states why the groups fix the whole-log result), plus the invariants of the
   definitions against plain counts of the input.
-- Drill-down (4,096 views of the 100M-event log in one batched call): the
-  invariants of the definitions on every view, and 32 views (the largest, the
-  smallest and random ones) bit-exact against the oracle's filter and summary.
+- Drill-down (4,096 views of the 100M-event log in one batched call, plus
+  four edge views: the largest attribute value alone, every value, an empty
+  window and an absent value): the invariants of the definitions on every
+  view; the view of every value equals the log's own summary; the other edge
+  views and 32 more (the largest, the smallest and random ones) bit-exact
+  against the oracle's filter and summary.
 - Serving (the resident 10M-case log with attributes, views, variants and uploads of about
   10k, 1M and 20M events): alone equals the shuffled mix; uploads and 8 views bit-exact
   against the oracle.
@@ -178,15 +181,32 @@ def test_drilldown_views(pm4g):
     L = synth.generate(synth.drilldown_log())
     A = L.n_activities
     views = synth.drilldown_specs(L, n_views=4096)
-    Q = len(views)
     sets = [v.attr_set for v in views]
     lo = [v.t_lo for v in views]
     hi = [v.t_hi for v in views]
+    # edge views, pinned below with the sample: the largest attribute value
+    # alone over the whole log; every attribute value over the whole log; a
+    # window before the first event (empty); an attribute value no case has
+    # (empty)
+    t0, t1 = int(L.ts_ns.min()), int(L.ts_ns.max())
+    amax = int(L.case_attr.max())
+    missing = int(np.setdiff1d(np.arange(amax + 2), L.case_attr)[-1])
+    edge = [(np.array([amax], np.int32), t0, t1), (np.unique(L.case_attr).astype(np.int32), t0, t1),
+            (np.array([amax], np.int32), t0 - 10, t0 - 1), (np.array([missing], np.int32), t0, t1)]
+    for a_, l_, h_ in edge:
+        sets.append(a_)
+        lo.append(l_)
+        hi.append(h_)
+    Q = len(sets)
     r = _resident(pm4g, L, with_attr=True)
     try:
         buf = pm4g.BatchBuffers(Q, A, 0)
         bspec = pm4g.BatchSpec(sets, lo, hi, [pm4g.TW_EVENTS] * Q)
         B = pm4g.pm4g_batch_dfg(r.log, out=buf, var_top_k=1000, spec=bspec)
+        # the whole log's own summary, for the view of every attribute value
+        whole_perf = pm4g.pm4g_perf_dfg(r.log)
+        whole_se = pm4g.pm4g_start_end(r.log, A)
+        whole_var = pm4g.pm4g_variants(r.log, top_k=1000)
     finally:
         _release(pm4g, r)
     # invariants on every view
@@ -211,7 +231,22 @@ def test_drilldown_views(pm4g):
     by_size = np.argsort(B.n_events, kind="stable")
     rng = np.random.default_rng(2204)
     pick = sorted(set(by_size[:4].tolist()) | set(by_size[-4:].tolist()) |
-                  set(rng.choice(Q, 24, replace=False).tolist()))
+                  set(rng.choice(Q, 24, replace=False).tolist()) | {Q - 4, Q - 2, Q - 1})
+    assert B.n_events[Q - 2] == 0 and B.n_events[Q - 1] == 0  # the empty edge views
+    # every attribute value over the whole log: the log's own summary (the
+    # single-log pass, against the oracle in the tests above)
+    w = Q - 3
+    assert B.n_events[w] == L.n_events
+    sw = B.sub(w)
+    for name in ("src", "dst", "count", "sum_lo", "sum_hi", "min", "max"):
+        assert np.array_equal(sw[name], getattr(whole_perf, name)), f"whole-log view: {name}"
+    assert np.array_equal(sw["mean"].view(np.uint64), whole_perf.mean.view(np.uint64))
+    for name, x in zip(("start", "end", "freq"), whole_se):
+        assert np.array_equal(getattr(B, name)[w], x), f"whole-log view: {name}"
+    a, b = int(B.var_off[w]), int(B.var_off[w + 1])
+    assert B.n_variants[w] == whole_var.n_variants
+    assert np.array_equal(B.var_count[a:b], whole_var.count) and np.array_equal(B.var_min_case[a:b],
+                                                                                 whole_var.min_case)
 
     def one(i):
         # The oracle filters the events of the cases whose attribute is in the
