@@ -89,7 +89,15 @@ __global__ void __launch_bounds__(256) k_filter_count(FilterArgs a) {
       for (uint64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) k += a.case_ok[s] ? a.len[s] : 0u;
     } else {
       const uint32_t lo = a.bucket_off[b], hi = a.bucket_off[b + 1];
-      for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) k += filter_keep(a, b, a.rec[i]) ? 1u : 0u;
+      uint32_t i = lo + threadIdx.x;
+      for (; i + 3 * blockDim.x < hi; i += 4 * blockDim.x) {  // four loads in flight
+        uint4 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = a.rec[i + u * blockDim.x];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k += filter_keep(a, b, r[u]) ? 1u : 0u;
+      }
+      for (; i < hi; i += blockDim.x) k += filter_keep(a, b, a.rec[i]) ? 1u : 0u;
     }
     k = __reduce_add_sync(kFull, k);
     __shared__ uint32_t s_k;
@@ -117,19 +125,42 @@ __global__ void __launch_bounds__(256) k_filter_write(FilterArgs a) {
       }
       continue;
     }
-    for (uint32_t t0 = lo; t0 < hi; t0 += blockDim.x) {
-      const uint32_t i = t0 + threadIdx.x;
-      uint4 r = make_uint4(0, 0, 0, 0);
-      bool keep = false;
-      if (i < hi) {
-        r = a.rec[i];
-        keep = filter_keep(a, b, r);
+    // 2,048 records a step: each warp takes 256 consecutive records, eight
+    // rounds of 32 (one load each, all in flight before the tests); a
+    // record's rank among the warp's kept ones comes from one ballot a round,
+    // and one block scan of the eight warps' totals places the warps
+    constexpr int kR = 8;
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, lt = (1u << lane) - 1u;
+    for (uint32_t t0 = lo; t0 < hi; t0 += 256 * kR) {
+      const uint32_t wb = t0 + w * 32 * kR + lane;
+      uint4 r[kR];
+#pragma unroll
+      for (int j = 0; j < kR; ++j)
+        if (wb + 32 * j < hi) r[j] = a.rec[wb + 32 * j];
+      uint32_t m[kR], cnt = 0;
+#pragma unroll
+      for (int j = 0; j < kR; ++j) {
+        m[j] = __ballot_sync(kFull, wb + 32 * j < hi && filter_keep(a, b, r[j]));
+        cnt += __popc(m[j]);
       }
-      uint32_t tot;
-      const uint32_t pre = block_exclusive_scan<256>(keep ? 1u : 0u, s_warp, tot);
-      if (keep) {
-        a.out[out + pre] = r;
-        if (a.keys_out) a.keys_out[out + pre] = r.x;
+      if (lane == 0) s_warp[w] = cnt;
+      __syncthreads();
+      uint32_t base = out, tot = 0;
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const uint32_t c = s_warp[v];
+        base += v < (int)w ? c : 0u;
+        tot += c;
+      }
+      __syncthreads();  // s_warp is read before the next step writes it
+#pragma unroll
+      for (int j = 0; j < kR; ++j) {
+        if ((m[j] >> lane) & 1u) {
+          const uint32_t dst = base + __popc(m[j] & lt);
+          a.out[dst] = r[j];
+          if (a.keys_out) a.keys_out[dst] = r[j].x;
+        }
+        base += __popc(m[j]);
       }
       out += tot;
     }
