@@ -26,8 +26,6 @@ struct FormatArgs {
 // Bucket partition (format.cu)
 constexpr int kPartThreads = 512;
 constexpr int kPartWarps = kPartThreads / 32;
-constexpr int kPartItems = 8;
-constexpr int kPartTile = kPartThreads * kPartItems;
 constexpr uint32_t kPartMaxBins = 512;
 static_assert(kPartMaxBins <= (uint32_t)kPartThreads, "one thread per digit");
 
