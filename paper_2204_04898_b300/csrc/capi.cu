@@ -435,8 +435,9 @@ static int fallback_bucket(pm4g_log *L, const SegArgs &a, uint32_t b, bool exp) 
   return check_launch(c, "k_fb_cases");
 }
 
-// Runs the segment pass over a bucketed log: fills act_s, len, hash, the DFG
-// table, the endpoint counts and (at load) the per-case attribute; sets C.
+// Runs the segment pass over a bucketed log: fills act_s, len, the DFG table,
+// the endpoint counts and (at load) the per-case attribute, and the case
+// offsets when the streaming pass formats the log; sets C.
 // err_in (optional): a device word to read back with the pass's own counters
 // (one synchronisation for both); its value goes to *err_out.
 // keys (optional): the first word of every bucketed record, in bucket order,
