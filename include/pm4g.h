@@ -74,8 +74,6 @@ extern "C" {
 #define PM4G_OPT_TEST_BUCKET_CAP 3   /* test only: events a bucket may hold in shared
                                         memory (>= 32); smaller values force the
                                         global-memory path; 0 = default */
-/* Launch choices of pm4g_batch_dfg (0 = default; results never depend on them;
- * an autotuner picks them by timing, see paper_2204_04898_b300/autotune.py): */
 /* Launch choices of pm4g_load_log's single-log pass (results never depend on
  * them; 0 = the library's default; set by the autotuner): */
 #define PM4G_OPT_EDGE_TABLE 7         /* global edge table: 0 = dense up to 4096 activities,
@@ -83,7 +81,10 @@ extern "C" {
 #define PM4G_OPT_LOAD_CLB 8           /* log2 of the case slots of a bucket, 1..8 */
 #define PM4G_OPT_LOAD_SPLITS 9        /* units each coarse bucket's second partition level is
                                         cut into, 1..64 */
-#define PM4G_OPT_STREAM_WARPS 10      /* warps per block of the streaming segment pass, 1..24 */
+#define PM4G_OPT_STREAM_WARPS 10      /* most warps per block of the streaming segment pass,
+                                        1..32; the pass takes fewer where its shared memory
+                                        (or, at 256-slot buckets, its 28-warp register
+                                        budget) does not allow that many */
 #define PM4G_OPT_STREAM_OFF 11        /* 1 = the sorting segment pass for every log (also those
                                         whose cases come in timestamp order) */
 #define PM4G_OPT_PART1_ITEMS 12       /* records a thread stages per tile in the first partition
@@ -95,6 +96,8 @@ extern "C" {
                                         first partition level, 1..9, when above the smallest
                                         that keeps the coarse buckets within one pass (fewer,
                                         larger coarse buckets); 0 = that smallest */
+/* Launch choices of pm4g_batch_dfg (0 = default; results never depend on them;
+ * an autotuner picks them by timing, see paper_2204_04898_b300/autotune.py): */
 #define PM4G_OPT_BATCH_CHUNK 4       /* cases a warp takes at once: 8, 16 (default) or 32 */
 #define PM4G_OPT_BATCH_STAGES 5      /* groups a batch of >= 64 views into caller-owned
                                         arrays is pipelined in: 1..16 (default 4) */
