@@ -153,8 +153,9 @@ class ClockSampler:
     this driver (measured: about 2.5 ms per sample, whatever fields are
     queried), so it samples once a second, and a timed region shorter than
     that is started so that one sample falls in its middle: the sampler's
-    phase is read from the arrival of its second sample, and the region's
-    length is estimated from the untimed warm-up steps."""
+    phase and period are read from the arrivals of its second and third
+    samples, and the region's length from one untimed step on a warm GPU
+    (the warm-up steps' time when no such step is given)."""
 
     Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
