@@ -1637,20 +1637,25 @@ static int ensure_case_variants(pm4g_log *L) {
   Ctx *c = L->ctx;
   const uint64_t R = L->R;
   const uint32_t V = L->V;
+  // the scratch first: cvar, once allocated, marks the ranks as formed
+  Scratch S(c);
+  uint32_t *rank_of = L->C ? S.get<uint32_t>(V) : nullptr;
+  if (L->C && !rank_of) return PM4G_ENOMEM;
   PM4G_TRY(alloc_buf(c, L->cvar, R));
   if (L->C == 0) return PM4G_OK;  // no case reads it
-  Scratch S(c);
-  uint32_t *rank_of = S.get<uint32_t>(V);
-  if (!rank_of) return PM4G_ENOMEM;
   VarArgs a{};
   a.n_slots = R;
   a.len = L->len.p;
   a.rep_of = L->rep_of.p;
   KTime t(c, "variants");
   k_rank_scatter<<<grid_for(V, 256, 65535), 256, 0, c->stream>>>(L->order.p, V, rank_of);
-  PM4G_TRY(check_launch(c, "k_rank_scatter"));
-  k_case_variant<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(a, L->rep_pos.p, rank_of, L->cvar.p);
-  return check_launch(c, "k_case_variant");
+  int st = check_launch(c, "k_rank_scatter");
+  if (st == PM4G_OK) {
+    k_case_variant<<<grid_for((int64_t)R, 256, 65535), 256, 0, c->stream>>>(a, L->rep_pos.p, rank_of, L->cvar.p);
+    st = check_launch(c, "k_case_variant");
+  }
+  if (st != PM4G_OK) free_buf(c, L->cvar);  // unfilled: the next request forms it again
+  return st;
 }
 
 int pm4g_variants(pm4g_log *L, int64_t top_k, uint32_t flags, pm4g_variants_t *out) {

@@ -165,21 +165,26 @@ inline int smem_optin_max() {
 
 // Device arrays of a log or context, through the context's allocator.
 template <class T>
-inline int alloc_buf(Ctx *c, DBuf<T> &b, size_t n) {
-  b.n = n;
-  b.p = (T *)dalloc(c, (n ? n : 1) * sizeof(T));
-  if (!b.p) {
-    set_error("device allocation of %zu bytes failed", (n ? n : 1) * sizeof(T));
-    return PM4G_ENOMEM;
-  }
-  return PM4G_OK;
-}
-
-template <class T>
 inline void free_buf(Ctx *c, DBuf<T> &b) {
   if (b.p) dfree(c, b.p, (b.n ? b.n : 1) * sizeof(T));
   b.p = nullptr;
   b.n = 0;
+}
+
+// A buffer that already holds an array gives it back first (in stream order):
+// a call retried after failing part way through its allocations, such as a
+// variant request that ran out of memory, leaves nothing behind.
+template <class T>
+inline int alloc_buf(Ctx *c, DBuf<T> &b, size_t n) {
+  free_buf(c, b);
+  b.n = n;
+  b.p = (T *)dalloc(c, (n ? n : 1) * sizeof(T));
+  if (!b.p) {
+    b.n = 0;
+    set_error("device allocation of %zu bytes failed", (n ? n : 1) * sizeof(T));
+    return PM4G_ENOMEM;
+  }
+  return PM4G_OK;
 }
 
 // Pinned host staging owned by the context (grown on demand): device-to-host
