@@ -195,66 +195,6 @@ def test_allocator_hook_failure_is_enomem(pm4g):
         pm4g.pm4g_ctx_destroy(ctx)
 
 
-def test_retry_after_enomem_leaks_nothing(pm4g):
-    """A variant request that runs out of device memory part way through its
-    allocations can be retried: the retry gives the oracle's table, and once
-    the log is freed no buffer of the allocator hook is left (a buffer the log
-    already held is given back before it is allocated again). Every point of
-    failure is tried, from the first allocation of the request on."""
-    import torch
-    state = {"budget": None}
-    live = {}
-
-    def alloc(nbytes, stream):
-        if state["budget"] is not None:
-            if state["budget"] == 0:
-                return 0
-            state["budget"] -= 1
-        t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        live[t.data_ptr()] = t
-        return t.data_ptr()
-
-    def free(ptr, nbytes, stream):
-        # the library frees in stream order; this hook's memory goes back to
-        # torch's pool at once, so the kernels that used it must be done
-        torch.cuda.synchronize()
-        live.pop(ptr, None)
-
-    L = synth.generate(synth.single_log(3000))
-    R = oracle.summarize(L.case_id, L.activity, L.ts_ns, L.n_activities)
-    ctx = pm4g.pm4g_ctx_create(0, allocator=(alloc, free))
-    try:
-        cols = [torch.from_numpy(x).cuda() for x in (L.case_id, L.activity, L.ts_ns)]
-        failed = 0
-        for k in range(64):
-            log = pm4g.pm4g_load_log(ctx, *cols, n_activities=L.n_activities)
-            try:
-                state["budget"] = k
-                try:
-                    pm4g.pm4g_variants(log, top_k=-1, cases=True)
-                    done = True
-                except pm4g.Pm4gError as e:
-                    assert e.status == pm4g.ENOMEM, e
-                    done = False
-                    failed += 1
-                state["budget"] = None
-                V = pm4g.pm4g_variants(log, top_k=-1, cases=True)
-                assert V.n_variants == R.n_variants
-                assert np.array_equal(V.count, R.var_count) and np.array_equal(V.min_case, R.var_min_case)
-                assert np.array_equal(V.off, R.var_off) and np.array_equal(V.acts, R.var_acts)
-                assert np.array_equal(V.case_ids, R.case_ids) and np.array_equal(V.case_variant, R.case_variant)
-            finally:
-                state["budget"] = None
-                pm4g.pm4g_log_free(log)
-            torch.cuda.synchronize()
-            assert not live, f"{len(live)} device buffers left after a failure at allocation {k}"
-            if done:
-                break
-        assert done and failed >= 3
-    finally:
-        pm4g.pm4g_ctx_destroy(ctx)
-
-
 # ---------------- drill-down filters ----------------
 def _filter_parity(pm4g, ctx, L, aset, t_lo, t_hi, mode):
     rows = oracle.filter_rows(L.case_id, L.activity, L.ts_ns, L.case_attr, L.n_activities, aset, t_lo, t_hi, mode)
