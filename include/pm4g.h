@@ -14,6 +14,9 @@
  *  - Every function returns an int status: PM4G_OK (0) or a negative code.
  *    No C++ exception crosses this boundary. pm4g_last_error() returns a
  *    message for the calling thread's most recent failure.
+ *  - A query or filter that returns PM4G_ENOMEM leaves its log usable and
+ *    holding no memory of the failed attempt; the same call may be retried
+ *    (with more memory free) and then gives the results it would have given.
  *  - A context (pm4g_ctx) binds one CUDA device and one stream; all work of
  *    the context and of its logs runs in order on that stream. A context is
  *    used by one thread at a time.
