@@ -122,8 +122,12 @@ typedef struct {
 
 /* Creates a context on CUDA device `device`. cuda_stream is a cudaStream_t to
  * run on (borrowed, not destroyed), or NULL for a stream the context owns.
- * alloc may be NULL: stream-ordered cudaMallocAsync is used. *out is set only
- * on success. */
+ * alloc may be NULL: stream-ordered cudaMallocAsync is used, and freed blocks
+ * (rounded up to size classes) are kept by the context for reuse, up to half
+ * the device memory, until an allocation fails or the context is destroyed;
+ * the device's default memory pool is then also set to keep what is freed
+ * into it for this process (its release threshold, a per-process setting).
+ * *out is set only on success. */
 int pm4g_ctx_create(pm4g_ctx **out, int device, void *cuda_stream, const pm4g_allocator *alloc);
 
 /* Destroys a context. Its logs must have been freed. NULL is accepted. */
