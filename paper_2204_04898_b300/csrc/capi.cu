@@ -860,36 +860,79 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         if (fail(run_segment(L, nullptr, L->has_attr))) break;
         break;
       }
-      // stats: case id range (column reduction)
-      const unsigned gs = (unsigned)c->num_sms * 4;
-      int2 *part = S.get<int2>(gs);
-      if (!part) {
+      // Case id range (the column reduction of Section 2.1). The buckets are
+      // laid out for a guess that should enclose every id: the smallest and
+      // largest of kRangeSamples evenly spaced rows, widened by 1/256 of
+      // their span on each side (slots outside the ids only stay empty). The
+      // bucket histogram checks every id against it on its own read of the
+      // column; only when an id falls outside, or when the guess would take
+      // the ids for sparse, does the reduction run (and the histogram again).
+      int mn = 0, mx = 0;
+      {
+        int2 smp = make_int2(INT32_MAX, INT32_MIN);
+        if (flags == PM4G_HOST_PTRS) {
+          for (int k = 0; k < kRangeSamples; ++k) {
+            const int32_t v = case_id[(n - 1) * k / (kRangeSamples - 1)];
+            smp.x = std::min(smp.x, v);
+            smp.y = std::max(smp.y, v);
+          }
+        } else {
+          int2 *d = S.get<int2>(1);
+          if (!d) {
+            fail(PM4G_ENOMEM);
+            break;
+          }
+          k_sample_range<<<1, 1024, 0, c->stream>>>(dcase, n, d);
+          if (fail(check_launch(c, "k_sample_range"))) break;
+          if (fail(d2h(c, &smp, d, sizeof(int2)))) break;
+        }
+        const int64_t pad = ((int64_t)smp.y - (int64_t)smp.x) / 256 + 1;
+        mn = (int)std::max<int64_t>(INT32_MIN, (int64_t)smp.x - pad);
+        mx = (int)std::min<int64_t>(INT32_MAX, (int64_t)smp.y + pad);
+      }
+      bool range_exact = false;
+      uint32_t *range_err = S.get<uint32_t>(1);
+      if (!range_err) {
         fail(PM4G_ENOMEM);
         break;
       }
-      {
-        KTime t(c, "stats");
-        k_stats<<<gs, 256, 0, c->stream>>>(dcase, n, part);
-        if (fail(check_launch(c, "k_stats"))) break;
-      }
-      std::vector<int2> hp(gs);
-      if (fail(d2h(c, hp.data(), part, gs * sizeof(int2)))) break;
-      int mn = INT32_MAX, mx = INT32_MIN;
-      for (auto &p : hp) {
-        mn = std::min(mn, p.x);
-        mx = std::max(mx, p.y);
+    case_range:
+      if (range_exact) {
+        const unsigned gs = (unsigned)c->num_sms * 4;
+        int2 *part = S.get<int2>(gs);
+        if (!part) {
+          fail(PM4G_ENOMEM);
+          break;
+        }
+        {
+          KTime t(c, "stats");
+          k_stats<<<gs, 256, 0, c->stream>>>(dcase, n, part);
+          if (fail(check_launch(c, "k_stats"))) break;
+        }
+        std::vector<int2> hp(gs);
+        if (fail(d2h(c, hp.data(), part, gs * sizeof(int2)))) break;
+        mn = INT32_MAX;
+        mx = INT32_MIN;
+        for (auto &p : hp) {
+          mn = std::min(mn, p.x);
+          mx = std::max(mx, p.y);
+        }
       }
       uint64_t R = (uint64_t)((int64_t)mx - (int64_t)mn + 1);
       const int32_t *keycol = dcase;
       L->min_case = mn;
-      if (R > std::max<uint64_t>(2 * (uint64_t)n, 1u << 20)) {
+      const bool sparse = R > std::max<uint64_t>(2 * (uint64_t)n, 1u << 20);
+      if (sparse && !range_exact) {  // decided on the exact range only
+        range_exact = true;
+        goto case_range;
+      }
+      if (sparse) {
         // sparse case ids: dense renumbering by rank of the distinct ids
         uint32_t *keys = S.get<uint32_t>(n), *vals = S.get<uint32_t>(n);
         uint32_t *k2 = S.get<uint32_t>(n), *v2 = S.get<uint32_t>(n);
         uint32_t *head = S.get<uint32_t>(n), *hpos = S.get<uint32_t>(n + 1);
         int32_t *dense = S.get<int32_t>(n);
-        int32_t *uq = S.get<int32_t>(n);
-        if (!keys || !vals || !k2 || !v2 || !head || !hpos || !dense || !uq) {
+        if (!keys || !vals || !k2 || !v2 || !head || !hpos || !dense) {
           set_error("pm4g_load_log: out of device memory for case renumbering");
           fail(PM4G_ENOMEM);
           break;
@@ -906,7 +949,6 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         if (fail(alloc_buf(c, L->uniq, Cu))) break;
         k_case_dense<<<g, 256, 0, c->stream>>>(keys, vals, head, hpos, n, dense, L->uniq.p);
         if (fail(check_launch(c, "k_case_dense"))) break;
-        (void)uq;
         keycol = dense;
         L->min_case = 0;
         R = Cu;
@@ -935,17 +977,6 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         fail(PM4G_ENOMEM);
         break;
       }
-      if (fail(alloc_buf(c, L->bucket_off, (size_t)L->nb + 1))) break;
-      if (fail(alloc_buf(c, L->rec, n))) break;
-      if (fail(alloc_buf(c, L->status, 1))) break;
-      uint32_t *err = L->status.p;
-      if (cudaMemsetAsync(err, 0, 4, c->stream) != cudaSuccess) {
-        fail(PM4G_ECUDA);
-        break;
-      }
-      // the first word of every record in bucket order, written by the
-      // partition's final level (the streaming pass counts cases from it)
-      uint32_t *keys = nullptr;
       FormatArgs fa{};
       fa.case_id = keycol;
       fa.activity = dact;
@@ -958,9 +989,12 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
       fa.n_act = A;
       fa.nb = L->nb;
       fa.mat = mat;
-      fa.bucket_off = L->bucket_off.p;
-      fa.rec = L->rec.p;
-      fa.err_flags = err;
+      fa.slot_hi = range_exact ? 0xFFFFFFFFu : (uint32_t)(R - 1);
+      fa.range_err = range_exact ? nullptr : range_err;
+      if (!range_exact && cudaMemsetAsync(range_err, 0, 4, c->stream) != cudaSuccess) {
+        fail(PM4G_ECUDA);
+        break;
+      }
       const uint32_t nbs_max = (uint32_t)std::min<int64_t>(((int64_t)c->smem_optin - 1024) / 4, 1 << 20);
       cudaFuncSetAttribute(k_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
       cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
@@ -979,6 +1013,28 @@ int pm4g_load_log(pm4g_ctx *c, const int32_t *case_id, const int32_t *activity, 
         }
       }
       if (st) break;
+      if (!range_exact) {
+        uint32_t outside = 0;
+        if (fail(d2h(c, &outside, range_err, 4))) break;
+        if (outside) {
+          range_exact = true;
+          goto case_range;
+        }
+      }
+      if (fail(alloc_buf(c, L->bucket_off, (size_t)L->nb + 1))) break;
+      if (fail(alloc_buf(c, L->rec, n))) break;
+      if (fail(alloc_buf(c, L->status, 1))) break;
+      uint32_t *err = L->status.p;
+      if (cudaMemsetAsync(err, 0, 4, c->stream) != cudaSuccess) {
+        fail(PM4G_ECUDA);
+        break;
+      }
+      fa.bucket_off = L->bucket_off.p;
+      fa.rec = L->rec.p;
+      fa.err_flags = err;
+      // the first word of every record in bucket order, written by the
+      // partition's final level (the streaming pass counts cases from it)
+      uint32_t *keys = nullptr;
       // Partition levels: one level when the buckets fit the bins of a pass,
       // two when coarse buckets of 2^fbits final buckets do; the record-by-
       // record scatter otherwise.

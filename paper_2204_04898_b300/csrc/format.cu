@@ -70,9 +70,37 @@ __device__ __forceinline__ int4 load4_i32(const int32_t *__restrict__ p, int64_t
   return q;
 }
 
+// An enclosing guess of the case id range is widened from the minimum and
+// maximum of kRangeSamples rows spread evenly over the column, the first and
+// last rows included (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_sample_range(const int32_t *__restrict__ case_id, int64_t n,
+                                                       int2 *__restrict__ out) {
+  int mn = INT_MAX, mx = INT_MIN;
+  for (int k = threadIdx.x; k < kRangeSamples; k += blockDim.x) {
+    const int v = case_id[(n - 1) * k / (kRangeSamples - 1)];
+    mn = min(mn, v);
+    mx = max(mx, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+    mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  }
+  __shared__ int2 s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = make_int2(mn, mx);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int2 r = s[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = make_int2(min(r.x, s[w].x), max(r.y, s[w].y));
+    *out = r;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Bucket histogram of one CTA's row chunk, for buckets [b_lo, b_lo + nbs).
-// mat is CTA-major: mat[p * nb + b].
+// mat is CTA-major: mat[p * nb + b]. The same read checks every case id
+// against the range the buckets were laid out for (range_err), so that a
+// guessed range needs no reduction of its own.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_bucket_hist(FormatArgs a, uint32_t b_lo, uint32_t nbs) {
   extern __shared__ uint32_t s_h[];
@@ -81,12 +109,14 @@ __global__ void __launch_bounds__(1024) k_bucket_hist(FormatArgs a, uint32_t b_l
   const int64_t r0 = (int64_t)blockIdx.x * a.chunk;
   const int64_t r1 = min(a.n, r0 + a.chunk);
   const bool al = ((uintptr_t)a.case_id & 15) == 0;
+  bool out = false;
   auto count4 = [&](int4 q, int64_t i) {
     const int32_t cc[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (i + k < r1) {
         const uint32_t slot = (uint32_t)cc[k] - (uint32_t)a.min_case;
+        out |= slot > a.slot_hi;
         const uint32_t b = (slot >> a.clb) - b_lo;
         if (b < nbs) atomicAdd(&s_h[b], 1u);
       }
@@ -104,7 +134,7 @@ __global__ void __launch_bounds__(1024) k_bucket_hist(FormatArgs a, uint32_t b_l
     for (int u = 0; u < 4; ++u) count4(q[u], i + u * step);
   }
   for (; i < r1; i += step) count4(load4_i32(a.case_id, i, r1, al), i);
-  __syncthreads();
+  if (__syncthreads_or(out) && threadIdx.x == 0 && a.range_err) atomicOr(a.range_err, 1u);
   uint32_t *row = a.mat + (int64_t)blockIdx.x * a.nb + b_lo;
   for (uint32_t b = threadIdx.x; b < nbs; b += blockDim.x) row[b] = s_h[b];
 }
@@ -168,13 +198,15 @@ __global__ void __launch_bounds__(1024) k_bucket_hist16(FormatArgs a) {
   const int64_t r0 = (int64_t)blockIdx.x * a.chunk;
   const int64_t r1 = min(a.n, r0 + a.chunk);
   const bool al = ((uintptr_t)a.case_id & 15) == 0;
-  bool ovf = false;
+  bool ovf = false, out = false;
   auto count4 = [&](int4 q, int64_t i) {
     const int32_t cc[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (i + k < r1) {
-        const uint32_t b = ((uint32_t)cc[k] - (uint32_t)a.min_case) >> a.clb;
+        const uint32_t slot = (uint32_t)cc[k] - (uint32_t)a.min_case;
+        out |= slot > a.slot_hi;
+        const uint32_t b = slot >> a.clb;
         if (b < a.nb) {
           const uint32_t sh = (b & 1u) * 16u;
           const uint32_t old = atomicAdd(&s_w[b >> 1], 1u << sh);
@@ -195,7 +227,7 @@ __global__ void __launch_bounds__(1024) k_bucket_hist16(FormatArgs a) {
   }
   for (; i < r1; i += step) count4(load4_i32(a.case_id, i, r1, al), i);
   if (ovf) s_ovf = 1;
-  __syncthreads();
+  if (__syncthreads_or(out) && threadIdx.x == 0 && a.range_err) atomicOr(a.range_err, 1u);
   uint32_t *row = a.mat + (int64_t)blockIdx.x * a.nb;
   if (!s_ovf) {
     for (uint32_t b = threadIdx.x; b < a.nb; b += blockDim.x) row[b] = (s_w[b >> 1] >> ((b & 1u) * 16u)) & 0xFFFFu;

@@ -21,6 +21,11 @@ struct FormatArgs {
   const uint32_t *bucket_off;
   uint4 *rec;
   uint32_t *err_flags;
+  // bucket histogram only: the largest slot a case id may take under
+  // min_case, and the word that is set when some id falls outside
+  // [min_case, min_case + slot_hi] (null: the range is known to hold all ids)
+  uint32_t slot_hi;
+  uint32_t *range_err;
 };
 
 // Bucket partition (format.cu)
@@ -68,6 +73,8 @@ __global__ void k_coarse_counts(const uint32_t *mat, uint32_t nb, int p_ctas, in
 __global__ void k_add_base(uint32_t *mat1, int p_ctas, uint32_t nc, const uint32_t *bucket_off, int fbits);
 
 __global__ void k_stats(const int32_t *case_id, int64_t n, int2 *partial);
+constexpr int kRangeSamples = 4096;
+__global__ void k_sample_range(const int32_t *case_id, int64_t n, int2 *out);
 __global__ void k_bucket_hist(FormatArgs a, uint32_t b_lo, uint32_t nbs);
 __global__ void k_bucket_hist16(FormatArgs a);
 __global__ void k_bucket_colprefix(uint32_t *mat, uint32_t nb, int p_ctas, uint32_t *total);

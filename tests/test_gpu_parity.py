@@ -312,6 +312,50 @@ def test_case_ordered_rows_take_the_streaming_pass(pm4g, ctx):
     assert pm4g.pm4g_ctx_timing(ctx, "sorted_windows")[0] > 0
 
 
+@pytest.mark.parametrize("device", [True, False], ids=["device", "host"])
+def test_case_id_range_guess(pm4g, ctx, device):
+    """The buckets are laid out for a case id range guessed from evenly spaced
+    rows and widened by 1/256 of its span on each side; the bucket histogram
+    confirms that every id lies inside. No column reduction runs when the
+    guess holds (ids in row order either way round, or spread over the rows
+    in time order); it runs, with the oracle's results all the same, when an
+    id elsewhere falls outside the widened span (below, above, or far enough
+    out to make the ids sparse) and when the guess itself looks sparse."""
+    L = synth.generate(synth.large_log(6000))
+    o = np.lexsort((np.arange(L.n_events), L.ts_ns, L.case_id))
+    case, act, ts = L.case_id[o].astype(np.int64), L.activity[o].copy(), L.ts_ns[o].copy()
+    n = len(case)
+    span = int(case.max() - case.min())
+    r = np.arange(n)
+    t = np.argsort(ts, kind="stable")  # the same events in time order
+    shapes = {
+        "ascending": (case + 11, True),
+        "descending": (case.max() - case - 5, True),
+        "time_ordered": (case[t], True),
+        "below_inside": (np.where(r == n // 2, case.min() - span // 8, case), False),
+        "above_inside": (np.where(r == n // 3 + 1, case.max() + span // 8, case), False),
+        "sparse_inside": (np.where(r == n // 4, 2**31 - 1, case), False),
+        "sparse_ends": (np.where(r == n - 1, -2**31, case), False),
+    }
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 1)
+    try:
+        for name, (c, no_reduction) in shapes.items():
+            c = c.astype(np.int32)
+            a, tt = (act[t], ts[t]) if name == "time_ordered" else (act, ts)
+            pm4g.pm4g_ctx_timing_reset(ctx)
+            check_log(pm4g, ctx, c, a, tt, L.n_activities, device=device)
+            ran = pm4g.pm4g_ctx_timing(ctx, "stats")[0]
+            assert (ran == 0) == no_reduction, name
+    finally:
+        pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
+    # one event: its id is the whole range
+    check_log(pm4g, ctx, np.array([-9], np.int32), np.array([0], np.int32), np.array([5], np.int64), 1,
+              device=device)
+    # ids at both ends of the int32 range around dense ones are sparse
+    check_log(pm4g, ctx, np.array([2**31 - 1, 3, 4, -2**31], np.int32), np.zeros(4, np.int32),
+              np.arange(4, dtype=np.int64), 1, device=device)
+
+
 def test_one_pass_16bit_histogram(pm4g, ctx):
     """Between 57,856 and 115,712 buckets the bucket histogram runs once with
     16-bit counters (8M events, case ids spread over 16M slots)."""
