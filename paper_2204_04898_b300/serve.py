@@ -213,16 +213,25 @@ class Server:
                     for r in rs:
                         self._finish(r, error=e)
 
+    def set_mem_budget(self, nbytes: int) -> None:
+        """Replace the upload budget while serving (for example when another
+        tenant of the device grows or shrinks). The budget is not sampled
+        again by itself: the engine's contexts keep freed blocks for reuse, so
+        the device's free memory under-counts what the server can still use.
+        Uploads waiting for memory are judged again against the new budget;
+        those that can no longer fit at all are refused."""
+        with self._mem:
+            self.mem_budget = max(0, int(nbytes))
+            self._mem.notify_all()
+
     def _admit(self, need: int) -> bool:
         """Reserve `need` bytes of the budget for an upload, waiting while
         admitted uploads hold what it needs; False if it can never fit (or
         the wait times out)."""
-        if need > self.mem_budget:
-            return False
         deadline = time.perf_counter() + self.admit_timeout
         with self._mem:
             while self._reserved + need > self.mem_budget:
-                if self._stop or time.perf_counter() > deadline:
+                if need > self.mem_budget or self._stop or time.perf_counter() > deadline:
                     return False
                 self._mem.wait(0.05)
             self._reserved += need

@@ -144,6 +144,36 @@ def test_upload_that_never_fits_is_refused():
         srv.close()
 
 
+def test_budget_set_while_serving():
+    """A waiting upload is admitted as soon as a larger budget covers it, and
+    refused once a smaller one can never hold it; uploads never exceed the
+    budget in force when they were admitted."""
+    eng = FakeEngine(upload_s=0.3)
+    srv = Server(eng, upload_slots=2, mem_budget=1000)
+    try:
+        first = srv.submit(_upload(800))
+        time.sleep(0.05)
+        second = srv.submit(_upload(700))      # waits: 800 + 700 > 1000
+        time.sleep(0.05)
+        assert not second.done.is_set()
+        srv.set_mem_budget(1500)               # now both fit
+        assert second.done.wait(5) and second.error is None
+        assert first.done.wait(5) and first.error is None
+        assert eng.max_active == 2 and eng.max_bytes == 1500
+        third = srv.submit(_upload(900))
+        time.sleep(0.05)
+        fourth = srv.submit(_upload(900))      # waits behind the third
+        time.sleep(0.05)
+        srv.set_mem_budget(500)                # neither can ever fit now
+        assert third.done.wait(5) and fourth.done.wait(5)
+        assert third.error is None             # admitted before the change
+        assert isinstance(fourth.error, MemoryError)
+        ok = srv.submit(_upload(400))
+        assert ok.done.wait(5) and ok.error is None
+    finally:
+        srv.close()
+
+
 def test_engine_failure_reaches_every_request_of_the_batch():
     eng = FakeEngine(batch_s=0.01)
     eng.fail_batch = True
