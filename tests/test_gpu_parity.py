@@ -356,6 +356,23 @@ def test_case_id_range_guess(pm4g, ctx, device):
               np.arange(4, dtype=np.int64), 1, device=device)
 
 
+@pytest.mark.parametrize("spec", [synth.single_log(), synth.very_large_log(40_000), synth.drilldown_log(20_000)],
+                         ids=lambda s: s.name)
+def test_workload_range_needs_no_reduction(pm4g, ctx, spec):
+    """On the benchmark workloads' logs the sampled case-id range holds, so
+    no column reduction runs (and the results are the oracle's)."""
+    L = synth.generate(spec)
+    pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 1)
+    try:
+        pm4g.pm4g_ctx_timing_reset(ctx)
+        check_log(pm4g, ctx, L.case_id, L.activity, L.ts_ns, L.n_activities, case_attr=L.case_attr,
+                  export=False)
+        assert pm4g.pm4g_ctx_timing(ctx, "stats")[0] == 0
+        assert pm4g.pm4g_ctx_timing(ctx, "bucket_hist")[0] >= 1
+    finally:
+        pm4g.pm4g_ctx_set_option(ctx, pm4g.OPT_TIMING, 0)
+
+
 def test_one_pass_16bit_histogram(pm4g, ctx):
     """Between 57,856 and 115,712 buckets the bucket histogram runs once with
     16-bit counters (8M events, case ids spread over 16M slots)."""
