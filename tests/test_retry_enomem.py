@@ -74,7 +74,7 @@ def _same(a, b, where="result"):
             assert va == vb, w
 
 
-def _request(pm4g, kind, log, L, ctx_data):
+def _request(pm4g, kind, log, ctx_data):
     if kind == "variants":
         return pm4g.pm4g_variants(log, top_k=-1, cases=True)
     if kind == "filter_window":
@@ -122,7 +122,7 @@ def test_retry_after_enomem(pm4g, kind):
         try:
             d = pm4g.pm4g_perf_dfg(log)
             data["pairs"] = [(int(d.src[0]), int(d.dst[0])), (int(d.src[-1]), int(d.dst[-1]))]
-            expected = _materialise(pm4g, kind, _request(pm4g, kind, log, L, data), A)
+            expected = _materialise(pm4g, kind, _request(pm4g, kind, log, data), A)
         finally:
             pm4g.pm4g_log_free(log)
         torch.cuda.synchronize()
@@ -134,7 +134,7 @@ def test_retry_after_enomem(pm4g, kind):
             try:
                 hook.budget = k
                 try:
-                    raw = _request(pm4g, kind, log, L, data)
+                    raw = _request(pm4g, kind, log, data)
                     done = True
                 except pm4g.Pm4gError as e:
                     assert e.status == pm4g.ENOMEM, e
@@ -142,7 +142,7 @@ def test_retry_after_enomem(pm4g, kind):
                 hook.budget = None
                 if done:
                     _same(_materialise(pm4g, kind, raw, A), expected)
-                _same(_materialise(pm4g, kind, _request(pm4g, kind, log, L, data), A), expected)
+                _same(_materialise(pm4g, kind, _request(pm4g, kind, log, data), A), expected)
             finally:
                 hook.budget = None
                 pm4g.pm4g_log_free(log)
